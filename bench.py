@@ -1,0 +1,325 @@
+"""Stereo-2K frame-rate benchmark of the structured-3DGS frame path on one B300.
+
+Workload: the synthetic city (2M anchors, 6 LOD levels, feature 32, k=10,
+hidden 32) along the 300-frame ascending stereo path, 1920x1080 per eye.
+A step is one stereo frame (both eyes) through the whole path: culling,
+derivation, projection, key generation, two radix sorts, blending.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form plain|unified]
+                    [--impl ours|reference]
+
+Prints one JSON line.  `value` is frames per second over all ranks (frames
+are independent; ranks render replicas of the path).  Each frame is timed
+with CUDA events on the rendering stream; a >L2 buffer is written between
+frames (untimed) so every frame starts with a cold L2.  The reference arm
+(--impl reference) times the CPU float64 oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stereo-2K FPS & ms/frame at >=40dB PSNR vs FP64 oracle; plain vs cached+BF16"
+UNIT = "frames/s"
+WORKLOAD = "city 2M anchors, stereo 1920x1080, 300-frame ascending path"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.rows = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def build_workload(n_frames=300):
+    import gen
+    t0 = time.time()
+    model, frames = gen.city_workload(n_frames=n_frames)
+    return model, frames, time.time() - t0
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+def oracle_frame_sample(model, L, R, subsample=16, phase=0):
+    """One stereo frame through the float64 oracle: all anchors filtered,
+    derived and projected, blending on 1/subsample of the pixel rows; the
+    blend time is scaled by `subsample` to a full frame.  Returns seconds."""
+    import oracle
+    t_fixed = t_blend = 0.0
+    for cam in (L, R):
+        t0 = time.perf_counter()
+        vr = oracle.view_gaussians(model, cam)
+        t1 = time.perf_counter()
+        ys = np.arange(phase % subsample, cam.height, subsample)
+        px, py = np.meshgrid(np.arange(cam.width), ys)
+        oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px.ravel(), py.ravel())
+        t2 = time.perf_counter()
+        t_fixed += t1 - t0
+        t_blend += t2 - t1
+    return t_fixed + t_blend * subsample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    model, frames, _ = build_workload()
+    for w in range(args.warmup):
+        oracle_frame_sample(model, *frames[w % len(frames)], phase=w)
+    ts = []
+    for s in range(args.steps):
+        f = (args.warmup + s * 37) % len(frames)
+        ts.append(oracle_frame_sample(model, *frames[f], phase=s))
+    mean = float(np.mean(ts))
+    cores = oracle.num_threads()
+    sample = ("per step: one stereo frame of the path, full filtering/derivation/projection in float64, "
+              "blending on every 16th pixel row, blend time x16")
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / mean, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "CPU float64 oracle", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": 1.0 / mean, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": 1.0 / mean, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def make_renderer(model, form, flags=0, use_graph=True):
+    import paper_2502_14938_b300 as pkg
+    r = pkg.Renderer(max_views=2, stereo_unify=(form == "unified"), flags=flags, use_graph=use_graph)
+    mid = r.load_model(model)
+    return r, mid
+
+
+def set_pair(r, mid, L, R):
+    import paper_2502_14938_b300 as pkg
+    r.set_cameras([pkg.to_camera(L, partner=1, model_id=mid), pkg.to_camera(R, partner=0, model_id=mid)])
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2502_14938_b300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    model, frames, t_gen = build_workload()
+    W, H = frames[0][0].width, frames[0][0].height
+    r, mid = make_renderer(model, args.form)
+    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    # warm-up over the whole path with stats: grows buffers to the path's needs
+    for f in range(len(frames)):
+        set_pair(r, mid, *frames[f])
+        r.render_frame(outs)
+    for w in range(args.warmup):
+        set_pair(r, mid, *frames[w % len(frames)])
+        r.render_frame(outs, stats=False)
+    r.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        wall0 = time.perf_counter()
+        for s in range(args.steps):
+            set_pair(r, mid, *frames[s % len(frames)])
+            flush.fill_(s & 0xFF)
+            evs[s][0].record(stream)
+            r.render_frame(outs, stats=False)
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    r.synchronize()  # raises on a deferred capacity / timeout error
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    total_ms = float(ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if rank != 0:
+        return
+    mean_ms = total_ms / args.steps
+    fps = world * args.steps / (total_ms / 1e3)
+
+    # ---- per-stage timing (eager launches with events on the library stream)
+    rt, mid_t = make_renderer(model, args.form, flags=pkg.FLAG_TIMING, use_graph=False)
+    stage = np.zeros(8)
+    stats_acc = {"visible_anchors": 0, "records": 0, "valid_records": 0, "pairs": 0}
+    n_st = min(args.steps, len(frames))
+    for s in range(n_st):
+        set_pair(rt, mid_t, *frames[s % len(frames)])
+        flush.fill_(s & 0xFF)
+        st = rt.render_frame(outs)
+        stage += np.array(st["ms_stage"])
+        for k in stats_acc:
+            stats_acc[k] += st[k]
+    stage /= n_st
+    for k in stats_acc:
+        stats_acc[k] /= n_st
+    rt.close()
+    names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
+    stage_ms = {n: float(stage[i]) for i, n in enumerate(names)}
+
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch / event time)
+    pk = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    P = stats_acc["pairs"]
+    Rv = stats_acc["valid_records"]
+    pixels = 2 * W * H
+    if dom == "blend":
+        alg_bytes = P * (4 + 48) + pixels * 12 + 2 * (W // 16 + 1) * (H // 16 + 1) * 8
+    elif dom == "sort_tile":
+        alg_bytes = P * 8 + 2 * P * 16
+    elif dom == "sort_depth":
+        alg_bytes = stats_acc["records"] * 4 + Rv * 4 + 4 * Rv * 16
+    elif dom == "derive+project":
+        alg_bytes = stats_acc["visible_anchors"] * (128 + 16 + 120) + stats_acc["records"] * 56
+    else:
+        alg_bytes = stats_acc["records"] * 8 + P * 8
+    dur_s = stage_ms[dom] / 1e3
+    achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"], "traffic": None,
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stage_ms[dom]}
+
+    # ---- quality: PSNR of sampled frames against the float64 oracle
+    import oracle
+    psnrs = []
+    for f in args.psnr_frames:
+        L, R = frames[f]
+        set_pair(r, mid, L, R)
+        r.render_frame(outs)
+        mse = 0.0
+        for v, cam in enumerate((L, R)):
+            (ref, _, _, _), _ = oracle.render_view(model, cam)
+            got = outs[v].cpu().numpy().astype(np.float64)
+            mse += float(np.mean((got - ref) ** 2)) / 2
+        psnrs.append(float("inf") if mse == 0 else 10 * np.log10(1.0 / mse))
+
+    # ---- end to end through the public API with host buffers
+    host = [torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
+    n_e2e = min(args.steps, 100)
+    t0 = time.perf_counter()
+    for s in range(n_e2e):
+        set_pair(r, mid, *frames[s % len(frames)])
+        r.render_frame_host(host, stats=False)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * (8 + 4 + 2 * 32 * 2 + 32 * 24),
+           "d2h_bytes_per_step": 2 * W * H * 3 * 4 + 128}
+
+    # ---- CPU baseline: the oracle on a bounded sample
+    cores = oracle.num_threads()
+    cts = [oracle_frame_sample(model, *frames[f], phase=i) for i, f in enumerate((0, 150))]
+    cpu = {"value": 1.0 / float(np.mean(cts)), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "2 stereo frames (0, 150): full float64 filtering/derivation/projection, "
+                     "blending on every 16th pixel row scaled x16"}
+
+    n_sort2 = 2  # 14 tile bits -> two 8-bit passes
+    launches_per_frame = 1 + 1 + 1 + 1 + (1 + 4) + 1 + 1 + (1 + n_sort2) + 1 + 1
+    line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": args.form, "precision": "fp32", "cache": "off",
+                       "stereo_unify": args.form == "unified", "tile": "16x16",
+                       "l2": "flushed between frames (256 MB write, untimed)",
+                       "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
+                       "psnr_db_min": min(psnrs) if psnrs else None, "psnr_frames": args.psnr_frames,
+                       "stage_ms": stage_ms, "per_frame": stats_acc, "gen_s": t_gen},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches_per_frame * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="plain", choices=["plain", "unified"])
+    ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 299])
+    args = ap.parse_args()
+    assert args.warmup >= 0 and args.steps >= 1
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * gsc.h - C ABI of the B300 structured-3DGS frame renderer (GS-Cache path).
+ *
+ * One context renders frames of structured 3D Gaussian Splatting models
+ * (anchors with a feature vector, decoded by small MLPs into k "neural
+ * Gaussians" each) on one GPU.  A frame runs, entirely in the library's own
+ * CUDA kernels:
+ *   1. anchor filtering: frustum + distance LOD            (Sec. 3.2, Alg. 1)
+ *   2. derivation: MLP(feature, view direction) -> Gaussians (Eq. 3, Sec. 6),
+ *      optionally reusing cached results across frames   (Sec. 4, Alg. 1, Eq. 4)
+ *      and sharing one derivation between two eyes        (Eq. 5-6)
+ *   3. splatting: EWA projection, exact tile coverage, key generation,
+ *      radix sort, front-to-back alpha blending            (Eq. 1-2, Sec. 3.1, Sec. 6)
+ *
+ * Conventions
+ *  - Every call returns a gsc_status (0 = GSC_OK).  Nothing throws across the
+ *    ABI.  On error gsc_last_error() returns a message for the context.
+ *  - The context owns every internal device buffer.  Output images are
+ *    caller-owned device memory (gsc_render_frame) or host memory
+ *    (gsc_render_frame_host).
+ *  - All work is enqueued on the CUDA stream given to gsc_create (NULL = the
+ *    legacy default stream).  gsc_render_frame with stats == NULL is
+ *    asynchronous; see its comment for deferred errors.
+ *  - Sizes fixed by this build: feature dim 32, k = 10 Gaussians per anchor,
+ *    MLP hidden width 32, three heads (opacity k, colour 3k, covariance 7k).
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef GSC_H
+#define GSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GSC_API __attribute__((visibility("default")))
+#else
+#define GSC_API
+#endif
+
+#define GSC_VERSION 1
+#define GSC_FEAT_DIM 32
+#define GSC_K 10
+#define GSC_HIDDEN 32
+#define GSC_MAX_VIEWS 32
+
+typedef struct gsc_ctx gsc_ctx;
+
+typedef enum {
+  GSC_OK = 0,
+  GSC_ERR_INVALID_ARG = -1,   /* null pointer, bad size, unsupported dims */
+  GSC_ERR_OOM = -2,           /* device or pinned-host allocation failed */
+  GSC_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the name) */
+  GSC_ERR_CAPACITY = -4,      /* pair buffer overflowed in an asynchronous frame; grown, re-render */
+  GSC_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up; frame output invalid */
+  GSC_ERR_STATE = -6,         /* call out of order (e.g. render before set_cameras) */
+  GSC_ERR_UNIMPLEMENTED = -7, /* requested form not built */
+  GSC_ERR_INTERNAL = -8
+} gsc_status;
+
+typedef enum { GSC_PREC_FP32 = 0, GSC_PREC_BF16 = 1, GSC_PREC_FP8 = 2 } gsc_precision;
+
+typedef enum {
+  GSC_REUSE_OFF = 0,      /* decode every visible anchor every frame */
+  GSC_REUSE_DEPTH = 1,    /* Alg. 1 dynamic cache depth (Eq. 4, linear guide) */
+  GSC_REUSE_LEARNED = 2   /* learned per-anchor reuse predictor, depth rule as fallback bound */
+} gsc_reuse_mode;
+
+/* flags */
+#define GSC_FLAG_DEBUG_ATTRS 0x1u  /* keep derived attributes for gsc_debug_attrs */
+#define GSC_FLAG_DEBUG_T 0x2u      /* keep per-pixel final transmittance */
+#define GSC_FLAG_TIMING 0x4u       /* per-stage CUDA-event timing into gsc_frame_stats */
+
+typedef struct {
+  uint32_t max_views;        /* cameras per frame, 1..GSC_MAX_VIEWS */
+  uint32_t precision;        /* gsc_precision of the derivation MLPs */
+  uint32_t reuse;            /* gsc_reuse_mode */
+  uint32_t stereo_unify;     /* 1: cameras with a stereo partner share one Eq. 5-6 derivation */
+  uint32_t cache_gaussians;  /* cache capacity in Gaussians per derivation view (0 = 4M) */
+  uint32_t max_depth;        /* D_max of Alg. 1 (0 = 10) */
+  uint32_t tile_w, tile_h;   /* blend tile in pixels (0 = 16 x 16); tile_w*tile_h <= 1024 */
+  uint64_t pair_capacity;    /* initial (tile, Gaussian) pair capacity (0 = 16M); grows */
+  float bg[3];               /* background colour */
+  uint32_t use_graph;        /* 1: replay the frame's launch sequence as a CUDA graph */
+  uint32_t flags;            /* GSC_FLAG_* */
+  uint32_t reserved[8];
+} gsc_config;
+
+/* Model description: host pointers, float32, row-major.  Copied by
+ * gsc_load_model; the caller keeps ownership.  World units are metres. */
+typedef struct {
+  uint32_t n_anchors;
+  uint32_t feat_dim;         /* must be 32 */
+  uint32_t k;                /* must be 10 */
+  uint32_t hidden;           /* must be 32 */
+  uint32_t n_levels;         /* LOD levels (1 = LOD off) */
+  float lod_dmax;            /* level l >= 1 drawn iff distance <= lod_dmax * 2^-l */
+  const float* pos;          /* [N][3] anchor positions */
+  const float* feat;         /* [N][32] anchor features */
+  const float* offset;       /* [N][k][3] Gaussian offsets: mu_j = pos + offset_j */
+  const float* scale;        /* [N] anchor scale s_a */
+  const uint8_t* level;      /* [N] LOD level, 0 = coarsest */
+  const float* W1[3];        /* per head [35][32], input = [feature(32), view dir(3)] */
+  const float* b1[3];        /* per head [32] */
+  const float* W2[3];        /* per head [32][out_h], out_h = k, 3k, 7k */
+  const float* b2[3];        /* per head [out_h] */
+} gsc_model_desc;
+
+/* Pinhole camera: camera coords c = R x + t (x right, y down, z forward),
+ * pixel (i, j) has its centre at (i + 0.5, j + 0.5). */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  uint32_t width, height;
+  float znear;
+  int32_t stereo_partner;    /* index of the other eye in the same gsc_set_cameras call, or -1 */
+  uint32_t model_id;         /* from gsc_load_model */
+  uint32_t viewer;           /* cache owner: cameras of one viewer share its derivation cache */
+} gsc_camera;
+
+typedef struct {
+  uint64_t visible_anchors;  /* summed over derivation views */
+  uint64_t derived_anchors;  /* anchors decoded by the MLPs this frame (cache misses) */
+  uint64_t records;          /* (Gaussian, camera) records projected */
+  uint64_t valid_records;    /* records that cover at least one tile */
+  uint64_t pairs;            /* (tile, Gaussian) pairs sorted and blended */
+  uint32_t cache_depth;      /* reuse depth chosen for the next frame (viewer 0) */
+  uint32_t error_flags;      /* bit 0 pair overflow, bit 1 wait timeout, bit 2 cache full */
+  float ms_stage[8];         /* with GSC_FLAG_TIMING: cull, derive, sort1, scan+keygen, sort2, ranges, blend, total */
+} gsc_frame_stats;
+
+/* Fill *cfg with the defaults (stereo 2K, FP32, no reuse, 16x16 tiles, graph on). */
+GSC_API void gsc_default_config(gsc_config* cfg);
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (may be NULL).  Returns GSC_ERR_INVALID_ARG for bad config values,
+ * GSC_ERR_OOM / GSC_ERR_CUDA on allocation failure (no context is returned). */
+GSC_API int gsc_create(gsc_ctx** out, const gsc_config* cfg, void* cuda_stream);
+
+/* Upload a model (Sec. 3.1 structured anchors; Eq. 3 decoder weights).
+ * Validates the description (null pointers, dims, NaN positions are
+ * rejected) and copies it into device memory; *model_id_out receives the id
+ * used by gsc_camera.model_id.  Synchronous with respect to the host buffers. */
+GSC_API int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* desc, uint32_t* model_id_out);
+
+/* Set the cameras of the next frames (host array of n <= max_views).  Stereo
+ * partners must reference each other, share intrinsics and model.  The
+ * values are copied; the library uploads them with the frame. */
+GSC_API int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n);
+
+/* Render one frame: out_rgb[i] is a caller-owned DEVICE pointer to a float32
+ * [height][width][3] image for camera i.  With stats != NULL the call waits
+ * for the frame, grows the pair buffer and re-renders if it overflowed, and
+ * fills *stats.  With stats == NULL the call only enqueues work; a pair
+ * overflow or a wait timeout of such a frame is reported by the next
+ * synchronising call (GSC_ERR_CAPACITY / GSC_ERR_TIMEOUT). */
+GSC_API int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats);
+
+/* Same as gsc_render_frame, but out_rgb[i] are HOST pointers (pinned or
+ * pageable); the device->host copies are part of the call, which returns
+ * when the images are in host memory. */
+GSC_API int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats);
+
+/* Empty every derivation cache (Sec. 4): the next frame decodes all anchors. */
+GSC_API int gsc_cache_reset(gsc_ctx* ctx);
+
+/* Wait for all enqueued frames and report deferred errors. */
+GSC_API int gsc_synchronize(gsc_ctx* ctx);
+
+/* Message of the last error of ctx (never NULL; "" after success). */
+GSC_API const char* gsc_last_error(const gsc_ctx* ctx);
+
+/* Free the context and all its device memory (waits for its stream). */
+GSC_API void gsc_destroy(gsc_ctx* ctx);
+
+GSC_API int gsc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSC_H */

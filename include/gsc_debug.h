@@ -1,0 +1,80 @@
+/*
+ * gsc_debug.h - test-only exports of the GS-Cache frame renderer.
+ *
+ * These read back the intermediate buffers of the LAST rendered frame so that
+ * each stage can be compared with an independent reference on its own.  All
+ * are synchronous (they wait for the context's stream) and copy into
+ * caller-owned HOST memory.  For each: pass cap = capacity of the output
+ * arrays in elements of the stated unit; *n receives the number available;
+ * nothing is written past cap.  Return values are gsc_status codes.
+ */
+#ifndef GSC_DEBUG_H
+#define GSC_DEBUG_H
+
+#include "gsc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Visible anchor ids (ascending) of derivation view d (anchor filtering,
+ * Sec. 3.2).  Derivation views are the cameras in order, except that with
+ * stereo_unify each stereo pair forms one view at the position of its
+ * lower-indexed camera.  Unit: uint32 ids. */
+GSC_API int gsc_debug_visible(gsc_ctx* ctx, uint32_t d, uint32_t* ids, uint64_t cap, uint64_t* n);
+
+/* Number of derivation views of the last frame and the camera each feeds. */
+GSC_API int gsc_debug_dviews(gsc_ctx* ctx, uint32_t* n_dviews, int32_t* first_cam /* [GSC_MAX_VIEWS] */);
+
+/* Derived attributes (Eq. 3) of derivation view d, needs GSC_FLAG_DEBUG_ATTRS:
+ * per visible anchor i and Gaussian j, 11 floats: alpha, colour(3),
+ * scale(3), quaternion(4) (w,x,y,z).  Unit: anchors ([n][k][11] floats). */
+GSC_API int gsc_debug_attrs(gsc_ctx* ctx, uint32_t d, float* attrs, uint64_t cap, uint64_t* n);
+
+/* Projected records, one per (camera, visible anchor, Gaussian), record
+ * index r = base(camera) + i*k + j.  Per record 12 floats: mean x, mean y,
+ * conic A, B, C (q = A dx^2 + 2 B dx dy + C dy^2), opacity, tau (coverage
+ * threshold on q), depth, colour(3), and the bits of a uint32 word
+ * (camera index in bits 0-15, bit 31 = record passed the projection tests);
+ * plus the sort key (depth bits, 0xFFFFFFFF when unused) and tile count.
+ * Unit: records. */
+GSC_API int gsc_debug_records(gsc_ctx* ctx, float* rec12, uint32_t* depth_key, uint32_t* tile_count,
+                      uint64_t cap, uint64_t* n);
+
+/* Sorted (key, value) pairs: key = tile_base(camera) + tile, value = record.
+ * Unit: pairs. */
+GSC_API int gsc_debug_pairs(gsc_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t cap, uint64_t* n);
+
+/* Records in depth order after the first sort (values only).  Unit: records. */
+GSC_API int gsc_debug_depth_order(gsc_ctx* ctx, uint32_t* vals, uint64_t cap, uint64_t* n);
+
+/* Tile ranges [start, end) into the sorted pairs, for every tile of every
+ * camera in key order.  Unit: tiles ([n][2] uint32). */
+GSC_API int gsc_debug_ranges(gsc_ctx* ctx, uint32_t* ranges, uint64_t cap, uint64_t* n);
+
+/* Final transmittance of camera v, needs GSC_FLAG_DEBUG_T.  Unit: pixels. */
+GSC_API int gsc_debug_final_T(gsc_ctx* ctx, uint32_t v, float* T, uint64_t cap, uint64_t* n);
+
+/* Upper bound on the polls of every bounded device-side wait (0 makes any
+ * wait that does not succeed at once give up).  Default 1 << 20. */
+GSC_API int gsc_debug_set_spin_limit(gsc_ctx* ctx, uint32_t limit);
+
+/* Standalone radix sort of n (key, value) pairs in host memory through the
+ * library's sort kernels (keys sorted on bits [0, bits), stable).  For
+ * testing the sort against a library sort.  Unit: pairs. */
+GSC_API int gsc_debug_sort_pairs(gsc_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n, uint32_t bits);
+
+/* Timeout path: runs a kernel whose bounded wait targets a word that no
+ * kernel writes, with the given poll limit.  Returns GSC_ERR_TIMEOUT when the
+ * wait gave up and reported it (the expected outcome); the context stays
+ * usable. */
+GSC_API int gsc_debug_wait_timeout(gsc_ctx* ctx, uint32_t spin_limit);
+
+/* Standalone exclusive scan of n uint32 values in host memory through the
+ * library's decoupled look-back scan kernel; *total receives the sum. */
+GSC_API int gsc_debug_scan(gsc_ctx* ctx, uint32_t* vals, uint64_t n, uint64_t* total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSC_DEBUG_H */

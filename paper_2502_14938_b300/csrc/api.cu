@@ -1,0 +1,881 @@
+// Host side of the C ABI (include/gsc.h, include/gsc_debug.h): context,
+// model upload, cameras, the per-frame launch sequence (replayed as a CUDA
+// graph), capacity growth and the debug read-backs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gsc.h"
+#include "gsc_debug.h"
+#include "gsc_internal.cuh"
+
+using namespace gsc;
+
+namespace {
+
+constexpr int NSLOT = 4;  // pinned FrameIn ring
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ModelHost {
+  uint32_t n = 0;
+  DevBuf px, py, pz, level, feat, offs, scale, w32;
+  ModelDev dev{};
+};
+
+struct Counters {  // tail of FrameDev read back after a frame
+  uint32_t vis_count[MAXV];
+  uint32_t item_base[MAXV + 1];
+  uint32_t rec_base[MAXV + 1];
+  uint32_t n_items, n_records;
+  uint32_t n_valid, n_pairs, n_pairs_used, err;
+};
+
+}  // namespace
+
+struct gsc_ctx {
+  gsc_config cfg{};
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_slot[NSLOT] = {};
+  cudaEvent_t ev_stage[9] = {};
+  int device = 0, n_sm = 148;
+  std::string err;
+  std::vector<ModelHost> models;
+  ModelDev* d_models = nullptr;
+  std::vector<gsc_camera> cams;
+  bool cams_set = false;
+  FrameIn* h_fin[NSLOT] = {};
+  int slot = 0;
+  FrameIn* d_fin = nullptr;
+  FrameDev* d_fd = nullptr;
+  Counters* h_cnt = nullptr;
+  bool pending = false;  // an asynchronous frame whose counters were not checked yet
+  // buffers
+  uint32_t vis_cap = 0, n_vis_slots = 0;
+  uint32_t* d_vis_buf = nullptr;
+  uint32_t** d_vis_tab = nullptr;
+  float* d_dbg_buf = nullptr;
+  float** d_dbg_tab = nullptr;
+  uint32_t rec_cap = 0;
+  Records rec{};
+  uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr;
+  uint32_t pair_cap = 0;
+  uint32_t *pk0 = nullptr, *pv0 = nullptr, *pk1 = nullptr, *pv1 = nullptr;
+  uint32_t ranges_cap = 0;
+  uint2* ranges = nullptr;
+  SortBufs sb{};
+  uint32_t status_tiles = 0;
+  unsigned long long* st_cull = nullptr;
+  uint32_t st_cull_words = 0;
+  unsigned long long* st_scan = nullptr;
+  // results of the last frame's sequence
+  uint32_t* order_out = nullptr;  // records in depth order
+  uint32_t* pkeys_out = nullptr;
+  uint32_t* pvals_out = nullptr;
+  // host-output images
+  float* d_img[MAXV] = {};
+  size_t d_img_bytes[MAXV] = {};
+  float* d_T[MAXV] = {};
+  size_t d_T_bytes[MAXV] = {};
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  // frame shape (host-known)
+  uint32_t total_tiles = 0, tile_bits = 1;
+  std::vector<int> models_used;
+  uint32_t spin_limit = 1u << 20;
+  bool timing = false;
+};
+
+namespace {
+
+int fail(gsc_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, e_ == cudaErrorMemoryAllocation ? GSC_ERR_OOM : GSC_ERR_CUDA, \
+                                       "%s: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+template <typename T>
+int dalloc(gsc_ctx* ctx, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) return GSC_OK;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return GSC_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int upload(gsc_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+  dfree(b.p);
+  b.p = nullptr;
+  b.bytes = bytes;
+  if (bytes == 0) return GSC_OK;
+  CK(cudaMalloc(&b.p, bytes));
+  CK(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+  return GSC_OK;
+}
+
+bool finite_all(const float* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+void invalidate_graph(gsc_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->graph_valid = false;
+}
+
+uint32_t models_max_n(const gsc_ctx* ctx) {
+  uint32_t m = 0;
+  for (const auto& mh : ctx->models) m = std::max(m, mh.n);
+  return m;
+}
+
+int ensure_status(gsc_ctx* ctx) {
+  const uint32_t need = std::max((ctx->rec_cap + 4095u) / 4096u, (ctx->pair_cap + 4095u) / 4096u) + 1u;
+  if (need > ctx->status_tiles) {
+    int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
+    if (r) return r;
+    CK(cudaMemset(ctx->sb.status, 0, (size_t)need * 256 * sizeof(unsigned long long)));
+    r = dalloc(ctx, &ctx->st_scan, (size_t)need);
+    if (r) return r;
+    CK(cudaMemset(ctx->st_scan, 0, (size_t)need * sizeof(unsigned long long)));
+    ctx->status_tiles = need;
+  }
+  const uint32_t cw = ((models_max_n(ctx) + 2047u) / 2048u + 1u) * 8u;
+  if (cw > ctx->st_cull_words) {
+    int r = dalloc(ctx, &ctx->st_cull, (size_t)cw);
+    if (r) return r;
+    CK(cudaMemset(ctx->st_cull, 0, (size_t)cw * sizeof(unsigned long long)));
+    ctx->st_cull_words = cw;
+  }
+  return GSC_OK;
+}
+
+int alloc_records(gsc_ctx* ctx, uint32_t cap) {
+  int r;
+  if ((r = dalloc(ctx, &ctx->rec.geo, cap)) || (r = dalloc(ctx, &ctx->rec.cop, cap)) ||
+      (r = dalloc(ctx, &ctx->rec.col, cap)) || (r = dalloc(ctx, &ctx->rec.key, cap)) ||
+      (r = dalloc(ctx, &ctx->rec.cnt, cap)) || (r = dalloc(ctx, &ctx->s1k0, cap)) ||
+      (r = dalloc(ctx, &ctx->s1v0, cap)) || (r = dalloc(ctx, &ctx->s1k1, cap)) ||
+      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)))
+    return r;
+  ctx->rec_cap = cap;
+  invalidate_graph(ctx);
+  return ensure_status(ctx);
+}
+
+int alloc_pairs(gsc_ctx* ctx, uint32_t cap) {
+  int r;
+  if ((r = dalloc(ctx, &ctx->pk0, cap)) || (r = dalloc(ctx, &ctx->pv0, cap)) || (r = dalloc(ctx, &ctx->pk1, cap)) ||
+      (r = dalloc(ctx, &ctx->pv1, cap)))
+    return r;
+  ctx->pair_cap = cap;
+  invalidate_graph(ctx);
+  return ensure_status(ctx);
+}
+
+// The launch sequence of one frame (everything after the FrameIn upload).
+void enqueue_sequence(gsc_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  FrameDev* fd = ctx->d_fd;
+  const bool tm = ctx->timing;
+  if (tm) cudaEventRecord(ctx->ev_stage[0], s);
+  launch_frame_begin(fd, ctx->d_fin, s);
+  cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
+  for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
+  launch_plan(fd, ctx->rec_cap, s);
+  if (tm) cudaEventRecord(ctx->ev_stage[1], s);
+  for (int m : ctx->models_used)
+    launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->rec, ctx->d_dbg_tab, ctx->n_sm, s);
+  if (tm) cudaEventRecord(ctx->ev_stage[2], s);
+  uint32_t *ok = nullptr, *ov = nullptr;
+  launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
+                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov);
+  ctx->order_out = ov;
+  if (tm) cudaEventRecord(ctx->ev_stage[3], s);
+  launch_scan_u32(ctx->rec.cnt, ov, &fd->n_valid, ctx->offs, &fd->n_pairs, ctx->st_scan, fd, SLOT_SCAN, ctx->n_sm, s);
+  launch_keygen(fd, ctx->rec, ov, ctx->offs, ctx->pk0, ctx->pv0, ctx->pair_cap, ctx->n_sm, s);
+  if (tm) cudaEventRecord(ctx->ev_stage[4], s);
+  uint32_t *pk = nullptr, *pv = nullptr;
+  launch_sort_impl(ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->pk0, ctx->pv0, &fd->n_pairs_used, nullptr,
+                   (int)ctx->tile_bits, 0, SLOT_SORT2, fd, ctx->sb, ctx->n_sm, s, &pk, &pv);
+  ctx->pkeys_out = pk;
+  ctx->pvals_out = pv;
+  if (tm) cudaEventRecord(ctx->ev_stage[5], s);
+  launch_ranges(fd, pk, ctx->ranges, ctx->n_sm, s);
+  if (tm) cudaEventRecord(ctx->ev_stage[6], s);
+  launch_blend(fd, ctx->ranges, pv, ctx->rec, ctx->d_fin, ctx->total_tiles, ctx->cfg.tile_w * ctx->cfg.tile_h, s);
+  if (tm) cudaEventRecord(ctx->ev_stage[7], s);
+}
+
+int build_graph(gsc_ctx* ctx) {
+  invalidate_graph(ctx);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_sequence(ctx);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  ctx->graph_valid = true;
+  return GSC_OK;
+}
+
+// Upload the frame description into the next pinned slot and enqueue the
+// frame.  out_rgb / out_T are device pointers per camera.
+int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
+  const int sl = ctx->slot;
+  ctx->slot = (ctx->slot + 1) % NSLOT;
+  CK(cudaEventSynchronize(ctx->ev_slot[sl]));
+  FrameIn* F = ctx->h_fin[sl];
+  std::memset(F, 0, sizeof(FrameIn));
+  F->n_cams = (uint32_t)ctx->cams.size();
+  F->unify = ctx->cfg.stereo_unify;
+  F->tile_w = ctx->cfg.tile_w;
+  F->tile_h = ctx->cfg.tile_h;
+  F->spin_limit = ctx->spin_limit;
+  for (int i = 0; i < 3; ++i) F->bg[i] = ctx->cfg.bg[i];
+  for (size_t i = 0; i < ctx->cams.size(); ++i) {
+    const gsc_camera& c = ctx->cams[i];
+    CamIn& d = F->cam[i];
+    std::memcpy(d.R, c.R, sizeof d.R);
+    std::memcpy(d.t, c.t, sizeof d.t);
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.W = c.width; d.H = c.height; d.znear = c.znear;
+    d.partner = c.stereo_partner;
+    d.model = c.model_id;
+    d.viewer = c.viewer;
+    F->out_rgb[i] = (unsigned long long)(uintptr_t)out_rgb[i];
+    F->out_T[i] = (unsigned long long)(uintptr_t)(out_T ? out_T[i] : nullptr);
+  }
+  CK(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  CK(cudaMemcpyAsync(ctx->d_fin, F, sizeof(FrameIn), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(ctx->ev_slot[sl], ctx->stream));
+  if (ctx->cfg.use_graph && !ctx->timing) {
+    if (!ctx->graph_valid) {
+      int r = build_graph(ctx);
+      if (r) return r;
+    }
+    CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  } else {
+    enqueue_sequence(ctx);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(ctx->h_cnt, &ctx->d_fd->vis_count[0], sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaEventRecord(ctx->ev_out, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+  ctx->pending = true;
+  return GSC_OK;
+}
+
+// Wait for the last frame and turn its counters into a status.  Grows a
+// buffer that overflowed (returns GSC_ERR_CAPACITY so the caller re-renders).
+int finish_frame(gsc_ctx* ctx) {
+  CK(cudaEventSynchronize(ctx->ev_out));
+  ctx->pending = false;
+  const Counters& c = *ctx->h_cnt;
+  if (c.err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (c.err & ERR_REC_OVERFLOW) {
+    // grow to the worst case of the current cameras (every anchor visible)
+    unsigned long long need = 0;
+    for (const auto& cam : ctx->cams) need += (unsigned long long)K * ctx->models[cam.model_id].n;
+    need = std::min<unsigned long long>(need, 0x3FFFFFFFull);
+    int r = alloc_records(ctx, (uint32_t)need);
+    if (r) return r;
+    return fail(ctx, GSC_ERR_CAPACITY, "record buffer grown to %u", ctx->rec_cap);
+  }
+  if (c.err & ERR_PAIR_OVERFLOW) {
+    unsigned long long need = (unsigned long long)c.n_pairs + c.n_pairs / 4 + 1024;
+    need = std::min<unsigned long long>(need, 0x3FFFFFFFull);
+    int r = alloc_pairs(ctx, (uint32_t)need);
+    if (r) return r;
+    return fail(ctx, GSC_ERR_CAPACITY, "pair buffer grown to %u", ctx->pair_cap);
+  }
+  return GSC_OK;
+}
+
+void fill_stats(gsc_ctx* ctx, gsc_frame_stats* st) {
+  const Counters& c = *ctx->h_cnt;
+  std::memset(st, 0, sizeof(*st));
+  uint64_t vis = 0;
+  for (uint32_t d = 0; d < MAXV; ++d) vis += c.vis_count[d];
+  st->visible_anchors = vis;
+  st->derived_anchors = c.n_items;
+  st->records = c.n_records;
+  st->valid_records = c.n_valid;
+  st->pairs = c.n_pairs;
+  st->cache_depth = 0;
+  st->error_flags = c.err;
+  if (ctx->timing) {
+    float tot = 0.f;
+    for (int i = 0; i < 7; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev_stage[i], ctx->ev_stage[i + 1]);
+      st->ms_stage[i] = ms;
+      tot += ms;
+    }
+    st->ms_stage[7] = tot;
+  }
+}
+
+int render_impl(gsc_ctx* ctx, float* const* out_dev, float* const* out_T, gsc_frame_stats* stats, bool sync) {
+  if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
+  if (ctx->pending && sync) {
+    // report an earlier asynchronous frame's problem before starting this one
+    int r = finish_frame(ctx);
+    if (r) return r;
+  }
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int r = enqueue_frame(ctx, out_dev, out_T);
+    if (r) return r;
+    if (!sync) return GSC_OK;
+    r = finish_frame(ctx);
+    if (r == GSC_ERR_CAPACITY) continue;  // grown: render the frame again
+    if (r) return r;
+    if (stats) fill_stats(ctx, stats);
+    ctx->err.clear();
+    return GSC_OK;
+  }
+  return fail(ctx, GSC_ERR_CAPACITY, "capacity still insufficient after growth");
+}
+
+}  // namespace
+
+extern "C" {
+
+void gsc_default_config(gsc_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->max_views = 2;
+  cfg->precision = GSC_PREC_FP32;
+  cfg->reuse = GSC_REUSE_OFF;
+  cfg->stereo_unify = 0;
+  cfg->cache_gaussians = 4u << 20;
+  cfg->max_depth = 10;
+  cfg->tile_w = 16;
+  cfg->tile_h = 16;
+  cfg->pair_capacity = 16u << 20;
+  cfg->use_graph = 1;
+}
+
+int gsc_version(void) { return GSC_VERSION; }
+
+int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
+  if (!out) return GSC_ERR_INVALID_ARG;
+  *out = nullptr;
+  gsc_config cfg;
+  if (cfg_in) cfg = *cfg_in; else gsc_default_config(&cfg);
+  if (cfg.tile_w == 0) cfg.tile_w = 16;
+  if (cfg.tile_h == 0) cfg.tile_h = 16;
+  if (cfg.max_depth == 0) cfg.max_depth = 10;
+  if (cfg.cache_gaussians == 0) cfg.cache_gaussians = 4u << 20;
+  if (cfg.pair_capacity == 0) cfg.pair_capacity = 16u << 20;
+  if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
+  const uint32_t nt = cfg.tile_w * cfg.tile_h;
+  if (nt == 0 || nt > 256 || nt % 32 != 0) return GSC_ERR_INVALID_ARG;
+  if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
+  if (cfg.precision != GSC_PREC_FP32 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
+  if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
+
+  gsc_ctx* ctx = new (std::nothrow) gsc_ctx();
+  if (!ctx) return GSC_ERR_OOM;
+  ctx->cfg = cfg;
+  ctx->timing = (cfg.flags & GSC_FLAG_TIMING) != 0;
+  ctx->user_stream = (cudaStream_t)cuda_stream;
+  auto bail = [&](int code) {
+    gsc_destroy(ctx);
+    return code;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(GSC_ERR_CUDA);
+  for (int i = 0; i < NSLOT; ++i) {
+    if (cudaEventCreateWithFlags(&ctx->ev_slot[i], cudaEventDisableTiming) != cudaSuccess) return bail(GSC_ERR_CUDA);
+    if (cudaMallocHost((void**)&ctx->h_fin[i], sizeof(FrameIn)) != cudaSuccess) return bail(GSC_ERR_OOM);
+  }
+  for (int i = 0; i < 9; ++i)
+    if (cudaEventCreate(&ctx->ev_stage[i]) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (cudaMallocHost((void**)&ctx->h_cnt, sizeof(Counters)) != cudaSuccess) return bail(GSC_ERR_OOM);
+  std::memset(ctx->h_cnt, 0, sizeof(Counters));
+  if (cudaMalloc((void**)&ctx->d_fin, sizeof(FrameIn)) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMalloc((void**)&ctx->d_fd, sizeof(FrameDev)) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMemset(ctx->d_fd, 0, sizeof(FrameDev)) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (cudaMalloc((void**)&ctx->d_models, sizeof(ModelDev) * MAX_MODELS) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMalloc((void**)&ctx->d_vis_tab, sizeof(uint32_t*) * MAXV) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMalloc((void**)&ctx->sb.hist, sizeof(uint32_t) * 4 * 256) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (alloc_pairs(ctx, (uint32_t)cfg.pair_capacity) != GSC_OK) return bail(GSC_ERR_OOM);
+  *out = ctx;
+  return GSC_OK;
+}
+
+void gsc_destroy(gsc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  invalidate_graph(ctx);
+  for (auto& m : ctx->models) {
+    dfree(m.px.p); dfree(m.py.p); dfree(m.pz.p); dfree(m.level.p);
+    dfree(m.feat.p); dfree(m.offs.p); dfree(m.scale.p); dfree(m.w32.p);
+  }
+  void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
+                  ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
+                  ctx->s1v1, ctx->offs, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
+                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd};
+  for (void* p : bufs) dfree(p);
+  for (int i = 0; i < MAXV; ++i) {
+    dfree(ctx->d_img[i]);
+    dfree(ctx->d_T[i]);
+  }
+  for (int i = 0; i < NSLOT; ++i) {
+    if (ctx->h_fin[i]) cudaFreeHost(ctx->h_fin[i]);
+    if (ctx->ev_slot[i]) cudaEventDestroy(ctx->ev_slot[i]);
+  }
+  for (int i = 0; i < 9; ++i)
+    if (ctx->ev_stage[i]) cudaEventDestroy(ctx->ev_stage[i]);
+  if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* gsc_last_error(const gsc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!d || !model_id_out) return fail(ctx, GSC_ERR_INVALID_ARG, "null argument");
+  if (d->feat_dim != FDIM || d->k != K || d->hidden != HID)
+    return fail(ctx, GSC_ERR_INVALID_ARG, "unsupported dims (feat %u, k %u, hidden %u)", d->feat_dim, d->k, d->hidden);
+  if (ctx->models.size() >= MAX_MODELS) return fail(ctx, GSC_ERR_INVALID_ARG, "at most %d models", MAX_MODELS);
+  if (d->n_anchors > (1u << 28)) return fail(ctx, GSC_ERR_INVALID_ARG, "too many anchors");
+  if (d->n_levels == 0 || d->n_levels > 32) return fail(ctx, GSC_ERR_INVALID_ARG, "n_levels must be 1..32");
+  const size_t n = d->n_anchors;
+  if (n > 0 && (!d->pos || !d->feat || !d->offset || !d->scale || !d->level))
+    return fail(ctx, GSC_ERR_INVALID_ARG, "null model array");
+  for (int h = 0; h < 3; ++h)
+    if (!d->W1[h] || !d->b1[h] || !d->W2[h] || !d->b2[h]) return fail(ctx, GSC_ERR_INVALID_ARG, "null MLP weights");
+  if (n > 0 && !finite_all(d->pos, 3 * n)) return fail(ctx, GSC_ERR_INVALID_ARG, "non-finite anchor position");
+  if (!(d->lod_dmax >= 0.f) || !std::isfinite(d->lod_dmax)) return fail(ctx, GSC_ERR_INVALID_ARG, "bad lod_dmax");
+  for (size_t i = 0; i < n; ++i)
+    if (d->level[i] >= d->n_levels) return fail(ctx, GSC_ERR_INVALID_ARG, "level >= n_levels at anchor %zu", i);
+  ModelHost mh;
+  mh.n = (uint32_t)n;
+  std::vector<float> xs(n), ys(n), zs(n);
+  for (size_t i = 0; i < n; ++i) {
+    xs[i] = d->pos[3 * i];
+    ys[i] = d->pos[3 * i + 1];
+    zs[i] = d->pos[3 * i + 2];
+  }
+  // packed float32 weights
+  std::vector<float> w(W_FLOATS, 0.f);
+  const int outd[3] = {K, 3 * K, 7 * K};
+  const int obase[3] = {0, K, 4 * K};
+  for (int h = 0; h < 3; ++h) {
+    for (int c = 0; c < IN; ++c)
+      for (int o = 0; o < HID; ++o) w[WOFF_W1 + c * NH + h * HID + o] = d->W1[h][c * HID + o];
+    for (int o = 0; o < HID; ++o) w[WOFF_B1 + h * HID + o] = d->b1[h][o];
+    for (int o = 0; o < outd[h]; ++o) {
+      for (int c = 0; c < HID; ++c) w[WOFF_W2T + (obase[h] + o) * HID + c] = d->W2[h][c * outd[h] + o];
+      w[WOFF_B2 + obase[h] + o] = d->b2[h][o];
+    }
+  }
+  int r;
+  if ((r = upload(ctx, mh.px, xs.data(), n * 4)) || (r = upload(ctx, mh.py, ys.data(), n * 4)) ||
+      (r = upload(ctx, mh.pz, zs.data(), n * 4)) || (r = upload(ctx, mh.level, d->level, n)) ||
+      (r = upload(ctx, mh.feat, d->feat, n * FDIM * 4)) || (r = upload(ctx, mh.offs, d->offset, n * K * 3 * 4)) ||
+      (r = upload(ctx, mh.scale, d->scale, n * 4)) || (r = upload(ctx, mh.w32, w.data(), w.size() * 4)))
+    return r;
+  mh.dev.n = mh.n;
+  mh.dev.n_levels = d->n_levels;
+  mh.dev.lod_dmax = d->lod_dmax;
+  mh.dev.px = (const float*)mh.px.p;
+  mh.dev.py = (const float*)mh.py.p;
+  mh.dev.pz = (const float*)mh.pz.p;
+  mh.dev.level = (const uint8_t*)mh.level.p;
+  mh.dev.feat = (const float4*)mh.feat.p;
+  mh.dev.offs = (const float*)mh.offs.p;
+  mh.dev.scale = (const float*)mh.scale.p;
+  mh.dev.w32 = (const float*)mh.w32.p;
+  const uint32_t id = (uint32_t)ctx->models.size();
+  CK(cudaMemcpy(ctx->d_models + id, &mh.dev, sizeof(ModelDev), cudaMemcpyHostToDevice));
+  ctx->models.push_back(mh);
+  *model_id_out = id;
+  ctx->cams_set = false;  // buffers are sized at the next gsc_set_cameras
+  invalidate_graph(ctx);
+  ctx->err.clear();
+  return GSC_OK;
+}
+
+int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!cams || n == 0) return fail(ctx, GSC_ERR_INVALID_ARG, "no cameras");
+  if (n > ctx->cfg.max_views) return fail(ctx, GSC_ERR_INVALID_ARG, "%u cameras > max_views %u", n, ctx->cfg.max_views);
+  uint32_t per_model[MAX_MODELS] = {0};
+  for (uint32_t i = 0; i < n; ++i) {
+    const gsc_camera& c = cams[i];
+    if (c.model_id >= ctx->models.size()) return fail(ctx, GSC_ERR_INVALID_ARG, "camera %u: unknown model", i);
+    if (c.width == 0 || c.height == 0 || c.width > 16384 || c.height > 16384)
+      return fail(ctx, GSC_ERR_INVALID_ARG, "camera %u: bad size", i);
+    if (!(c.fx > 0.f) || !(c.fy > 0.f) || !(c.znear > 0.f) || !finite_all(c.R, 9) || !finite_all(c.t, 3) ||
+        !std::isfinite(c.cx) || !std::isfinite(c.cy))
+      return fail(ctx, GSC_ERR_INVALID_ARG, "camera %u: bad intrinsics or pose", i);
+    if (c.stereo_partner >= 0) {
+      const uint32_t p = (uint32_t)c.stereo_partner;
+      if (p >= n || p == i || cams[p].stereo_partner != (int32_t)i)
+        return fail(ctx, GSC_ERR_INVALID_ARG, "camera %u: stereo partner must reference back", i);
+      if (cams[p].model_id != c.model_id || cams[p].width != c.width || cams[p].height != c.height ||
+          cams[p].fx != c.fx || cams[p].fy != c.fy)
+        return fail(ctx, GSC_ERR_INVALID_ARG, "camera %u: stereo partner must share model and intrinsics", i);
+    }
+    const bool second_eye = ctx->cfg.stereo_unify && c.stereo_partner >= 0 && (uint32_t)c.stereo_partner < i;
+    if (!second_eye) per_model[c.model_id]++;
+  }
+  for (uint32_t m = 0; m < MAX_MODELS; ++m)
+    if (per_model[m] > 8) return fail(ctx, GSC_ERR_INVALID_ARG, "more than 8 derivation views of model %u", m);
+  // shape of the frame
+  bool shape_same = ctx->cams.size() == n;
+  for (uint32_t i = 0; shape_same && i < n; ++i) {
+    const gsc_camera& a = ctx->cams[i];
+    const gsc_camera& b = cams[i];
+    shape_same = a.width == b.width && a.height == b.height && a.model_id == b.model_id &&
+                 a.stereo_partner == b.stereo_partner;
+  }
+  ctx->cams.assign(cams, cams + n);
+  if (shape_same && ctx->cams_set) return GSC_OK;
+  invalidate_graph(ctx);
+  uint32_t tiles = 0;
+  for (const auto& c : ctx->cams)
+    tiles += ((c.width + ctx->cfg.tile_w - 1) / ctx->cfg.tile_w) * ((c.height + ctx->cfg.tile_h - 1) / ctx->cfg.tile_h);
+  ctx->total_tiles = tiles;
+  uint32_t bits = 1;
+  while ((1u << bits) < tiles && bits < 31) ++bits;
+  ctx->tile_bits = bits;
+  ctx->models_used.clear();
+  for (uint32_t m = 0; m < MAX_MODELS; ++m)
+    if (per_model[m]) ctx->models_used.push_back((int)m);
+  int r;
+  if (tiles > ctx->ranges_cap) {
+    if ((r = dalloc(ctx, &ctx->ranges, tiles))) return r;
+    ctx->ranges_cap = tiles;
+  }
+  // visible-id lists: one slot per derivation view, each sized for the largest model
+  const uint32_t vcap = std::max<uint32_t>(models_max_n(ctx), 1u);
+  if (vcap > ctx->vis_cap || n > ctx->n_vis_slots) {
+    const uint32_t slots = std::max(n, ctx->n_vis_slots);
+    if ((r = dalloc(ctx, &ctx->d_vis_buf, (size_t)vcap * slots))) return r;
+    std::vector<uint32_t*> tab(MAXV, nullptr);
+    for (uint32_t i = 0; i < slots; ++i) tab[i] = ctx->d_vis_buf + (size_t)vcap * i;
+    CK(cudaMemcpy(ctx->d_vis_tab, tab.data(), sizeof(uint32_t*) * MAXV, cudaMemcpyHostToDevice));
+    ctx->vis_cap = vcap;
+    ctx->n_vis_slots = slots;
+    if (ctx->cfg.flags & GSC_FLAG_DEBUG_ATTRS) {
+      if ((r = dalloc(ctx, &ctx->d_dbg_buf, (size_t)vcap * slots * K * 11))) return r;
+      std::vector<float*> dt(MAXV, nullptr);
+      for (uint32_t i = 0; i < slots; ++i) dt[i] = ctx->d_dbg_buf + (size_t)vcap * K * 11 * i;
+      if (!ctx->d_dbg_tab) CK(cudaMalloc((void**)&ctx->d_dbg_tab, sizeof(float*) * MAXV));
+      CK(cudaMemcpy(ctx->d_dbg_tab, dt.data(), sizeof(float*) * MAXV, cudaMemcpyHostToDevice));
+    }
+  }
+  // records: worst case (every anchor visible), capped at 64M then grown on demand
+  unsigned long long worst = 0;
+  for (const auto& c : ctx->cams) worst += (unsigned long long)K * ctx->models[c.model_id].n;
+  const uint32_t want = (uint32_t)std::min<unsigned long long>(std::max<unsigned long long>(worst, 1024ull), 64ull << 20);
+  if (want > ctx->rec_cap) {
+    if ((r = alloc_records(ctx, want))) return r;
+  }
+  if ((r = ensure_status(ctx))) return r;
+  ctx->cams_set = true;
+  ctx->err.clear();
+  return GSC_OK;
+}
+
+int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!out_rgb) return fail(ctx, GSC_ERR_INVALID_ARG, "null output table");
+  for (size_t i = 0; i < ctx->cams.size(); ++i)
+    if (!out_rgb[i]) return fail(ctx, GSC_ERR_INVALID_ARG, "null output image %zu", i);
+  float* Ts[MAXV] = {};
+  if (ctx->cfg.flags & GSC_FLAG_DEBUG_T) {
+    for (size_t i = 0; i < ctx->cams.size(); ++i) {
+      const size_t b = (size_t)ctx->cams[i].width * ctx->cams[i].height * 4;
+      if (ctx->d_T_bytes[i] < b) {
+        dfree(ctx->d_T[i]);
+        ctx->d_T[i] = nullptr;
+        CK(cudaMalloc((void**)&ctx->d_T[i], b));
+        ctx->d_T_bytes[i] = b;
+      }
+      Ts[i] = ctx->d_T[i];
+    }
+  }
+  return render_impl(ctx, out_rgb, (ctx->cfg.flags & GSC_FLAG_DEBUG_T) ? Ts : nullptr, stats, stats != nullptr);
+}
+
+int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!out_rgb) return fail(ctx, GSC_ERR_INVALID_ARG, "null output table");
+  if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
+  float* outs[MAXV] = {};
+  for (size_t i = 0; i < ctx->cams.size(); ++i) {
+    if (!out_rgb[i]) return fail(ctx, GSC_ERR_INVALID_ARG, "null output image %zu", i);
+    const size_t b = (size_t)ctx->cams[i].width * ctx->cams[i].height * 3 * 4;
+    if (ctx->d_img_bytes[i] < b) {
+      dfree(ctx->d_img[i]);
+      ctx->d_img[i] = nullptr;
+      CK(cudaMalloc((void**)&ctx->d_img[i], b));
+      ctx->d_img_bytes[i] = b;
+    }
+    outs[i] = ctx->d_img[i];
+  }
+  gsc_frame_stats tmp;
+  int r = render_impl(ctx, outs, nullptr, stats ? stats : &tmp, true);
+  if (r) return r;
+  for (size_t i = 0; i < ctx->cams.size(); ++i) {
+    const size_t b = (size_t)ctx->cams[i].width * ctx->cams[i].height * 3 * 4;
+    CK(cudaMemcpyAsync(out_rgb[i], outs[i], b, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSC_OK;
+}
+
+int gsc_cache_reset(gsc_ctx* ctx) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  ctx->err.clear();
+  return GSC_OK;  // no cache in the plain forms
+}
+
+int gsc_synchronize(gsc_ctx* ctx) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->pending) return finish_frame(ctx);
+  return GSC_OK;
+}
+
+// ------------------------------------------------------------------ debug exports
+static int dbg_sync(gsc_ctx* ctx) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GSC_OK;
+}
+
+static int dbg_copy(gsc_ctx* ctx, void* dst, const void* src, uint64_t count, uint64_t cap, size_t elem) {
+  const uint64_t m = std::min(count, cap);
+  if (m && dst) CK(cudaMemcpy(dst, src, m * elem, cudaMemcpyDeviceToHost));
+  return GSC_OK;
+}
+
+int gsc_debug_visible(gsc_ctx* ctx, uint32_t d, uint32_t* ids, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (d >= MAXV || !n) return fail(ctx, GSC_ERR_INVALID_ARG, "bad view");
+  uint32_t cnt = ctx->h_cnt->vis_count[d];
+  *n = cnt;
+  if (!ctx->d_vis_buf || d >= ctx->n_vis_slots) return cnt ? GSC_ERR_STATE : GSC_OK;
+  return dbg_copy(ctx, ids, ctx->d_vis_buf + (size_t)ctx->vis_cap * d, cnt, cap, 4);
+}
+
+int gsc_debug_dviews(gsc_ctx* ctx, uint32_t* n_dviews, int32_t* first_cam) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  FrameDev* h = (FrameDev*)malloc(sizeof(FrameDev));
+  if (!h) return GSC_ERR_OOM;
+  cudaError_t e = cudaMemcpy(h, ctx->d_fd, sizeof(FrameDev), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free(h);
+    return fail(ctx, GSC_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  if (n_dviews) *n_dviews = h->n_dviews;
+  if (first_cam)
+    for (int i = 0; i < MAXV; ++i) first_cam[i] = i < (int)h->n_dviews ? h->dview_cam[i][0] : -1;
+  free(h);
+  return GSC_OK;
+}
+
+int gsc_debug_attrs(gsc_ctx* ctx, uint32_t d, float* attrs, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!(ctx->cfg.flags & GSC_FLAG_DEBUG_ATTRS) || !ctx->d_dbg_buf)
+    return fail(ctx, GSC_ERR_STATE, "context was created without GSC_FLAG_DEBUG_ATTRS");
+  if (d >= ctx->n_vis_slots || !n) return fail(ctx, GSC_ERR_INVALID_ARG, "bad view");
+  const uint32_t cnt = ctx->h_cnt->vis_count[d];
+  *n = cnt;
+  return dbg_copy(ctx, attrs, ctx->d_dbg_buf + (size_t)ctx->vis_cap * K * 11 * d, cnt, cap, sizeof(float) * K * 11);
+}
+
+int gsc_debug_records(gsc_ctx* ctx, float* rec12, uint32_t* depth_key, uint32_t* tile_count, uint64_t cap,
+                      uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!n) return GSC_ERR_INVALID_ARG;
+  const uint32_t cnt = ctx->h_cnt->n_records;
+  *n = cnt;
+  const uint64_t m = std::min<uint64_t>(cnt, cap);
+  if (m == 0) return GSC_OK;
+  if (rec12) {
+    std::vector<float4> g(m), c(m), o(m);
+    CK(cudaMemcpy(g.data(), ctx->rec.geo, m * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(c.data(), ctx->rec.cop, m * 16, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(o.data(), ctx->rec.col, m * 16, cudaMemcpyDeviceToHost));
+    for (uint64_t i = 0; i < m; ++i) {
+      float* q = rec12 + i * 12;
+      q[0] = g[i].x; q[1] = g[i].y; q[2] = g[i].z; q[3] = g[i].w;
+      q[4] = c[i].x; q[5] = c[i].y; q[6] = c[i].z; q[7] = c[i].w;
+      q[8] = o[i].x; q[9] = o[i].y; q[10] = o[i].z; q[11] = o[i].w;
+    }
+  }
+  if (depth_key) CK(cudaMemcpy(depth_key, ctx->rec.key, m * 4, cudaMemcpyDeviceToHost));
+  if (tile_count) CK(cudaMemcpy(tile_count, ctx->rec.cnt, m * 4, cudaMemcpyDeviceToHost));
+  return GSC_OK;
+}
+
+int gsc_debug_pairs(gsc_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!n) return GSC_ERR_INVALID_ARG;
+  const uint32_t cnt = ctx->h_cnt->n_pairs_used;
+  *n = cnt;
+  if ((r = dbg_copy(ctx, keys, ctx->pkeys_out, cnt, cap, 4))) return r;
+  return dbg_copy(ctx, vals, ctx->pvals_out, cnt, cap, 4);
+}
+
+int gsc_debug_depth_order(gsc_ctx* ctx, uint32_t* vals, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!n) return GSC_ERR_INVALID_ARG;
+  const uint32_t cnt = ctx->h_cnt->n_valid;
+  *n = cnt;
+  return dbg_copy(ctx, vals, ctx->order_out, cnt, cap, 4);
+}
+
+int gsc_debug_ranges(gsc_ctx* ctx, uint32_t* ranges, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!n) return GSC_ERR_INVALID_ARG;
+  *n = ctx->total_tiles;
+  return dbg_copy(ctx, ranges, ctx->ranges, ctx->total_tiles, cap, 8);
+}
+
+int gsc_debug_final_T(gsc_ctx* ctx, uint32_t v, float* T, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!(ctx->cfg.flags & GSC_FLAG_DEBUG_T)) return fail(ctx, GSC_ERR_STATE, "context was created without GSC_FLAG_DEBUG_T");
+  if (v >= ctx->cams.size() || !n) return fail(ctx, GSC_ERR_INVALID_ARG, "bad camera");
+  const uint64_t cnt = (uint64_t)ctx->cams[v].width * ctx->cams[v].height;
+  *n = cnt;
+  return dbg_copy(ctx, T, ctx->d_T[v], cnt, cap, 4);
+}
+
+int gsc_debug_set_spin_limit(gsc_ctx* ctx, uint32_t limit) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  ctx->spin_limit = limit;
+  return GSC_OK;
+}
+
+int gsc_debug_sort_pairs(gsc_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t n, uint32_t bits) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!keys || !vals || bits == 0 || bits > 32 || n > 0x3FFFFFFFull) return fail(ctx, GSC_ERR_INVALID_ARG, "bad sort args");
+  if (n == 0) return GSC_OK;
+  if (n > ctx->pair_cap) {
+    int r = alloc_pairs(ctx, (uint32_t)n);
+    if (r) return r;
+  }
+  int r = ensure_status(ctx);
+  if (r) return r;
+  uint32_t* d_n = nullptr;
+  CK(cudaMalloc((void**)&d_n, 4));
+  const uint32_t n32 = (uint32_t)n;
+  CK(cudaMemcpy(d_n, &n32, 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->pk0, keys, n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->pv0, vals, n * 4, cudaMemcpyHostToDevice));
+  launch_bump_epoch(ctx->d_fd, ctx->spin_limit, ctx->stream);
+  uint32_t *ok = nullptr, *ov = nullptr;
+  launch_sort_impl(ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->pk0, ctx->pv0, d_n, nullptr, (int)bits, 0, SLOT_SORT2,
+                   ctx->d_fd, ctx->sb, ctx->n_sm, ctx->stream, &ok, &ov);
+  CK(cudaStreamSynchronize(ctx->stream));
+  uint32_t err = 0;
+  CK(cudaMemcpy(&err, &ctx->d_fd->err, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(keys, ok, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vals, ov, n * 4, cudaMemcpyDeviceToHost));
+  cudaFree(d_n);
+  invalidate_graph(ctx);
+  if (err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  return GSC_OK;
+}
+
+int gsc_debug_wait_timeout(gsc_ctx* ctx, uint32_t spin_limit) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  launch_bump_epoch(ctx->d_fd, spin_limit, ctx->stream);
+  launch_wait_probe(ctx->d_fd, ctx->st_scan, ctx->stream);
+  CK(cudaStreamSynchronize(ctx->stream));
+  uint32_t err = 0;
+  CK(cudaMemcpy(&err, &ctx->d_fd->err, 4, cudaMemcpyDeviceToHost));
+  if (err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  return fail(ctx, GSC_ERR_INTERNAL, "the probe's wait did not time out");
+}
+
+int gsc_debug_scan(gsc_ctx* ctx, uint32_t* vals, uint64_t n, uint64_t* total) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!vals || !total || n > 0x3FFFFFFFull) return fail(ctx, GSC_ERR_INVALID_ARG, "bad scan args");
+  *total = 0;
+  if (n == 0) return GSC_OK;
+  if (n > ctx->pair_cap) {
+    int r = alloc_pairs(ctx, (uint32_t)n);
+    if (r) return r;
+  }
+  int r = ensure_status(ctx);
+  if (r) return r;
+  uint32_t* d_n = nullptr;
+  CK(cudaMalloc((void**)&d_n, 8));
+  const uint32_t n32 = (uint32_t)n;
+  CK(cudaMemcpy(d_n, &n32, 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->pk0, vals, n * 4, cudaMemcpyHostToDevice));
+  launch_bump_epoch(ctx->d_fd, ctx->spin_limit, ctx->stream);
+  launch_scan_u32(ctx->pk0, nullptr, d_n, ctx->pk1, d_n + 1, ctx->st_scan, ctx->d_fd, SLOT_SCAN, ctx->n_sm, ctx->stream);
+  CK(cudaStreamSynchronize(ctx->stream));
+  uint32_t tot = 0, err = 0;
+  CK(cudaMemcpy(&tot, d_n + 1, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&err, &ctx->d_fd->err, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vals, ctx->pk1, n * 4, cudaMemcpyDeviceToHost));
+  cudaFree(d_n);
+  *total = tot;
+  if (err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  return GSC_OK;
+}
+
+}  // extern "C"

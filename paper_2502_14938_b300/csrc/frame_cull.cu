@@ -1,0 +1,324 @@
+// Frame setup, anchor filtering (K1) and the per-frame plan.
+#include "gsc_internal.cuh"
+
+namespace gsc {
+
+// ------------------------------------------------------------------ frame setup
+// Camera centre p = -R^T t, float64 in a fixed order (each op rounded).
+__device__ void center64(const float* R, const float* t, double* p) {
+  for (int i = 0; i < 3; ++i) {
+    double s = __dmul_rn((double)R[i], (double)t[0]);
+    s = __dadd_rn(s, __dmul_rn((double)R[3 + i], (double)t[1]));
+    s = __dadd_rn(s, __dmul_rn((double)R[6 + i], (double)t[2]));
+    p[i] = -s;
+  }
+}
+
+__device__ void fill_camdev(CamDev& c, const CamIn& in, const FrameIn& fin) {
+  for (int i = 0; i < 9; ++i) c.R[i] = in.R[i];
+  for (int i = 0; i < 3; ++i) c.t[i] = in.t[i];
+  c.fx = in.fx; c.fy = in.fy; c.cx = in.cx; c.cy = in.cy;
+  c.W = (int)in.W; c.H = (int)in.H; c.znear = in.znear;
+  c.model = (int)in.model;
+  double p[3];
+  center64(c.R, c.t, p);
+  for (int i = 0; i < 3; ++i) c.pc[i] = __double2float_rn(p[i]);
+  c.gx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.W), c.fx));
+  c.gy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.H), c.fy));
+  c.ntx = (c.W + (int)fin.tile_w - 1) / (int)fin.tile_w;
+  c.nty = (c.H + (int)fin.tile_h - 1) / (int)fin.tile_h;
+}
+
+// Unified camera of a stereo pair (Eq. 5-6): d_u = normalised mean forward
+// axis; p_u = mean centre - d_u |p1 - p2| / (2 tan(theta/2)) with
+// 2 tan(theta/2) = W / fx (horizontal field of view); right/down axes from
+// the mean down axis orthogonalised against d_u.  Float64, every operation
+// rounded explicitly (no contraction), result rounded once to float32.
+__device__ void unified_camera(const CamIn& L, const CamIn& Rr, CamIn& U) {
+  double p1[3], p2[3];
+  center64(L.R, L.t, p1);
+  center64(Rr.R, Rr.t, p2);
+  double d[3], y[3], pm[3];
+  for (int i = 0; i < 3; ++i) {
+    d[i] = __dmul_rn(__dadd_rn((double)L.R[6 + i], (double)Rr.R[6 + i]), 0.5);
+    y[i] = __dmul_rn(__dadd_rn((double)L.R[3 + i], (double)Rr.R[3 + i]), 0.5);
+    pm[i] = __dmul_rn(__dadd_rn(p1[i], p2[i]), 0.5);
+  }
+  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+  double du[3];
+  for (int i = 0; i < 3; ++i) du[i] = __ddiv_rn(d[i], dn);
+  const double bx = __dsub_rn(p1[0], p2[0]), by = __dsub_rn(p1[1], p2[1]), bz = __dsub_rn(p1[2], p2[2]);
+  const double b = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)));
+  const double back = __ddiv_rn(__dmul_rn(b, (double)L.fx), (double)L.W);
+  double pu[3];
+  for (int i = 0; i < 3; ++i) pu[i] = __dsub_rn(pm[i], __dmul_rn(du[i], back));
+  double xr[3] = {__dsub_rn(__dmul_rn(y[1], du[2]), __dmul_rn(y[2], du[1])),
+                  __dsub_rn(__dmul_rn(y[2], du[0]), __dmul_rn(y[0], du[2])),
+                  __dsub_rn(__dmul_rn(y[0], du[1]), __dmul_rn(y[1], du[0]))};
+  const double xn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(xr[0], xr[0]), __dmul_rn(xr[1], xr[1])), __dmul_rn(xr[2], xr[2])));
+  double xu[3];
+  for (int i = 0; i < 3; ++i) xu[i] = __ddiv_rn(xr[i], xn);
+  double yu[3] = {__dsub_rn(__dmul_rn(du[1], xu[2]), __dmul_rn(du[2], xu[1])),
+                  __dsub_rn(__dmul_rn(du[2], xu[0]), __dmul_rn(du[0], xu[2])),
+                  __dsub_rn(__dmul_rn(du[0], xu[1]), __dmul_rn(du[1], xu[0]))};
+  double Ru[9] = {xu[0], xu[1], xu[2], yu[0], yu[1], yu[2], du[0], du[1], du[2]};
+  U = L;
+  for (int i = 0; i < 9; ++i) U.R[i] = __double2float_rn(Ru[i]);
+  for (int r = 0; r < 3; ++r) {
+    double s = __dmul_rn(Ru[r * 3 + 0], pu[0]);
+    s = __dadd_rn(s, __dmul_rn(Ru[r * 3 + 1], pu[1]));
+    s = __dadd_rn(s, __dmul_rn(Ru[r * 3 + 2], pu[2]));
+    U.t[r] = __double2float_rn(-s);
+  }
+}
+
+__global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const FrameIn& F = *fin;
+  fd->frame = fd->frame + 1;
+  fd->n_cams = F.n_cams;
+  fd->tile_w = F.tile_w;
+  fd->tile_h = F.tile_h;
+  fd->spin_limit = F.spin_limit;
+  uint32_t tb = 0;
+  for (uint32_t c = 0; c < F.n_cams; ++c) {
+    fill_camdev(fd->cam[c], F.cam[c], F);
+    fd->cam[c].tile_base = tb;
+    tb += (uint32_t)(fd->cam[c].ntx * fd->cam[c].nty);
+  }
+  fd->total_tiles = tb;
+  uint32_t bits = 1;
+  while ((1u << bits) < tb && bits < 31) ++bits;
+  fd->tile_bits = bits;
+  // derivation views
+  uint32_t nd = 0;
+  for (uint32_t c = 0; c < F.n_cams; ++c) fd->dview_of_cam[c] = -1;
+  for (uint32_t c = 0; c < F.n_cams; ++c) {
+    if (fd->dview_of_cam[c] >= 0) continue;
+    const int p = F.cam[c].partner;
+    const bool pair = F.unify && p > (int)c && p < (int)F.n_cams && F.cam[p].partner == (int)c;
+    if (pair) {
+      CamIn U;
+      unified_camera(F.cam[c], F.cam[p], U);
+      fill_camdev(fd->dcam[nd], U, F);
+      fd->dview_cam[nd][0] = (int)c;
+      fd->dview_cam[nd][1] = p;
+      fd->dview_of_cam[c] = (int)nd;
+      fd->dview_of_cam[p] = (int)nd;
+    } else {
+      fd->dcam[nd] = fd->cam[c];
+      fd->dview_cam[nd][0] = (int)c;
+      fd->dview_cam[nd][1] = -1;
+      fd->dview_of_cam[c] = (int)nd;
+    }
+    fd->vis_count[nd] = 0;
+    ++nd;
+  }
+  fd->n_dviews = nd;
+  fd->n_valid = 0;
+  fd->n_pairs = 0;
+  fd->n_pairs_used = 0;
+  fd->err = 0;
+  for (int i = 0; i < 32; ++i) fd->ctr[i] = 0;
+}
+
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s) {
+  k_frame_begin<<<1, 32, 0, s>>>(fd, fin);
+}
+
+// New epoch for standalone uses of the look-back kernels (debug sort / scan).
+__global__ void k_bump_epoch(FrameDev* fd, uint32_t spin_limit) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  fd->frame = fd->frame + 1;
+  fd->spin_limit = spin_limit;
+  fd->err = 0;
+  fd->n_valid = 0;
+  for (int i = 0; i < 32; ++i) fd->ctr[i] = 0;
+}
+
+void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s) {
+  k_bump_epoch<<<1, 32, 0, s>>>(fd, spin_limit);
+}
+
+// Timeout-path probe: one thread waits, through the look-back routine, for
+// a predecessor word under an epoch that no kernel ever writes.  The wait
+// must give up after spin_limit polls and set ERR_TIMEOUT.
+__global__ void k_wait_probe(FrameDev* fd, unsigned long long* words) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint32_t never = fd->frame * 64u + (uint32_t)SLOT_AUX + 7u;
+  (void)lb_exclusive(words, 1, 1, never ^ 0x80000000u, fd->spin_limit, &fd->err);
+}
+
+void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(fd, words);
+}
+
+// ------------------------------------------------------------------ culling (K1)
+// Anchor filtering (Sec. 3.2; Alg. 1 "anchors indexing and filtering"): for
+// every derivation view of this model, frustum test with a 1.3 guard band and
+// the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max 2^-l)^2,
+// level 0 always).  Float32 with an explicit operation order.  Each thread
+// owns CULL_IPT consecutive anchors; a block scan of per-thread counts plus a
+// decoupled look-back across tiles gives an order-preserving compaction
+// (ascending anchor ids), one pass over the positions.
+constexpr int CULL_NT = 256;
+constexpr int CULL_IPT = 8;
+constexpr int CULL_TILE = CULL_NT * CULL_IPT;
+constexpr int CULL_MAXD = 8;
+
+__global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
+                                                  uint32_t* const* __restrict__ vis, unsigned long long* status) {
+  __shared__ int s_d[CULL_MAXD];
+  __shared__ int s_nd;
+  __shared__ float s_cam[CULL_MAXD][20];
+  __shared__ uint32_t s_warp[CULL_NT / 32 + 1];
+  __shared__ uint32_t s_total[CULL_MAXD];
+  __shared__ uint32_t s_base[CULL_MAXD];
+  __shared__ uint32_t s_tile;
+
+  const ModelDev md = models[model];
+  if (threadIdx.x == 0) {
+    int nd = 0;
+    for (uint32_t d = 0; d < fd->n_dviews; ++d) {
+      if (fd->dcam[d].model != model) continue;
+      if (nd < CULL_MAXD) s_d[nd++] = (int)d;  // the host admits at most 8 views per model
+    }
+    s_nd = nd;
+  }
+  __syncthreads();
+  const int nd = s_nd;
+  if (threadIdx.x < nd * 20) {
+    const int ld = threadIdx.x / 20, f = threadIdx.x % 20;
+    const CamDev& c = fd->dcam[s_d[ld]];
+    float v;
+    if (f < 9) v = c.R[f];
+    else if (f < 12) v = c.t[f - 9];
+    else if (f < 15) v = c.pc[f - 12];
+    else if (f == 15) v = c.znear;
+    else if (f == 16) v = c.gx;
+    else if (f == 17) v = c.gy;
+    else v = 0.f;
+    s_cam[ld][f] = v;
+  }
+  __syncthreads();
+  if (nd == 0) return;
+
+  const uint32_t n = md.n;
+  const uint32_t ntiles = (n + CULL_TILE - 1) / CULL_TILE;
+  const uint32_t epoch = fd->frame * 64u + (uint32_t)(SLOT_CULL + model);
+  const uint32_t spin = fd->spin_limit;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&fd->ctr[SLOT_CULL + model], 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= ntiles) break;
+    const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
+    float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
+    int lv[CULL_IPT];
+#pragma unroll
+    for (int i = 0; i < CULL_IPT; ++i) {
+      const uint32_t a = a0 + i;
+      if (a < n) {
+        x[i] = __ldg(md.px + a);
+        y[i] = __ldg(md.py + a);
+        z[i] = __ldg(md.pz + a);
+        lv[i] = md.level[a];
+      } else {
+        x[i] = y[i] = z[i] = 0.f;
+        lv[i] = -1;
+      }
+    }
+    uint32_t excl[CULL_MAXD], mask[CULL_MAXD];
+#pragma unroll
+    for (int ld = 0; ld < CULL_MAXD; ++ld) {
+      excl[ld] = 0;
+      mask[ld] = 0;
+      if (ld >= nd) continue;
+      const float* c = s_cam[ld];
+      uint32_t m = 0;
+#pragma unroll
+      for (int i = 0; i < CULL_IPT; ++i) {
+        if (lv[i] < 0) continue;
+        const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
+        const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
+        const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
+        bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
+        if (v && lv[i] >= 1) {
+          const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
+          const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+          const float thr = ldexpf(md.lod_dmax, -lv[i]);
+          v = d2 <= __fmul_rn(thr, thr);
+        }
+        if (v) m |= 1u << i;
+      }
+      mask[ld] = m;
+      uint32_t tot;
+      excl[ld] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m), s_warp, &tot);
+      if (threadIdx.x == 0) s_total[ld] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x < (uint32_t)nd) {
+      const int ld = threadIdx.x;
+      const uint32_t tot = s_total[ld];
+      unsigned long long* w = status + (size_t)t * CULL_MAXD + ld;
+      uint32_t pre = 0;
+      if (t == 0) {
+        st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
+      } else {
+        st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
+        pre = lb_exclusive(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
+        st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
+      }
+      s_base[ld] = pre;
+      if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ld = 0; ld < CULL_MAXD; ++ld) {
+      if (ld >= nd) continue;
+      uint32_t* out = vis[s_d[ld]];
+      uint32_t o = s_base[ld] + excl[ld];
+      uint32_t m = mask[ld];
+      while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        out[o++] = a0 + (uint32_t)i;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
+                 unsigned long long* status, int n_sm, cudaStream_t s) {
+  k_cull<<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
+}
+
+// ------------------------------------------------------------------ plan
+__global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t acc = 0;
+  for (uint32_t d = 0; d < fd->n_dviews; ++d) {
+    fd->item_base[d] = acc;
+    acc += fd->vis_count[d];
+  }
+  fd->item_base[fd->n_dviews] = acc;
+  fd->n_items = acc;
+  unsigned long long r = 0;
+  for (uint32_t c = 0; c < fd->n_cams; ++c) {
+    fd->rec_base[c] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+    r += (unsigned long long)K * fd->vis_count[fd->dview_of_cam[c]];
+  }
+  fd->rec_base[fd->n_cams] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+  if (r > rec_cap) {
+    atomicOr(&fd->err, ERR_REC_OVERFLOW);
+    fd->n_records = rec_cap;
+  } else {
+    fd->n_records = (uint32_t)r;
+  }
+}
+
+void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s) { k_plan<<<1, 32, 0, s>>>(fd, rec_cap); }
+
+}  // namespace gsc

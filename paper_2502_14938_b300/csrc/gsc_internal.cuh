@@ -1,0 +1,276 @@
+// Internal device-side definitions of the GS-Cache frame renderer (sm_103a).
+//
+// Frame data flow (all sizes live in device memory, so one frame is a fixed
+// launch sequence that can be replayed as a CUDA graph without host reads):
+//   frame_begin  -> per-camera constants, unified cameras (Eq. 5-6), counters
+//   cull         -> ascending visible anchor ids per derivation view (K1)
+//   plan         -> record bases per camera
+//   derive       -> MLP decode (Eq. 3) fused with EWA projection and exact
+//                   tile counting (Eq. 1-2, Sec. 6): one record per
+//                   (camera, anchor, Gaussian)
+//   sort #1      -> records in depth order (32-bit depth key, invalid dropped)
+//   scan+keygen  -> (tile key, record) pairs in depth order
+//   sort #2      -> stable sort by tile key => (tile, depth, Gaussian id)
+//   ranges+blend -> per-tile front-to-back alpha blending
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "gsc.h"
+
+namespace gsc {
+
+constexpr int K = GSC_K;            // Gaussians per anchor
+constexpr int FDIM = GSC_FEAT_DIM;  // anchor feature width
+constexpr int HID = GSC_HIDDEN;     // hidden width of each head
+constexpr int IN = FDIM + 3;        // MLP input: feature + unit view direction
+constexpr int NH = 3 * HID;         // concatenated hidden width of the 3 heads
+constexpr int NOUT = K + 3 * K + 7 * K;  // 110 head outputs
+constexpr int MAXV = GSC_MAX_VIEWS;
+constexpr int MAX_MODELS = 8;
+constexpr int REC_F4 = 3;           // float4s per record
+
+// packed float32 weights: W1cat [IN][NH], b1cat [NH], W2T [NOUT][HID], b2cat [NOUT]
+constexpr int WOFF_W1 = 0;
+constexpr int WOFF_B1 = WOFF_W1 + IN * NH;
+constexpr int WOFF_W2T = WOFF_B1 + NH;
+constexpr int WOFF_B2 = WOFF_W2T + NOUT * HID;
+constexpr int W_FLOATS = WOFF_B2 + NOUT;
+
+enum : uint32_t { ERR_PAIR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_CACHE_FULL = 4u, ERR_REC_OVERFLOW = 8u };
+
+constexpr uint32_t INVALID_KEY = 0xFFFFFFFFu;
+constexpr uint32_t REC_VALID_BIT = 0x80000000u;
+
+struct CamIn {  // host-provided camera, uploaded each frame
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  uint32_t W, H;
+  float znear;
+  int32_t partner;
+  uint32_t model;
+  uint32_t viewer;
+};
+
+struct CamDev {  // camera with derived constants (computed on device)
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t W, H;
+  float znear;
+  float pc[3];     // centre -R^T t (float64 then rounded)
+  float gx, gy;    // 1.3 * (0.5 W / fx), 1.3 * (0.5 H / fy) in float32
+  int32_t ntx, nty;
+  uint32_t tile_base;
+  int32_t model;
+};
+
+struct FrameIn {  // host -> device per frame
+  uint32_t n_cams;
+  uint32_t unify;
+  uint32_t tile_w, tile_h;
+  uint32_t spin_limit;
+  uint32_t pad[3];
+  float bg[4];
+  unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
+  unsigned long long out_T[MAXV];    // float* [H][W] per camera or 0
+  CamIn cam[MAXV];
+};
+
+struct FrameDev {  // device-resident per-frame plan and counters
+  uint32_t frame;               // frame counter, starts at 1 (epochs of look-back words)
+  uint32_t n_cams, n_dviews;
+  uint32_t tile_w, tile_h;
+  uint32_t total_tiles, tile_bits;
+  uint32_t spin_limit;
+  CamDev cam[MAXV];
+  CamDev dcam[MAXV];
+  int32_t dview_of_cam[MAXV];
+  int32_t dview_cam[MAXV][2];   // cameras fed by a derivation view (-1 unused)
+  // after culling
+  uint32_t vis_count[MAXV];
+  uint32_t item_base[MAXV + 1];  // prefix over derivation views of vis_count
+  uint32_t rec_base[MAXV + 1];   // prefix over cameras of K * vis_count[dview]
+  uint32_t n_items, n_records;
+  // counters of the frame
+  uint32_t n_valid;             // records with key != INVALID (set by sort #1 histogram)
+  uint32_t n_pairs;             // pairs requested (may exceed capacity)
+  uint32_t n_pairs_used;        // min(n_pairs, capacity)
+  uint32_t err;
+  uint32_t ctr[32];             // dynamic tile counters of look-back kernels
+};
+
+struct ModelDev {
+  uint32_t n, n_levels;
+  float lod_dmax;
+  uint32_t pad;
+  const float* px;
+  const float* py;
+  const float* pz;
+  const uint8_t* level;
+  const float4* feat;     // [N][8]
+  const float* offs;      // [N][K][3]
+  const float* scale;     // [N]
+  const float* w32;       // packed weights, W_FLOATS
+};
+
+struct Records {
+  float4* geo;    // mean x, mean y, A, B
+  float4* cop;    // C, opacity, tau_cov, depth
+  float4* col;    // r, g, b, bits(view | valid bit)
+  uint32_t* key;  // depth bits or INVALID_KEY
+  uint32_t* cnt;  // covered tiles
+};
+
+// ----------------------------------------------------------------- look-back words
+// 64-bit status word: [63:32] epoch, [31:30] flag (1 aggregate, 2 inclusive prefix), [29:0] value
+__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, uint32_t flag, uint32_t v) {
+  return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (unsigned long long)(v & 0x3FFFFFFFu);
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive prefix of tile t from its predecessors' words (stride apart),
+// polling at most spin_limit times in total; on timeout sets ERR_TIMEOUT and
+// returns what it has (the frame is then reported invalid).  Once any wait
+// of the launch has timed out, the others give up at their next check, so
+// a failure costs one timeout, not one per tile.  The partial prefix is
+// never larger than the true one, so the writes it steers stay in bounds.
+__device__ __forceinline__ uint32_t lb_exclusive(const unsigned long long* words, uint32_t stride, uint32_t t,
+                                                 uint32_t epoch, uint32_t spin_limit, uint32_t* err) {
+  uint32_t excl = 0;
+  int j = (int)t - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    unsigned long long w = ld_relaxed_u64(words + (size_t)j * stride);
+    uint32_t ep = (uint32_t)(w >> 32);
+    uint32_t flag = (uint32_t)(w >> 30) & 3u;
+    if (ep != epoch || flag == 0) {
+      if (++spins > spin_limit) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      if ((spins & 255u) == 0 && (*(volatile uint32_t*)err & ERR_TIMEOUT)) break;
+      __nanosleep(64);
+      continue;
+    }
+    excl += (uint32_t)(w & 0x3FFFFFFFu);
+    if (flag == 2) break;
+    --j;
+  }
+  return excl;
+}
+
+// ----------------------------------------------------------------- small helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  // s_warp: NT/32 + 1 words of shared memory
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = (lane < (uint32_t)(NT / 32)) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= (uint32_t)o) s += y;
+    }
+    if (lane < (uint32_t)(NT / 32)) s_warp[lane] = s;  // inclusive per warp
+    if (lane == (uint32_t)(NT / 32) - 1) s_warp[NT / 32] = s;
+  }
+  __syncthreads();
+  uint32_t base = (w == 0) ? 0u : s_warp[w - 1];
+  if (total) *total = s_warp[NT / 32];
+  uint32_t r = base + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Tiles covered by the ellipse q(D) = A Dx^2 + 2 B Dx Dy + C Dy^2 <= tau
+// (opacity-aware extent, Sec. 6): a tile counts iff the hull of its pixel
+// centres meets the ellipse.  Per tile row the restricted ellipse is convex,
+// so its x-range comes from the closed-form extreme points
+//   Dy* = -B sqrt(tau / (C det)),  x(Dy) = (-B Dy +- sqrt(A tau - det Dy^2)) / A.
+// Every operation is a correctly rounded float32 op (no contraction), so the
+// count pass and the emit pass agree exactly.  f(tile) is called per tile.
+template <typename Fn>
+__device__ __forceinline__ void cover_tiles_f32(float mx, float my, float A, float B, float C, float tau,
+                                                int W, int H, int TW, int TH, Fn f) {
+  const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+  if (!(tau > 0.f) || !(det > 0.f) || !(A > 0.f) || !(C > 0.f)) return;
+  const int ntx = (W + TW - 1) / TW, nty = (H + TH - 1) / TH;
+  const float ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, A), det));
+  const float ys = __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau, __fmul_rn(C, det))));
+  const float fTW = (float)TW, fTH = (float)TH;
+  float fy0 = ceilf(__fdiv_rn(__fsub_rn(__fsub_rn(my, ey), __fsub_rn(fTH, 0.5f)), fTH));
+  float fy1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(my, ey), 0.5f), fTH));
+  fy0 = fminf(fmaxf(fy0, 0.f), (float)nty);
+  fy1 = fminf(fmaxf(fy1, -1.f), (float)(nty - 1));
+  const int ty0 = (int)fy0, ty1 = (int)fy1;
+  for (int ty = ty0; ty <= ty1; ++ty) {
+    float b0 = __fsub_rn(__fadd_rn((float)(ty * TH), 0.5f), my);
+    float b1 = __fsub_rn(__fsub_rn((float)(ty * TH + TH), 0.5f), my);
+    b0 = fmaxf(b0, -ey);
+    b1 = fminf(b1, ey);
+    if (b0 > b1) continue;
+    const float yr = fminf(fmaxf(ys, b0), b1);
+    const float yl = fminf(fmaxf(-ys, b0), b1);
+    const float dr = __fsub_rn(__fmul_rn(A, tau), __fmul_rn(det, __fmul_rn(yr, yr)));
+    const float dl = __fsub_rn(__fmul_rn(A, tau), __fmul_rn(det, __fmul_rn(yl, yl)));
+    const float xr = __fdiv_rn(__fadd_rn(__fmul_rn(-B, yr), __fsqrt_rn(fmaxf(dr, 0.f))), A);
+    const float xl = __fdiv_rn(__fsub_rn(__fmul_rn(-B, yl), __fsqrt_rn(fmaxf(dl, 0.f))), A);
+    float fx0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(mx, xl), __fsub_rn(fTW, 0.5f)), fTW));
+    float fx1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(mx, xr), 0.5f), fTW));
+    fx0 = fminf(fmaxf(fx0, 0.f), (float)ntx);
+    fx1 = fminf(fmaxf(fx1, -1.f), (float)(ntx - 1));
+    const int tx0 = (int)fx0, tx1 = (int)fx1;
+    for (int tx = tx0; tx <= tx1; ++tx) f(ty * ntx + tx);
+  }
+}
+
+// ----------------------------------------------------------------- launchers (host)
+struct SortBufs {
+  uint32_t* hist;                 // [4][256] global digit counts
+  unsigned long long* status;     // look-back words [tiles][256]
+};
+
+// counter / epoch slots of the look-back kernels within one frame
+enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28 };
+
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s);
+void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
+void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
+void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
+                 unsigned long long* status, int n_sm, cudaStream_t s);
+void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
+void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, Records rec,
+                       float* const* dbg_attrs, int n_sm, cudaStream_t s);
+void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                      uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
+                      int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
+                      uint32_t** vout);
+void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
+                     uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
+                     cudaStream_t s);
+void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
+                   uint32_t* pvals, uint32_t cap, int n_sm, cudaStream_t s);
+void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);
+void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
+                  uint32_t total_tiles, uint32_t tile_threads, cudaStream_t s);
+
+}  // namespace gsc

@@ -1,0 +1,170 @@
+// LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits,
+// "onesweep" style: one kernel computes the digit histograms of every pass;
+// each pass is then one kernel in which a block ranks a 4096-key tile
+// (warp match + per-warp digit counters, stable), obtains its per-digit
+// global offsets by a decoupled look-back over the preceding tiles, and
+// scatters through shared memory so that global writes are mostly
+// contiguous.  Stable, so sorting records by depth and then pairs by tile
+// yields the (tile, depth, Gaussian id) order of the key definition.
+// Tiles are taken from an atomic counter in increasing order: a block only
+// waits on tiles already held by running blocks, and every wait is bounded.
+#include "gsc_internal.cuh"
+
+namespace gsc {
+
+constexpr int SORT_NT = 256;
+constexpr int SORT_IPT = 16;
+constexpr int SORT_TILE = SORT_NT * SORT_IPT;
+constexpr int SORT_WARPS = SORT_NT / 32;
+
+__global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
+                                                   int npass, int drop_invalid, uint32_t* __restrict__ hist,
+                                                   uint32_t* n_valid_out) {
+  __shared__ uint32_t s_h[4][256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t n = *n_ptr;
+  uint32_t nv = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (drop_invalid && k == INVALID_KEY) continue;
+    ++nv;
+    for (int p = 0; p < npass; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < npass; ++p)
+    for (int d = threadIdx.x; d < 256; d += blockDim.x)
+      if (s_h[p][d]) atomicAdd(&hist[p * 256 + d], s_h[p][d]);
+  if (n_valid_out) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    if ((threadIdx.x & 31) == 0 && nv) atomicAdd(n_valid_out, nv);
+  }
+}
+
+__global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                       const uint32_t* __restrict__ n_ptr, int shift,
+                                                       const uint32_t* __restrict__ hist_p, int drop_invalid,
+                                                       unsigned long long* status, FrameDev* fd, int slot) {
+  __shared__ uint32_t s_gbase[256];
+  __shared__ uint32_t s_whist[SORT_WARPS][256];
+  __shared__ uint32_t s_dstart[256];
+  __shared__ uint32_t s_gofs[256];
+  __shared__ uint32_t s_keys[SORT_TILE];
+  __shared__ uint32_t s_vals[SORT_TILE];
+  __shared__ uint32_t s_warp[SORT_NT / 32 + 1];
+  __shared__ uint32_t s_tile;
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  {
+    uint32_t tot;
+    s_gbase[tid] = block_exclusive_scan<SORT_NT>(hist_p[tid], s_warp, &tot);
+  }
+  const uint32_t n = *n_ptr;
+  const uint32_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+  const uint32_t epoch = fd->frame * 64u + (uint32_t)slot;
+  const uint32_t spin = fd->spin_limit;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&fd->ctr[slot], 1u);
+    for (int i = tid; i < SORT_WARPS * 256; i += SORT_NT) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= ntiles) break;
+    const uint32_t base = t * SORT_TILE + warp * 32u * SORT_IPT;
+    uint32_t key[SORT_IPT], val[SORT_IPT], rank[SORT_IPT];
+#pragma unroll
+    for (int i = 0; i < SORT_IPT; ++i) {
+      const uint32_t idx = base + (uint32_t)i * 32u + lane;
+      bool valid = idx < n;
+      uint32_t k = valid ? kin[idx] : INVALID_KEY;
+      if (drop_invalid && k == INVALID_KEY) valid = false;
+      key[i] = valid ? k : INVALID_KEY;
+      val[i] = valid ? (vin ? vin[idx] : idx) : 0u;
+      const uint32_t d = (k >> shift) & 0xFFu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x1000u);
+      uint32_t pre = 0;
+      if (valid) pre = s_whist[warp][d];
+      rank[i] = valid ? pre + (uint32_t)__popc(peers & lt_mask) : 0xFFFFFFFFu;
+      __syncwarp();
+      if (valid && (peers & lt_mask) == 0) s_whist[warp][d] = pre + (uint32_t)__popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: warp-exclusive offsets, tile total
+    uint32_t tot_d = 0;
+    {
+      const uint32_t d = tid;
+#pragma unroll
+      for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t c = s_whist[w][d];
+        s_whist[w][d] = tot_d;
+        tot_d += c;
+      }
+    }
+    uint32_t tile_total;
+    s_dstart[tid] = block_exclusive_scan<SORT_NT>(tot_d, s_warp, &tile_total);
+    {
+      const uint32_t d = tid;
+      unsigned long long* w = status + (size_t)t * 256 + d;
+      uint32_t pre = 0;
+      if (t == 0) {
+        st_relaxed_u64(w, lb_pack(epoch, 2u, tot_d));
+      } else {
+        st_relaxed_u64(w, lb_pack(epoch, 1u, tot_d));
+        pre = lb_exclusive(status + d, 256, t, epoch, spin, &fd->err);
+        st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot_d));
+      }
+      s_gofs[d] = s_gbase[d] + pre;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SORT_IPT; ++i) {
+      if (rank[i] == 0xFFFFFFFFu) continue;
+      const uint32_t d = (key[i] >> shift) & 0xFFu;
+      const uint32_t p = s_dstart[d] + s_whist[warp][d] + rank[i];
+      s_keys[p] = key[i];
+      s_vals[p] = val[i];
+    }
+    __syncthreads();
+    for (uint32_t p = tid; p < tile_total; p += SORT_NT) {
+      const uint32_t k = s_keys[p];
+      const uint32_t d = (k >> shift) & 0xFFu;
+      const uint32_t o = s_gofs[d] + (p - s_dstart[d]);
+      kout[o] = k;
+      vout[o] = s_vals[p];
+    }
+    __syncthreads();
+  }
+}
+
+// Sort n_in (from device memory) pairs on bits [0, bits).  drop_invalid:
+// keys equal to INVALID_KEY are removed (their count is not part of the
+// output; *n_valid_out receives the kept count).  Ping-pongs between
+// (k0, v0) and (k1, v1); *kout / *vout get the buffers holding the result.
+// Uses counter / epoch slots slot_base .. slot_base + passes - 1.
+void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                      uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
+                      int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
+                      uint32_t** vout) {
+  const int npass = (bits + 7) / 8;
+  cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * 4 * 256, s);
+  k_sort_hist<<<n_sm * 4, 256, 0, s>>>(kin, n_in, npass, drop_invalid, sb.hist, n_valid_out);
+  const uint32_t* ci = kin;
+  const uint32_t* cv = vin;
+  for (int p = 0; p < npass; ++p) {
+    uint32_t* ok = (p % 2 == 0) ? k0 : k1;
+    uint32_t* ov = (p % 2 == 0) ? v0 : v1;
+    const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
+    k_sort_pass<<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256, p == 0 ? drop_invalid : 0,
+                                             sb.status, fd, slot_base + p);
+    ci = ok;
+    cv = ov;
+  }
+  *kout = const_cast<uint32_t*>(ci);
+  *vout = const_cast<uint32_t*>(cv);
+}
+
+}  // namespace gsc

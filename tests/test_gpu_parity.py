@@ -1,0 +1,321 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work (visible sets, depth order, tile keys, sorted pairs, ranges) is
+compared bit for bit; float work against the oracle's float64 values:
+derived attributes <= 1e-5 relative (+1e-6 absolute), pixels <= 1e-3
+max-abs.  Pixels where an alpha/stop threshold decision lies within 1e-4
+(relative) of its threshold in the oracle can legitimately flip between
+float32 and float64; they are excluded from the max-abs check, counted, and
+must stay rare.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from conftest import axis_camera, single_gaussian_model
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-3
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_14938_b300 as pkg
+    pkg.lib()
+
+
+def make_renderer(model, cams, partners=None, flags=0, **kw):
+    import paper_2502_14938_b300 as pkg
+    r = pkg.Renderer(max_views=max(len(cams), 1), flags=flags, **kw)
+    mid = r.load_model(model)
+    partners = partners or [-1] * len(cams)
+    r.set_cameras([pkg.to_camera(c, partner=p, model_id=mid) for c, p in zip(cams, partners)])
+    return r
+
+
+def render(r, cams):
+    outs = [torch.zeros((c.height, c.width, 3), dtype=torch.float32, device="cuda") for c in cams]
+    st = r.render_frame(outs)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs], st
+
+
+def check_image(got, ref, margin, tag=""):
+    ok = margin >= MARGIN
+    err = np.abs(got.astype(np.float64) - ref)
+    e_ok = err[ok].max() if ok.any() else 0.0
+    frac = 1.0 - ok.mean()
+    assert e_ok <= PIX_TOL, f"{tag}: max-abs {e_ok:.3e} on decided pixels"
+    assert frac < 0.01, f"{tag}: {frac:.4f} of pixels near a threshold"
+    # near-threshold pixels still differ by at most one threshold-sized term
+    if (~ok).any():
+        assert err[~ok].max() < 0.05, f"{tag}: near-threshold pixel off by {err[~ok].max():.3e}"
+    return e_ok, frac
+
+
+def check_keygen_and_sort(r, cams, tile=16):
+    """Stage-isolated: the GPU's float32 records through the oracle's float32
+    coverage give the same per-record tile counts, and sorting the oracle's
+    pairs by (tile key, depth key, record) gives the GPU's sorted pairs."""
+    rec, dkey, cnt = r.debug_records()
+    view = (rec[:, 11].view(np.uint32) & 0xFFFF).astype(np.int32)
+    valid = (rec[:, 11].view(np.uint32) >> 31).astype(np.uint8)
+    ntiles = [((c.width + tile - 1) // tile) * ((c.height + tile - 1) // tile) for c in cams]
+    base = np.concatenate([[0], np.cumsum(ntiles)])
+    keys_all, vals_all = [], []
+    counts = np.zeros(len(rec), np.uint32)
+    for v, c in enumerate(cams):
+        sel = np.nonzero(view == v)[0]
+        cn, k, vv = oracle.keygen_f32(rec[sel, 0], rec[sel, 1], rec[sel, 2], rec[sel, 3], rec[sel, 4],
+                                      rec[sel, 6], np.zeros(len(sel)), valid[sel], c.width, c.height, tile, tile)
+        counts[sel] = cn
+        keys_all.append(k.astype(np.int64) + base[v])
+        vals_all.append(sel[vv])
+    assert np.array_equal(counts, cnt), "tile counts differ"
+    # depth order: records with tiles, stable by depth key
+    has = np.nonzero(cnt > 0)[0]
+    assert np.all(dkey[has] != 0xFFFFFFFF) and np.all(dkey[cnt == 0] == 0xFFFFFFFF)
+    exp_order = has[np.argsort(dkey[has], kind="stable")]
+    assert np.array_equal(r.debug_depth_order(), exp_order.astype(np.uint32))
+    keys = np.concatenate(keys_all)
+    vals = np.concatenate(vals_all).astype(np.int64)
+    o = np.lexsort((vals, dkey[vals], keys))
+    gk, gv = r.debug_pairs()
+    assert len(gk) == len(keys)
+    assert np.array_equal(gk, keys[o].astype(np.uint32))
+    assert np.array_equal(gv, vals[o].astype(np.uint32))
+    # ranges
+    rg = r.debug_ranges()
+    exp = np.zeros((base[-1], 2), np.uint32)
+    if len(gk):
+        starts = np.nonzero(np.r_[True, gk[1:] != gk[:-1]])[0]
+        ends = np.r_[starts[1:], len(gk)]
+        exp[gk[starts], 0] = starts
+        exp[gk[starts], 1] = ends
+    assert np.array_equal(rg, exp)
+    return len(gk)
+
+
+def check_attrs(got, ref, tag=""):
+    ref = ref.astype(np.float64)
+    err = np.abs(got.astype(np.float64) - ref)
+    bad = err > 1e-5 * np.abs(ref) + 1e-6
+    assert not bad.any(), f"{tag}: {bad.sum()} attrs off, worst {err.max():.3e}"
+
+
+# ------------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("o,sig_s,z0", [(0.5, 0.5, 10.0), (0.999, 0.7, 4.0), (0.05, 0.3, 25.0)])
+def test_single_gaussian_closed_form(o, sig_s, z0):
+    from scipy.special import expit
+    m = single_gaussian_model(o=o, sig_s=sig_s, z0=z0)
+    cam = axis_camera()
+    r = make_renderer(m, [cam])
+    (img,), st = render(r, [cam])
+    b2 = [b.astype(np.float64) for b in m.b2]
+    o_ = np.tanh(b2[0][0])
+    col = expit(b2[1][0:3])
+    s = float(m.scale[0]) * expit(b2[2][0])
+    sig2 = (cam.fx * s / z0) ** 2 + 0.3
+    xs = np.arange(cam.width) + 0.5 - cam.cx
+    ys = np.arange(cam.height) + 0.5 - cam.cy
+    r2 = xs[None, :] ** 2 + ys[:, None] ** 2
+    al = np.minimum(0.99, o_ * np.exp(-r2 / (2 * sig2)))
+    al = np.where(al >= 1 / 255, al, 0.0)
+    exp = al[..., None] * col[None, None, :]
+    near = np.abs(np.log(np.maximum(o_ * np.exp(-r2 / (2 * sig2)), 1e-300) * 255)) < MARGIN
+    err = np.abs(img - exp)[~near]
+    assert err.max() < 1e-5
+    assert st["valid_records"] == 1
+    r.close()
+
+
+# ------------------------------------------------------------------ tiny scene, every stage
+def test_tiny_scene_every_stage():
+    import paper_2502_14938_b300 as pkg
+    m, cam = gen.tiny_scene(), gen.tiny_camera()
+    r = make_renderer(m, [cam], flags=pkg.FLAG_DEBUG_ATTRS | pkg.FLAG_DEBUG_T)
+    (img,), st = render(r, [cam])
+    ids = oracle.cull(m, cam)
+    assert np.array_equal(r.debug_visible(0), ids)
+    attrs, kept = oracle.derive(m, oracle.camera_center(cam), ids)
+    check_attrs(r.debug_attrs(0), attrs, "tiny attrs")
+    n_pairs = check_keygen_and_sort(r, [cam])
+    assert n_pairs == st["pairs"] > 0
+    (ref, T, mg, nc), vr = oracle.render_view(m, cam)
+    check_image(img, ref, mg, "tiny")
+    Tg = r.debug_final_T(0).reshape(cam.height, cam.width)
+    assert np.all(Tg >= 1e-4 * (1 - 1e-6)) and np.all(Tg <= 1.0)
+    assert np.all(img.max(axis=-1) <= 1 - Tg + 1e-5)
+    assert np.abs(Tg - T)[mg >= MARGIN].max() < 1e-3
+    r.close()
+
+
+def test_big_gaussians_many_tiles():
+    """Large, elongated Gaussians near the camera that span many tiles and cross the border."""
+    m = gen.tiny_scene(seed=7, n=60)
+    m.offs *= 10
+    m.scale *= 30
+    cam = gen.tiny_camera(200, 150)
+    r = make_renderer(m, [cam])
+    (img,), st = render(r, [cam])
+    check_keygen_and_sort(r, [cam])
+    (ref, T, mg, nc), _ = oracle.render_view(m, cam)
+    check_image(img, ref, mg, "big")
+    r.close()
+
+
+def test_empty_view_is_background():
+    m = gen.tiny_scene()
+    cam = gen.tiny_camera()
+    cam.t = np.array([0, 0, -30.0], np.float32)  # scene behind the camera
+    r = make_renderer(m, [cam], bg=(0.25, 0.5, 0.75))
+    (img,), st = render(r, [cam])
+    assert st["visible_anchors"] == 0 and st["pairs"] == 0
+    assert np.array_equal(img, np.broadcast_to(np.array([0.25, 0.5, 0.75], np.float32), img.shape))
+    r.close()
+
+
+# ------------------------------------------------------------------ city scale
+@pytest.fixture(scope="module")
+def city():
+    return gen.city_workload()
+
+
+@pytest.mark.parametrize("frame", [0, 150, 299])
+def test_city_stereo_frame(city, frame):
+    import paper_2502_14938_b300 as pkg
+    model, frames = city
+    L, R = frames[frame]
+    r = make_renderer(model, [L, R], partners=[1, 0], flags=pkg.FLAG_DEBUG_ATTRS)
+    imgs, st = render(r, [L, R])
+    for v, cam in enumerate((L, R)):
+        ids = oracle.cull(model, cam)
+        assert np.array_equal(r.debug_visible(v), ids), f"eye {v} visible set"
+        attrs, _ = oracle.derive(model, oracle.camera_center(cam), ids)
+        check_attrs(r.debug_attrs(v), attrs, f"city eye {v}")
+    check_keygen_and_sort(r, [L, R])
+    rs = np.random.default_rng(frame)
+    for v, cam in enumerate((L, R)):
+        px = rs.integers(0, cam.width, 20000)
+        py = rs.integers(0, cam.height, 20000)
+        # plus one full tile at the image centre and the ragged bottom-right tile
+        tx, ty = np.meshgrid(np.arange(16), np.arange(16))
+        px = np.r_[px, 960 + tx.ravel(), (1920 - 16) + tx.ravel()]
+        py = np.r_[py, 528 + ty.ravel(), np.minimum(1072 + ty.ravel(), 1079)]
+        vr = oracle.view_gaussians(model, cam)
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        check_image(imgs[v][py, px], ref, mg, f"city f{frame} eye {v}")
+    r.close()
+
+
+def test_city_unified_stereo(city):
+    """Eq. 5-6 form: one derivation from the unified camera feeds both eyes."""
+    import paper_2502_14938_b300 as pkg
+    model, frames = city
+    L, R = frames[100]
+    r = make_renderer(model, [L, R], partners=[1, 0], flags=pkg.FLAG_DEBUG_ATTRS, stereo_unify=True)
+    imgs, st = render(r, [L, R])
+    nd, first = r.debug_dviews()
+    assert nd == 1 and first == [0]
+    U = oracle.unified_camera(L, R)
+    ids = oracle.cull(model, U)
+    assert np.array_equal(r.debug_visible(0), ids)
+    attrs, kept = oracle.derive(model, oracle.camera_center(U), ids)
+    check_attrs(r.debug_attrs(0), attrs, "unified attrs")
+    check_keygen_and_sort(r, [L, R])
+    rs = np.random.default_rng(5)
+    for v, cam in enumerate((L, R)):
+        px = rs.integers(0, cam.width, 20000)
+        py = rs.integers(0, cam.height, 20000)
+        vr = oracle.view_gaussians(model, cam, derive_cam=U)
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        check_image(imgs[v][py, px], ref, mg, f"unified eye {v}")
+    r.close()
+
+
+# ------------------------------------------------------------------ sort and scan kernels
+@pytest.mark.parametrize("n,bits", [(1, 8), (1000, 7), (4097, 14), (1_000_003, 32), (5_000_000, 17)])
+def test_radix_sort_matches_stable_argsort(n, bits):
+    import paper_2502_14938_b300 as pkg
+    r = pkg.Renderer(max_views=1)
+    rs = np.random.default_rng(n)
+    keys = rs.integers(0, 2 ** bits, n, dtype=np.uint64).astype(np.uint32)
+    if n > 10:
+        keys[: n // 10] = keys[0]  # many equal keys: stability matters
+    vals = np.arange(n, dtype=np.uint32)
+    k, v = r.debug_sort_pairs(keys, vals, bits)
+    o = np.argsort(keys, kind="stable")
+    assert np.array_equal(k, keys[o]) and np.array_equal(v, vals[o])
+    r.close()
+
+
+@pytest.mark.parametrize("n", [1, 4095, 4096, 4097, 3_000_001])
+def test_scan_matches_cumsum(n):
+    import paper_2502_14938_b300 as pkg
+    r = pkg.Renderer(max_views=1)
+    rs = np.random.default_rng(n)
+    vals = rs.integers(0, 40, n).astype(np.uint32)
+    out, tot = r.debug_scan(vals)
+    exp = np.concatenate([[0], np.cumsum(vals.astype(np.int64))[:-1]])
+    assert np.array_equal(out.astype(np.int64), exp)
+    assert tot == int(vals.astype(np.int64).sum())
+    r.close()
+
+
+# ------------------------------------------------------------------ launch modes and capacity
+def test_graph_eager_host_and_growth_agree():
+    m, cam = gen.tiny_scene(), gen.tiny_camera()
+    imgs = []
+    for kw in ({}, {"use_graph": False}, {"pair_capacity": 1000}):
+        r = make_renderer(m, [cam], **kw)
+        (img,), st = render(r, [cam])
+        (img2,), _ = render(r, [cam])  # replay
+        assert np.array_equal(img, img2)
+        imgs.append(img)
+        host = np.zeros((cam.height, cam.width, 3), np.float32)
+        r.render_frame_host([host])
+        assert np.array_equal(host, img)
+        r.close()
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
+
+
+def test_invalid_arguments_are_rejected():
+    import paper_2502_14938_b300 as pkg
+    m, cam = gen.tiny_scene(n=50), gen.tiny_camera()
+    r = pkg.Renderer(max_views=2)
+    outs = [torch.zeros((cam.height, cam.width, 3), device="cuda")]
+    with pytest.raises(pkg.GscError) as e:
+        r.render_frame(outs)
+    assert e.value.code == -6
+    bad = gen.tiny_scene(n=50)
+    bad.pos[3, 1] = np.nan
+    with pytest.raises(pkg.GscError) as e:
+        r.load_model(bad)
+    assert e.value.code == -1
+    mid = r.load_model(m)
+    with pytest.raises(pkg.GscError) as e:
+        r.set_cameras([pkg.to_camera(cam, partner=1, model_id=mid), pkg.to_camera(cam, partner=-1, model_id=mid)])
+    assert e.value.code == -1
+    with pytest.raises(pkg.GscError):
+        r.set_cameras([pkg.to_camera(cam, model_id=7)])
+    r.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device-side wait on a word nothing writes gives up after its poll
+    limit and reports GSC_ERR_TIMEOUT; the next frame renders normally."""
+    import paper_2502_14938_b300 as pkg
+    m, cam = gen.tiny_scene(n=300), gen.tiny_camera(64, 64)
+    r = make_renderer(m, [cam])
+    assert r.debug_wait_timeout(1000) == -5
+    (img,), st = render(r, [cam])
+    assert st["error_flags"] == 0
+    (ref, T, mg, nc), _ = oracle.render_view(m, cam)
+    check_image(img, ref, mg, "after timeout")
+    r.close()
