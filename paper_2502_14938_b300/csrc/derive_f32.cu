@@ -23,17 +23,21 @@ struct ProjCam {
   float t[3];
   float fx, fy, cx, cy;
   float znear, gx, gy;
+  float pc[3], pc_lo[3];
   int W, H;
   uint32_t rec_base;
   uint32_t cam;
 };
 
 // EWA projection of one Gaussian + opacity-aware exact tile count.
-// mu32 = x_a + o (float32 adds, the same rounding as the oracle's ordering
-// depth); depth tz = ((R6 mu_x + R7 mu_y) + R8 mu_z) + t2 without contraction.
-__device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3], float alpha,
-                                              bool kept, const float col[3], const float s[3], const float q[4],
-                                              int TW, int TH) {
+// Decisions use the pinned depth: mu32 = x_a + o (float32 adds) and
+// tz = ((R6 mu_x + R7 mu_y) + R8 mu_z) + t2 without contraction (the order
+// the oracle uses for its ordering depth).  The geometry uses camera-relative
+// coordinates rel = ((x_a - c_hi) - c_lo) + o, which avoid the cancellation of
+// R x + t at city scale.
+__device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3],
+                                              const float rel[3], float alpha, bool kept, const float col[3],
+                                              const float s[3], const float q[4], int TW, int TH) {
   const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mu[0]), __fmul_rn(c.R[7], mu[1])),
                                        __fmul_rn(c.R[8], mu[2])), c.t[2]);
   float4 geo = make_float4(0.f, 0.f, 0.f, 0.f), cop = make_float4(0.f, 0.f, 0.f, tz);
@@ -42,11 +46,12 @@ __device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uin
   float4 colv = make_float4(col[0], col[1], col[2], 0.f);
   bool valid = kept && (tz > c.znear) && (alpha >= (1.0f / 255.0f));
   if (valid) {
-    const float tx = c.R[0] * mu[0] + c.R[1] * mu[1] + c.R[2] * mu[2] + c.t[0];
-    const float ty = c.R[3] * mu[0] + c.R[4] * mu[1] + c.R[5] * mu[2] + c.t[1];
-    const float iz = 1.0f / tz;
-    const float txc = fminf(fmaxf(tx * iz, -c.gx), c.gx) * tz;
-    const float tyc = fminf(fmaxf(ty * iz, -c.gy), c.gy) * tz;
+    const float tx = c.R[0] * rel[0] + c.R[1] * rel[1] + c.R[2] * rel[2];
+    const float ty = c.R[3] * rel[0] + c.R[4] * rel[1] + c.R[5] * rel[2];
+    const float tza = c.R[6] * rel[0] + c.R[7] * rel[1] + c.R[8] * rel[2];
+    const float iz = 1.0f / tza;
+    const float txc = fminf(fmaxf(tx * iz, -c.gx), c.gx) * tza;
+    const float tyc = fminf(fmaxf(ty * iz, -c.gy), c.gy) * tza;
     const float j00 = c.fx * iz, j02 = -c.fx * txc * iz * iz;
     const float j11 = c.fy * iz, j12 = -c.fy * tyc * iz * iz;
     // T = J W (2x3)
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(DER_NT) k_derive_f32(const ModelDev* __restric
   __shared__ uint32_t s_b[MAXV + 1];
   __shared__ int s_nd;
   __shared__ ProjCam s_cam[MAXV][2];
-  __shared__ float s_pc[MAXV][3];
+  __shared__ float s_pc[MAXV][6];
 
   const ModelDev md = models[model];
   for (int i = threadIdx.x; i < W_FLOATS; i += DER_NT) s_w[i] = md.w32[i];
@@ -112,9 +117,10 @@ __global__ void __launch_bounds__(DER_NT) k_derive_f32(const ModelDev* __restric
       s_d[nd] = (int)d;
       s_b[nd] = acc;
       acc += fd->vis_count[d];
-      s_pc[nd][0] = fd->dcam[d].pc[0];
-      s_pc[nd][1] = fd->dcam[d].pc[1];
-      s_pc[nd][2] = fd->dcam[d].pc[2];
+      for (int u = 0; u < 3; ++u) {
+        s_pc[nd][u] = fd->dcam[d].pc[u];
+        s_pc[nd][3 + u] = fd->dcam[d].pc_lo[u];
+      }
       for (int e = 0; e < 2; ++e) {
         const int ci = fd->dview_cam[d][e];
         ProjCam& pc = s_cam[nd][e];
@@ -125,6 +131,10 @@ __global__ void __launch_bounds__(DER_NT) k_derive_f32(const ModelDev* __restric
         for (int i = 0; i < 3; ++i) pc.t[i] = c.t[i];
         pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
         pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
+        for (int i = 0; i < 3; ++i) {
+          pc.pc[i] = c.pc[i];
+          pc.pc_lo[i] = c.pc_lo[i];
+        }
         pc.W = c.W; pc.H = c.H;
         pc.rec_base = fd->rec_base[ci];
       }
@@ -145,8 +155,10 @@ __global__ void __launch_bounds__(DER_NT) k_derive_f32(const ModelDev* __restric
     const uint32_t i = item - s_b[ld];
     const uint32_t a = vis[d][i];
     const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
-    // view direction from the derivation camera
-    float vx = xa - s_pc[ld][0], vy = ya - s_pc[ld][1], vz = za - s_pc[ld][2];
+    // view direction from the derivation camera's double-float centre
+    float vx = (xa - s_pc[ld][0]) - s_pc[ld][3];
+    float vy = (ya - s_pc[ld][1]) - s_pc[ld][4];
+    float vz = (za - s_pc[ld][2]) - s_pc[ld][5];
     const float vn = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
     vx *= vn; vy *= vn; vz *= vn;
     // ---- layer 1 (three heads concatenated): h = ReLU(W1cat^T x + b1cat)
@@ -236,14 +248,17 @@ __global__ void __launch_bounds__(DER_NT) k_derive_f32(const ModelDev* __restric
         o[7] = q[0]; o[8] = q[1]; o[9] = q[2]; o[10] = q[3];
       }
       const float* op = md.offs + ((size_t)a * K + j) * 3;
-      const float mu[3] = {__fadd_rn(xa, __ldg(op)), __fadd_rn(ya, __ldg(op + 1)), __fadd_rn(za, __ldg(op + 2))};
+      const float o3[3] = {__ldg(op), __ldg(op + 1), __ldg(op + 2)};
+      const float mu[3] = {__fadd_rn(xa, o3[0]), __fadd_rn(ya, o3[1]), __fadd_rn(za, o3[2])};
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const ProjCam& pc = s_cam[ld][e];
         if (pc.cam == 0xFFFFFFFFu) continue;
         const uint32_t r = pc.rec_base + i * K + (uint32_t)j;
         if (r >= rec_cap) continue;
-        project_write(pc, rec, r, mu, alpha, kept, col, s, q, TW, TH);
+        const float rel[3] = {((xa - pc.pc[0]) - pc.pc_lo[0]) + o3[0], ((ya - pc.pc[1]) - pc.pc_lo[1]) + o3[1],
+                              ((za - pc.pc[2]) - pc.pc_lo[2]) + o3[2]};
+        project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
       }
     }
   }

@@ -22,7 +22,10 @@ __device__ void fill_camdev(CamDev& c, const CamIn& in, const FrameIn& fin) {
   c.model = (int)in.model;
   double p[3];
   center64(c.R, c.t, p);
-  for (int i = 0; i < 3; ++i) c.pc[i] = __double2float_rn(p[i]);
+  for (int i = 0; i < 3; ++i) {
+    c.pc[i] = __double2float_rn(p[i]);
+    c.pc_lo[i] = __double2float_rn(p[i] - (double)c.pc[i]);
+  }
   c.gx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.W), c.fx));
   c.gy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.H), c.fy));
   c.ntx = (c.W + (int)fin.tile_w - 1) / (int)fin.tile_w;

@@ -60,6 +60,7 @@ struct CamDev {  // camera with derived constants (computed on device)
   int32_t W, H;
   float znear;
   float pc[3];     // centre -R^T t (float64 then rounded)
+  float pc_lo[3];  // float64 centre - pc: (pc, pc_lo) is a double-float centre
   float gx, gy;    // 1.3 * (0.5 W / fx), 1.3 * (0.5 H / fy) in float32
   int32_t ntx, nty;
   uint32_t tile_base;
