@@ -158,12 +158,31 @@ def set_pair(r, mid, L, R):
     r.set_cameras([pkg.to_camera(L, partner=1, model_id=mid), pkg.to_camera(R, partner=0, model_id=mid)])
 
 
+def run_profile(args):
+    """Minimal run for profilers: W + K frames from --frame, no extras.
+    Per frame: 16 library kernels (frame setup, cull, plan, derive, depth
+    sort histogram + 4 passes, scan, keygen, tile sort histogram + 2 passes,
+    ranges, blend) and one torch fill between frames."""
+    import torch
+    model, frames, _ = build_workload()
+    W, H = frames[0][0].width, frames[0][0].height
+    r, mid = make_renderer(model, args.form)
+    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    for s in range(args.warmup + args.steps):
+        set_pair(r, mid, *frames[(args.frame + s) % len(frames)])
+        st = r.render_frame(outs)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": True, "frames": args.warmup + args.steps, "last": st}), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2502_14938_b300 as pkg
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    if args.profile:
+        return run_profile(args)
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     r, mid = make_renderer(model, args.form)
@@ -301,6 +320,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="plain", choices=["plain", "unified"])
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 299])
+    ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
+    ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))

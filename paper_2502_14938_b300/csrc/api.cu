@@ -39,6 +39,7 @@ struct Counters {  // tail of FrameDev read back after a frame
   uint32_t rec_base[MAXV + 1];
   uint32_t n_items, n_records;
   uint32_t n_valid, n_pairs, n_pairs_used, err;
+  uint32_t n_records_need;
 };
 
 }  // namespace
@@ -311,10 +312,11 @@ int finish_frame(gsc_ctx* ctx) {
   const Counters& c = *ctx->h_cnt;
   if (c.err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (c.err & ERR_REC_OVERFLOW) {
-    // grow to the worst case of the current cameras (every anchor visible)
-    unsigned long long need = 0;
-    for (const auto& cam : ctx->cams) need += (unsigned long long)K * ctx->models[cam.model_id].n;
-    need = std::min<unsigned long long>(need, 0x3FFFFFFFull);
+    // grow to the frame's requirement plus headroom, at most the worst case
+    unsigned long long worst = 0;
+    for (const auto& cam : ctx->cams) worst += (unsigned long long)K * ctx->models[cam.model_id].n;
+    unsigned long long need = (unsigned long long)c.n_records_need + c.n_records_need / 2 + 1024;
+    need = std::min<unsigned long long>(std::min(need, worst), 0x3FFFFFFFull);
     int r = alloc_records(ctx, (uint32_t)need);
     if (r) return r;
     return fail(ctx, GSC_ERR_CAPACITY, "record buffer grown to %u", ctx->rec_cap);
@@ -616,7 +618,7 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
   // records: worst case (every anchor visible), capped at 64M then grown on demand
   unsigned long long worst = 0;
   for (const auto& c : ctx->cams) worst += (unsigned long long)K * ctx->models[c.model_id].n;
-  const uint32_t want = (uint32_t)std::min<unsigned long long>(std::max<unsigned long long>(worst, 1024ull), 64ull << 20);
+  const uint32_t want = (uint32_t)std::min<unsigned long long>(std::max<unsigned long long>(worst, 1024ull), 8ull << 20);
   if (want > ctx->rec_cap) {
     if ((r = alloc_records(ctx, want))) return r;
   }

@@ -314,6 +314,7 @@ __global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {
     r += (unsigned long long)K * fd->vis_count[fd->dview_of_cam[c]];
   }
   fd->rec_base[fd->n_cams] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+  fd->n_records_need = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
   if (r > rec_cap) {
     atomicOr(&fd->err, ERR_REC_OVERFLOW);
     fd->n_records = rec_cap;

@@ -99,6 +99,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t n_pairs;             // pairs requested (may exceed capacity)
   uint32_t n_pairs_used;        // min(n_pairs, capacity)
   uint32_t err;
+  uint32_t n_records_need;      // records the frame asked for (may exceed capacity)
   uint32_t ctr[32];             // dynamic tile counters of look-back kernels
 };
 
