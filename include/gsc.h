@@ -179,6 +179,37 @@ GSC_API void gsc_destroy(gsc_ctx* ctx);
 
 GSC_API int gsc_version(void);
 
+/* Largest n accepted by gsc_scan_u32_noalloc. */
+#define GSC_NOALLOC_SCAN_MAX_N (1u << 24)
+
+/* Exclusive prefix sum of n uint32 values for callers that cannot allocate
+ * device memory: a frame loop under a real-time budget (an allocation can
+ * synchronise the device and stall the frame) or a host application whose
+ * pool owns every device allocation and that hands plug-ins only the
+ * buffers they work on.  The paper has no counterpart to this call; it is a
+ * service of the library, built on the same decoupled look-back scan the
+ * renderer uses for its pair offsets.
+ *   d_in    device pointer, n uint32 values (read only)
+ *   d_out   device pointer, n uint32 results: d_out[i] = sum of d_in[0..i-1];
+ *           may equal d_in (in place)
+ *   n       0 .. GSC_NOALLOC_SCAN_MAX_N (16,777,216); larger n returns
+ *           GSC_ERR_INVALID_ARG before any work is enqueued
+ *   d_total device pointer to one uint32 receiving the sum, or NULL
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * The call allocates nothing: its working memory is a fixed 32,800-byte
+ * device array inside the library, present on every GPU that loads the
+ * library until the process exits.  The first call on a device looks that
+ * array's address up (cudaGetSymbolAddress, with the device current); make
+ * that first call before any stream capture.  Calls whose work overlaps on
+ * the GPU (other threads or streams) share the array and race: serialise
+ * them.  The call is synchronous: it returns after the scan has finished on
+ * the stream.  Returns GSC_OK; GSC_ERR_INVALID_ARG for bad pointers or n, or
+ * when the sum of the inputs reaches 2^30 (the results are then not valid);
+ * GSC_ERR_TIMEOUT if a bounded device-side wait gave up; GSC_ERR_CUDA if a
+ * CUDA call failed. */
+GSC_API int gsc_scan_u32_noalloc(const uint32_t* d_in, uint32_t* d_out, uint64_t n, uint32_t* d_total,
+                                 void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

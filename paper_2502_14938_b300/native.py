@@ -104,6 +104,7 @@ def lib():
             "gsc_debug_sort_pairs": (I, [P, P, P, U64, U32]),
             "gsc_debug_scan": (I, [P, P, U64, P]),
             "gsc_debug_wait_timeout": (I, [P, U32]),
+            "gsc_scan_u32_noalloc": (I, [P, P, U64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -130,6 +131,18 @@ def _p(a) -> C.c_void_p:
     if isinstance(a, np.ndarray):
         return a.ctypes.data_as(C.c_void_p)
     return C.c_void_p(int(a))
+
+
+def scan_u32_noalloc(d_in: int, d_out: int, n: int, d_total: int = 0, stream: int = 0) -> None:
+    """gsc_scan_u32_noalloc on caller-owned device buffers (pointers as ints).
+
+    For callers that cannot allocate device memory where they scan; the
+    library uses a fixed internal device array as working memory.  Raises
+    GscError on a non-zero status."""
+    rc = lib().gsc_scan_u32_noalloc(C.c_void_p(d_in or None), C.c_void_p(d_out or None), int(n),
+                                    C.c_void_p(d_total or None), C.c_void_p(stream or None))
+    if rc != GSC_OK:
+        raise GscError(rc, "gsc_scan_u32_noalloc failed")
 
 
 def default_config() -> Config:
