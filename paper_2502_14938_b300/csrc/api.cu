@@ -40,6 +40,7 @@ struct Counters {  // tail of FrameDev read back after a frame
   uint32_t n_items, n_records;
   uint32_t n_valid, n_pairs, n_pairs_used, err;
   uint32_t n_records_need;
+  uint32_t n_big;
 };
 
 }  // namespace
@@ -71,7 +72,7 @@ struct gsc_ctx {
   float** d_dbg_tab = nullptr;
   uint32_t rec_cap = 0;
   Records rec{};
-  uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr;
+  uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr, *big = nullptr;
   uint32_t pair_cap = 0;
   uint32_t *pk0 = nullptr, *pv0 = nullptr, *pk1 = nullptr, *pv1 = nullptr;
   uint32_t ranges_cap = 0;
@@ -165,7 +166,8 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  const uint32_t need = std::max((ctx->rec_cap + 4095u) / 4096u, (ctx->pair_cap + 4095u) / 4096u) + 1u;
+  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096
+  const uint32_t need = std::max((ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 4095u) / 4096u) + 1u;
   if (need > ctx->status_tiles) {
     int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
     if (r) return r;
@@ -191,7 +193,7 @@ int alloc_records(gsc_ctx* ctx, uint32_t cap) {
       (r = dalloc(ctx, &ctx->rec.col, cap)) || (r = dalloc(ctx, &ctx->rec.key, cap)) ||
       (r = dalloc(ctx, &ctx->rec.cnt, cap)) || (r = dalloc(ctx, &ctx->s1k0, cap)) ||
       (r = dalloc(ctx, &ctx->s1v0, cap)) || (r = dalloc(ctx, &ctx->s1k1, cap)) ||
-      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)))
+      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)))
     return r;
   ctx->rec_cap = cap;
   invalidate_graph(ctx);
@@ -224,15 +226,15 @@ void enqueue_sequence(gsc_ctx* ctx) {
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
-                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov);
+                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov, 8);
   ctx->order_out = ov;
   if (tm) cudaEventRecord(ctx->ev_stage[3], s);
   launch_scan_u32(ctx->rec.cnt, ov, &fd->n_valid, ctx->offs, &fd->n_pairs, ctx->st_scan, fd, SLOT_SCAN, ctx->n_sm, s);
-  launch_keygen(fd, ctx->rec, ov, ctx->offs, ctx->pk0, ctx->pv0, ctx->pair_cap, ctx->n_sm, s);
+  launch_keygen(fd, ctx->rec, ov, ctx->offs, ctx->pk0, ctx->pv0, ctx->pair_cap, ctx->big, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[4], s);
   uint32_t *pk = nullptr, *pv = nullptr;
   launch_sort_impl(ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->pk0, ctx->pv0, &fd->n_pairs_used, nullptr,
-                   (int)ctx->tile_bits, 0, SLOT_SORT2, fd, ctx->sb, ctx->n_sm, s, &pk, &pv);
+                   (int)ctx->tile_bits, 0, SLOT_SORT2, fd, ctx->sb, ctx->n_sm, s, &pk, &pv, 16);
   ctx->pkeys_out = pk;
   ctx->pvals_out = pv;
   if (tm) cudaEventRecord(ctx->ev_stage[5], s);
@@ -410,6 +412,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   const uint32_t nt = cfg.tile_w * cfg.tile_h;
   if (nt == 0 || nt > 256 || nt % 32 != 0) return GSC_ERR_INVALID_ARG;
+  if (cfg.tile_w % 8 != 0 || cfg.tile_h % 4 != 0) return GSC_ERR_INVALID_ARG;  // 8x4 pixel block per warp
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
   if (cfg.precision != GSC_PREC_FP32 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
@@ -424,6 +427,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
     return code;
   };
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (prepare_derive_f32() != cudaSuccess) return bail(GSC_ERR_CUDA);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -458,7 +462,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   }
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
-                  ctx->s1v1, ctx->offs, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
+                  ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < MAXV; ++i) {
@@ -828,7 +832,7 @@ int gsc_debug_sort_pairs(gsc_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t 
   launch_bump_epoch(ctx->d_fd, ctx->spin_limit, ctx->stream);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->pk0, ctx->pv0, d_n, nullptr, (int)bits, 0, SLOT_SORT2,
-                   ctx->d_fd, ctx->sb, ctx->n_sm, ctx->stream, &ok, &ov);
+                   ctx->d_fd, ctx->sb, ctx->n_sm, ctx->stream, &ok, &ov, 16);
   CK(cudaStreamSynchronize(ctx->stream));
   uint32_t err = 0;
   CK(cudaMemcpy(&err, &ctx->d_fd->err, 4, cudaMemcpyDeviceToHost));

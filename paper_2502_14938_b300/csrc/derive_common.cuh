@@ -1,0 +1,175 @@
+// Pieces shared by the derivation kernels (float32 CUDA-core and tcgen05
+// tensor-core): the per-block list of derivation views, the activation
+// epilogue of Eq. 3 and the EWA projection + exact tile count (Eq. 1-2,
+// Sec. 6) that turns one derived Gaussian into one record per camera.
+#pragma once
+#include "gsc_internal.cuh"
+
+namespace gsc {
+
+struct ProjCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float znear, gx, gy;
+  float pc[3], pc_lo[3];
+  int W, H;
+  uint32_t rec_base;
+  uint32_t cam;
+};
+
+// Derivation views of one model, staged in shared memory by one thread.
+struct DViewSet {
+  int nd;
+  int d[MAXV];
+  uint32_t base[MAXV + 1];  // prefix of visible counts over the listed views
+  float pc[MAXV][6];        // double-float centre of each derivation camera
+  ProjCam cam[MAXV][2];     // cameras fed by each view (cam = 0xFFFFFFFF unused)
+};
+
+__device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd, int model) {
+  int nd = 0;
+  uint32_t acc = 0;
+  for (uint32_t d = 0; d < fd->n_dviews; ++d) {
+    if (fd->dcam[d].model != model) continue;
+    S.d[nd] = (int)d;
+    S.base[nd] = acc;
+    acc += fd->vis_count[d];
+    for (int u = 0; u < 3; ++u) {
+      S.pc[nd][u] = fd->dcam[d].pc[u];
+      S.pc[nd][3 + u] = fd->dcam[d].pc_lo[u];
+    }
+    for (int e = 0; e < 2; ++e) {
+      const int ci = fd->dview_cam[d][e];
+      ProjCam& pc = S.cam[nd][e];
+      pc.cam = ci < 0 ? 0xFFFFFFFFu : (uint32_t)ci;
+      if (ci < 0) continue;
+      const CamDev& c = fd->cam[ci];
+      for (int i = 0; i < 9; ++i) pc.R[i] = c.R[i];
+      for (int i = 0; i < 3; ++i) {
+        pc.t[i] = c.t[i];
+        pc.pc[i] = c.pc[i];
+        pc.pc_lo[i] = c.pc_lo[i];
+      }
+      pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
+      pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
+      pc.W = c.W; pc.H = c.H;
+      pc.rec_base = fd->rec_base[ci];
+    }
+    ++nd;
+  }
+  S.base[nd] = acc;
+  S.nd = nd;
+}
+
+// EWA projection of one Gaussian + opacity-aware exact tile count.
+// Decisions use the pinned depth: mu32 = x_a + o (float32 adds) and
+// tz = ((R6 mu_x + R7 mu_y) + R8 mu_z) + t2 without contraction (the order
+// the oracle uses for its ordering depth).  The geometry uses camera-relative
+// coordinates rel = ((x_a - c_hi) - c_lo) + o, which avoid the cancellation of
+// R x + t at city scale.
+__device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3],
+                                              const float rel[3], float alpha, bool kept, const float col[3],
+                                              const float s[3], const float q[4], int TW, int TH) {
+  const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mu[0]), __fmul_rn(c.R[7], mu[1])),
+                                       __fmul_rn(c.R[8], mu[2])), c.t[2]);
+  float4 geo = make_float4(0.f, 0.f, 0.f, 0.f), cop = make_float4(0.f, 0.f, 0.f, tz);
+  uint32_t flag = c.cam;
+  uint32_t cnt = 0;
+  float4 colv = make_float4(col[0], col[1], col[2], 0.f);
+  const bool valid = kept && (tz > c.znear) && (alpha >= (1.0f / 255.0f));
+  if (valid) {
+    const float tx = c.R[0] * rel[0] + c.R[1] * rel[1] + c.R[2] * rel[2];
+    const float ty = c.R[3] * rel[0] + c.R[4] * rel[1] + c.R[5] * rel[2];
+    const float tza = c.R[6] * rel[0] + c.R[7] * rel[1] + c.R[8] * rel[2];
+    const float iz = 1.0f / tza;
+    const float txc = fminf(fmaxf(tx * iz, -c.gx), c.gx) * tza;
+    const float tyc = fminf(fmaxf(ty * iz, -c.gy), c.gy) * tza;
+    const float j00 = c.fx * iz, j02 = -c.fx * txc * iz * iz;
+    const float j11 = c.fy * iz, j12 = -c.fy * tyc * iz * iz;
+    float T0[3], T1[3];  // T = J W (2x3)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = j00 * c.R[k] + j02 * c.R[6 + k];
+      T1[k] = j11 * c.R[3 + k] + j12 * c.R[6 + k];
+    }
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    const float Rq[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    float U0[3], U1[3];  // U = T R(q) diag(s); Sigma' = U U^T + 0.3 I
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float m0 = Rq[k] * s[k], m1 = Rq[3 + k] * s[k], m2 = Rq[6 + k] * s[k];
+      U0[k] = T0[0] * m0 + T0[1] * m1 + T0[2] * m2;
+      U1[k] = T1[0] * m0 + T1[1] * m1 + T1[2] * m2;
+    }
+    const float a = U0[0] * U0[0] + U0[1] * U0[1] + U0[2] * U0[2] + 0.3f;
+    const float b = U0[0] * U1[0] + U0[1] * U1[1] + U0[2] * U1[2];
+    const float cc = U1[0] * U1[0] + U1[1] * U1[1] + U1[2] * U1[2] + 0.3f;
+    const float det = a * cc - b * b;
+    if (det > 0.f) {
+      const float id = 1.0f / det;
+      const float A = cc * id, B = -b * id, C = a * id;
+      const float mx = c.fx * tx * iz + c.cx, my = c.fy * ty * iz + c.cy;
+      const float tau = 2.0f * logf(255.0f * alpha);
+      const float tauc = tau * (1.0f + 0.0009765625f) + 0.0009765625f;
+      geo = make_float4(mx, my, A, B);
+      cop = make_float4(C, alpha, tauc, tz);
+      cnt = cover_count_f32(mx, my, A, B, C, tauc, c.W, c.H, TW, TH);
+      flag |= REC_VALID_BIT;
+    }
+  }
+  colv.w = __uint_as_float(flag);
+  rec.geo[r] = geo;
+  rec.cop[r] = cop;
+  rec.col[r] = colv;
+  rec.key[r] = cnt > 0 ? __float_as_uint(tz) : INVALID_KEY;
+  rec.cnt[r] = cnt;
+}
+
+// Activations of Eq. 3 for Gaussian j of one anchor from its 11 head
+// outputs z = [op_j, col_3j..3j+2, cov_7j..7j+6], then one record per camera
+// the derivation view feeds.  sa: anchor scale; (xa, ya, za): anchor
+// position; offs: the anchor's [K][3] offsets.
+__device__ __forceinline__ void gaussian_epilogue(const float z[11], int j, uint32_t i, float sa, float xa, float ya,
+                                                  float za, const float* __restrict__ offs, const ProjCam* cams,
+                                                  Records rec, uint32_t rec_cap, float* dbg, int TW, int TH) {
+  const float alpha = tanhf(z[0]);
+  const bool kept = z[0] > 0.f;
+  float col[3], s[3], q[4];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) col[u] = 1.0f / (1.0f + expf(-z[1 + u]));
+#pragma unroll
+  for (int u = 0; u < 3; ++u) s[u] = sa * (1.0f / (1.0f + expf(-z[4 + u])));
+  const float qn2 = z[7] * z[7] + z[8] * z[8] + z[9] * z[9] + z[10] * z[10];
+  if (qn2 < 1e-24f) {
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+  } else {
+    const float iq = 1.0f / sqrtf(qn2);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = z[7 + u] * iq;
+  }
+  if (dbg) {
+    float* o = dbg + ((size_t)i * K + j) * 11;
+    o[0] = alpha;
+    o[1] = col[0]; o[2] = col[1]; o[3] = col[2];
+    o[4] = s[0]; o[5] = s[1]; o[6] = s[2];
+    o[7] = q[0]; o[8] = q[1]; o[9] = q[2]; o[10] = q[3];
+  }
+  const float* op = offs + j * 3;
+  const float o3[3] = {__ldg(op), __ldg(op + 1), __ldg(op + 2)};
+  const float mu[3] = {__fadd_rn(xa, o3[0]), __fadd_rn(ya, o3[1]), __fadd_rn(za, o3[2])};
+#pragma unroll 1
+  for (int e = 0; e < 2; ++e) {
+    const ProjCam& pc = cams[e];
+    if (pc.cam == 0xFFFFFFFFu) continue;
+    const uint32_t r = pc.rec_base + i * K + (uint32_t)j;
+    if (r >= rec_cap) continue;
+    const float rel[3] = {((xa - pc.pc[0]) - pc.pc_lo[0]) + o3[0], ((ya - pc.pc[1]) - pc.pc_lo[1]) + o3[1],
+                          ((za - pc.pc[2]) - pc.pc_lo[2]) + o3[2]};
+    project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
+  }
+}
+
+}  // namespace gsc

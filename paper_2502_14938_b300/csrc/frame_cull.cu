@@ -121,6 +121,7 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin) {
   fd->n_valid = 0;
   fd->n_pairs = 0;
   fd->n_pairs_used = 0;
+  fd->n_big = 0;
   fd->err = 0;
   for (int i = 0; i < 32; ++i) fd->ctr[i] = 0;
 }

@@ -100,6 +100,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t n_pairs_used;        // min(n_pairs, capacity)
   uint32_t err;
   uint32_t n_records_need;      // records the frame asked for (may exceed capacity)
+  uint32_t n_big;               // records in the key generation's large-record list
   uint32_t ctr[32];             // dynamic tile counters of look-back kernels
 };
 
@@ -210,39 +211,81 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 //   Dy* = -B sqrt(tau / (C det)),  x(Dy) = (-B Dy +- sqrt(A tau - det Dy^2)) / A.
 // Every operation is a correctly rounded float32 op (no contraction), so the
 // count pass and the emit pass agree exactly.  f(tile) is called per tile.
+struct Cover {
+  float mx, my, A, B, tau, det, ey, ys, fTW;
+  int ntx, ty0, ty1;
+};
+
+// Rows [ty0, ty1] of tiles the ellipse can touch; false if it covers nothing.
+__device__ __forceinline__ bool cover_setup(Cover& cv, float mx, float my, float A, float B, float C, float tau,
+                                            int W, int H, int TW, int TH) {
+  const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
+  if (!(tau > 0.f) || !(det > 0.f) || !(A > 0.f) || !(C > 0.f)) return false;
+  const int nty = (H + TH - 1) / TH;
+  cv.ntx = (W + TW - 1) / TW;
+  cv.mx = mx; cv.my = my; cv.A = A; cv.B = B; cv.tau = tau; cv.det = det;
+  cv.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, A), det));
+  cv.ys = __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau, __fmul_rn(C, det))));
+  cv.fTW = (float)TW;
+  const float fTH = (float)TH;
+  float fy0 = ceilf(__fdiv_rn(__fsub_rn(__fsub_rn(my, cv.ey), __fsub_rn(fTH, 0.5f)), fTH));
+  float fy1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(my, cv.ey), 0.5f), fTH));
+  fy0 = fminf(fmaxf(fy0, 0.f), (float)nty);
+  fy1 = fminf(fmaxf(fy1, -1.f), (float)(nty - 1));
+  cv.ty0 = (int)fy0;
+  cv.ty1 = (int)fy1;
+  return cv.ty0 <= cv.ty1;
+}
+
+// Column range [tx0, tx1] of tile row ty (empty when tx0 > tx1).
+__device__ __forceinline__ void cover_row(const Cover& cv, int ty, int TH, int& tx0, int& tx1) {
+  float b0 = __fsub_rn(__fadd_rn((float)(ty * TH), 0.5f), cv.my);
+  float b1 = __fsub_rn(__fsub_rn((float)(ty * TH + TH), 0.5f), cv.my);
+  b0 = fmaxf(b0, -cv.ey);
+  b1 = fminf(b1, cv.ey);
+  if (b0 > b1) {
+    tx0 = 1;
+    tx1 = 0;
+    return;
+  }
+  const float yr = fminf(fmaxf(cv.ys, b0), b1);
+  const float yl = fminf(fmaxf(-cv.ys, b0), b1);
+  const float dr = __fsub_rn(__fmul_rn(cv.A, cv.tau), __fmul_rn(cv.det, __fmul_rn(yr, yr)));
+  const float dl = __fsub_rn(__fmul_rn(cv.A, cv.tau), __fmul_rn(cv.det, __fmul_rn(yl, yl)));
+  const float xr = __fdiv_rn(__fadd_rn(__fmul_rn(-cv.B, yr), __fsqrt_rn(fmaxf(dr, 0.f))), cv.A);
+  const float xl = __fdiv_rn(__fsub_rn(__fmul_rn(-cv.B, yl), __fsqrt_rn(fmaxf(dl, 0.f))), cv.A);
+  float fx0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(cv.mx, xl), __fsub_rn(cv.fTW, 0.5f)), cv.fTW));
+  float fx1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(cv.mx, xr), 0.5f), cv.fTW));
+  fx0 = fminf(fmaxf(fx0, 0.f), (float)cv.ntx);
+  fx1 = fminf(fmaxf(fx1, -1.f), (float)(cv.ntx - 1));
+  tx0 = (int)fx0;
+  tx1 = (int)fx1;
+}
+
 template <typename Fn>
 __device__ __forceinline__ void cover_tiles_f32(float mx, float my, float A, float B, float C, float tau,
                                                 int W, int H, int TW, int TH, Fn f) {
-  const float det = __fsub_rn(__fmul_rn(A, C), __fmul_rn(B, B));
-  if (!(tau > 0.f) || !(det > 0.f) || !(A > 0.f) || !(C > 0.f)) return;
-  const int ntx = (W + TW - 1) / TW, nty = (H + TH - 1) / TH;
-  const float ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, A), det));
-  const float ys = __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau, __fmul_rn(C, det))));
-  const float fTW = (float)TW, fTH = (float)TH;
-  float fy0 = ceilf(__fdiv_rn(__fsub_rn(__fsub_rn(my, ey), __fsub_rn(fTH, 0.5f)), fTH));
-  float fy1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(my, ey), 0.5f), fTH));
-  fy0 = fminf(fmaxf(fy0, 0.f), (float)nty);
-  fy1 = fminf(fmaxf(fy1, -1.f), (float)(nty - 1));
-  const int ty0 = (int)fy0, ty1 = (int)fy1;
-  for (int ty = ty0; ty <= ty1; ++ty) {
-    float b0 = __fsub_rn(__fadd_rn((float)(ty * TH), 0.5f), my);
-    float b1 = __fsub_rn(__fsub_rn((float)(ty * TH + TH), 0.5f), my);
-    b0 = fmaxf(b0, -ey);
-    b1 = fminf(b1, ey);
-    if (b0 > b1) continue;
-    const float yr = fminf(fmaxf(ys, b0), b1);
-    const float yl = fminf(fmaxf(-ys, b0), b1);
-    const float dr = __fsub_rn(__fmul_rn(A, tau), __fmul_rn(det, __fmul_rn(yr, yr)));
-    const float dl = __fsub_rn(__fmul_rn(A, tau), __fmul_rn(det, __fmul_rn(yl, yl)));
-    const float xr = __fdiv_rn(__fadd_rn(__fmul_rn(-B, yr), __fsqrt_rn(fmaxf(dr, 0.f))), A);
-    const float xl = __fdiv_rn(__fsub_rn(__fmul_rn(-B, yl), __fsqrt_rn(fmaxf(dl, 0.f))), A);
-    float fx0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(mx, xl), __fsub_rn(fTW, 0.5f)), fTW));
-    float fx1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(mx, xr), 0.5f), fTW));
-    fx0 = fminf(fmaxf(fx0, 0.f), (float)ntx);
-    fx1 = fminf(fmaxf(fx1, -1.f), (float)(ntx - 1));
-    const int tx0 = (int)fx0, tx1 = (int)fx1;
-    for (int tx = tx0; tx <= tx1; ++tx) f(ty * ntx + tx);
+  Cover cv;
+  if (!cover_setup(cv, mx, my, A, B, C, tau, W, H, TW, TH)) return;
+  for (int ty = cv.ty0; ty <= cv.ty1; ++ty) {
+    int tx0, tx1;
+    cover_row(cv, ty, TH, tx0, tx1);
+    for (int tx = tx0; tx <= tx1; ++tx) f(ty * cv.ntx + tx);
   }
+}
+
+// Number of covered tiles (same arithmetic as cover_tiles_f32).
+__device__ __forceinline__ uint32_t cover_count_f32(float mx, float my, float A, float B, float C, float tau, int W,
+                                                    int H, int TW, int TH) {
+  Cover cv;
+  if (!cover_setup(cv, mx, my, A, B, C, tau, W, H, TW, TH)) return 0;
+  uint32_t n = 0;
+  for (int ty = cv.ty0; ty <= cv.ty1; ++ty) {
+    int tx0, tx1;
+    cover_row(cv, ty, TH, tx0, tx1);
+    if (tx1 >= tx0) n += (uint32_t)(tx1 - tx0 + 1);
+  }
+  return n;
 }
 
 // ----------------------------------------------------------------- launchers (host)
@@ -260,17 +303,18 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
 void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
                  unsigned long long* status, int n_sm, cudaStream_t s);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
+cudaError_t prepare_derive_f32();
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, Records rec,
                        float* const* dbg_attrs, int n_sm, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
-                      uint32_t** vout);
+                      uint32_t** vout, int ipt);
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
                      cudaStream_t s);
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
-                   uint32_t* pvals, uint32_t cap, int n_sm, cudaStream_t s);
+                   uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
                   uint32_t total_tiles, uint32_t tile_threads, cudaStream_t s);

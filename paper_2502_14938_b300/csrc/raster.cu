@@ -80,9 +80,18 @@ void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t*
 // For the i-th record in depth order, emit (tile_base(camera) + tile, record)
 // at offs[i] .. offs[i] + cnt - 1, tiles in row-major order of the exact
 // coverage.  Pairs beyond the capacity are not written and flag an overflow.
+// A record covering at most KG_SMALL tiles is emitted by its own thread.
+// Larger ones (near-camera Gaussians, up to thousands of tiles) cluster at
+// the front of the depth order, so they go to a work list that a second
+// kernel spreads over all warps, one record per warp: lane l computes the
+// range of tile row ty0 + l (32 rows at once), a warp scan gives each row's
+// offset, and the lanes write the tiles of each row.  The float32 row ranges
+// are the ones the count pass used, so the pairs and their order are the same.
+constexpr uint32_t KG_SMALL = 32;
+
 __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Records rec, const uint32_t* __restrict__ order,
                                                 const uint32_t* __restrict__ offs, uint32_t* __restrict__ pkeys,
-                                                uint32_t* __restrict__ pvals, uint32_t cap) {
+                                                uint32_t* __restrict__ pvals, uint32_t cap, uint32_t* __restrict__ big) {
   const uint32_t n = fd->n_valid;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const uint32_t np = fd->n_pairs;
@@ -92,13 +101,17 @@ __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Recor
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t r = order[i];
+    const uint32_t c = rec.cnt[r];
+    if (c > KG_SMALL) {
+      big[atomicAdd(&fd->n_big, 1u)] = i;
+      continue;
+    }
     uint32_t o = offs[i];
     const float4 g = rec.geo[r];
-    const float4 c = rec.cop[r];
-    const uint32_t cam = __float_as_uint(rec.col[r].w) & 0xFFFFu;
-    const CamDev& cd = fd->cam[cam];
+    const float4 cp = rec.cop[r];
+    const CamDev& cd = fd->cam[__float_as_uint(rec.col[r].w) & 0xFFFFu];
     const uint32_t tb = cd.tile_base;
-    cover_tiles_f32(g.x, g.y, g.z, g.w, c.x, c.z, cd.W, cd.H, TW, TH, [&](int tile) {
+    cover_tiles_f32(g.x, g.y, g.z, g.w, cp.x, cp.z, cd.W, cd.H, TW, TH, [&](int tile) {
       if (o < cap) {
         pkeys[o] = tb + (uint32_t)tile;
         pvals[o] = r;
@@ -108,9 +121,63 @@ __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Recor
   }
 }
 
+__global__ void __launch_bounds__(256) k_keygen_big(FrameDev* __restrict__ fd, Records rec,
+                                                    const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
+                                                    uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                                    uint32_t cap, const uint32_t* __restrict__ big) {
+  const uint32_t nb = fd->n_big;
+  const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t e = 0;
+    if (lane == 0) e = atomicAdd(&fd->ctr[SLOT_AUX], 1u);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e >= nb) break;
+    const uint32_t i = big[e];
+    const uint32_t r = order[i];
+    uint32_t o = offs[i];
+    const float4 g = rec.geo[r];
+    const float4 cp = rec.cop[r];
+    const CamDev& cd = fd->cam[__float_as_uint(rec.col[r].w) & 0xFFFFu];
+    const uint32_t tb = cd.tile_base;
+    Cover cv;
+    if (!cover_setup(cv, g.x, g.y, g.z, g.w, cp.x, cp.z, cd.W, cd.H, TW, TH)) continue;
+    for (int c0 = cv.ty0; c0 <= cv.ty1; c0 += 32) {
+      const int ty = c0 + (int)lane;
+      int tx0 = 1, tx1 = 0;
+      if (ty <= cv.ty1) cover_row(cv, ty, TH, tx0, tx1);
+      const uint32_t len = tx1 >= tx0 ? (uint32_t)(tx1 - tx0 + 1) : 0u;
+      uint32_t incl = len;
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+        if (lane >= (uint32_t)s) incl += y;
+      }
+      const uint32_t excl = incl - len;
+      const uint32_t chunk = __shfl_sync(0xffffffffu, incl, 31);
+      const int rows = min(32, cv.ty1 - c0 + 1);
+      for (int rr = 0; rr < rows; ++rr) {
+        const uint32_t l = __shfl_sync(0xffffffffu, len, rr);
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, rr);
+        const int x0 = __shfl_sync(0xffffffffu, tx0, rr);
+        const uint32_t kb = tb + (uint32_t)((c0 + rr) * cv.ntx + x0);
+        for (uint32_t u = lane; u < l; u += 32u) {
+          const uint32_t oi = o + ex + u;
+          if (oi < cap) {
+            pkeys[oi] = kb + u;
+            pvals[oi] = r;
+          }
+        }
+      }
+      o += chunk;
+    }
+  }
+}
+
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
-                   uint32_t* pvals, uint32_t cap, int n_sm, cudaStream_t s) {
-  k_keygen<<<n_sm * 8, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap);
+                   uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s) {
+  k_keygen<<<n_sm * 8, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap, big);
+  k_keygen_big<<<n_sm * 4, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap, big);
 }
 
 // ------------------------------------------------------------------ tile ranges (K9)
@@ -128,23 +195,31 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 }
 
 // ------------------------------------------------------------------ blend (K10)
-// One block per (camera, tile), one thread per pixel.  The tile's records
-// are staged into shared memory one batch at a time; each pixel walks them
+// One block per (camera, tile), one thread per pixel; warp w owns an 8x4
+// block of pixels.  The tile's records are staged into shared memory one
+// batch at a time, each turned into the tile-local quadratic of its power in
+// the exp2 domain,
+//   log2(o) - (log2 e / 2) q(D) = F + X (D + A' X + B' Y) + Y (E + C' Y),
+// with (X, Y) the pixel centre relative to the tile centre, plus the
+// Gaussian's opacity-aware bounding box.  Each pixel then walks the batch
 // front to back:
-//   D = pixel centre - mean, power = -(A Dx^2 + C Dy^2)/2 - B Dx Dy,
-//   alpha = min(0.99, o exp(power)), skipped if < 1/255;
+//   skip if the power is below log2(1/255) (alpha < 1/255);
+//   alpha = min(0.99, 2^power);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
 //   C += c alpha T, T *= 1 - alpha;  out = C + T bg.
-// A warp whose pixels are all finished skips the batch; the block stops
-// once every pixel is finished.
+// A warp skips a Gaussian whose box misses its 8x4 pixels, and skips the
+// whole batch once its pixels are finished; the block stops once all are.
 constexpr int BLEND_MAX_NT = 256;
+constexpr float LOG2E_HALF = 0.72134752044448170368f;  // log2(e) / 2
+constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
 
 __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
-  __shared__ float4 s_geo[BLEND_MAX_NT];
-  __shared__ float2 s_co[BLEND_MAX_NT];
-  __shared__ float4 s_col[BLEND_MAX_NT];
+  __shared__ float4 s_q0[BLEND_MAX_NT];   // F, D, E, A'
+  __shared__ float4 s_q1[BLEND_MAX_NT];   // B', C', r, g
+  __shared__ float4 s_bb[BLEND_MAX_NT];   // b, xmin, xmax, ymin
+  __shared__ float s_ymax[BLEND_MAX_NT];
   const uint32_t tile_key = blockIdx.x;
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   const int nt = TW * TH;
@@ -153,10 +228,18 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restri
   const CamDev& cd = fd->cam[cam];
   const uint32_t tl = tile_key - cd.tile_base;
   const int tx = (int)(tl % (uint32_t)cd.ntx), ty = (int)(tl / (uint32_t)cd.ntx);
-  const int px = tx * TW + (int)threadIdx.x % TW;
-  const int py = ty * TH + (int)threadIdx.x / TW;
+  // warp -> 8x4 pixel block, lane -> pixel
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int wpr = TW >> 3;  // warp blocks per tile row
+  const int bx = (warp % wpr) * 8, by = (warp / wpr) * 4;
+  const int lx = bx + (lane & 7), ly = by + (lane >> 3);
+  const int px = tx * TW + lx, py = ty * TH + ly;
   const bool inside = px < cd.W && py < cd.H;
-  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+  const float ox = (float)(tx * TW) + 0.5f * (float)TW, oy = (float)(ty * TH) + 0.5f * (float)TH;
+  const float X = ((float)px + 0.5f) - ox, Y = ((float)py + 0.5f) - oy;
+  // the warp's pixel-centre box in tile-local coordinates
+  const float wx0 = ((float)(tx * TW + bx) + 0.5f) - ox, wx1 = wx0 + 7.f;
+  const float wy0 = ((float)(ty * TH + by) + 0.5f) - oy, wy1 = wy0 + 3.f;
   const uint2 rg = ranges[tile_key];
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   bool done = !inside;
@@ -165,33 +248,44 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restri
     const uint32_t idx = b + threadIdx.x;
     if (idx < rg.y) {
       const uint32_t r = vals[idx];
-      s_geo[threadIdx.x] = rec.geo[r];
-      const float4 c = rec.cop[r];
-      s_co[threadIdx.x] = make_float2(c.x, c.y);
-      s_col[threadIdx.x] = rec.col[r];
+      const float4 g = rec.geo[r];   // mean x, mean y, A, B
+      const float4 c = rec.cop[r];   // C, opacity, tau, depth
+      const float4 cl = rec.col[r];
+      const float mxl = g.x - ox, myl = g.y - oy;
+      const float A = g.z, B = g.w, Cc = c.x;
+      const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
+      s_q0[threadIdx.x] = make_float4(__log2f(c.y) - LOG2E_HALF * q0, 2.f * LOG2E_HALF * (A * mxl + B * myl),
+                                      2.f * LOG2E_HALF * (B * mxl + Cc * myl), -LOG2E_HALF * A);
+      s_q1[threadIdx.x] = make_float4(-2.f * LOG2E_HALF * B, -LOG2E_HALF * Cc, cl.x, cl.y);
+      const float idet = 1.f / (A * Cc - B * B);
+      const float ex = sqrtf(c.z * Cc * idet), ey = sqrtf(c.z * A * idet);
+      s_bb[threadIdx.x] = make_float4(cl.z, mxl - ex, mxl + ex, myl - ey);
+      s_ymax[threadIdx.x] = myl + ey;
     }
     __syncthreads();
     const int cnt = min(nt, (int)(rg.y - b));
-    if (!__all_sync(0xffffffffu, done)) {
-      for (int u = 0; u < cnt && !done; ++u) {
-        const float4 g = s_geo[u];
-        const float2 co = s_co[u];
-        const float dx = X - g.x, dy = Y - g.y;
-        const float power = -0.5f * (g.z * dx * dx + co.x * dy * dy) - g.w * dx * dy;
-        const float alpha = fminf(0.99f, co.y * __expf(power));
-        if (alpha < (1.0f / 255.0f)) continue;
-        const float tt = T * (1.f - alpha);
-        if (tt < 1e-4f) {
-          done = true;
-          break;
-        }
-        const float4 cl = s_col[u];
-        const float w = alpha * T;
-        C0 += cl.x * w;
-        C1 += cl.y * w;
-        C2 += cl.z * w;
-        T = tt;
+    if (__all_sync(0xffffffffu, done)) continue;
+    for (int u = 0; u < cnt; ++u) {
+      const float4 bb = s_bb[u];
+      if (bb.z < wx0 || bb.y > wx1 || bb.w > wy1 || s_ymax[u] < wy0) continue;  // box misses the warp
+      if (done) continue;
+      const float4 q0 = s_q0[u];
+      const float4 q1 = s_q1[u];
+      const float t1 = fmaf(q0.w, X, fmaf(q1.x, Y, q0.y));
+      const float t2 = fmaf(q1.y, Y, q0.z);
+      const float p = fmaf(t1, X, fmaf(t2, Y, q0.x));
+      if (p < LOG2_MIN_ALPHA) continue;
+      const float alpha = fminf(0.99f, exp2f(p));
+      const float tt = fmaf(-T, alpha, T);
+      if (tt < 1e-4f) {
+        done = true;
+        continue;
       }
+      const float w = alpha * T;
+      C0 = fmaf(q1.z, w, C0);
+      C1 = fmaf(q1.w, w, C1);
+      C2 = fmaf(bb.x, w, C2);
+      T = tt;
     }
   }
   if (inside) {

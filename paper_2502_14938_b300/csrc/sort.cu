@@ -13,8 +13,6 @@
 namespace gsc {
 
 constexpr int SORT_NT = 256;
-constexpr int SORT_IPT = 16;
-constexpr int SORT_TILE = SORT_NT * SORT_IPT;
 constexpr int SORT_WARPS = SORT_NT / 32;
 
 __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
@@ -42,11 +40,13 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ 
   }
 }
 
+template <int SORT_IPT>
 __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                        uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                        const uint32_t* __restrict__ n_ptr, int shift,
                                                        const uint32_t* __restrict__ hist_p, int drop_invalid,
                                                        unsigned long long* status, FrameDev* fd, int slot) {
+  constexpr int SORT_TILE = SORT_NT * SORT_IPT;
   __shared__ uint32_t s_gbase[256];
   __shared__ uint32_t s_whist[SORT_WARPS][256];
   __shared__ uint32_t s_dstart[256];
@@ -144,11 +144,12 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
 // keys equal to INVALID_KEY are removed (their count is not part of the
 // output; *n_valid_out receives the kept count).  Ping-pongs between
 // (k0, v0) and (k1, v1); *kout / *vout get the buffers holding the result.
-// Uses counter / epoch slots slot_base .. slot_base + passes - 1.
+// Uses counter / epoch slots slot_base .. slot_base + passes - 1.  ipt 8
+// (2048-key tiles, for the smaller record sort) or 16 (4096-key tiles).
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
-                      uint32_t** vout) {
+                      uint32_t** vout, int ipt) {
   const int npass = (bits + 7) / 8;
   cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * 4 * 256, s);
   k_sort_hist<<<n_sm * 4, 256, 0, s>>>(kin, n_in, npass, drop_invalid, sb.hist, n_valid_out);
@@ -158,8 +159,12 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ok = (p % 2 == 0) ? k0 : k1;
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
-    k_sort_pass<<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256, p == 0 ? drop_invalid : 0,
-                                             sb.status, fd, slot_base + p);
+    if (ipt == 8)
+      k_sort_pass<8><<<n_sm * 4, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256,
+                                                  p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
+    else
+      k_sort_pass<16><<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256,
+                                                   p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     ci = ok;
     cv = ov;
   }
