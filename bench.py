@@ -146,9 +146,20 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
+# Forms of the frame path: the plain float32 method and the AI-systems forms.
+FORMS = {
+    "plain": dict(precision="fp32", stereo_unify=False, reuse="off"),
+    "unified": dict(precision="fp32", stereo_unify=True, reuse="off"),
+    "bf16": dict(precision="bf16", stereo_unify=False, reuse="off"),
+    "bf16_unified": dict(precision="bf16", stereo_unify=True, reuse="off"),
+}
+HEADLINE = "bf16_unified"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP/FMA x max SM clock
+
+
 def make_renderer(model, form, flags=0, use_graph=True):
     import paper_2502_14938_b300 as pkg
-    r = pkg.Renderer(max_views=2, stereo_unify=(form == "unified"), flags=flags, use_graph=use_graph)
+    r = pkg.Renderer(max_views=2, flags=flags, use_graph=use_graph, **FORMS[form])
     mid = r.load_model(model)
     return r, mid
 
@@ -160,9 +171,9 @@ def set_pair(r, mid, L, R):
 
 def run_profile(args):
     """Minimal run for profilers: W + K frames from --frame, no extras.
-    Per frame: 16 library kernels (frame setup, cull, plan, derive, depth
-    sort histogram + 4 passes, scan, keygen, tile sort histogram + 2 passes,
-    ranges, blend) and one torch fill between frames."""
+    Per frame: 17 library kernels (frame setup, cull, plan, derive - two for
+    the tensor-core forms - depth sort histogram + 4 passes, scan, keygen x2,
+    tile sort histogram + 2 passes, ranges, blend)."""
     import torch
     model, frames, _ = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
@@ -172,12 +183,101 @@ def run_profile(args):
         set_pair(r, mid, *frames[(args.frame + s) % len(frames)])
         st = r.render_frame(outs)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_run": True, "frames": args.warmup + args.steps, "last": st}), flush=True)
+    print(json.dumps({"profile_run": True, "form": args.form, "frames": args.warmup + args.steps, "last": st}),
+          flush=True)
+
+
+def time_form(model, frames, form, steps, warmup, flush, world, clk=None):
+    """Per-frame CUDA-event times (ms) of `steps` frames of the path; L2 flushed between frames."""
+    import torch
+    W, H = frames[0][0].width, frames[0][0].height
+    r, mid = make_renderer(model, form)
+    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    for f in range(len(frames)):  # one pass over the path with stats grows buffers to its needs
+        set_pair(r, mid, *frames[f])
+        r.render_frame(outs)
+    for w in range(warmup):
+        set_pair(r, mid, *frames[w % len(frames)])
+        r.render_frame(outs, stats=False)
+    r.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clk:
+        clk.__enter__()
+    wall0 = time.perf_counter()
+    for s in range(steps):
+        set_pair(r, mid, *frames[s % len(frames)])
+        flush.fill_(s & 0xFF)
+        evs[s][0].record(stream)
+        r.render_frame(outs, stats=False)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if clk:
+        clk.__exit__()
+    r.synchronize()  # raises on a deferred capacity / timeout error
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    return r, mid, outs, ms, wall
+
+
+def stage_profile(model, frames, form, n, flush):
+    """Per-stage CUDA-event times on the library's stream (eager launches)."""
+    import paper_2502_14938_b300 as pkg
+    import torch
+    W, H = frames[0][0].width, frames[0][0].height
+    rt, mid = make_renderer(model, form, flags=pkg.FLAG_TIMING, use_graph=False)
+    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    stage = np.zeros(8)
+    acc = {"visible_anchors": 0, "derived_anchors": 0, "records": 0, "valid_records": 0, "pairs": 0}
+    for s in range(n):
+        set_pair(rt, mid, *frames[s % len(frames)])
+        flush.fill_(s & 0xFF)
+        st = rt.render_frame(outs)
+        stage += np.array(st["ms_stage"])
+        for k in acc:
+            acc[k] += st[k]
+    rt.close()
+    names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
+    return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, {k: v / n for k, v in acc.items()}
+
+
+def roofline(stage_ms, st, form, W, H, n_anchors):
+    """Dominant stage: algorithmic work per launch / its event time, against a peak."""
+    pk = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    P, Rv, R, V = st["pairs"], st["valid_records"], st["records"], st["visible_anchors"]
+    pixels = 2 * W * H
+    dur = stage_ms[dom] / 1e3
+    feat_b = 64 if FORMS[form]["precision"] == "bf16" else 128
+    if dom == "blend":
+        # FP32 lane work per (pixel, pair): 5 FMA quadratic, exp2, clamp, T update FMA, weight, 3 colour FMA
+        flop = P * 256 * 20.0
+        ach = flop / dur / 1e12
+        return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "peak_src": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                "traffic": None, "alg_flop_per_launch": flop, "ms_per_launch": stage_ms[dom],
+                "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
+    if dom == "sort_tile":
+        b = P * 4 + 2 * P * 16
+    elif dom == "sort_depth":
+        b = R * 8 + Rv * 8 + 3 * Rv * 16
+    elif dom == "derive+project":
+        b = V * (feat_b + 16 + 120) + R * 56
+    elif dom == "scan+keygen":
+        b = Rv * 16 + P * 8
+    else:
+        b = n_anchors * 13 + V * 4
+    ach = b / dur / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "peak_src": pk["src"], "traffic": None, "alg_bytes_per_launch": b,
+            "ms_per_launch": stage_ms[dom]}
 
 
 def run_ours(args, rank, world):
     import torch
-    import paper_2502_14938_b300 as pkg
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -185,86 +285,31 @@ def run_ours(args, rank, world):
         return run_profile(args)
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
-    r, mid = make_renderer(model, args.form)
-    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
-    # warm-up over the whole path with stats: grows buffers to the path's needs
-    for f in range(len(frames)):
-        set_pair(r, mid, *frames[f])
-        r.render_frame(outs)
-    for w in range(args.warmup):
-        set_pair(r, mid, *frames[w % len(frames)])
-        r.render_frame(outs, stats=False)
-    r.synchronize()
-    stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
-        wall0 = time.perf_counter()
-        for s in range(args.steps):
-            set_pair(r, mid, *frames[s % len(frames)])
-            flush.fill_(s & 0xFF)
-            evs[s][0].record(stream)
-            r.render_frame(outs, stats=False)
-            evs[s][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-    r.synchronize()  # raises on a deferred capacity / timeout error
-    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    form = args.form
+    clk = ClockSampler(dev)
+    r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, world, clk)
     total_ms = float(ms.sum())
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
+    others = {}
+    for f2 in args.compare:
+        if f2 == form:
+            continue
+        r2, _, _, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1)
+        others[f2] = {"fps": 1000.0 / float(ms2.mean()), "ms_mean": float(ms2.mean()),
+                      "p99_ms": float(np.percentile(ms2, 99))}
+        r2.close()
     if rank != 0:
         return
     mean_ms = total_ms / args.steps
     fps = world * args.steps / (total_ms / 1e3)
+    stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush)
+    roof = roofline(stage_ms, per_frame, form, W, H, model.n)
 
-    # ---- per-stage timing (eager launches with events on the library stream)
-    rt, mid_t = make_renderer(model, args.form, flags=pkg.FLAG_TIMING, use_graph=False)
-    stage = np.zeros(8)
-    stats_acc = {"visible_anchors": 0, "records": 0, "valid_records": 0, "pairs": 0}
-    n_st = min(args.steps, len(frames))
-    for s in range(n_st):
-        set_pair(rt, mid_t, *frames[s % len(frames)])
-        flush.fill_(s & 0xFF)
-        st = rt.render_frame(outs)
-        stage += np.array(st["ms_stage"])
-        for k in stats_acc:
-            stats_acc[k] += st[k]
-    stage /= n_st
-    for k in stats_acc:
-        stats_acc[k] /= n_st
-    rt.close()
-    names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
-    stage_ms = {n: float(stage[i]) for i, n in enumerate(names)}
-
-    # ---- roofline of the dominant kernel (algorithmic bytes per launch / event time)
-    pk = peaks()
-    dom = max(stage_ms, key=stage_ms.get)
-    P = stats_acc["pairs"]
-    Rv = stats_acc["valid_records"]
-    pixels = 2 * W * H
-    if dom == "blend":
-        alg_bytes = P * (4 + 48) + pixels * 12 + 2 * (W // 16 + 1) * (H // 16 + 1) * 8
-    elif dom == "sort_tile":
-        alg_bytes = P * 8 + 2 * P * 16
-    elif dom == "sort_depth":
-        alg_bytes = stats_acc["records"] * 4 + Rv * 4 + 4 * Rv * 16
-    elif dom == "derive+project":
-        alg_bytes = stats_acc["visible_anchors"] * (128 + 16 + 120) + stats_acc["records"] * 56
-    else:
-        alg_bytes = stats_acc["records"] * 8 + P * 8
-    dur_s = stage_ms[dom] / 1e3
-    achieved = alg_bytes / dur_s / 1e9 if dur_s > 0 else 0.0
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"], "traffic": None,
-            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stage_ms[dom]}
-
-    # ---- quality: PSNR of sampled frames against the float64 oracle
+    # ---- quality: PSNR of sampled frames against the float64 oracle (plain method)
     import oracle
     psnrs = []
     for f in args.psnr_frames:
@@ -296,19 +341,18 @@ def run_ours(args, rank, world):
            "sample": "2 stereo frames (0, 150): full float64 filtering/derivation/projection, "
                      "blending on every 16th pixel row scaled x16"}
 
-    n_sort2 = 2  # 14 tile bits -> two 8-bit passes
-    launches_per_frame = 1 + 1 + 1 + 1 + (1 + 4) + 1 + 1 + (1 + n_sort2) + 1 + 1
+    derive_launches = 2 if FORMS[form]["precision"] == "bf16" else 1
+    launches_per_frame = 1 + 1 + 1 + derive_launches + (1 + 4) + 1 + 2 + (1 + 2) + 1 + 1
+    cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tile": "16x16",
+           "l2": "flushed between frames (256 MB write, untimed)",
+           "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
+           "psnr_db_min": min(psnrs) if psnrs else None, "psnr_frames": args.psnr_frames,
+           "compare": others, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": args.form, "precision": "fp32", "cache": "off",
-                       "stereo_unify": args.form == "unified", "tile": "16x16",
-                       "l2": "flushed between frames (256 MB write, untimed)",
-                       "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
-                       "psnr_db_min": min(psnrs) if psnrs else None, "psnr_frames": args.psnr_frames,
-                       "stage_ms": stage_ms, "per_frame": stats_acc, "gen_s": t_gen},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": launches_per_frame * args.steps}
+            "vs_baseline": None, "dtype": "bf16+f32" if FORMS[form]["precision"] == "bf16" else "f32",
+            "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk.summary(), "gpu_launches": launches_per_frame * args.steps}
     print(json.dumps(line), flush=True)
 
 
@@ -318,7 +362,8 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "unified"])
+    ap.add_argument("--form", default=HEADLINE, choices=sorted(FORMS))
+    ap.add_argument("--compare", nargs="*", default=["plain"], help="other forms timed for comparison")
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 299])
     ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
     ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")

@@ -29,7 +29,7 @@ struct DevBuf {
 
 struct ModelHost {
   uint32_t n = 0;
-  DevBuf px, py, pz, level, feat, offs, scale, w32;
+  DevBuf px, py, pz, level, feat, offs, scale, w32, feat_bf16, w_tc;
   ModelDev dev{};
 };
 
@@ -73,6 +73,7 @@ struct gsc_ctx {
   uint32_t rec_cap = 0;
   Records rec{};
   uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr, *big = nullptr;
+  float4* attrs = nullptr;  // derived attributes, 3 float4 per Gaussian in frame item order
   uint32_t pair_cap = 0;
   uint32_t *pk0 = nullptr, *pv0 = nullptr, *pk1 = nullptr, *pv1 = nullptr;
   uint32_t ranges_cap = 0;
@@ -99,6 +100,10 @@ struct gsc_ctx {
   std::vector<int> models_used;
   uint32_t spin_limit = 1u << 20;
   bool timing = false;
+  // tensor-core forms: compact feature rows of the frame + their tensor map
+  uint4* compact = nullptr;
+  uint64_t compact_rows = 0;
+  CUtensorMap tmap_feat{};
 };
 
 namespace {
@@ -193,7 +198,8 @@ int alloc_records(gsc_ctx* ctx, uint32_t cap) {
       (r = dalloc(ctx, &ctx->rec.col, cap)) || (r = dalloc(ctx, &ctx->rec.key, cap)) ||
       (r = dalloc(ctx, &ctx->rec.cnt, cap)) || (r = dalloc(ctx, &ctx->s1k0, cap)) ||
       (r = dalloc(ctx, &ctx->s1v0, cap)) || (r = dalloc(ctx, &ctx->s1k1, cap)) ||
-      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)))
+      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)) ||
+      (r = dalloc(ctx, &ctx->attrs, (size_t)cap * 3)))
     return r;
   ctx->rec_cap = cap;
   invalidate_graph(ctx);
@@ -222,7 +228,12 @@ void enqueue_sequence(gsc_ctx* ctx) {
   launch_plan(fd, ctx->rec_cap, s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
-    launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->rec, ctx->d_dbg_tab, ctx->n_sm, s);
+    if (ctx->cfg.precision == GSC_PREC_BF16)
+      launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, &ctx->tmap_feat,
+                       ctx->compact, ctx->n_sm, s);
+    else
+      launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, ctx->n_sm, s);
+  launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, ctx->rec, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
@@ -412,9 +423,11 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   const uint32_t nt = cfg.tile_w * cfg.tile_h;
   if (nt == 0 || nt > 256 || nt % 32 != 0) return GSC_ERR_INVALID_ARG;
-  if (cfg.tile_w % 8 != 0 || cfg.tile_h % 4 != 0) return GSC_ERR_INVALID_ARG;  // 8x4 pixel block per warp
+  // 8x4 pixel block per warp; powers of two keep the coverage arithmetic exact
+  if (cfg.tile_w % 8 != 0 || cfg.tile_h % 4 != 0) return GSC_ERR_INVALID_ARG;
+  if ((cfg.tile_w & (cfg.tile_w - 1)) != 0 || (cfg.tile_h & (cfg.tile_h - 1)) != 0) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
-  if (cfg.precision != GSC_PREC_FP32 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
+  if (cfg.precision == GSC_PREC_FP8 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
 
   gsc_ctx* ctx = new (std::nothrow) gsc_ctx();
@@ -427,7 +440,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
     return code;
   };
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(GSC_ERR_CUDA);
-  if (prepare_derive_f32() != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (prepare_derive_f32() != cudaSuccess || prepare_derive_tc() != cudaSuccess) return bail(GSC_ERR_CUDA);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -459,11 +472,12 @@ void gsc_destroy(gsc_ctx* ctx) {
   for (auto& m : ctx->models) {
     dfree(m.px.p); dfree(m.py.p); dfree(m.pz.p); dfree(m.level.p);
     dfree(m.feat.p); dfree(m.offs.p); dfree(m.scale.p); dfree(m.w32.p);
+    dfree(m.feat_bf16.p); dfree(m.w_tc.p);
   }
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
-                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd};
+                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < MAXV; ++i) {
     dfree(ctx->d_img[i]);
@@ -528,6 +542,19 @@ int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out
       (r = upload(ctx, mh.feat, d->feat, n * FDIM * 4)) || (r = upload(ctx, mh.offs, d->offset, n * K * 3 * 4)) ||
       (r = upload(ctx, mh.scale, d->scale, n * 4)) || (r = upload(ctx, mh.w32, w.data(), w.size() * 4)))
     return r;
+  // tensor-core forms: bf16 features (converted on the device) and the weight image
+  std::vector<uint8_t> img;
+  pack_tc_weights(d->W1, d->b1, d->W2, d->b2, img);
+  if ((r = upload(ctx, mh.w_tc, img.data(), img.size()))) return r;
+  mh.feat_bf16.bytes = n * FDIM * 2;
+  if (n) {
+    CK(cudaMalloc(&mh.feat_bf16.p, mh.feat_bf16.bytes));
+    launch_to_bf16((const float*)mh.feat.p, mh.feat_bf16.p, n * FDIM, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+  }
+  mh.dev.feat_bf16 = mh.feat_bf16.p;
+  mh.dev.w_tc = mh.w_tc.p;
   mh.dev.n = mh.n;
   mh.dev.n_levels = d->n_levels;
   mh.dev.lod_dmax = d->lod_dmax;
@@ -617,6 +644,17 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
       for (uint32_t i = 0; i < slots; ++i) dt[i] = ctx->d_dbg_buf + (size_t)vcap * K * 11 * i;
       if (!ctx->d_dbg_tab) CK(cudaMalloc((void**)&ctx->d_dbg_tab, sizeof(float*) * MAXV));
       CK(cudaMemcpy(ctx->d_dbg_tab, dt.data(), sizeof(float*) * MAXV, cudaMemcpyHostToDevice));
+    }
+  }
+  // tensor-core forms: compact bf16 feature rows for every visible anchor of a model
+  if (ctx->cfg.precision != GSC_PREC_FP32) {
+    const uint64_t rows = (uint64_t)ctx->vis_cap * ctx->n_vis_slots;
+    if (rows > ctx->compact_rows) {
+      if ((r = dalloc(ctx, &ctx->compact, (size_t)rows * 4))) return r;  // 64 bytes = 4 x uint4 per row
+      if (encode_feat_tmap(&ctx->tmap_feat, ctx->compact, rows) != 0)
+        return fail(ctx, GSC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      ctx->compact_rows = rows;
+      invalidate_graph(ctx);
     }
   }
   // records: worst case (every anchor visible), capped at 64M then grown on demand

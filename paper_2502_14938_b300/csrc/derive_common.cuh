@@ -23,6 +23,7 @@ struct DViewSet {
   int nd;
   int d[MAXV];
   uint32_t base[MAXV + 1];  // prefix of visible counts over the listed views
+  uint32_t gbase[MAXV];     // frame-wide item index of each listed view's first anchor
   float pc[MAXV][6];        // double-float centre of each derivation camera
   ProjCam cam[MAXV][2];     // cameras fed by each view (cam = 0xFFFFFFFF unused)
 };
@@ -34,6 +35,7 @@ __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd,
     if (fd->dcam[d].model != model) continue;
     S.d[nd] = (int)d;
     S.base[nd] = acc;
+    S.gbase[nd] = fd->item_base[d];
     acc += fd->vis_count[d];
     for (int u = 0; u < 3; ++u) {
       S.pc[nd][u] = fd->dcam[d].pc[u];
@@ -129,14 +131,15 @@ __device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uin
 }
 
 // Activations of Eq. 3 for Gaussian j of one anchor from its 11 head
-// outputs z = [op_j, col_3j..3j+2, cov_7j..7j+6], then one record per camera
-// the derivation view feeds.  sa: anchor scale; (xa, ya, za): anchor
-// position; offs: the anchor's [K][3] offsets.
-__device__ __forceinline__ void gaussian_epilogue(const float z[11], int j, uint32_t i, float sa, float xa, float ya,
-                                                  float za, const float* __restrict__ offs, const ProjCam* cams,
-                                                  Records rec, uint32_t rec_cap, float* dbg, int TW, int TH) {
+// outputs z = [op_j, col_3j..3j+2, cov_7j..7j+6]:
+//   alpha = tanh(z_op) (the Gaussian is kept iff alpha > 0), c = sigmoid(z_col),
+//   s = s_a sigmoid(z_cov[0..2]) (the per-anchor scale broadcast to the
+//   Gaussian), q = z_cov[3..6] / |.| (identity below 1e-12).
+// Stored as 3 float4 at attrs[3 idx ..]: (alpha, c), (s, q_w), (q_x, q_y, q_z, 0).
+// dbg (optional): the 11 attributes at dbg[11 (i K + j)].
+__device__ __forceinline__ void gaussian_activate_store(const float z[11], int j, uint32_t i, float sa, float4* attrs,
+                                                        size_t idx, float* dbg) {
   const float alpha = tanhf(z[0]);
-  const bool kept = z[0] > 0.f;
   float col[3], s[3], q[4];
 #pragma unroll
   for (int u = 0; u < 3; ++u) col[u] = 1.0f / (1.0f + expf(-z[1 + u]));
@@ -150,25 +153,16 @@ __device__ __forceinline__ void gaussian_epilogue(const float z[11], int j, uint
 #pragma unroll
     for (int u = 0; u < 4; ++u) q[u] = z[7 + u] * iq;
   }
+  // alpha carries the mask: tanh(z) > 0 exactly when z > 0
+  attrs[3 * idx + 0] = make_float4(z[0] > 0.f ? alpha : -1.f, col[0], col[1], col[2]);
+  attrs[3 * idx + 1] = make_float4(s[0], s[1], s[2], q[0]);
+  attrs[3 * idx + 2] = make_float4(q[1], q[2], q[3], 0.f);
   if (dbg) {
     float* o = dbg + ((size_t)i * K + j) * 11;
     o[0] = alpha;
     o[1] = col[0]; o[2] = col[1]; o[3] = col[2];
     o[4] = s[0]; o[5] = s[1]; o[6] = s[2];
     o[7] = q[0]; o[8] = q[1]; o[9] = q[2]; o[10] = q[3];
-  }
-  const float* op = offs + j * 3;
-  const float o3[3] = {__ldg(op), __ldg(op + 1), __ldg(op + 2)};
-  const float mu[3] = {__fadd_rn(xa, o3[0]), __fadd_rn(ya, o3[1]), __fadd_rn(za, o3[2])};
-#pragma unroll 1
-  for (int e = 0; e < 2; ++e) {
-    const ProjCam& pc = cams[e];
-    if (pc.cam == 0xFFFFFFFFu) continue;
-    const uint32_t r = pc.rec_base + i * K + (uint32_t)j;
-    if (r >= rec_cap) continue;
-    const float rel[3] = {((xa - pc.pc[0]) - pc.pc_lo[0]) + o3[0], ((ya - pc.pc[1]) - pc.pc_lo[1]) + o3[1],
-                          ((za - pc.pc[2]) - pc.pc_lo[2]) + o3[2]};
-    project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
   }
 }
 

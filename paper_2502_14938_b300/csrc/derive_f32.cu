@@ -66,7 +66,7 @@ __device__ __forceinline__ void df_dots(const float (&h)[NH], const float* __res
 
 __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restrict__ models, int model,
                                                          FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
-                                                         Records rec, float* const* __restrict__ dbg_attrs) {
+                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs) {
   extern __shared__ __align__(16) float s_dyn[];
   float* s_w = s_dyn;
   float* s_h = s_dyn + DF_W;
@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
   const uint32_t total = S.base[nd];
   const uint32_t ntiles = (total + DF_TA - 1) / DF_TA;
   const uint32_t rec_cap = fd->n_records;
-  const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   const int t = threadIdx.x;
 
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -195,8 +194,8 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
 #pragma unroll
       for (int u = 0; u < 7; ++u) z[4 + u] = zr[4 * K + 7 * j + u];
       float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
-      gaussian_epilogue(z, j, M.vi[a], M.sa[a], M.pos[a][0], M.pos[a][1], M.pos[a][2],
-                        md.offs + (size_t)M.anchor[a] * K * 3, S.cam[ld], rec, rec_cap, dbg, TW, TH);
+      const size_t idx = (size_t)(S.gbase[ld] + M.vi[a]) * K + j;
+      if (idx < rec_cap) gaussian_activate_store(z, j, M.vi[a], M.sa[a], attrs, idx, dbg);
     }
     __syncthreads();
   }
@@ -206,9 +205,9 @@ cudaError_t prepare_derive_f32() {
   return cudaFuncSetAttribute(k_derive_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DF_SMEM_BYTES);
 }
 
-void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, Records rec,
+void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                        float* const* dbg_attrs, int n_sm, cudaStream_t s) {
-  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, rec, dbg_attrs);
+  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs);
 }
 
 }  // namespace gsc

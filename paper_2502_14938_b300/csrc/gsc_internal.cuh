@@ -13,8 +13,11 @@
 //   sort #2      -> stable sort by tile key => (tile, depth, Gaussian id)
 //   ranges+blend -> per-tile front-to-back alpha blending
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
+
 #include <cstdint>
+#include <vector>
 
 #include "gsc.h"
 
@@ -116,6 +119,8 @@ struct ModelDev {
   const float* offs;      // [N][K][3]
   const float* scale;     // [N]
   const float* w32;       // packed weights, W_FLOATS
+  const void* feat_bf16;  // [N][32] bf16 (tensor-core forms)
+  const void* w_tc;       // tensor-core weight image (40,960 bytes)
 };
 
 struct Records {
@@ -210,9 +215,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 // so its x-range comes from the closed-form extreme points
 //   Dy* = -B sqrt(tau / (C det)),  x(Dy) = (-B Dy +- sqrt(A tau - det Dy^2)) / A.
 // Every operation is a correctly rounded float32 op (no contraction), so the
-// count pass and the emit pass agree exactly.  f(tile) is called per tile.
+// count pass and the emit pass agree exactly.  Tile sizes are powers of two,
+// so x / TW is computed as x * (1/TW), which is the same correctly rounded
+// value.  f(tile) is called per tile.
 struct Cover {
-  float mx, my, A, B, tau, det, ey, ys, fTW;
+  float mx, my, A, B, tau, det, ey, ys, fTW, rTW;
   int ntx, ty0, ty1;
 };
 
@@ -227,9 +234,10 @@ __device__ __forceinline__ bool cover_setup(Cover& cv, float mx, float my, float
   cv.ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(tau, A), det));
   cv.ys = __fmul_rn(-B, __fsqrt_rn(__fdiv_rn(tau, __fmul_rn(C, det))));
   cv.fTW = (float)TW;
-  const float fTH = (float)TH;
-  float fy0 = ceilf(__fdiv_rn(__fsub_rn(__fsub_rn(my, cv.ey), __fsub_rn(fTH, 0.5f)), fTH));
-  float fy1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(my, cv.ey), 0.5f), fTH));
+  cv.rTW = 1.0f / (float)TW;
+  const float fTH = (float)TH, rTH = 1.0f / (float)TH;
+  float fy0 = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(my, cv.ey), __fsub_rn(fTH, 0.5f)), rTH));
+  float fy1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(my, cv.ey), 0.5f), rTH));
   fy0 = fminf(fmaxf(fy0, 0.f), (float)nty);
   fy1 = fminf(fmaxf(fy1, -1.f), (float)(nty - 1));
   cv.ty0 = (int)fy0;
@@ -254,8 +262,8 @@ __device__ __forceinline__ void cover_row(const Cover& cv, int ty, int TH, int& 
   const float dl = __fsub_rn(__fmul_rn(cv.A, cv.tau), __fmul_rn(cv.det, __fmul_rn(yl, yl)));
   const float xr = __fdiv_rn(__fadd_rn(__fmul_rn(-cv.B, yr), __fsqrt_rn(fmaxf(dr, 0.f))), cv.A);
   const float xl = __fdiv_rn(__fsub_rn(__fmul_rn(-cv.B, yl), __fsqrt_rn(fmaxf(dl, 0.f))), cv.A);
-  float fx0 = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(cv.mx, xl), __fsub_rn(cv.fTW, 0.5f)), cv.fTW));
-  float fx1 = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(cv.mx, xr), 0.5f), cv.fTW));
+  float fx0 = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(cv.mx, xl), __fsub_rn(cv.fTW, 0.5f)), cv.rTW));
+  float fx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(cv.mx, xr), 0.5f), cv.rTW));
   fx0 = fminf(fmaxf(fx0, 0.f), (float)cv.ntx);
   fx1 = fminf(fmaxf(fx1, -1.f), (float)(cv.ntx - 1));
   tx0 = (int)fx0;
@@ -304,8 +312,18 @@ void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* v
                  unsigned long long* status, int n_sm, cudaStream_t s);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();
-void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, Records rec,
+cudaError_t prepare_derive_tc();
+void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
+void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
+                      float* const* dbg_attrs, const CUtensorMap* tmap, uint4* compact, int n_sm, cudaStream_t s);
+int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows);
+void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
+                     const float* const b2[3], std::vector<uint8_t>& img);
+void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                        float* const* dbg_attrs, int n_sm, cudaStream_t s);
+// derived attributes (3 float4 per Gaussian, frame-wide item order) -> records
+void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs, Records rec,
+                    int n_sm, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
