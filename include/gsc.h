@@ -81,7 +81,8 @@ typedef struct {
   uint32_t stereo_unify;     /* 1: cameras with a stereo partner share one Eq. 5-6 derivation */
   uint32_t cache_gaussians;  /* cache capacity in Gaussians per derivation view (0 = 4M) */
   uint32_t max_depth;        /* D_max of Alg. 1 (0 = 10) */
-  uint32_t tile_w, tile_h;   /* blend tile in pixels (0 = 16 x 16): tile_w % 8 == 0, tile_h % 4 == 0, 32 <= tile_w*tile_h <= 256 */
+  uint32_t tile_w, tile_h;   /* blend tile in pixels (0 = 16 x 16): tile_w in {8, 16, 32}, tile_h a power of
+                                two and a multiple of 128 / tile_w, 128 <= tile_w * tile_h <= 1024 */
   uint64_t pair_capacity;    /* initial (tile, Gaussian) pair capacity (0 = 16M); grows */
   float bg[3];               /* background colour */
   uint32_t use_graph;        /* 1: replay the frame's launch sequence as a CUDA graph */

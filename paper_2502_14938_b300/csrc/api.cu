@@ -421,11 +421,12 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.cache_gaussians == 0) cfg.cache_gaussians = 4u << 20;
   if (cfg.pair_capacity == 0) cfg.pair_capacity = 16u << 20;
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
-  const uint32_t nt = cfg.tile_w * cfg.tile_h;
-  if (nt == 0 || nt > 256 || nt % 32 != 0) return GSC_ERR_INVALID_ARG;
-  // 8x4 pixel block per warp; powers of two keep the coverage arithmetic exact
-  if (cfg.tile_w % 8 != 0 || cfg.tile_h % 4 != 0) return GSC_ERR_INVALID_ARG;
-  if ((cfg.tile_w & (cfg.tile_w - 1)) != 0 || (cfg.tile_h & (cfg.tile_h - 1)) != 0) return GSC_ERR_INVALID_ARG;
+  // blend: a lane owns 4 pixels of one column, a warp 32 / tile_w column
+  // strips; powers of two keep the coverage arithmetic exact
+  const uint32_t npx = cfg.tile_w * cfg.tile_h;
+  if (cfg.tile_w != 8 && cfg.tile_w != 16 && cfg.tile_w != 32) return GSC_ERR_INVALID_ARG;
+  if (cfg.tile_h == 0 || (cfg.tile_h & (cfg.tile_h - 1)) != 0) return GSC_ERR_INVALID_ARG;
+  if (npx < 128 || npx > 1024 || cfg.tile_h % ((32 / cfg.tile_w) * 4) != 0) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
   if (cfg.precision == GSC_PREC_FP8 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;

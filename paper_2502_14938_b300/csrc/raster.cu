@@ -195,22 +195,23 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 }
 
 // ------------------------------------------------------------------ blend (K10)
-// One block per (camera, tile), one thread per pixel; warp w owns an 8x4
-// block of pixels.  The tile's records are staged into shared memory one
-// batch at a time, each turned into the tile-local quadratic of its power in
-// the exp2 domain,
-//   log2(o) - (log2 e / 2) q(D) = F + X (D + A' X + B' Y) + Y (E + C' Y),
-// with (X, Y) the pixel centre relative to the tile centre, plus the
-// Gaussian's opacity-aware bounding box.  Each pixel then walks the batch
-// front to back:
+// One block per (camera, tile); each lane owns a vertical strip of 4 pixels
+// (lanes of a warp cover the tile's columns, so a warp owns a band of rows).
+// The tile's records are staged into shared memory one batch at a time,
+// each turned into the tile-local quadratic of its power in the exp2 domain,
+//   log2(o) - (log2 e / 2) q(D) = [F + X (D + A' X)] + Y [(E + B' X) + C' Y],
+// with (X, Y) the pixel centre relative to the tile centre: the bracket in X
+// is per lane, so a pixel costs 2 FMA.  Each pixel walks the batch front to
+// back:
 //   skip if the power is below log2(1/255) (alpha < 1/255);
 //   alpha = min(0.99, 2^power);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
 //   C += c alpha T, T *= 1 - alpha;  out = C + T bg.
-// A warp skips a Gaussian whose box misses its 8x4 pixels, and skips the
-// whole batch once its pixels are finished; the block stops once all are.
+// A warp skips a Gaussian whose opacity-aware box misses its band, and a
+// batch once all its pixels are finished; the block stops once all are.
+constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical)
 constexpr int BLEND_MAX_NT = 256;
-constexpr float LOG2E_HALF = 0.72134752044448170368f;  // log2(e) / 2
+constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
 
 __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
@@ -222,29 +223,33 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restri
   __shared__ float s_ymax[BLEND_MAX_NT];
   const uint32_t tile_key = blockIdx.x;
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
-  const int nt = TW * TH;
+  const int nt = (int)blockDim.x;  // TW * TH / BLEND_PPL
   uint32_t cam = 0;
   while (cam + 1 < fd->n_cams && fd->cam[cam + 1].tile_base <= tile_key) ++cam;
   const CamDev& cd = fd->cam[cam];
   const uint32_t tl = tile_key - cd.tile_base;
   const int tx = (int)(tl % (uint32_t)cd.ntx), ty = (int)(tl / (uint32_t)cd.ntx);
-  // warp -> 8x4 pixel block, lane -> pixel
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-  const int wpr = TW >> 3;  // warp blocks per tile row
-  const int bx = (warp % wpr) * 8, by = (warp / wpr) * 4;
-  const int lx = bx + (lane & 7), ly = by + (lane >> 3);
-  const int px = tx * TW + lx, py = ty * TH + ly;
-  const bool inside = px < cd.W && py < cd.H;
+  const int groups = 32 / TW;                       // strips per column within a warp
+  const int band = groups * BLEND_PPL;              // rows per warp
+  const int lx = lane % TW, ly0 = warp * band + (lane / TW) * BLEND_PPL;
+  const int px = tx * TW + lx, py0 = ty * TH + ly0;
   const float ox = (float)(tx * TW) + 0.5f * (float)TW, oy = (float)(ty * TH) + 0.5f * (float)TH;
-  const float X = ((float)px + 0.5f) - ox, Y = ((float)py + 0.5f) - oy;
-  // the warp's pixel-centre box in tile-local coordinates
-  const float wx0 = ((float)(tx * TW + bx) + 0.5f) - ox, wx1 = wx0 + 7.f;
-  const float wy0 = ((float)(ty * TH + by) + 0.5f) - oy, wy1 = wy0 + 3.f;
+  const float X = ((float)px + 0.5f) - ox;
+  const float Y0 = ((float)py0 + 0.5f) - oy;
+  const float wx0 = ((float)(tx * TW) + 0.5f) - ox, wx1 = wx0 + (float)(TW - 1);
+  const float wy0 = ((float)(ty * TH + warp * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
   const uint2 rg = ranges[tile_key];
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  bool done = !inside;
+  float T[BLEND_PPL], C0[BLEND_PPL], C1[BLEND_PPL], C2[BLEND_PPL];
+  unsigned live = 0;  // bit k: pixel k still blending
+#pragma unroll
+  for (int k = 0; k < BLEND_PPL; ++k) {
+    T[k] = 1.f;
+    C0[k] = C1[k] = C2[k] = 0.f;
+    if (px < cd.W && py0 + k < cd.H) live |= 1u << k;
+  }
   for (uint32_t b = rg.x; b < rg.y; b += (uint32_t)nt) {
-    if (__syncthreads_count(done) == nt) break;
+    if (__syncthreads_count(live != 0) == 0) break;
     const uint32_t idx = b + threadIdx.x;
     if (idx < rg.y) {
       const uint32_t r = vals[idx];
@@ -264,43 +269,52 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restri
     }
     __syncthreads();
     const int cnt = min(nt, (int)(rg.y - b));
-    if (__all_sync(0xffffffffu, done)) continue;
+    if (!__any_sync(0xffffffffu, live != 0)) continue;
     for (int u = 0; u < cnt; ++u) {
       const float4 bb = s_bb[u];
-      if (bb.z < wx0 || bb.y > wx1 || bb.w > wy1 || s_ymax[u] < wy0) continue;  // box misses the warp
-      if (done) continue;
+      if (bb.z < wx0 || bb.y > wx1 || bb.w > wy1 || s_ymax[u] < wy0) continue;  // box misses the band
+      if (!live) continue;
       const float4 q0 = s_q0[u];
       const float4 q1 = s_q1[u];
-      const float t1 = fmaf(q0.w, X, fmaf(q1.x, Y, q0.y));
-      const float t2 = fmaf(q1.y, Y, q0.z);
-      const float p = fmaf(t1, X, fmaf(t2, Y, q0.x));
-      if (p < LOG2_MIN_ALPHA) continue;
-      const float alpha = fminf(0.99f, exp2f(p));
-      const float tt = fmaf(-T, alpha, T);
-      if (tt < 1e-4f) {
-        done = true;
-        continue;
+      const float pa = fmaf(X, fmaf(q0.w, X, q0.y), q0.x);  // F + X (D + A' X)
+      const float pb = fmaf(q1.x, X, q0.z);                 // E + B' X
+#pragma unroll
+      for (int k = 0; k < BLEND_PPL; ++k) {
+        if (!(live & (1u << k))) continue;
+        const float Y = Y0 + (float)k;
+        const float p = fmaf(Y, fmaf(q1.y, Y, pb), pa);
+        if (p < LOG2_MIN_ALPHA) continue;
+        const float alpha = fminf(0.99f, exp2f(p));
+        const float tt = fmaf(-T[k], alpha, T[k]);
+        if (tt < 1e-4f) {
+          live &= ~(1u << k);
+          continue;
+        }
+        const float w = alpha * T[k];
+        C0[k] = fmaf(q1.z, w, C0[k]);
+        C1[k] = fmaf(q1.w, w, C1[k]);
+        C2[k] = fmaf(bb.x, w, C2[k]);
+        T[k] = tt;
       }
-      const float w = alpha * T;
-      C0 = fmaf(q1.z, w, C0);
-      C1 = fmaf(q1.w, w, C1);
-      C2 = fmaf(bb.x, w, C2);
-      T = tt;
     }
   }
-  if (inside) {
-    float* out = reinterpret_cast<float*>(fin->out_rgb[cam]);
+  float* out = reinterpret_cast<float*>(fin->out_rgb[cam]);
+  float* outT = reinterpret_cast<float*>(fin->out_T[cam]);
+#pragma unroll
+  for (int k = 0; k < BLEND_PPL; ++k) {
+    const int py = py0 + k;
+    if (px >= cd.W || py >= cd.H) continue;
     const size_t p = ((size_t)py * cd.W + px) * 3;
-    out[p + 0] = C0 + T * fin->bg[0];
-    out[p + 1] = C1 + T * fin->bg[1];
-    out[p + 2] = C2 + T * fin->bg[2];
-    if (fin->out_T[cam]) reinterpret_cast<float*>(fin->out_T[cam])[(size_t)py * cd.W + px] = T;
+    out[p + 0] = C0[k] + T[k] * fin->bg[0];
+    out[p + 1] = C1[k] + T[k] * fin->bg[1];
+    out[p + 2] = C2[k] + T[k] * fin->bg[2];
+    if (outT) outT[(size_t)py * cd.W + px] = T[k];
   }
 }
 
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
                   uint32_t total_tiles, uint32_t tile_threads, cudaStream_t s) {
-  k_blend<<<total_tiles, tile_threads, 0, s>>>(fd, ranges, vals, rec, fin);
+  k_blend<<<total_tiles, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
 }
 
 }  // namespace gsc
