@@ -1,0 +1,127 @@
+"""Cache-centric reuse of derived Gaussians (Sec. 4, Alg. 1, Eq. 4): the
+oracle's plain simulation of the policy, one frame at a time.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py).
+
+Readings (the paper gives the algorithm's branches, not its data layout):
+- A cache line holds the derived attributes of one anchor's k Gaussians in
+  float16 (round to nearest even), the anchor id and the frame it was decoded
+  in; anchors map to lines through a per-anchor index ("the anchor indices
+  are translated to the cache indices by index mapping", Sec. 4).
+- Reuse depth d: a line decoded `age` frames ago is reused iff age <= d
+  ("results of the previous d frames").  Lines older than the maximum depth
+  D_max are invalid (Alg. 1, "reach max cache reuse depth -> invalidate").
+- A visible anchor is a hit (reuse), a refresh (valid line, too old for the
+  current depth: decoded again into the same line) or new (no valid line:
+  decoded, and given the next free line).  Free lines (never used, or past
+  D_max) are handed out in ascending line order to new anchors in ascending
+  anchor order; new anchors left without a line are decoded but not cached.
+  The 0% / 100% duplicate branches of Alg. 1 are the cases "all new" and
+  "all hits".
+- Eq. 4 with the linear guiding function of the experiments: after a frame
+  with V visible anchors of which m were decoded (the update rate u = m/V,
+  equal to the miss rate), the next depth is round(D_max (1 - u)) clamped to
+  [1, D_max], computed in integers as floor((2 D_max (V - m) + V) / (2 V)).
+- In its own frame a decoded anchor is rendered with its fresh attributes;
+  a hit is rendered with the cached float16 attributes.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ATTR = 11
+
+
+def next_depth(depth: int, visible: int, misses: int, d_max: int) -> int:
+    """Linear guiding function of Eq. 4 (integer rounding, half up)."""
+    if visible <= 0:
+        return depth
+    v, m = int(visible), int(misses)
+    d = (2 * d_max * (v - m) + v) // (2 * v)
+    return int(min(max(d, 1), d_max))
+
+
+class CacheSim:
+    """Alg. 1 for one derivation view."""
+
+    def __init__(self, n_anchors: int, slots: int, k: int = 10, max_depth: int = 10):
+        self.k = k
+        self.D = int(max_depth)
+        self.slot_of = np.full(n_anchors, -1, np.int64)
+        self.slot_anchor = np.full(slots, -1, np.int64)
+        self.slot_frame = np.zeros(slots, np.int64)
+        self.slot_attr = np.zeros((slots, k, ATTR), np.float16)
+        self.t = 0
+        self.depth = self.D
+
+    def reset(self):
+        self.slot_of[:] = -1
+        self.slot_anchor[:] = -1
+        self.slot_frame[:] = 0
+        self.t = 0
+        self.depth = self.D
+
+    def step(self, ids: np.ndarray):
+        """Classify the ascending visible ids of one frame.  Returns
+        (hit mask, line per anchor or -1, depth used this frame)."""
+        self.t += 1
+        t = self.t
+        ids = np.asarray(ids, np.int64)
+        s = self.slot_of[ids]
+        valid = s >= 0
+        sv = np.where(valid, s, 0)
+        valid &= self.slot_anchor[sv] == ids
+        age = t - self.slot_frame[sv]
+        valid &= age <= self.D
+        hit = valid & (age <= self.depth)
+        line = np.where(valid, s, -1)
+        free = np.nonzero((self.slot_anchor < 0) | (t - self.slot_frame > self.D))[0]
+        new_idx = np.nonzero(~valid)[0]
+        n = min(len(new_idx), len(free))
+        line[new_idx[:n]] = free[:n]
+        # the lines of every decoded anchor now belong to it and to this frame
+        dec = (~hit) & (line >= 0)
+        self.slot_anchor[line[dec]] = ids[dec]
+        self.slot_frame[line[dec]] = t
+        self.slot_of[ids[dec]] = line[dec]
+        used = self.depth
+        self.last = dict(visible=len(ids), misses=int((~hit).sum()), hits=int(hit.sum()),
+                         new=len(new_idx), cached_new=n)
+        self.depth = next_depth(self.depth, len(ids), int((~hit).sum()), self.D)
+        return hit, line, used
+
+    def store(self, line: np.ndarray, decoded: np.ndarray, attrs: np.ndarray):
+        """Write fresh attributes [n,k,11] of the decoded anchors into their lines (float16)."""
+        sel = decoded & (line >= 0)
+        self.slot_attr[line[sel]] = attrs[sel].astype(np.float16)
+
+    def cached_attrs(self, line: np.ndarray, hit: np.ndarray) -> np.ndarray:
+        return self.slot_attr[line[hit]].astype(np.float64)
+
+
+def cached_derive(model, dcam, sim: CacheSim, quant=None):
+    """The derivation step of one frame in the cached form, for the derivation
+    camera dcam: filtering, the policy, fresh derivation of the decoded
+    anchors, float16 lines for the hits.  Returns (ids, attrs [V,k,11],
+    kept [V,k], hit mask, line per anchor, depth used)."""
+    import oracle
+    ids = oracle.cull(model, dcam)
+    hit, line, used = sim.step(ids)
+    attrs = np.zeros((len(ids), model.k, ATTR), np.float64)
+    miss = ~hit
+    if miss.any():
+        a_m, _ = oracle.derive(model, oracle.camera_center(dcam), ids[miss], quant)
+        attrs[miss] = a_m
+        sim.store(line[miss], np.ones(int(miss.sum()), bool), a_m)
+    if hit.any():
+        attrs[hit] = sim.cached_attrs(line, hit)
+    kept = (attrs[..., 0] > 0).astype(np.uint8)
+    return ids, attrs, kept, hit, line, used
+
+
+def project_view(model, cam, ids, attrs, kept):
+    """Records of one camera from attributes of the visible anchors."""
+    import oracle
+    rec, d32 = oracle.project_records(model, cam, ids, attrs, kept)
+    gid = (np.asarray(ids, np.int64)[:, None] * model.k + np.arange(model.k)[None, :]).reshape(-1)
+    return oracle.ViewResult(ids=ids, attrs=attrs, kept=kept, rec=rec, depth32=d32, gid=gid)
