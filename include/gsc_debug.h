@@ -55,6 +55,14 @@ GSC_API int gsc_debug_ranges(gsc_ctx* ctx, uint32_t* ranges, uint64_t cap, uint6
 /* Final transmittance of camera v, needs GSC_FLAG_DEBUG_T.  Unit: pixels. */
 GSC_API int gsc_debug_final_T(gsc_ctx* ctx, uint32_t v, float* T, uint64_t cap, uint64_t* n);
 
+/* Cache of derivation view d in the reuse forms (Sec. 4, Alg. 1): per visible
+ * anchor of the last frame its line status (line index | 0x80000000 for a
+ * reuse, the line index for a decode into a line, 0x7FFFFFFF for a decode
+ * without a line), and 8 state words: frame counter, depth for the next
+ * frame, misses, new anchors, free lines, visible anchors, D_max, lines.
+ * Unit: visible anchors. */
+GSC_API int gsc_debug_cache(gsc_ctx* ctx, uint32_t d, uint32_t* vstat, uint64_t cap, uint64_t* n, uint32_t* state8);
+
 /* Upper bound on the polls of every bounded device-side wait (0 makes any
  * wait that does not succeed at once give up).  Default 1 << 20. */
 GSC_API int gsc_debug_set_spin_limit(gsc_ctx* ctx, uint32_t limit);

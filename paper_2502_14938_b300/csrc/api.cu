@@ -41,6 +41,8 @@ struct Counters {  // tail of FrameDev read back after a frame
   uint32_t n_valid, n_pairs, n_pairs_used, err;
   uint32_t n_records_need;
   uint32_t n_big;
+  uint32_t n_derived;
+  uint32_t cache_depth;
 };
 
 }  // namespace
@@ -104,6 +106,11 @@ struct gsc_ctx {
   uint4* compact = nullptr;
   uint64_t compact_rows = 0;
   CUtensorMap tmap_feat{};
+  // caches of derived Gaussians, one per derivation view (Sec. 4)
+  int n_caches = 0;
+  CacheDev h_caches[MAX_CACHES] = {};
+  uint32_t cache_na[MAX_CACHES] = {};  // anchors of each cache's model
+  CacheDev* d_caches = nullptr;
 };
 
 namespace {
@@ -171,8 +178,11 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096
-  const uint32_t need = std::max((ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 4095u) / 4096u) + 1u;
+  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096 (the
+  // cache scans run over visible anchors and over cache lines)
+  const uint32_t lines = std::max<uint32_t>(ctx->cfg.cache_gaussians / K, 1u);
+  const uint32_t need = std::max({(ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 4095u) / 4096u,
+                                  (ctx->vis_cap + 4095u) / 4096u, (lines + 4095u) / 4096u}) + 1u;
   if (need > ctx->status_tiles) {
     int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
     if (r) return r;
@@ -216,6 +226,70 @@ int alloc_pairs(gsc_ctx* ctx, uint32_t cap) {
   return ensure_status(ctx);
 }
 
+// ------------------------------------------------------------------ caches (Sec. 4)
+void free_cache(CacheDev& c) {
+  void* p[] = {c.slot_of, c.slot_anchor, c.slot_frame, c.slot_attr, c.vstat, c.new_flag, c.new_rank,
+               c.free_flag, c.free_rank, c.free_list, c.miss, c.state};
+  for (void* q : p) dfree(q);
+  c = CacheDev{};
+}
+
+// Empty cache: no anchor has a line, every line unused, t = 0, depth = D_max.
+int init_cache(gsc_ctx* ctx, CacheDev& c, uint32_t n_anchors) {
+  if (n_anchors) CK(cudaMemset(c.slot_of, 0xFF, (size_t)n_anchors * 4));
+  CK(cudaMemset(c.slot_anchor, 0xFF, (size_t)c.S * 4));
+  CK(cudaMemset(c.slot_frame, 0, (size_t)c.S * 4));
+  uint32_t st[CS_WORDS] = {0};
+  st[CS_DEPTH] = ctx->cfg.max_depth;
+  st[CS_DMAX] = ctx->cfg.max_depth;
+  st[CS_S] = c.S;
+  CK(cudaMemcpy(c.state, st, sizeof st, cudaMemcpyHostToDevice));
+  return GSC_OK;
+}
+
+// One cache per derivation view of the current cameras (the views are found
+// as k_frame_begin finds them: a stereo pair under stereo_unify is one view).
+int setup_caches(gsc_ctx* ctx) {
+  for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
+  ctx->n_caches = 0;
+  if (ctx->cfg.reuse == GSC_REUSE_OFF) return GSC_OK;
+  const size_t n = ctx->cams.size();
+  std::vector<int> dof(n, -1);
+  std::vector<uint32_t> dv_model;
+  for (size_t c = 0; c < n; ++c) {
+    if (dof[c] >= 0) continue;
+    const int p = ctx->cams[c].stereo_partner;
+    const bool pair = ctx->cfg.stereo_unify && p > (int)c && p < (int)n && ctx->cams[p].stereo_partner == (int)c;
+    dof[c] = (int)dv_model.size();
+    if (pair) dof[p] = (int)dv_model.size();
+    dv_model.push_back(ctx->cams[c].model_id);
+  }
+  if (dv_model.size() > (size_t)MAX_CACHES)
+    return fail(ctx, GSC_ERR_INVALID_ARG, "at most %d derivation views with a cache", MAX_CACHES);
+  const uint32_t S = std::max<uint32_t>(ctx->cfg.cache_gaussians / K, 1u);
+  const uint32_t vcap = ctx->vis_cap;
+  for (size_t d = 0; d < dv_model.size(); ++d) {
+    CacheDev& c = ctx->h_caches[d];
+    const uint32_t na = ctx->models[dv_model[d]].n;
+    c.S = S;
+    c.active = 1;
+    int r;
+    if ((r = dalloc(ctx, &c.slot_of, std::max(na, 1u))) || (r = dalloc(ctx, &c.slot_anchor, S)) ||
+        (r = dalloc(ctx, &c.slot_frame, S)) || (r = dalloc(ctx, &c.slot_attr, (size_t)S * K * 3)) ||
+        (r = dalloc(ctx, &c.vstat, vcap)) || (r = dalloc(ctx, &c.new_flag, vcap)) ||
+        (r = dalloc(ctx, &c.new_rank, vcap)) || (r = dalloc(ctx, &c.free_flag, S)) ||
+        (r = dalloc(ctx, &c.free_rank, S)) || (r = dalloc(ctx, &c.free_list, S)) || (r = dalloc(ctx, &c.miss, vcap)) ||
+        (r = dalloc(ctx, &c.state, CS_WORDS)))
+      return r;
+    if ((r = init_cache(ctx, c, na))) return r;
+    ctx->cache_na[d] = na;
+    ctx->n_caches = (int)d + 1;
+  }
+  if (!ctx->d_caches) CK(cudaMalloc((void**)&ctx->d_caches, sizeof(CacheDev) * MAX_CACHES));
+  CK(cudaMemcpy(ctx->d_caches, ctx->h_caches, sizeof(CacheDev) * MAX_CACHES, cudaMemcpyHostToDevice));
+  return GSC_OK;
+}
+
 // The launch sequence of one frame (everything after the FrameIn upload).
 void enqueue_sequence(gsc_ctx* ctx) {
   cudaStream_t s = ctx->stream;
@@ -226,14 +300,18 @@ void enqueue_sequence(gsc_ctx* ctx) {
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
   for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
   launch_plan(fd, ctx->rec_cap, s);
+  CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
+  if (caches)
+    launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->st_scan, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
     if (ctx->cfg.precision == GSC_PREC_BF16)
-      launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, &ctx->tmap_feat,
+      launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, &ctx->tmap_feat,
                        ctx->compact, ctx->n_sm, s);
     else
-      launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, ctx->n_sm, s);
-  launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, ctx->rec, ctx->n_sm, s);
+      launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->n_sm, s);
+  launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->n_sm, s);
+  if (caches) launch_cache_policy(ctx->d_caches, ctx->n_caches, fd, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
@@ -350,11 +428,11 @@ void fill_stats(gsc_ctx* ctx, gsc_frame_stats* st) {
   uint64_t vis = 0;
   for (uint32_t d = 0; d < MAXV; ++d) vis += c.vis_count[d];
   st->visible_anchors = vis;
-  st->derived_anchors = c.n_items;
+  st->derived_anchors = c.n_derived;
   st->records = c.n_records;
   st->valid_records = c.n_valid;
   st->pairs = c.n_pairs;
-  st->cache_depth = 0;
+  st->cache_depth = ctx->n_caches ? c.cache_depth : 0;
   st->error_flags = c.err;
   if (ctx->timing) {
     float tot = 0.f;
@@ -428,7 +506,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.tile_h == 0 || (cfg.tile_h & (cfg.tile_h - 1)) != 0) return GSC_ERR_INVALID_ARG;
   if (npx < 128 || npx > 1024 || cfg.tile_h % ((32 / cfg.tile_w) * 4) != 0) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
-  if (cfg.precision == GSC_PREC_FP8 || cfg.reuse != GSC_REUSE_OFF) return GSC_ERR_UNIMPLEMENTED;
+  if (cfg.precision == GSC_PREC_FP8 || cfg.reuse == GSC_REUSE_LEARNED) return GSC_ERR_UNIMPLEMENTED;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
 
   gsc_ctx* ctx = new (std::nothrow) gsc_ctx();
@@ -480,6 +558,8 @@ void gsc_destroy(gsc_ctx* ctx) {
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs};
   for (void* p : bufs) dfree(p);
+  for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
+  dfree(ctx->d_caches);
   for (int i = 0; i < MAXV; ++i) {
     dfree(ctx->d_img[i]);
     dfree(ctx->d_T[i]);
@@ -658,7 +738,9 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
       invalidate_graph(ctx);
     }
   }
-  // records: worst case (every anchor visible), capped at 64M then grown on demand
+  // caches of derived Gaussians (reuse forms): fresh for a new camera layout
+  if ((r = setup_caches(ctx))) return r;
+  // records: worst case (every anchor visible), capped at 8M then grown on demand
   unsigned long long worst = 0;
   for (const auto& c : ctx->cams) worst += (unsigned long long)K * ctx->models[c.model_id].n;
   const uint32_t want = (uint32_t)std::min<unsigned long long>(std::max<unsigned long long>(worst, 1024ull), 8ull << 20);
@@ -719,10 +801,31 @@ int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* 
   return GSC_OK;
 }
 
+static int dbg_sync(gsc_ctx* ctx);
+static int dbg_copy(gsc_ctx* ctx, void* dst, const void* src, uint64_t count, uint64_t cap, size_t elem);
+
 int gsc_cache_reset(gsc_ctx* ctx) {
   if (!ctx) return GSC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < ctx->n_caches; ++i) {
+    int r = init_cache(ctx, ctx->h_caches[i], ctx->cache_na[i]);
+    if (r) return r;
+  }
   ctx->err.clear();
-  return GSC_OK;  // no cache in the plain forms
+  return GSC_OK;
+}
+
+int gsc_debug_cache(gsc_ctx* ctx, uint32_t d, uint32_t* vstat, uint64_t cap, uint64_t* n, uint32_t* state8) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (d >= (uint32_t)ctx->n_caches || !n) return fail(ctx, GSC_ERR_INVALID_ARG, "no cache for view %u", d);
+  const CacheDev& c = ctx->h_caches[d];
+  uint32_t st[CS_WORDS];
+  CK(cudaMemcpy(st, c.state, sizeof st, cudaMemcpyDeviceToHost));
+  if (state8)
+    for (int i = 0; i < CS_WORDS; ++i) state8[i] = st[i];
+  *n = st[CS_VIS];
+  return dbg_copy(ctx, vstat, c.vstat, st[CS_VIS], cap, 4);
 }
 
 int gsc_synchronize(gsc_ctx* ctx) {

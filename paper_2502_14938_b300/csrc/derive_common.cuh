@@ -3,6 +3,8 @@
 // epilogue of Eq. 3 and the EWA projection + exact tile count (Eq. 1-2,
 // Sec. 6) that turns one derived Gaussian into one record per camera.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "gsc_internal.cuh"
 
 namespace gsc {
@@ -24,11 +26,17 @@ struct DViewSet {
   int d[MAXV];
   uint32_t base[MAXV + 1];  // prefix of visible counts over the listed views
   uint32_t gbase[MAXV];     // frame-wide item index of each listed view's first anchor
+  const uint32_t* miss[MAXV];  // cached views: visible indices to decode (else null: all)
+  const uint32_t* vstat[MAXV]; // cached views: line status per visible index
+  uint2* lattr[MAXV];          // cached views: float16 line attributes
   float pc[MAXV][6];        // double-float centre of each derivation camera
   ProjCam cam[MAXV][2];     // cameras fed by each view (cam = 0xFFFFFFFF unused)
 };
 
-__device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd, int model) {
+// Work of the decoder: every visible anchor of the model's views, or for a
+// view with a cache only its misses.
+__device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd, int model,
+                                                const CacheDev* caches) {
   int nd = 0;
   uint32_t acc = 0;
   for (uint32_t d = 0; d < fd->n_dviews; ++d) {
@@ -36,7 +44,11 @@ __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd,
     S.d[nd] = (int)d;
     S.base[nd] = acc;
     S.gbase[nd] = fd->item_base[d];
-    acc += fd->vis_count[d];
+    const bool cached = caches && d < (uint32_t)MAX_CACHES && caches[d].active;
+    S.miss[nd] = cached ? caches[d].miss : nullptr;
+    S.vstat[nd] = cached ? caches[d].vstat : nullptr;
+    S.lattr[nd] = cached ? caches[d].slot_attr : nullptr;
+    acc += cached ? caches[d].state[CS_MISSES] : fd->vis_count[d];
     for (int u = 0; u < 3; ++u) {
       S.pc[nd][u] = fd->dcam[d].pc[u];
       S.pc[nd][3 + u] = fd->dcam[d].pc_lo[u];
@@ -135,10 +147,16 @@ __device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uin
 //   alpha = tanh(z_op) (the Gaussian is kept iff alpha > 0), c = sigmoid(z_col),
 //   s = s_a sigmoid(z_cov[0..2]) (the per-anchor scale broadcast to the
 //   Gaussian), q = z_cov[3..6] / |.| (identity below 1e-12).
-// Stored as 3 float4 at attrs[3 idx ..]: (alpha, c), (s, q_w), (q_x, q_y, q_z, 0).
+// Stored as 3 float4 at attrs[3 idx ..]: (alpha, c), (s, q_w), (q_x, q_y, q_z, 0),
+// and as 12 float16 (round to nearest even) at line[0..2] when given.
 // dbg (optional): the 11 attributes at dbg[11 (i K + j)].
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 __device__ __forceinline__ void gaussian_activate_store(const float z[11], int j, uint32_t i, float sa, float4* attrs,
-                                                        size_t idx, float* dbg) {
+                                                        size_t idx, float* dbg, uint2* line = nullptr) {
   const float alpha = tanhf(z[0]);
   float col[3], s[3], q[4];
 #pragma unroll
@@ -154,9 +172,15 @@ __device__ __forceinline__ void gaussian_activate_store(const float z[11], int j
     for (int u = 0; u < 4; ++u) q[u] = z[7 + u] * iq;
   }
   // alpha carries the mask: tanh(z) > 0 exactly when z > 0
-  attrs[3 * idx + 0] = make_float4(z[0] > 0.f ? alpha : -1.f, col[0], col[1], col[2]);
+  const float am = z[0] > 0.f ? alpha : -1.f;
+  attrs[3 * idx + 0] = make_float4(am, col[0], col[1], col[2]);
   attrs[3 * idx + 1] = make_float4(s[0], s[1], s[2], q[0]);
   attrs[3 * idx + 2] = make_float4(q[1], q[2], q[3], 0.f);
+  if (line) {
+    line[0] = make_uint2(pack_half2(am, col[0]), pack_half2(col[1], col[2]));
+    line[1] = make_uint2(pack_half2(s[0], s[1]), pack_half2(s[2], q[0]));
+    line[2] = make_uint2(pack_half2(q[1], q[2]), pack_half2(q[3], 0.f));
+  }
   if (dbg) {
     float* o = dbg + ((size_t)i * K + j) * 11;
     o[0] = alpha;

@@ -66,7 +66,8 @@ __device__ __forceinline__ void df_dots(const float (&h)[NH], const float* __res
 
 __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restrict__ models, int model,
                                                          FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
-                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs) {
+                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
+                                                         const CacheDev* __restrict__ caches) {
   extern __shared__ __align__(16) float s_dyn[];
   float* s_w = s_dyn;
   float* s_h = s_dyn + DF_W;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
     for (int i = threadIdx.x; i < W_FLOATS / 4; i += DF_NT) reinterpret_cast<float4*>(s_w)[i] = src[i];
     for (int i = (W_FLOATS / 4) * 4 + threadIdx.x; i < W_FLOATS; i += DF_NT) s_w[i] = md.w32[i];
   }
-  if (threadIdx.x == 0) build_dview_set(S, fd, model);
+  if (threadIdx.x == 0) build_dview_set(S, fd, model, caches);
   __syncthreads();
   const int nd = S.nd;
   const uint32_t total = S.base[nd];
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
       if (item < total) {
         ld = 0;
         while (item >= S.base[ld + 1]) ++ld;
-        const uint32_t vi = item - S.base[ld];
+        const uint32_t u = item - S.base[ld];
+        const uint32_t vi = S.miss[ld] ? S.miss[ld][u] : u;
         const uint32_t a = vis[S.d[ld]][vi];
         M.anchor[t] = a;
         M.vi[t] = vi;
@@ -195,7 +197,12 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
       for (int u = 0; u < 7; ++u) z[4 + u] = zr[4 * K + 7 * j + u];
       float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
       const size_t idx = (size_t)(S.gbase[ld] + M.vi[a]) * K + j;
-      if (idx < rec_cap) gaussian_activate_store(z, j, M.vi[a], M.sa[a], attrs, idx, dbg);
+      uint2* line = nullptr;
+      if (S.vstat[ld]) {
+        const uint32_t st = S.vstat[ld][M.vi[a]];
+        if (st != LINE_NONE && !(st & LINE_HIT)) line = S.lattr[ld] + ((size_t)st * K + j) * 3;
+      }
+      if (idx < rec_cap) gaussian_activate_store(z, j, M.vi[a], M.sa[a], attrs, idx, dbg, line);
     }
     __syncthreads();
   }
@@ -206,8 +213,8 @@ cudaError_t prepare_derive_f32() {
 }
 
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                       float* const* dbg_attrs, int n_sm, cudaStream_t s) {
-  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs);
+                       float* const* dbg_attrs, const CacheDev* caches, int n_sm, cudaStream_t s) {
+  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches);
 }
 
 }  // namespace gsc

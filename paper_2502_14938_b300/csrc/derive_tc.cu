@@ -125,31 +125,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // Compact BF16 features of this model's visible anchors, in the model-local
 // item order of the derivation kernel (rows of 64 bytes, the TMA source).
 __global__ void k_gather_bf16(const ModelDev* __restrict__ models, int model, const FrameDev* __restrict__ fd,
-                              uint32_t* const* __restrict__ vis, uint4* __restrict__ out) {
-  __shared__ int s_d[MAXV];
-  __shared__ uint32_t s_b[MAXV + 1];
-  __shared__ int s_nd;
-  if (threadIdx.x == 0) {
-    int nd = 0;
-    uint32_t acc = 0;
-    for (uint32_t d = 0; d < fd->n_dviews; ++d) {
-      if (fd->dcam[d].model != model) continue;
-      s_d[nd] = (int)d;
-      s_b[nd] = acc;
-      acc += fd->vis_count[d];
-      ++nd;
-    }
-    s_b[nd] = acc;
-    s_nd = nd;
-  }
+                              uint32_t* const* __restrict__ vis, uint4* __restrict__ out,
+                              const CacheDev* __restrict__ caches) {
+  __shared__ DViewSet S;
+  if (threadIdx.x == 0) build_dview_set(S, fd, model, caches);
   __syncthreads();
   const uint4* src = reinterpret_cast<const uint4*>(models[model].feat_bf16);
-  const uint32_t total = s_b[s_nd];
+  const uint32_t total = S.base[S.nd];
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total * 4u; u += gridDim.x * blockDim.x) {
     const uint32_t item = u >> 2, part = u & 3u;
     int ld = 0;
-    while (item >= s_b[ld + 1]) ++ld;
-    const uint32_t a = vis[s_d[ld]][item - s_b[ld]];
+    while (item >= S.base[ld + 1]) ++ld;
+    const uint32_t w = item - S.base[ld];
+    const uint32_t vi = S.miss[ld] ? S.miss[ld][w] : w;
+    const uint32_t a = vis[S.d[ld]][vi];
     out[u] = src[(size_t)a * 4 + part];
   }
 }
@@ -158,6 +147,7 @@ __global__ void k_gather_bf16(const ModelDev* __restrict__ models, int model, co
 __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restrict__ models, int model,
                                                         FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
+                                                        const CacheDev* __restrict__ caches,
                                                         const __grid_constant__ CUtensorMap tmap_feat) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ DViewSet S;
@@ -184,7 +174,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     if (t < TC_M) z5[t] = make_uint4(0, 0, 0, 0);
   }
   if (t == 0) {
-    build_dview_set(S, fd, model);
+    build_dview_set(S, fd, model, caches);
     mbar_init(tma_bar, 1);
     mbar_init(mma_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -219,7 +209,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       if (item < total) {
         ld = 0;
         while (item >= S.base[ld + 1]) ++ld;
-        const uint32_t vi = item - S.base[ld];
+        const uint32_t w = item - S.base[ld];
+        const uint32_t vi = S.miss[ld] ? S.miss[ld][w] : w;
         const uint32_t a = vis[S.d[ld]][vi];
         m_anchor[t] = a;
         m_vi[t] = vi;
@@ -324,7 +315,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         for (int u = 0; u < 11; ++u) z[u] = v[u] + s_b2[16 * j + u];
         float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
         const size_t idx = (size_t)(S.gbase[ld] + m_vi[row]) * K + j;
-        if (idx < rec_cap) gaussian_activate_store(z, j, m_vi[row], m_sa[row], attrs, idx, dbg);
+        uint2* line = nullptr;
+        if (S.vstat[ld]) {
+          const uint32_t st = S.vstat[ld][m_vi[row]];
+          if (st != LINE_NONE && !(st & LINE_HIT)) line = S.lattr[ld] + ((size_t)st * K + j) * 3;
+        }
+        if (idx < rec_cap) gaussian_activate_store(z, j, m_vi[row], m_sa[row], attrs, idx, dbg, line);
       }
     }
     tc_fence_before();
@@ -419,10 +415,10 @@ void pack_tc_weights(const float* const W1[3], const float* const b1[3], const f
 }
 
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CUtensorMap* tmap, uint4* compact, int n_sm,
-                      cudaStream_t s) {
-  k_gather_bf16<<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact);
-  k_derive_tc<<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, *tmap);
+                      float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
+                      int n_sm, cudaStream_t s) {
+  k_gather_bf16<<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
+  k_derive_tc<<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
 }
 
 }  // namespace gsc

@@ -122,8 +122,9 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin) {
   fd->n_pairs = 0;
   fd->n_pairs_used = 0;
   fd->n_big = 0;
+  fd->n_derived = 0;
   fd->err = 0;
-  for (int i = 0; i < 32; ++i) fd->ctr[i] = 0;
+  for (int i = 0; i < 64; ++i) fd->ctr[i] = 0;
 }
 
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s) {
@@ -137,7 +138,7 @@ __global__ void k_bump_epoch(FrameDev* fd, uint32_t spin_limit) {
   fd->spin_limit = spin_limit;
   fd->err = 0;
   fd->n_valid = 0;
-  for (int i = 0; i < 32; ++i) fd->ctr[i] = 0;
+  for (int i = 0; i < 64; ++i) fd->ctr[i] = 0;
 }
 
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s) {
@@ -309,6 +310,7 @@ __global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {
   }
   fd->item_base[fd->n_dviews] = acc;
   fd->n_items = acc;
+  fd->n_derived = acc;  // lowered by the cache policy when views reuse
   unsigned long long r = 0;
   for (uint32_t c = 0; c < fd->n_cams; ++c) {
     fd->rec_base[c] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);

@@ -104,7 +104,9 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t err;
   uint32_t n_records_need;      // records the frame asked for (may exceed capacity)
   uint32_t n_big;               // records in the key generation's large-record list
-  uint32_t ctr[32];             // dynamic tile counters of look-back kernels
+  uint32_t n_derived;           // anchors decoded this frame (visible minus cache hits)
+  uint32_t cache_depth;         // reuse depth of derivation view 0 for the next frame
+  uint32_t ctr[64];             // dynamic tile counters of look-back kernels
 };
 
 struct ModelDev {
@@ -121,6 +123,27 @@ struct ModelDev {
   const float* w32;       // packed weights, W_FLOATS
   const void* feat_bf16;  // [N][32] bf16 (tensor-core forms)
   const void* w_tc;       // tensor-core weight image (40,960 bytes)
+};
+
+// One derivation view's cache of derived Gaussians (Sec. 4).
+enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_WORDS };
+constexpr uint32_t LINE_HIT = 0x80000000u;   // vstat: the anchor reuses its line
+constexpr uint32_t LINE_NONE = 0x7FFFFFFFu;  // vstat: decoded without a line
+struct CacheDev {
+  uint32_t* slot_of;      // [N of the model] line of an anchor (0xFFFFFFFF none)
+  uint32_t* slot_anchor;  // [S] anchor of a line (0xFFFFFFFF unused)
+  uint32_t* slot_frame;   // [S] frame of the line's last decode
+  uint2* slot_attr;       // [S][K][3]: 12 float16 per Gaussian (alpha, c, s, q, 0)
+  uint32_t* vstat;        // [visible] line | LINE_HIT, or LINE_NONE
+  uint32_t* new_flag;     // [visible]
+  uint32_t* new_rank;     // [visible]
+  uint32_t* free_flag;    // [S]
+  uint32_t* free_rank;    // [S]
+  uint32_t* free_list;    // [S]
+  uint32_t* miss;         // [visible] visible indices to decode
+  uint32_t* state;        // [CS_WORDS]
+  uint32_t S;
+  uint32_t active;
 };
 
 struct Records {
@@ -303,7 +326,8 @@ struct SortBufs {
 };
 
 // counter / epoch slots of the look-back kernels within one frame
-enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28 };
+enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28, SLOT_CACHE = 32 };
+constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
@@ -315,15 +339,20 @@ cudaError_t prepare_derive_f32();
 cudaError_t prepare_derive_tc();
 void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CUtensorMap* tmap, uint4* compact, int n_sm, cudaStream_t s);
+                      float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
+                      int n_sm, cudaStream_t s);
 int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows);
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img);
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                       float* const* dbg_attrs, int n_sm, cudaStream_t s);
-// derived attributes (3 float4 per Gaussian, frame-wide item order) -> records
-void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs, Records rec,
-                    int n_sm, cudaStream_t s);
+                       float* const* dbg_attrs, const CacheDev* caches, int n_sm, cudaStream_t s);
+// derived attributes (3 float4 per Gaussian, frame-wide item order; cache
+// hits from their lines) -> records
+void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
+                    const CacheDev* caches, Records rec, int n_sm, cudaStream_t s);
+void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
+                        unsigned long long* scan_status, int n_sm, cudaStream_t s);
+void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,

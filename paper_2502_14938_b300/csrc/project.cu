@@ -15,15 +15,20 @@ constexpr int PJ_NT = 256;
 
 __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ models, FrameDev* __restrict__ fd,
                                                    uint32_t* const* __restrict__ vis, const float4* __restrict__ attrs,
-                                                   Records rec) {
+                                                   const CacheDev* __restrict__ caches, Records rec) {
   __shared__ uint32_t s_ibase[MAXV + 1];
   __shared__ int s_model[MAXV];
+  __shared__ const uint32_t* s_vstat[MAXV];
+  __shared__ const uint2* s_lattr[MAXV];
   __shared__ ProjCam s_cam[MAXV][2];
   if (threadIdx.x == 0) {
     const int nd = (int)fd->n_dviews;
     for (int d = 0; d < nd; ++d) {
       s_ibase[d] = fd->item_base[d];
       s_model[d] = fd->dcam[d].model;
+      const bool cached = caches && d < MAX_CACHES && caches[d].active;
+      s_vstat[d] = cached ? caches[d].vstat : nullptr;
+      s_lattr[d] = cached ? caches[d].slot_attr : nullptr;
       for (int e = 0; e < 2; ++e) {
         const int ci = fd->dview_cam[d][e];
         ProjCam& pc = s_cam[d][e];
@@ -57,9 +62,25 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
     const uint32_t vi = item - s_ibase[d];
     const ModelDev& md = models[s_model[d]];
     const uint32_t a = vis[d][vi];
-    const float4 a0 = attrs[3 * (size_t)g + 0];
-    const float4 a1 = attrs[3 * (size_t)g + 1];
-    const float4 a2 = attrs[3 * (size_t)g + 2];
+    float4 a0, a1, a2;
+    const uint32_t st = s_vstat[d] ? s_vstat[d][vi] : LINE_NONE;
+    if (st & LINE_HIT) {  // reuse: the float16 line decoded in an earlier frame
+      const uint2* l = s_lattr[d] + ((size_t)(st & ~LINE_HIT) * K + j) * 3;
+      const uint2 h0 = l[0], h1 = l[1], h2 = l[2];
+      const float2 x0 = __half22float2(*reinterpret_cast<const __half2*>(&h0.x));
+      const float2 x1 = __half22float2(*reinterpret_cast<const __half2*>(&h0.y));
+      const float2 x2 = __half22float2(*reinterpret_cast<const __half2*>(&h1.x));
+      const float2 x3 = __half22float2(*reinterpret_cast<const __half2*>(&h1.y));
+      const float2 x4 = __half22float2(*reinterpret_cast<const __half2*>(&h2.x));
+      const float2 x5 = __half22float2(*reinterpret_cast<const __half2*>(&h2.y));
+      a0 = make_float4(x0.x, x0.y, x1.x, x1.y);
+      a1 = make_float4(x2.x, x2.y, x3.x, x3.y);
+      a2 = make_float4(x4.x, x4.y, x5.x, x5.y);
+    } else {
+      a0 = attrs[3 * (size_t)g + 0];
+      a1 = attrs[3 * (size_t)g + 1];
+      a2 = attrs[3 * (size_t)g + 2];
+    }
     const float alpha = a0.x;
     const bool kept = alpha > 0.f;
     const float col[3] = {a0.y, a0.z, a0.w};
@@ -82,9 +103,9 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
   }
 }
 
-void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs, Records rec,
-                    int n_sm, cudaStream_t s) {
-  k_project<<<n_sm * 8, PJ_NT, 0, s>>>(models, fd, vis, attrs, rec);
+void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
+                    const CacheDev* caches, Records rec, int n_sm, cudaStream_t s) {
+  k_project<<<n_sm * 8, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec);
 }
 
 }  // namespace gsc

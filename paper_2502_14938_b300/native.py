@@ -105,6 +105,7 @@ def lib():
             "gsc_debug_scan": (I, [P, P, U64, P]),
             "gsc_debug_wait_timeout": (I, [P, U32]),
             "gsc_scan_u32_noalloc": (I, [P, P, U64, P, P]),
+            "gsc_debug_cache": (I, [P, U32, P, U64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -327,6 +328,16 @@ class Renderer:
         T = np.zeros(max(n.value, 1), np.float32)
         self._check(lib().gsc_debug_final_T(self.ctx, v, _p(T), n.value, C.byref(n)))
         return T[: n.value]
+
+    def debug_cache(self, d: int):
+        """(line status per visible anchor, state dict) of derivation view d's cache."""
+        n = C.c_uint64()
+        st = (C.c_uint32 * 8)()
+        self._check(lib().gsc_debug_cache(self.ctx, d, None, 0, C.byref(n), st))
+        v = np.zeros(max(n.value, 1), np.uint32)
+        self._check(lib().gsc_debug_cache(self.ctx, d, _p(v), n.value, C.byref(n), st))
+        keys = ["t", "depth", "misses", "new", "free", "visible", "d_max", "lines"]
+        return v[: n.value], dict(zip(keys, list(st)))
 
     def debug_set_spin_limit(self, limit: int):
         self._check(lib().gsc_debug_set_spin_limit(self.ctx, limit))

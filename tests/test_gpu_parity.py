@@ -46,12 +46,12 @@ def render(r, cams):
     return [o.cpu().numpy() for o in outs], st
 
 
-def check_image(got, ref, margin, tag=""):
+def check_image(got, ref, margin, tag="", tol=PIX_TOL):
     ok = margin >= MARGIN
     err = np.abs(got.astype(np.float64) - ref)
     e_ok = err[ok].max() if ok.any() else 0.0
     frac = 1.0 - ok.mean()
-    if e_ok > PIX_TOL:
+    if e_ok > tol:
         k = np.unravel_index(np.argmax(np.where(ok[..., None] if err.ndim > ok.ndim else ok, err, 0)), err.shape)
         raise AssertionError(f"{tag}: max-abs {e_ok:.3e} on decided pixels at {k}: got {got[k[:-1]]} "
                              f"ref {ref[k[:-1]]} margin {margin[k[:-1]]}")
