@@ -133,6 +133,8 @@ def run_reference(args, rank, world):
         f = (args.warmup + s * 37) % len(frames)
         ts.append(oracle_frame_sample(model, *frames[f], phase=s))
     mean = float(np.mean(ts))
+    batched = run_batched(args, flush) if args.batched else None
+
     cores = oracle.num_threads()
     sample = ("per step: one stereo frame of the path, full filtering/derivation/projection in float64, "
               "blending on every 16th pixel row, blend time x16")
@@ -279,6 +281,104 @@ def roofline(stage_ms, st, form, W, H, n_anchors):
             "ms_per_launch": stage_ms[dom]}
 
 
+BATCHED_FORM = dict(stereo_unify=True, precision="bf16", reuse="depth")
+
+
+def run_batched(args, flush):
+    """Batched multi-viewer form: 3 scenes (0.5M / 2M / 4M anchors), 8 viewers,
+    13 images (1280x720 mono up to 1920x1080 stereo) rendered as one frame
+    (one graph replay), tiling chosen by the autotuner.  Compared with the
+    same frame untuned (16x16, one block per tile) and with the 8 viewers
+    rendered by 8 separate contexts one after another.  A frame = all 13 images."""
+    import torch
+    import gen
+    import paper_2502_14938_b300 as pkg
+    from paper_2502_14938_b300 import autotune
+    t0 = time.perf_counter()
+    models, viewers, frame_fn = gen.multiviewer_workload()
+    t_gen = time.perf_counter() - t0
+    n = max(1, min(args.steps, 100))
+    frames = [frame_fn(t) for t in range(n)]
+    n_img = len(frames[0])
+    pixels = sum(c.width * c.height for _, _, c, _ in frames[0])
+    outs = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device="cuda") for _, _, c, _ in frames[0]]
+
+    def cams(imgs, mid_of, sel=None):
+        """gsc cameras of the images `sel` (all by default); partners renumbered within `sel`."""
+        sel = list(range(len(imgs))) if sel is None else sel
+        remap = {j: i for i, j in enumerate(sel)}
+        return [pkg.to_camera(imgs[j][2], partner=remap.get(imgs[j][3], -1), model_id=mid_of(imgs[j][1]),
+                              viewer=imgs[j][0]) for j in sel]
+
+    r = pkg.Renderer(max_views=n_img, **BATCHED_FORM)
+    mids = [r.load_model(m) for m in models]
+    cam_lists = [cams(f, lambda sc: mids[sc]) for f in frames]
+
+    def timed(setup, render):
+        for f in range(n):  # grow buffers, warm the graph
+            setup(f)
+            render()
+        torch.cuda.synchronize()
+        for rr in rends:
+            rr.cache_reset()
+        stream = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for f in range(n):
+            setup(f)
+            flush.fill_(f & 0xFF)
+            evs[f][0].record(stream)
+            render()
+            evs[f][1].record(stream)
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in evs])
+        return {"fps": 1000.0 / float(ms.mean()), "ms_mean": float(ms.mean()),
+                "p99_ms": float(np.percentile(ms, 99)), "images_per_s": n_img * 1000.0 / float(ms.mean()),
+                "mpix_per_s": pixels / 1e3 / float(ms.mean())}
+
+    rends = [r]
+    r.set_tiling(16, 16, 0)
+    untuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda: r.render_frame(outs, stats=False))
+    r.set_cameras(cam_lists[0])
+    t1 = time.perf_counter()
+    best = autotune.tune(r, outs, args.tiling_cache, reps=3)
+    t_tune = time.perf_counter() - t1
+    tuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda: r.render_frame(outs, stats=False))
+    reuse = []
+    for f in range(n):
+        r.set_cameras(cam_lists[f])
+        st = r.render_frame(outs)
+        reuse.append(1.0 - st["derived_anchors"] / max(st["visible_anchors"], 1))
+
+    # the same viewers, one context per viewer, rendered one after another
+    sep = []
+    for v in range(len(viewers)):
+        sel = [i for i, im in enumerate(frames[0]) if im[0] == v]
+        rv = pkg.Renderer(max_views=len(sel), **BATCHED_FORM)
+        rv.set_tiling(best["tile_w"], best["tile_h"], best["blocks_per_sm"])
+        mid = rv.load_model(models[frames[0][sel[0]][1]])
+        sep.append((rv, sel, [cams(f, lambda sc, m=mid: m, sel) for f in frames]))
+    rends = [x[0] for x in sep]
+
+    def sep_setup(f):
+        for rv, sel, cl in sep:
+            rv.set_cameras(cl[f])
+
+    def sep_render():
+        for rv, sel, _ in sep:
+            rv.render_frame([outs[i] for i in sel], stats=False)
+
+    separate = timed(sep_setup, sep_render)
+    for rv, _, _ in sep:
+        rv.close()
+    r.close()
+    return {"workload": "3 city scenes 0.5M/2M/4M anchors, 8 viewers, 13 images (5 stereo pairs + 3 mono, "
+                        "1280x720..1920x1080), BF16 + cache + unified stereo, one frame = all 13 images",
+            "frames": n, "images": n_img, "pixels_per_frame": pixels, "tuned": tuned,
+            "tiling": {k: best[k] for k in ("tile_w", "tile_h", "blocks_per_sm", "ms")},
+            "untuned_16x16_per_tile": untuned, "separate_contexts": separate,
+            "reuse_frac_mean": float(np.mean(reuse)), "tune_s": t_tune, "gen_s": t_gen}
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -344,6 +444,8 @@ def run_ours(args, rank, world):
            "d2h_bytes_per_step": 2 * W * H * 3 * 4 + 128}
 
     # ---- CPU baseline: the oracle on a bounded sample
+    batched = run_batched(args, flush) if args.batched else None
+
     cores = oracle.num_threads()
     cts = [oracle_frame_sample(model, *frames[f], phase=i) for i, f in enumerate((0, 150))]
     cpu = {"value": 1.0 / float(np.mean(cts)), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -357,7 +459,7 @@ def run_ours(args, rank, world):
            "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
-           "compare": others, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
+           "compare": others, "batched": batched, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+f32" if FORMS[form]["precision"] == "bf16" else "f32",
@@ -377,6 +479,9 @@ def main():
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 150, 299])
     ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
     ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")
+    ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the batched multi-viewer form (reported under config.batched)")
+    ap.add_argument("--tiling-cache", default=None, help="JSON file the autotuner reads / writes")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -87,7 +87,9 @@ typedef struct {
   float bg[3];               /* background colour */
   uint32_t use_graph;        /* 1: replay the frame's launch sequence as a CUDA graph */
   uint32_t flags;            /* GSC_FLAG_* */
-  uint32_t reserved[8];
+  uint32_t blocks_per_sm;    /* blend: 0 = one block per tile; n = persistent grid of n blocks per SM
+                                taking the tiles of all cameras from one counter */
+  uint32_t reserved[7];
 } gsc_config;
 
 /* Model description: host pointers, float32, row-major.  Copied by
@@ -165,6 +167,13 @@ GSC_API int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stat
  * pageable); the device->host copies are part of the call, which returns
  * when the images are in host memory. */
 GSC_API int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats);
+
+/* Change the blend tiling of a context in place (models and cameras stay):
+ * tile_w x tile_h as for gsc_config, blocks_per_sm as for gsc_config.  Used
+ * by the autotuner (Sec. 4 renders eyes "independently or in batching"; the
+ * tile shape and grid of the batched frame are picked by timing).  Invalid
+ * values return GSC_ERR_INVALID_ARG and leave the tiling unchanged. */
+GSC_API int gsc_set_tiling(gsc_ctx* ctx, uint32_t tile_w, uint32_t tile_h, uint32_t blocks_per_sm);
 
 /* Empty every derivation cache (Sec. 4): the next frame decodes all anchors. */
 GSC_API int gsc_cache_reset(gsc_ctx* ctx);

@@ -1,0 +1,87 @@
+"""Timed sweep of the blend tiling (tile W x H, blocks per SM) for one workload.
+
+The tile shape changes how many (tile, Gaussian) pairs a frame generates and
+sorts, and how much of a tile's Gaussian list each pixel walks; the number of
+resident blocks per SM decides whether the blend runs one block per tile or as
+a persistent kernel pulling tiles from a counter.  Neither is predictable from
+first principles across image sizes and scenes, so the choice is measured:
+every candidate renders the same frame a few times (whole frame, CUDA events
+on the renderer's stream) and the fastest wins.  Results persist to a JSON
+file keyed by the device name and the workload signature, so a later run with
+the same workload loads the choice instead of sweeping again.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
+
+TILE_SHAPES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (8, 32))
+BLOCKS_PER_SM: Tuple[int, ...] = (0, 4, 8, 16, 32)  # 0 = one block per tile
+
+
+def workload_key(renderer, extra: str = "") -> str:
+    """Device name + cameras (size, model) + form flags: what the best tiling depends on."""
+    import torch
+    cfg = renderer.cfg
+    cams = ";".join(f"{c.width}x{c.height}m{c.model_id}p{c.stereo_partner}" for c in renderer.cams)
+    form = f"prec{cfg.precision}-reuse{cfg.reuse}-unify{cfg.stereo_unify}"
+    return f"{torch.cuda.get_device_name()}|{form}|{cams}|{extra}"
+
+
+def time_frames(renderer, outs, reps: int = 5, warmup: int = 2) -> float:
+    """Median ms of one rendered frame (device time on the renderer's stream)."""
+    import torch
+    for _ in range(warmup):
+        renderer.render_frame(outs, stats=False)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        renderer.render_frame(outs, stats=False)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def sweep(renderer, outs, shapes: Iterable[Tuple[int, int]] = TILE_SHAPES,
+          blocks: Iterable[int] = BLOCKS_PER_SM, reps: int = 5) -> List[Dict]:
+    """Every (shape, blocks/SM) candidate timed on the renderer's current
+    cameras; returns the table sorted fastest first.  The renderer keeps the
+    fastest tiling when this returns."""
+    rows = []
+    for tw, th in shapes:
+        for bps in blocks:
+            renderer.set_tiling(tw, th, bps)
+            rows.append({"tile_w": tw, "tile_h": th, "blocks_per_sm": bps,
+                         "ms": time_frames(renderer, outs, reps)})
+    rows.sort(key=lambda r: r["ms"])
+    best = rows[0]
+    renderer.set_tiling(best["tile_w"], best["tile_h"], best["blocks_per_sm"])
+    return rows
+
+
+def tune(renderer, outs, path: Optional[str] = None, extra_key: str = "", retune: bool = False,
+         **kw) -> Dict:
+    """Load the tiling for this workload from `path`, or sweep and store it.
+    Applies the chosen tiling to `renderer` and returns its table entry."""
+    key = workload_key(renderer, extra_key)
+    db = {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            db = json.load(f)
+    if key in db and not retune:
+        best = db[key]["best"]
+        renderer.set_tiling(best["tile_w"], best["tile_h"], best["blocks_per_sm"])
+        return dict(best, source="cache")
+    rows = sweep(renderer, outs, **kw)
+    db[key] = {"best": rows[0], "table": rows}
+    if path:
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1)
+        os.replace(tmp, path)
+    return dict(rows[0], source="sweep")

@@ -97,6 +97,7 @@ struct gsc_ctx {
   // graph
   cudaGraphExec_t gexec = nullptr;
   bool graph_valid = false;
+  bool replay_next = false;  // next enqueue re-renders a cached frame without new cache decisions
   // frame shape (host-known)
   uint32_t total_tiles = 0, tile_bits = 1;
   std::vector<int> models_used;
@@ -226,6 +227,34 @@ int alloc_pairs(gsc_ctx* ctx, uint32_t cap) {
   return ensure_status(ctx);
 }
 
+// Blend tilings: a lane owns 4 pixels of one column and a warp 32 / tile_w
+// column strips; powers of two keep the coverage arithmetic exact.
+bool tiling_ok(uint32_t tw, uint32_t th, uint32_t bps) {
+  if (tw != 8 && tw != 16 && tw != 32) return false;
+  if (th == 0 || (th & (th - 1)) != 0) return false;
+  const uint32_t npx = tw * th;
+  if (npx < 128 || npx > 1024 || th % ((32 / tw) * 4) != 0) return false;
+  return bps <= 32;
+}
+
+// Tile count, tile-key bits and the range table for the current cameras and tiling.
+int retile(gsc_ctx* ctx) {
+  uint32_t tiles = 0;
+  for (const auto& c : ctx->cams)
+    tiles += ((c.width + ctx->cfg.tile_w - 1) / ctx->cfg.tile_w) * ((c.height + ctx->cfg.tile_h - 1) / ctx->cfg.tile_h);
+  ctx->total_tiles = tiles;
+  uint32_t bits = 1;
+  while ((1u << bits) < tiles && bits < 31) ++bits;
+  ctx->tile_bits = bits;
+  if (tiles > ctx->ranges_cap) {
+    int r = dalloc(ctx, &ctx->ranges, tiles);
+    if (r) return r;
+    ctx->ranges_cap = tiles;
+  }
+  invalidate_graph(ctx);
+  return GSC_OK;
+}
+
 // ------------------------------------------------------------------ caches (Sec. 4)
 void free_cache(CacheDev& c) {
   void* p[] = {c.slot_of, c.slot_anchor, c.slot_frame, c.slot_attr, c.vstat, c.new_flag, c.new_rank,
@@ -291,7 +320,12 @@ int setup_caches(gsc_ctx* ctx) {
 }
 
 // The launch sequence of one frame (everything after the FrameIn upload).
-void enqueue_sequence(gsc_ctx* ctx) {
+// replay: the frame is being rendered again after a buffer grew.  Its cache
+// decisions (hit / line / miss lists, the next reuse depth) were taken and
+// committed by the first attempt, and derivation rewrites the same lines
+// with the same values, so the cache kernels are left out and the policy
+// only restates the frame's counts.
+void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   cudaStream_t s = ctx->stream;
   FrameDev* fd = ctx->d_fd;
   const bool tm = ctx->timing;
@@ -301,7 +335,7 @@ void enqueue_sequence(gsc_ctx* ctx) {
   for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
-  if (caches)
+  if (caches && !replay)
     launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->st_scan, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
@@ -311,7 +345,7 @@ void enqueue_sequence(gsc_ctx* ctx) {
     else
       launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->n_sm, s);
   launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->n_sm, s);
-  if (caches) launch_cache_policy(ctx->d_caches, ctx->n_caches, fd, s);
+  if (caches) launch_cache_policy(ctx->d_caches, ctx->n_caches, fd, replay, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
@@ -329,7 +363,8 @@ void enqueue_sequence(gsc_ctx* ctx) {
   if (tm) cudaEventRecord(ctx->ev_stage[5], s);
   launch_ranges(fd, pk, ctx->ranges, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[6], s);
-  launch_blend(fd, ctx->ranges, pv, ctx->rec, ctx->d_fin, ctx->total_tiles, ctx->cfg.tile_w * ctx->cfg.tile_h, s);
+  launch_blend(fd, ctx->ranges, pv, ctx->rec, ctx->d_fin, ctx->total_tiles, ctx->cfg.tile_w * ctx->cfg.tile_h,
+               ctx->cfg.blocks_per_sm, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[7], s);
 }
 
@@ -378,7 +413,11 @@ int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
   CK(cudaMemcpyAsync(ctx->d_fin, F, sizeof(FrameIn), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaEventRecord(ctx->ev_slot[sl], ctx->stream));
-  if (ctx->cfg.use_graph && !ctx->timing) {
+  if (ctx->replay_next) {
+    ctx->replay_next = false;
+    enqueue_sequence(ctx, true);
+    CK(cudaGetLastError());
+  } else if (ctx->cfg.use_graph && !ctx->timing) {
     if (!ctx->graph_valid) {
       int r = build_graph(ctx);
       if (r) return r;
@@ -458,7 +497,10 @@ int render_impl(gsc_ctx* ctx, float* const* out_dev, float* const* out_T, gsc_fr
     if (r) return r;
     if (!sync) return GSC_OK;
     r = finish_frame(ctx);
-    if (r == GSC_ERR_CAPACITY) continue;  // grown: render the frame again
+    if (r == GSC_ERR_CAPACITY) {  // grown: render the frame again
+      ctx->replay_next = ctx->n_caches > 0;
+      continue;
+    }
     if (r) return r;
     if (stats) fill_stats(ctx, stats);
     ctx->err.clear();
@@ -499,12 +541,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.cache_gaussians == 0) cfg.cache_gaussians = 4u << 20;
   if (cfg.pair_capacity == 0) cfg.pair_capacity = 16u << 20;
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
-  // blend: a lane owns 4 pixels of one column, a warp 32 / tile_w column
-  // strips; powers of two keep the coverage arithmetic exact
-  const uint32_t npx = cfg.tile_w * cfg.tile_h;
-  if (cfg.tile_w != 8 && cfg.tile_w != 16 && cfg.tile_w != 32) return GSC_ERR_INVALID_ARG;
-  if (cfg.tile_h == 0 || (cfg.tile_h & (cfg.tile_h - 1)) != 0) return GSC_ERR_INVALID_ARG;
-  if (npx < 128 || npx > 1024 || cfg.tile_h % ((32 / cfg.tile_w) * 4) != 0) return GSC_ERR_INVALID_ARG;
+  if (!tiling_ok(cfg.tile_w, cfg.tile_h, cfg.blocks_per_sm)) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
   if (cfg.precision == GSC_PREC_FP8 || cfg.reuse == GSC_REUSE_LEARNED) return GSC_ERR_UNIMPLEMENTED;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
@@ -694,21 +731,11 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
   ctx->cams.assign(cams, cams + n);
   if (shape_same && ctx->cams_set) return GSC_OK;
   invalidate_graph(ctx);
-  uint32_t tiles = 0;
-  for (const auto& c : ctx->cams)
-    tiles += ((c.width + ctx->cfg.tile_w - 1) / ctx->cfg.tile_w) * ((c.height + ctx->cfg.tile_h - 1) / ctx->cfg.tile_h);
-  ctx->total_tiles = tiles;
-  uint32_t bits = 1;
-  while ((1u << bits) < tiles && bits < 31) ++bits;
-  ctx->tile_bits = bits;
   ctx->models_used.clear();
   for (uint32_t m = 0; m < MAX_MODELS; ++m)
     if (per_model[m]) ctx->models_used.push_back((int)m);
   int r;
-  if (tiles > ctx->ranges_cap) {
-    if ((r = dalloc(ctx, &ctx->ranges, tiles))) return r;
-    ctx->ranges_cap = tiles;
-  }
+  if ((r = retile(ctx))) return r;
   // visible-id lists: one slot per derivation view, each sized for the largest model
   const uint32_t vcap = std::max<uint32_t>(models_max_n(ctx), 1u);
   if (vcap > ctx->vis_cap || n > ctx->n_vis_slots) {
@@ -803,6 +830,22 @@ int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* 
 
 static int dbg_sync(gsc_ctx* ctx);
 static int dbg_copy(gsc_ctx* ctx, void* dst, const void* src, uint64_t count, uint64_t cap, size_t elem);
+
+int gsc_set_tiling(gsc_ctx* ctx, uint32_t tile_w, uint32_t tile_h, uint32_t blocks_per_sm) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!tiling_ok(tile_w, tile_h, blocks_per_sm))
+    return fail(ctx, GSC_ERR_INVALID_ARG, "unsupported tiling %ux%u, %u blocks/SM", tile_w, tile_h, blocks_per_sm);
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->cfg.tile_w = tile_w;
+  ctx->cfg.tile_h = tile_h;
+  ctx->cfg.blocks_per_sm = blocks_per_sm;
+  if (ctx->cams_set) {
+    int r = retile(ctx);
+    if (r) return r;
+  }
+  ctx->err.clear();
+  return GSC_OK;
+}
 
 int gsc_cache_reset(gsc_ctx* ctx) {
   if (!ctx) return GSC_ERR_INVALID_ARG;

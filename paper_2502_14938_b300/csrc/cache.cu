@@ -82,7 +82,9 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, const Frame
   }
 }
 
-__global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd) {
+// replay != 0: the frame's decisions and the depth update were already made
+// by an earlier attempt at the same frame; only the frame counts are restated.
+__global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd, int replay) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   uint32_t hits = 0;
   for (int c = 0; c < n; ++c) {
@@ -91,7 +93,7 @@ __global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd) {
     const uint32_t V = fd->vis_count[c], m = st[CS_MISSES], D = st[CS_DMAX];
     st[CS_VIS] = V;
     hits += V - m;
-    if (V > 0) {
+    if (!replay && V > 0) {
       const unsigned long long num = 2ull * D * (V - m) + V;
       uint32_t d = (uint32_t)(num / (2ull * V));
       st[CS_DEPTH] = d < 1u ? 1u : (d > D ? D : d);
@@ -118,8 +120,8 @@ void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, Fr
   }
 }
 
-void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s) {
-  k_cache_policy<<<1, 32, 0, s>>>(caches, n_caches, fd);
+void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, bool replay, cudaStream_t s) {
+  k_cache_policy<<<1, 32, 0, s>>>(caches, n_caches, fd, replay ? 1 : 0);
 }
 
 }  // namespace gsc

@@ -14,7 +14,7 @@ struct ProjCam {
   float t[3];
   float fx, fy, cx, cy;
   float znear, gx, gy;
-  float pc[3], pc_lo[3];
+  float pc[3], pc_lo[3], dt[3];
   int W, H;
   uint32_t rec_base;
   uint32_t cam;
@@ -64,6 +64,7 @@ __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd,
         pc.t[i] = c.t[i];
         pc.pc[i] = c.pc[i];
         pc.pc_lo[i] = c.pc_lo[i];
+        pc.dt[i] = c.dt[i];
       }
       pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
       pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
@@ -93,9 +94,11 @@ __device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uin
   float4 colv = make_float4(col[0], col[1], col[2], 0.f);
   const bool valid = kept && (tz > c.znear) && (alpha >= (1.0f / 255.0f));
   if (valid) {
-    const float tx = c.R[0] * rel[0] + c.R[1] * rel[1] + c.R[2] * rel[2];
-    const float ty = c.R[3] * rel[0] + c.R[4] * rel[1] + c.R[5] * rel[2];
-    const float tza = c.R[6] * rel[0] + c.R[7] * rel[1] + c.R[8] * rel[2];
+    // camera coordinates R mu + t as R (mu - pc) + (t + R pc): the large
+    // parts cancel exactly in the camera-relative position
+    const float tx = c.R[0] * rel[0] + c.R[1] * rel[1] + c.R[2] * rel[2] + c.dt[0];
+    const float ty = c.R[3] * rel[0] + c.R[4] * rel[1] + c.R[5] * rel[2] + c.dt[1];
+    const float tza = c.R[6] * rel[0] + c.R[7] * rel[1] + c.R[8] * rel[2] + c.dt[2];
     const float iz = 1.0f / tza;
     const float txc = fminf(fmaxf(tx * iz, -c.gx), c.gx) * tza;
     const float tyc = fminf(fmaxf(ty * iz, -c.gy), c.gy) * tza;

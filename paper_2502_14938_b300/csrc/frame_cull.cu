@@ -26,6 +26,11 @@ __device__ void fill_camdev(CamDev& c, const CamIn& in, const FrameIn& fin) {
     c.pc[i] = __double2float_rn(p[i]);
     c.pc_lo[i] = __double2float_rn(p[i] - (double)c.pc[i]);
   }
+  for (int i = 0; i < 3; ++i) {
+    double s = (double)c.t[i];
+    for (int k = 0; k < 3; ++k) s = __dadd_rn(s, __dmul_rn((double)c.R[3 * i + k], p[k]));
+    c.dt[i] = __double2float_rn(s);
+  }
   c.gx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.W), c.fx));
   c.gy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.H), c.fy));
   c.ntx = (c.W + (int)fin.tile_w - 1) / (int)fin.tile_w;

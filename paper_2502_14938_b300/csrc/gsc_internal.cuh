@@ -64,6 +64,8 @@ struct CamDev {  // camera with derived constants (computed on device)
   float znear;
   float pc[3];     // centre -R^T t (float64 then rounded)
   float pc_lo[3];  // float64 centre - pc: (pc, pc_lo) is a double-float centre
+  float dt[3];     // t + R pc in float64: what R (x - pc) misses of R x + t when the
+                   // float32 R is not exactly orthonormal (|dt| ~ 1e-7 |t|)
   float gx, gy;    // 1.3 * (0.5 W / fx), 1.3 * (0.5 H / fy) in float32
   int32_t ntx, nty;
   uint32_t tile_base;
@@ -326,7 +328,8 @@ struct SortBufs {
 };
 
 // counter / epoch slots of the look-back kernels within one frame
-enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28, SLOT_CACHE = 32 };
+enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28, SLOT_BLEND = 29,
+             SLOT_CACHE = 32 };
 constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s);
@@ -352,7 +355,7 @@ void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, 
                     const CacheDev* caches, Records rec, int n_sm, cudaStream_t s);
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s);
-void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s);
+void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, bool replay, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
@@ -364,6 +367,6 @@ void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint3
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
-                  uint32_t total_tiles, uint32_t tile_threads, cudaStream_t s);
+                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, int n_sm, cudaStream_t s);
 
 }  // namespace gsc

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
           pc.t[i] = c.t[i];
           pc.pc[i] = c.pc[i];
           pc.pc_lo[i] = c.pc_lo[i];
+          pc.dt[i] = c.dt[i];
         }
         pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
         pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;

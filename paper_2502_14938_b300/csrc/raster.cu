@@ -214,14 +214,20 @@ constexpr int BLEND_MAX_NT = 256;
 constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
 
-__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ vals, Records rec,
-                                                        const FrameIn* __restrict__ fin) {
-  __shared__ float4 s_q0[BLEND_MAX_NT];   // F, D, E, A'
-  __shared__ float4 s_q1[BLEND_MAX_NT];   // B', C', r, g
-  __shared__ float4 s_bb[BLEND_MAX_NT];   // b, xmin, xmax, ymin
-  __shared__ float s_ymax[BLEND_MAX_NT];
-  const uint32_t tile_key = blockIdx.x;
+struct BlendSmem {
+  float4 q0[BLEND_MAX_NT];   // F, D, E, A'
+  float4 q1[BLEND_MAX_NT];   // B', C', r, g
+  float4 bb[BLEND_MAX_NT];   // b, xmin, xmax, ymin
+  float ymax[BLEND_MAX_NT];
+};
+
+__device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, const FrameDev* __restrict__ fd,
+                                           const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                           const Records& rec, const FrameIn* __restrict__ fin) {
+  float4* s_q0 = sm.q0;
+  float4* s_q1 = sm.q1;
+  float4* s_bb = sm.bb;
+  float* s_ymax = sm.ymax;
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   const int nt = (int)blockDim.x;  // TW * TH / BLEND_PPL
   uint32_t cam = 0;
@@ -312,9 +318,40 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restri
   }
 }
 
+// One block per tile of every camera.
+__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ vals, Records rec,
+                                                        const FrameIn* __restrict__ fin) {
+  __shared__ BlendSmem sm;
+  blend_tile(blockIdx.x, sm, fd, ranges, vals, rec, fin);
+}
+
+// Persistent form: a fixed grid (blocks per SM x SMs) whose blocks take the
+// tiles of all cameras - of every viewer in a batched frame - from one
+// counter, so long and short tiles balance across the machine.
+__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend_persistent(FrameDev* __restrict__ fd,
+                                                                   const uint2* __restrict__ ranges,
+                                                                   const uint32_t* __restrict__ vals, Records rec,
+                                                                   const FrameIn* __restrict__ fin) {
+  __shared__ BlendSmem sm;
+  __shared__ uint32_t s_tile;
+  const uint32_t total = fd->total_tiles;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(&fd->ctr[SLOT_BLEND], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= total) break;
+    blend_tile(tile, sm, fd, ranges, vals, rec, fin);
+  }
+}
+
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
-                  uint32_t total_tiles, uint32_t tile_threads, cudaStream_t s) {
-  k_blend<<<total_tiles, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
+                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, int n_sm, cudaStream_t s) {
+  if (blocks_per_sm == 0)
+    k_blend<<<total_tiles, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
+  else
+    k_blend_persistent<<<n_sm * blocks_per_sm, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
 }
 
 }  // namespace gsc

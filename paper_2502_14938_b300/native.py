@@ -40,7 +40,7 @@ class Config(C.Structure):
                 ("stereo_unify", C.c_uint32), ("cache_gaussians", C.c_uint32), ("max_depth", C.c_uint32),
                 ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("pair_capacity", C.c_uint64),
                 ("bg", C.c_float * 3), ("use_graph", C.c_uint32), ("flags", C.c_uint32),
-                ("reserved", C.c_uint32 * 8)]
+                ("blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 7)]
 
 
 class ModelDesc(C.Structure):
@@ -106,6 +106,7 @@ def lib():
             "gsc_debug_wait_timeout": (I, [P, U32]),
             "gsc_scan_u32_noalloc": (I, [P, P, U64, P, P]),
             "gsc_debug_cache": (I, [P, U32, P, U64, P, P]),
+            "gsc_set_tiling": (I, [P, U32, U32, U32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -172,7 +173,7 @@ class Renderer:
     def __init__(self, max_views: int = 2, precision: str = "fp32", reuse: str = "off",
                  stereo_unify: bool = False, tile: tuple = (16, 16), pair_capacity: int = 0,
                  bg=(0.0, 0.0, 0.0), use_graph: bool = True, flags: int = 0, stream=None,
-                 cache_gaussians: int = 0, max_depth: int = 0):
+                 cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0):
         cfg = default_config()
         cfg.max_views = max_views
         cfg.precision = PREC[precision]
@@ -186,6 +187,7 @@ class Renderer:
         cfg.flags = flags
         cfg.cache_gaussians = cache_gaussians
         cfg.max_depth = max_depth
+        cfg.blocks_per_sm = blocks_per_sm
         self.cfg = cfg
         self.ctx = C.c_void_p()
         if stream is None:
@@ -261,6 +263,10 @@ class Renderer:
         st = FrameStats()
         self._check(lib().gsc_render_frame_host(self.ctx, ptrs, C.byref(st) if stats else None))
         return st.as_dict() if stats else None
+
+    def set_tiling(self, tile_w: int, tile_h: int, blocks_per_sm: int = 0):
+        """Blend tiling of this context (the autotuner's knob)."""
+        self._check(lib().gsc_set_tiling(self.ctx, tile_w, tile_h, blocks_per_sm))
 
     def cache_reset(self):
         self._check(lib().gsc_cache_reset(self.ctx))

@@ -41,10 +41,15 @@ def set_cams(r, cams, partners, mid=0):
     r.set_cameras([pkg.to_camera(c, partner=p, model_id=mid) for c, p in zip(cams, partners)])
 
 
-def test_cached_tiny_path_matches_oracle_simulation():
+@pytest.mark.parametrize("pair_capacity", [0, 256])
+def test_cached_tiny_path_matches_oracle_simulation(pair_capacity):
+    """pair_capacity 256: frames overflow the pair buffer, which grows and the
+    frame renders again; the second attempt must reuse the first attempt's
+    cache decisions, not take new ones on the already updated cache."""
     m = gen.tiny_scene()
     lines = 1500  # small pool: lines run out, so the overflow path is exercised too
-    r = make_renderer(m, [gen.tiny_camera()], reuse="depth", cache_gaussians=lines * 10)
+    r = make_renderer(m, [gen.tiny_camera()], reuse="depth", cache_gaussians=lines * 10,
+                      pair_capacity=pair_capacity)
     sim = CacheSim(m.n, lines, max_depth=10)
     for f in range(24):
         ang = 0.004 * f if f < 12 else 0.5  # slow pan, then a jump
