@@ -7,9 +7,9 @@ import numpy as np
 
 from .rng import Stream, splitmix64, stream_seed
 from .scenes import (FEAT_DIM, HIDDEN, IN_DIM, K_GAUSS, Model, city_scene,
-                     glorot_mlps, head_out_dims, tiny_scene)
+                     glorot_mlps, head_out_dims, reuse_mlp_init, tiny_scene)
 from .cameras import (Camera, HeadPose, city_path, look_rotation, path_extent,
-                      pinhole, stereo_frames, stereo_pair, tiny_camera)
+                      pinhole, reuse_path, stereo_frames, stereo_pair, tiny_camera)
 
 
 def city_workload(n_anchors: int = 2_000_000, seed: int = 10, path_seed: int = 11,
@@ -24,9 +24,9 @@ def city_workload(n_anchors: int = 2_000_000, seed: int = 10, path_seed: int = 1
 
 __all__ = [
     "Stream", "splitmix64", "stream_seed", "FEAT_DIM", "HIDDEN", "IN_DIM", "K_GAUSS",
-    "Model", "city_scene", "glorot_mlps", "head_out_dims", "tiny_scene", "Camera",
+    "Model", "city_scene", "glorot_mlps", "head_out_dims", "reuse_mlp_init", "tiny_scene", "Camera",
     "HeadPose", "city_path", "look_rotation", "path_extent", "pinhole", "stereo_frames",
-    "stereo_pair", "tiny_camera", "city_workload", "multiviewer_workload", "MV_SCENES", "MV_VIEWERS",
+    "stereo_pair", "tiny_camera", "city_workload", "reuse_path", "multiviewer_workload", "MV_SCENES", "MV_VIEWERS",
 ]
 
 

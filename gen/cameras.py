@@ -111,3 +111,23 @@ def stereo_frames(poses: List[HeadPose], width: int = 1920, height: int = 1080,
     """List of (left, right) Camera pairs along a path."""
     return [stereo_pair(look_rotation(p.yaw, p.pitch), p.pos, width, height, hfov_deg, baseline)
             for p in poses]
+
+
+def reuse_path(seed: int = 12, n_frames: int = 120, speed: float = 1.0) -> List[HeadPose]:
+    """Ascending city path (same corridor as `city_path(seed=11)`) with a
+    seeded look-around: the head yaw swings A sin(2 pi t / P + phi) about the
+    heading (A 45-60 deg, P 24-32 frames), the pitch B sin(2 pi t / Q + psi)
+    (B 4-8 deg), so consecutive frames share roughly 80-95% of their visible
+    anchors.  Seed 12: the evaluation path of the cached form; seeds 20-29:
+    training paths of the reuse predictor; seed 30: its held-out path."""
+    st = Stream(seed, "look")
+    A, P, phi = np.deg2rad(st.uniform(1, 45.0, 60.0)[0]), st.uniform(1, 24.0, 32.0)[0], st.uniform(1, 0.0, 2 * np.pi)[0]
+    B, Q, psi = np.deg2rad(st.uniform(1, 4.0, 8.0)[0]), st.uniform(1, 30.0, 50.0)[0], st.uniform(1, 0.0, 2 * np.pi)[0]
+    start = st.uniform(1, 0.0, 150.0)[0]  # metres along the corridor
+    base = city_path(n_frames=n_frames, seed=11, speed=speed)
+    d = np.array([np.cos(np.deg2rad(45.0)), np.sin(np.deg2rad(45.0)), 0.0])
+    out = []
+    for t, q in enumerate(base):
+        out.append(HeadPose(pos=q.pos + start * d, yaw=q.yaw + A * np.sin(2 * np.pi * t / P + phi),
+                            pitch=q.pitch + B * np.sin(2 * np.pi * t / Q + psi)))
+    return out

@@ -171,3 +171,14 @@ def city_scene(n: int = 2_000_000, seed: int = 10, mlp_seed: int = 1,
               W1=W1, b1=b1, W2=W2, b2=b2, k=k, name=f"city{n}_s{seed}")
     m.validate()
     return m
+
+
+def reuse_mlp_init(seed: int = 7) -> np.ndarray:
+    """Initial parameters of the 36 -> 64 -> 1 reuse predictor, flat float32
+    [W1 (36x64, input-major), b1 (64), w2 (64), b2 (1)]: Glorot-uniform
+    weights, zero biases."""
+    st = Stream(seed, "reuse_mlp")
+    a1 = np.sqrt(6.0 / (36 + 64))
+    a2 = np.sqrt(6.0 / (64 + 1))
+    return np.concatenate([st.uniform(36 * 64, -a1, a1), np.zeros(64), st.uniform(64, -a2, a2),
+                           np.zeros(1)]).astype(np.float32)

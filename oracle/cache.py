@@ -24,6 +24,9 @@ Readings (the paper gives the algorithm's branches, not its data layout):
   [1, D_max], computed in integers as floor((2 D_max (V - m) + V) / (2 V)).
 - In its own frame a decoded anchor is rendered with its fresh attributes;
   a hit is rendered with the cached float16 attributes.
+- Learned form (an extension, see oracle.predictor): a valid line is reused
+  iff the predictor says so; every decoded line also keeps the unit
+  direction camera -> anchor it was decoded for (the predictor's input).
 """
 from __future__ import annotations
 
@@ -51,6 +54,7 @@ class CacheSim:
         self.slot_anchor = np.full(slots, -1, np.int64)
         self.slot_frame = np.zeros(slots, np.int64)
         self.slot_attr = np.zeros((slots, k, ATTR), np.float16)
+        self.slot_dir = np.zeros((slots, 3), np.float32)
         self.t = 0
         self.depth = self.D
 
@@ -58,14 +62,14 @@ class CacheSim:
         self.slot_of[:] = -1
         self.slot_anchor[:] = -1
         self.slot_frame[:] = 0
+        self.slot_dir[:] = 0
         self.t = 0
         self.depth = self.D
 
-    def step(self, ids: np.ndarray):
-        """Classify the ascending visible ids of one frame.  Returns
-        (hit mask, line per anchor or -1, depth used this frame)."""
-        self.t += 1
-        t = self.t
+    def peek(self, ids: np.ndarray):
+        """(valid mask, line or -1, age) of the visible ids as the next frame
+        will find them, without changing the cache."""
+        t = self.t + 1
         ids = np.asarray(ids, np.int64)
         s = self.slot_of[ids]
         valid = s >= 0
@@ -73,8 +77,19 @@ class CacheSim:
         valid &= self.slot_anchor[sv] == ids
         age = t - self.slot_frame[sv]
         valid &= age <= self.D
-        hit = valid & (age <= self.depth)
-        line = np.where(valid, s, -1)
+        return valid, np.where(valid, s, -1), age
+
+    def step(self, ids: np.ndarray, d_now=None, reuse=None):
+        """Classify the ascending visible ids of one frame.  Returns
+        (hit mask, line per anchor or -1, depth used this frame).
+        d_now: unit directions camera -> anchor this frame (stored with the
+        decoded lines); reuse: learned decision, a function of (valid mask,
+        line) giving a mask, used instead of the depth rule."""
+        valid, line, age = self.peek(ids)
+        self.t += 1
+        t = self.t
+        ids = np.asarray(ids, np.int64)
+        hit = valid & (age <= self.depth) if reuse is None else valid & reuse(valid, line)
         free = np.nonzero((self.slot_anchor < 0) | (t - self.slot_frame > self.D))[0]
         new_idx = np.nonzero(~valid)[0]
         n = min(len(new_idx), len(free))
@@ -84,6 +99,8 @@ class CacheSim:
         self.slot_anchor[line[dec]] = ids[dec]
         self.slot_frame[line[dec]] = t
         self.slot_of[ids[dec]] = line[dec]
+        if d_now is not None:
+            self.slot_dir[line[dec]] = np.asarray(d_now, np.float32)[dec]
         used = self.depth
         self.last = dict(visible=len(ids), misses=int((~hit).sum()), hits=int(hit.sum()),
                          new=len(new_idx), cached_new=n)
@@ -99,14 +116,26 @@ class CacheSim:
         return self.slot_attr[line[hit]].astype(np.float64)
 
 
-def cached_derive(model, dcam, sim: CacheSim, quant=None):
+def cached_derive(model, dcam, sim: CacheSim, quant=None, theta=None):
     """The derivation step of one frame in the cached form, for the derivation
-    camera dcam: filtering, the policy, fresh derivation of the decoded
-    anchors, float16 lines for the hits.  Returns (ids, attrs [V,k,11],
-    kept [V,k], hit mask, line per anchor, depth used)."""
+    camera dcam: filtering, the policy (the depth rule, or the predictor with
+    parameters theta), fresh derivation of the decoded anchors, float16 lines
+    for the hits.  Returns (ids, attrs [V,k,11], kept [V,k], hit mask, line
+    per anchor, depth used)."""
     import oracle
+    from oracle import predictor as P
     ids = oracle.cull(model, dcam)
-    hit, line, used = sim.step(ids)
+    d_now, dist = P.pinned_dir(model.pos[ids], oracle.camera_center(dcam))
+    reuse = None
+    if theta is not None:
+        def reuse(valid, line):
+            out = np.zeros(len(ids), bool)
+            v = np.nonzero(valid)[0]
+            if len(v):
+                z = P.features(model.feat[ids[v]], d_now[v], sim.slot_dir[line[v]], dist[v])
+                out[v] = P.decide(z, theta)
+            return out
+    hit, line, used = sim.step(ids, d_now, reuse)
     attrs = np.zeros((len(ids), model.k, ATTR), np.float64)
     miss = ~hit
     if miss.any():
@@ -117,6 +146,28 @@ def cached_derive(model, dcam, sim: CacheSim, quant=None):
         attrs[hit] = sim.cached_attrs(line, hit)
     kept = (attrs[..., 0] > 0).astype(np.uint8)
     return ids, attrs, kept, hit, line, used
+
+
+def collect_samples(model, dcam, sim: CacheSim, quant=None):
+    """Predictor training samples of the coming frame (call before
+    cached_derive for the same frame): for every visible anchor holding a
+    valid line, its inputs z and its label (oracle.predictor.label of the
+    float16 line against a fresh float64 derivation of this frame).  Returns
+    (visible indices, z [n,36], labels [n], label margins [n]): the margin is
+    how far the closest of the label's comparisons lies from its threshold."""
+    import oracle
+    from oracle import predictor as P
+    ids = oracle.cull(model, dcam)
+    valid, line, _ = sim.peek(ids)
+    v = np.nonzero(valid)[0]
+    pc = oracle.camera_center(dcam)
+    d_now, dist = P.pinned_dir(model.pos[ids[v]], pc)
+    z = P.features(model.feat[ids[v]], d_now, sim.slot_dir[line[v]], dist)
+    if len(v) == 0:
+        return v, z, np.zeros(0, bool), np.zeros(0)
+    fresh, _ = oracle.derive(model, pc, ids[v], quant)
+    cached = sim.slot_attr[line[v]].astype(np.float64)
+    return v, z, P.label(cached, fresh), P.label_margin(cached, fresh)
 
 
 def project_view(model, cam, ids, attrs, kept):
