@@ -66,13 +66,14 @@ typedef enum { GSC_PREC_FP32 = 0, GSC_PREC_BF16 = 1, GSC_PREC_FP8 = 2 } gsc_prec
 typedef enum {
   GSC_REUSE_OFF = 0,      /* decode every visible anchor every frame */
   GSC_REUSE_DEPTH = 1,    /* Alg. 1 dynamic cache depth (Eq. 4, linear guide) */
-  GSC_REUSE_LEARNED = 2   /* learned per-anchor reuse predictor, depth rule as fallback bound */
+  GSC_REUSE_LEARNED = 2   /* learned per-anchor reuse predictor (gsc_reuse_*); lines past D_max stay invalid */
 } gsc_reuse_mode;
 
 /* flags */
 #define GSC_FLAG_DEBUG_ATTRS 0x1u  /* keep derived attributes for gsc_debug_attrs */
 #define GSC_FLAG_DEBUG_T 0x2u      /* keep per-pixel final transmittance */
 #define GSC_FLAG_TIMING 0x4u       /* per-stage CUDA-event timing into gsc_frame_stats */
+#define GSC_FLAG_REUSE_COLLECT 0x8u /* reuse forms: record predictor inputs + labels (gsc_reuse_collect) */
 
 typedef struct {
   uint32_t max_views;        /* cameras per frame, 1..GSC_MAX_VIEWS */
@@ -174,6 +175,48 @@ GSC_API int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame
  * tile shape and grid of the batched frame are picked by timing).  Invalid
  * values return GSC_ERR_INVALID_ARG and leave the tiling unchanged. */
 GSC_API int gsc_set_tiling(gsc_ctx* ctx, uint32_t tile_w, uint32_t tile_h, uint32_t blocks_per_sm);
+
+/* ---- learned reuse predictor -------------------------------------------
+ * An extension of the cache of Sec. 4 (the paper reuses by the depth rule of
+ * Alg. 1 / Eq. 4 only): with reuse = GSC_REUSE_LEARNED a valid line (age <=
+ * D_max) is reused iff p = sigmoid(w2 . relu(W1^T z + b1) + b2) >= 0.5, else
+ * the anchor is decoded again.  z (36 floats): the anchor feature (32),
+ * 1024 x the change of the unit direction from the derivation camera centre
+ * to the anchor since the line was decoded (3), and plog2(distance) - 8 (1),
+ * plog2(m 2^e) = e + (m - 1), m in [1, 2).  The decision uses float32 in a
+ * fixed operation order with bfloat16-rounded weights.  Parameters are a
+ * flat float array: W1 [36][64] input-major, b1 [64], w2 [64], b2 [1]. */
+#define GSC_REUSE_NPARAM 2433
+
+/* Set the predictor's float32 master weights (host array of n_params =
+ * GSC_REUSE_NPARAM finite floats, copied).  Required before rendering in
+ * the learned form and before training. */
+GSC_API int gsc_reuse_set_weights(gsc_ctx* ctx, const float* params, uint32_t n_params);
+
+/* Copy the float32 master weights (e.g. after gsc_reuse_train) to params. */
+GSC_API int gsc_reuse_get_weights(gsc_ctx* ctx, float* params, uint32_t n_params);
+
+/* Training samples of the last frame (context created with
+ * GSC_FLAG_REUSE_COLLECT and a reuse form): for derivation view dview, one
+ * sample per visible anchor that held a valid line before the frame, in
+ * visible order: z [n][36], label (1: reusing the line keeps every kept
+ * Gaussian's opacity and opacity-weighted colour within 1/255 of a fresh
+ * decode of this frame, and the same Gaussians kept; 0 otherwise) and the
+ * anchor's index in the view's visible list.  Any output may be NULL; *n
+ * receives the number of samples, at most cap are written.  Host memory. */
+GSC_API int gsc_reuse_collect(gsc_ctx* ctx, uint32_t dview, float* z, uint8_t* label, uint32_t* vis_index,
+                              uint64_t cap, uint64_t* n);
+
+/* Train the predictor on the GPU from the current weights: n samples
+ * (z [n][36] float, label [n] 0/1, host memory), `epochs` passes in
+ * mini-batches of `batch`, Adam with step size lr (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on float32 master weights, forward/backward with their bfloat16
+ * rounding, mean binary cross-entropy.  order: epochs x n sample indices
+ * (host), or NULL for a shuffle per epoch drawn from SplitMix64(seed).
+ * epoch_loss (may be NULL) receives the mean loss of each epoch.  The
+ * trained weights replace the context's; the Adam state starts from zero. */
+GSC_API int gsc_reuse_train(gsc_ctx* ctx, const float* z, const uint8_t* label, uint64_t n, uint32_t epochs,
+                            uint32_t batch, float lr, uint64_t seed, const uint32_t* order, float* epoch_loss);
 
 /* Empty every derivation cache (Sec. 4): the next frame decodes all anchors. */
 GSC_API int gsc_cache_reset(gsc_ctx* ctx);

@@ -82,6 +82,13 @@ GSC_API int gsc_debug_wait_timeout(gsc_ctx* ctx, uint32_t spin_limit);
  * library's decoupled look-back scan kernel; *total receives the sum. */
 GSC_API int gsc_debug_scan(gsc_ctx* ctx, uint32_t* vals, uint64_t n, uint64_t* total);
 
+/* Gradient of the predictor's mean binary cross-entropy over n samples (host
+ * z [n][36], label [n]) at the current weights (bfloat16-rounded, as in
+ * training), one forward/backward through the training kernels: grad
+ * [GSC_REUSE_NPARAM] and *loss (may be NULL), host memory. */
+GSC_API int gsc_debug_reuse_grad(gsc_ctx* ctx, const float* z, const uint8_t* label, uint64_t n, float* grad,
+                                 float* loss);
+
 #ifdef __cplusplus
 }
 #endif

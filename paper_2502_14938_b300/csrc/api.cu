@@ -112,6 +112,11 @@ struct gsc_ctx {
   CacheDev h_caches[MAX_CACHES] = {};
   uint32_t cache_na[MAX_CACHES] = {};  // anchors of each cache's model
   CacheDev* d_caches = nullptr;
+  // reuse predictor: float32 master weights and their bfloat16 rounding
+  float* rw_theta = nullptr;
+  float* rw_w = nullptr;
+  bool reuse_set = false;
+  float4* attrs_fresh = nullptr;  // collection: every visible anchor derived afresh
 };
 
 namespace {
@@ -212,6 +217,7 @@ int alloc_records(gsc_ctx* ctx, uint32_t cap) {
       (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)) ||
       (r = dalloc(ctx, &ctx->attrs, (size_t)cap * 3)))
     return r;
+  if ((ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && (r = dalloc(ctx, &ctx->attrs_fresh, (size_t)cap * 3))) return r;
   ctx->rec_cap = cap;
   invalidate_graph(ctx);
   return ensure_status(ctx);
@@ -258,7 +264,7 @@ int retile(gsc_ctx* ctx) {
 // ------------------------------------------------------------------ caches (Sec. 4)
 void free_cache(CacheDev& c) {
   void* p[] = {c.slot_of, c.slot_anchor, c.slot_frame, c.slot_attr, c.vstat, c.new_flag, c.new_rank,
-               c.free_flag, c.free_rank, c.free_list, c.miss, c.state};
+               c.free_flag, c.free_rank, c.free_list, c.miss, c.state, c.slot_dir, c.cz, c.clab};
   for (void* q : p) dfree(q);
   c = CacheDev{};
 }
@@ -308,7 +314,10 @@ int setup_caches(gsc_ctx* ctx) {
         (r = dalloc(ctx, &c.vstat, vcap)) || (r = dalloc(ctx, &c.new_flag, vcap)) ||
         (r = dalloc(ctx, &c.new_rank, vcap)) || (r = dalloc(ctx, &c.free_flag, S)) ||
         (r = dalloc(ctx, &c.free_rank, S)) || (r = dalloc(ctx, &c.free_list, S)) || (r = dalloc(ctx, &c.miss, vcap)) ||
-        (r = dalloc(ctx, &c.state, CS_WORDS)))
+        (r = dalloc(ctx, &c.state, CS_WORDS)) || (r = dalloc(ctx, &c.slot_dir, S)))
+      return r;
+    if ((ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) &&
+        ((r = dalloc(ctx, &c.cz, (size_t)vcap * 36)) || (r = dalloc(ctx, &c.clab, vcap))))
       return r;
     if ((r = init_cache(ctx, c, na))) return r;
     ctx->cache_na[d] = na;
@@ -335,8 +344,18 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
+  const bool collect = caches && (ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && !replay;
+  if (collect)  // fresh attributes of every visible anchor, for the labels
+    for (int m : ctx->models_used)
+      if (ctx->cfg.precision == GSC_PREC_BF16)
+        launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, &ctx->tmap_feat,
+                         ctx->compact, ctx->n_sm, s);
+      else
+        launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, ctx->n_sm, s);
   if (caches && !replay)
-    launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->st_scan, ctx->n_sm, s);
+    launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
+                       ctx->cfg.reuse == GSC_REUSE_LEARNED, collect ? ctx->attrs_fresh : nullptr, ctx->st_scan,
+                       ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
     if (ctx->cfg.precision == GSC_PREC_BF16)
@@ -487,6 +506,8 @@ void fill_stats(gsc_ctx* ctx, gsc_frame_stats* st) {
 
 int render_impl(gsc_ctx* ctx, float* const* out_dev, float* const* out_T, gsc_frame_stats* stats, bool sync) {
   if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
+  if (ctx->cfg.reuse == GSC_REUSE_LEARNED && !ctx->reuse_set)
+    return fail(ctx, GSC_ERR_STATE, "the learned reuse form needs predictor weights (gsc_reuse_set_weights)");
   if (ctx->pending && sync) {
     // report an earlier asynchronous frame's problem before starting this one
     int r = finish_frame(ctx);
@@ -543,7 +564,8 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   if (!tiling_ok(cfg.tile_w, cfg.tile_h, cfg.blocks_per_sm)) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
-  if (cfg.precision == GSC_PREC_FP8 || cfg.reuse == GSC_REUSE_LEARNED) return GSC_ERR_UNIMPLEMENTED;
+  if (cfg.precision == GSC_PREC_FP8) return GSC_ERR_UNIMPLEMENTED;
+  if ((cfg.flags & GSC_FLAG_REUSE_COLLECT) && cfg.reuse == GSC_REUSE_OFF) return GSC_ERR_INVALID_ARG;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
 
   gsc_ctx* ctx = new (std::nothrow) gsc_ctx();
@@ -593,7 +615,8 @@ void gsc_destroy(gsc_ctx* ctx) {
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
-                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs};
+                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
+                  ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
   dfree(ctx->d_caches);
@@ -844,6 +867,186 @@ int gsc_set_tiling(gsc_ctx* ctx, uint32_t tile_w, uint32_t tile_h, uint32_t bloc
     if (r) return r;
   }
   ctx->err.clear();
+  return GSC_OK;
+}
+
+// ------------------------------------------------------------------ reuse predictor (K12)
+int gsc_reuse_set_weights(gsc_ctx* ctx, const float* params, uint32_t n_params) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!params || n_params != GSC_REUSE_NPARAM)
+    return fail(ctx, GSC_ERR_INVALID_ARG, "predictor takes %d parameters", GSC_REUSE_NPARAM);
+  if (!finite_all(params, n_params)) return fail(ctx, GSC_ERR_INVALID_ARG, "non-finite predictor parameter");
+  CK(cudaStreamSynchronize(ctx->stream));
+  int r;
+  if (!ctx->rw_theta && ((r = dalloc(ctx, &ctx->rw_theta, GSC_REUSE_NPARAM)) ||
+                         (r = dalloc(ctx, &ctx->rw_w, GSC_REUSE_NPARAM))))
+    return r;
+  CK(cudaMemcpy(ctx->rw_theta, params, sizeof(float) * GSC_REUSE_NPARAM, cudaMemcpyHostToDevice));
+  launch_reuse_round(ctx->rw_theta, ctx->rw_w, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->reuse_set = true;
+  ctx->err.clear();
+  return GSC_OK;
+}
+
+int gsc_reuse_get_weights(gsc_ctx* ctx, float* params, uint32_t n_params) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!params || n_params != GSC_REUSE_NPARAM)
+    return fail(ctx, GSC_ERR_INVALID_ARG, "predictor takes %d parameters", GSC_REUSE_NPARAM);
+  if (!ctx->reuse_set) return fail(ctx, GSC_ERR_STATE, "no predictor weights");
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(params, ctx->rw_theta, sizeof(float) * GSC_REUSE_NPARAM, cudaMemcpyDeviceToHost));
+  return GSC_OK;
+}
+
+int gsc_reuse_collect(gsc_ctx* ctx, uint32_t dview, float* z, uint8_t* label, uint32_t* vis_index, uint64_t cap,
+                      uint64_t* n) {
+  if (!ctx || !n) return GSC_ERR_INVALID_ARG;
+  if (!(ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) || ctx->n_caches == 0)
+    return fail(ctx, GSC_ERR_STATE, "collection needs a cached form created with GSC_FLAG_REUSE_COLLECT");
+  if (ctx->pending) {
+    int r = finish_frame(ctx);
+    if (r) return r;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (dview >= (uint32_t)ctx->n_caches) return fail(ctx, GSC_ERR_INVALID_ARG, "no cache for view %u", dview);
+  const uint32_t V = ctx->h_cnt->vis_count[dview];
+  std::vector<uint8_t> lab(V);
+  if (V) CK(cudaMemcpy(lab.data(), ctx->h_caches[dview].clab, V, cudaMemcpyDeviceToHost));
+  uint64_t cnt = 0;
+  for (uint32_t i = 0; i < V; ++i) cnt += lab[i] != 255;
+  *n = cnt;
+  if (!z && !label && !vis_index) return GSC_OK;
+  std::vector<float> zz;
+  if (z) {
+    zz.resize((size_t)V * 36);
+    if (V) CK(cudaMemcpy(zz.data(), ctx->h_caches[dview].cz, zz.size() * 4, cudaMemcpyDeviceToHost));
+  }
+  uint64_t o = 0;
+  for (uint32_t i = 0; i < V && o < cap; ++i) {
+    if (lab[i] == 255) continue;
+    if (z) std::memcpy(z + o * 36, zz.data() + (size_t)i * 36, 36 * 4);
+    if (label) label[o] = lab[i];
+    if (vis_index) vis_index[o] = i;
+    ++o;
+  }
+  return GSC_OK;
+}
+
+namespace {
+uint64_t splitmix64_next(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct TrainBufs {
+  float *Z = nullptr, *Y = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *part = nullptr, *loss = nullptr;
+  uint32_t *order = nullptr, *ctl = nullptr;
+  ~TrainBufs() {
+    void* p[] = {Z, Y, m, v, grad, part, loss, order, ctl};
+    for (void* q : p) dfree(q);
+  }
+};
+
+int reuse_upload(gsc_ctx* ctx, TrainBufs& B, const float* z, const uint8_t* y, uint64_t n, uint32_t epochs,
+                 uint32_t batch, const uint32_t* order, uint64_t seed, ReuseTrain& T) {
+  int r;
+  if ((r = dalloc(ctx, &B.Z, (size_t)n * 36)) || (r = dalloc(ctx, &B.Y, (size_t)n)) ||
+      (r = dalloc(ctx, &B.order, (size_t)n * epochs)) || (r = dalloc(ctx, &B.m, GSC_REUSE_NPARAM)) ||
+      (r = dalloc(ctx, &B.v, GSC_REUSE_NPARAM)) || (r = dalloc(ctx, &B.grad, GSC_REUSE_NPARAM)) ||
+      (r = dalloc(ctx, &B.part, (size_t)reuse_blocks(batch) * (GSC_REUSE_NPARAM + 1))) ||
+      (r = dalloc(ctx, &B.loss, epochs)) || (r = dalloc(ctx, &B.ctl, 2)))
+    return r;
+  std::vector<float> yf(n);
+  for (uint64_t i = 0; i < n; ++i) {
+    if (y[i] > 1) return fail(ctx, GSC_ERR_INVALID_ARG, "label %llu is %u (0 or 1 expected)", (unsigned long long)i, y[i]);
+    yf[i] = (float)y[i];
+  }
+  if (!finite_all(z, (size_t)n * 36)) return fail(ctx, GSC_ERR_INVALID_ARG, "non-finite predictor input");
+  std::vector<uint32_t> ord((size_t)n * epochs);
+  if (order) {
+    for (size_t i = 0; i < ord.size(); ++i) {
+      if (order[i] >= n) return fail(ctx, GSC_ERR_INVALID_ARG, "order[%zu] out of range", i);
+      ord[i] = order[i];
+    }
+  } else {  // a Fisher-Yates shuffle per epoch from SplitMix64(seed)
+    uint64_t st = seed;
+    for (uint32_t e = 0; e < epochs; ++e) {
+      uint32_t* o = ord.data() + (size_t)e * n;
+      for (uint64_t i = 0; i < n; ++i) o[i] = (uint32_t)i;
+      for (uint64_t i = n - 1; i > 0; --i) std::swap(o[i], o[splitmix64_next(st) % (i + 1)]);
+    }
+  }
+  CK(cudaMemcpy(B.Z, z, (size_t)n * 36 * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.Y, yf.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B.order, ord.data(), ord.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(B.m, 0, GSC_REUSE_NPARAM * 4));
+  CK(cudaMemset(B.v, 0, GSC_REUSE_NPARAM * 4));
+  CK(cudaMemset(B.loss, 0, (size_t)epochs * 4));
+  CK(cudaMemset(B.ctl, 0, 8));
+  T = ReuseTrain{B.Z, B.Y, B.order, ctx->rw_theta, ctx->rw_w, B.m, B.v, B.grad, B.part, B.loss, B.ctl};
+  return GSC_OK;
+}
+}  // namespace
+
+int gsc_reuse_train(gsc_ctx* ctx, const float* z, const uint8_t* y, uint64_t n, uint32_t epochs, uint32_t batch,
+                    float lr, uint64_t seed, const uint32_t* order, float* epoch_loss) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!z || !y || n == 0 || n > (1ull << 26) || epochs == 0 || batch == 0 || !(lr > 0.f) || !std::isfinite(lr) ||
+      n * (uint64_t)epochs > (1ull << 31))
+    return fail(ctx, GSC_ERR_INVALID_ARG, "bad training arguments");
+  if (!ctx->reuse_set) return fail(ctx, GSC_ERR_STATE, "set initial predictor weights first");
+  if (ctx->pending) {
+    int r = finish_frame(ctx);
+    if (r) return r;
+  }
+  batch = (uint32_t)std::min<uint64_t>(batch, n);
+  TrainBufs B;
+  ReuseTrain T{};
+  int r = reuse_upload(ctx, B, z, y, n, epochs, batch, order, seed, T);
+  if (r) return r;
+  // one epoch as a graph: every mini-batch's fwd/bwd, reduce and Adam step
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  for (uint64_t b0 = 0; b0 < n; b0 += batch) {
+    const uint32_t nb = (uint32_t)std::min<uint64_t>(batch, n - b0);
+    launch_reuse_batch(T, (uint32_t)n, (uint32_t)b0, nb, lr, 1.0f / (float)n, ctx->stream);
+  }
+  launch_reuse_epoch_end(T, ctx->stream);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "training graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "training graph instantiate: %s", cudaGetErrorString(e));
+  for (uint32_t ep = 0; ep < epochs && e == cudaSuccess; ++ep) e = cudaGraphLaunch(ge, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "training: %s", cudaGetErrorString(e));
+  if (epoch_loss) CK(cudaMemcpy(epoch_loss, B.loss, (size_t)epochs * 4, cudaMemcpyDeviceToHost));
+  ctx->err.clear();
+  return GSC_OK;
+}
+
+int gsc_debug_reuse_grad(gsc_ctx* ctx, const float* z, const uint8_t* y, uint64_t n, float* grad, float* loss) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!z || !y || !grad || n == 0 || n > (1ull << 24)) return fail(ctx, GSC_ERR_INVALID_ARG, "bad arguments");
+  if (!ctx->reuse_set) return fail(ctx, GSC_ERR_STATE, "set predictor weights first");
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<uint32_t> ident(n);
+  for (uint64_t i = 0; i < n; ++i) ident[i] = (uint32_t)i;
+  TrainBufs B;
+  ReuseTrain T{};
+  int r = reuse_upload(ctx, B, z, y, n, 1, (uint32_t)n, ident.data(), 0, T);
+  if (r) return r;
+  launch_reuse_batch(T, (uint32_t)n, 0, (uint32_t)n, 0.f, 1.0f / (float)n, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(grad, B.grad, GSC_REUSE_NPARAM * 4, cudaMemcpyDeviceToHost));
+  if (loss) CK(cudaMemcpy(loss, B.loss, 4, cudaMemcpyDeviceToHost));
   return GSC_OK;
 }
 

@@ -17,9 +17,22 @@
 //            (Eq. 4, linear guiding function), computed in integers.
 // The decoder writes fresh attributes of misses into their lines; the
 // projection reads hits from their lines.
-#include "gsc_internal.cuh"
+//
+// Learned form (reuse = learned): a valid line is reused iff the predictor
+// of reuse_common.cuh says so (instead of age <= depth); every decoded line
+// is stamped with the unit direction camera -> anchor it was decoded for.
+// Collection (training data): between probe and assign, every visible anchor
+// holding a valid line gets its predictor inputs and a label comparing the
+// line with a fresh derivation of the same frame.
+#include "reuse_common.cuh"
 
 namespace gsc {
+
+// Derivation camera of cache c (the unified camera of a stereo pair) and anchor a's position.
+__device__ __forceinline__ float anchor_dir(const ModelDev& md, const CamDev& cam, uint32_t a, float d[3]) {
+  const float x[3] = {md.px[a], md.py[a], md.pz[a]};
+  return pinned_dir(x, cam.pc, cam.pc_lo, d);
+}
 
 __global__ void k_cache_tick(CacheDev* caches, int n) {
   const int c = threadIdx.x;
@@ -31,20 +44,43 @@ __global__ void k_cache_tick(CacheDev* caches, int n) {
   st[CS_FREE] = 0;
 }
 
-__global__ void k_cache_probe(CacheDev* __restrict__ caches, int c, const FrameDev* __restrict__ fd,
-                              uint32_t* const* __restrict__ vis) {
+// rw: predictor weights (learned form), else unused.
+__global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ caches, int c,
+                                                     const FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
+                                                     const ModelDev* __restrict__ models,
+                                                     const float* __restrict__ rw, int learned) {
+  __shared__ float s_w[RPARAM];
   const CacheDev cd = caches[c];
   const uint32_t V = fd->vis_count[c];
   const uint32_t t = cd.state[CS_T], depth = cd.state[CS_DEPTH], D = cd.state[CS_DMAX];
   const uint32_t* ids = vis[c];
   const uint32_t stride = gridDim.x * blockDim.x;
+  if (learned) {
+    for (int i = threadIdx.x; i < RPARAM; i += blockDim.x) s_w[i] = rw[i];
+    __syncthreads();
+  }
+  const CamDev& cam = fd->dcam[c];
+  const ModelDev& md = models[cam.model];
   for (uint32_t vi = blockIdx.x * blockDim.x + threadIdx.x; vi < V; vi += stride) {
     const uint32_t a = ids[vi];
     const uint32_t s = cd.slot_of[a];
     bool valid = s < cd.S && cd.slot_anchor[s] == a;
     const uint32_t age = valid ? t - cd.slot_frame[s] : 0xFFFFFFFFu;
     valid = valid && age <= D;
-    const bool hit = valid && age <= depth;
+    bool hit;
+    if (learned) {
+      hit = false;
+      if (valid) {
+        float dn[3], z[RZ];
+        const float dist = anchor_dir(md, cam, a, dn);
+        const float4 dl4 = cd.slot_dir[s];
+        const float dl[3] = {dl4.x, dl4.y, dl4.z};
+        reuse_features(reinterpret_cast<const float*>(md.feat + (size_t)a * (FDIM / 4)), dn, dl, dist, z);
+        hit = reuse_logit(s_w, z) >= 0.f;
+      }
+    } else {
+      hit = valid && age <= depth;
+    }
     cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
     cd.new_flag[vi] = valid ? 0u : 1u;
     if (!hit) cd.miss[atomicAdd(&cd.state[CS_MISSES], 1u)] = vi;
@@ -60,8 +96,10 @@ __global__ void k_cache_free_list(CacheDev* __restrict__ caches, int c) {
 }
 
 __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, const FrameDev* __restrict__ fd,
-                               uint32_t* const* __restrict__ vis) {
+                               uint32_t* const* __restrict__ vis, const ModelDev* __restrict__ models) {
   const CacheDev cd = caches[c];
+  const CamDev& cam = fd->dcam[c];
+  const ModelDev& md = models[cam.model];
   const uint32_t V = fd->vis_count[c];
   const uint32_t t = cd.state[CS_T], n_free = cd.state[CS_FREE];
   const uint32_t* ids = vis[c];
@@ -79,6 +117,56 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, const Frame
     cd.slot_anchor[line] = a;
     cd.slot_frame[line] = t;
     cd.slot_of[a] = line;
+    float d[3];
+    anchor_dir(md, cam, a, d);
+    cd.slot_dir[line] = make_float4(d[0], d[1], d[2], 0.f);
+  }
+}
+
+// Collection: predictor inputs and label of every visible anchor holding a
+// valid line, before this frame touches the lines.  Label 1 iff the line and
+// the fresh derivation (attrs_fresh, this frame, frame item order) keep the
+// same Gaussians and, over the kept ones, |d alpha| <= 1/255 and
+// max_channel |d c| * alpha_fresh <= 1/255.
+__global__ void k_reuse_label(CacheDev* __restrict__ caches, int c, const FrameDev* __restrict__ fd,
+                              uint32_t* const* __restrict__ vis, const ModelDev* __restrict__ models,
+                              const float4* __restrict__ attrs_fresh) {
+  const CacheDev cd = caches[c];
+  const uint32_t V = fd->vis_count[c];
+  const uint32_t* ids = vis[c];
+  const CamDev& cam = fd->dcam[c];
+  const ModelDev& md = models[cam.model];
+  const uint32_t item0 = fd->item_base[c];
+  const float thr = 1.0f / 255.0f;
+  for (uint32_t vi = blockIdx.x * blockDim.x + threadIdx.x; vi < V; vi += gridDim.x * blockDim.x) {
+    const uint32_t st = cd.vstat[vi];
+    if (st == LINE_NONE) {
+      cd.clab[vi] = 255;
+      continue;
+    }
+    const uint32_t s = st & ~LINE_HIT, a = ids[vi];
+    float dn[3], z[RZ];
+    const float dist = anchor_dir(md, cam, a, dn);
+    const float4 dl4 = cd.slot_dir[s];
+    const float dl[3] = {dl4.x, dl4.y, dl4.z};
+    reuse_features(reinterpret_cast<const float*>(md.feat + (size_t)a * (FDIM / 4)), dn, dl, dist, z);
+    float* zo = cd.cz + (size_t)vi * RZ;
+#pragma unroll
+    for (int k = 0; k < RZ; ++k) zo[k] = z[k];
+    bool ok = true;
+    for (int j = 0; j < K; ++j) {
+      const uint2 h0 = cd.slot_attr[((size_t)s * K + j) * 3];
+      const float2 ac = __half22float2(*reinterpret_cast<const __half2*>(&h0.x));
+      const float2 cc = __half22float2(*reinterpret_cast<const __half2*>(&h0.y));
+      const float4 f = attrs_fresh[3 * ((size_t)(item0 + vi) * K + j)];
+      const bool kc = ac.x > 0.f, kf = f.x > 0.f;
+      if (kc != kf) ok = false;
+      if (kf) {
+        const float dc = fmaxf(fmaxf(fabsf(ac.y - f.y), fabsf(cc.x - f.z)), fabsf(cc.y - f.w)) * f.x;
+        if (fabsf(ac.x - f.x) > thr || dc > thr) ok = false;
+      }
+    }
+    cd.clab[vi] = ok ? 1 : 0;
   }
 }
 
@@ -105,18 +193,20 @@ __global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd, int replay
 
 // caches: device array; host: its host-side mirror (same device pointers).
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
+                        const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s) {
   k_cache_tick<<<1, 32, 0, s>>>(caches, n_caches);
   for (int c = 0; c < n_caches; ++c) {
     if (!host[c].active) continue;
     const CacheDev& h = host[c];
-    k_cache_probe<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis);
+    k_cache_probe<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w, learned ? 1 : 0);
+    if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
     launch_scan_u32(h.new_flag, nullptr, &fd->vis_count[c], h.new_rank, h.state + CS_NEW, scan_status, fd,
                     SLOT_CACHE + 2 * c, n_sm, s);
     launch_scan_u32(h.free_flag, nullptr, h.state + CS_S, h.free_rank, h.state + CS_FREE, scan_status, fd,
                     SLOT_CACHE + 2 * c + 1, n_sm, s);
     k_cache_free_list<<<n_sm * 4, 256, 0, s>>>(caches, c);
-    k_cache_assign<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis);
+    k_cache_assign<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models);
   }
 }
 

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const ModelDev md = models[model];
-  {  // weights image (bf16 operands + fp32 biases), 40,960 bytes
+  {  // weights image (bf16 operands, zeroed H staging area, fp32 biases), 65,536 bytes
     const uint4* src = reinterpret_cast<const uint4*>(md.w_tc);
     uint4* dst = reinterpret_cast<uint4*>(smem + TC_W1);
     for (int i = t; i < (int)((TC_META - TC_W1) / 16); i += TC_NT) dst[i] = src[i];
@@ -386,10 +386,11 @@ static uint16_t host_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
-// The 40,960-byte shared-memory image of the tensor-core MLP weights:
+// The 65,536-byte shared-memory image of the tensor-core MLP weights:
 // W1cat as the B operand [96 rows (hidden) x 48 K] and the Gaussian-major
 // block-diagonal W2 as the B operand [160 rows x 96 K], both in K-chunks of
-// 8 bf16 x all rows (16 bytes per row), then b1 [96] and b2 [160] in fp32.
+// 8 bf16 x all rows (16 bytes per row), the hidden-activation staging area
+// (zeros here), then b1 [96] and b2 [160] in fp32.
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img) {
   img.assign(TC_META - TC_W1, 0);

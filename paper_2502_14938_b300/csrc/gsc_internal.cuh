@@ -124,7 +124,7 @@ struct ModelDev {
   const float* scale;     // [N]
   const float* w32;       // packed weights, W_FLOATS
   const void* feat_bf16;  // [N][32] bf16 (tensor-core forms)
-  const void* w_tc;       // tensor-core weight image (40,960 bytes)
+  const void* w_tc;       // tensor-core weight image (65,536 bytes)
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
@@ -144,6 +144,9 @@ struct CacheDev {
   uint32_t* free_list;    // [S]
   uint32_t* miss;         // [visible] visible indices to decode
   uint32_t* state;        // [CS_WORDS]
+  float4* slot_dir;       // [S] unit direction camera -> anchor when the line was decoded
+  float* cz;              // [visible][36] predictor inputs of the frame (collection)
+  uint8_t* clab;          // [visible] label: 1 reuse ok, 0 not, 255 no valid line (collection)
   uint32_t S;
   uint32_t active;
 };
@@ -353,7 +356,29 @@ void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t
 // hits from their lines) -> records
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
                     const CacheDev* caches, Records rec, int n_sm, cudaStream_t s);
+// Reuse-predictor training buffers (device): samples, order, parameters,
+// Adam moments, gradient, per-block partials, per-epoch loss, counters
+// (ctl[0] Adam steps taken, ctl[1] epoch).
+struct ReuseTrain {
+  const float* Z;         // [n][36]
+  const float* Y;         // [n] labels 0 / 1
+  const uint32_t* order;  // [epochs][n]
+  float* theta;           // [2433] float32 master
+  float* w;               // [2433] bfloat16-rounded copy (forward / inference)
+  float* m;
+  float* v;
+  float* grad;
+  float* part;            // [blocks][2434]
+  float* loss;            // [epochs]
+  uint32_t* ctl;          // [2]
+};
+void launch_reuse_round(const float* theta, float* w, cudaStream_t s);
+int reuse_blocks(uint32_t nb);
+void launch_reuse_batch(const ReuseTrain& T, uint32_t n_total, uint32_t b0, uint32_t nb, float lr, float loss_scale,
+                        cudaStream_t s);
+void launch_reuse_epoch_end(const ReuseTrain& T, cudaStream_t s);
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
+                        const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s);
 void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, bool replay, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,

@@ -27,6 +27,8 @@ REUSE = {"off": 0, "depth": 1, "learned": 2}
 FLAG_DEBUG_ATTRS = 0x1
 FLAG_DEBUG_T = 0x2
 FLAG_TIMING = 0x4
+FLAG_REUSE_COLLECT = 0x8
+REUSE_NPARAM = 2433
 
 
 class GscError(RuntimeError):
@@ -107,6 +109,11 @@ def lib():
             "gsc_scan_u32_noalloc": (I, [P, P, U64, P, P]),
             "gsc_debug_cache": (I, [P, U32, P, U64, P, P]),
             "gsc_set_tiling": (I, [P, U32, U32, U32]),
+            "gsc_reuse_set_weights": (I, [P, P, U32]),
+            "gsc_reuse_get_weights": (I, [P, P, U32]),
+            "gsc_reuse_collect": (I, [P, U32, P, P, P, U64, P]),
+            "gsc_reuse_train": (I, [P, P, P, U64, U32, U32, C.c_float, U64, P, P]),
+            "gsc_debug_reuse_grad": (I, [P, P, P, U64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -267,6 +274,50 @@ class Renderer:
     def set_tiling(self, tile_w: int, tile_h: int, blocks_per_sm: int = 0):
         """Blend tiling of this context (the autotuner's knob)."""
         self._check(lib().gsc_set_tiling(self.ctx, tile_w, tile_h, blocks_per_sm))
+
+    # ---------------------------------------------------------------- reuse predictor
+    def reuse_set_weights(self, theta):
+        t = np.ascontiguousarray(theta, np.float32)
+        assert t.shape == (REUSE_NPARAM,)
+        self._check(lib().gsc_reuse_set_weights(self.ctx, _p(t), REUSE_NPARAM))
+
+    def reuse_get_weights(self) -> np.ndarray:
+        t = np.zeros(REUSE_NPARAM, np.float32)
+        self._check(lib().gsc_reuse_get_weights(self.ctx, _p(t), REUSE_NPARAM))
+        return t
+
+    def reuse_collect(self, d: int):
+        """(z [n,36], label [n], visible index [n]) of derivation view d's last frame."""
+        n = C.c_uint64()
+        self._check(lib().gsc_reuse_collect(self.ctx, d, None, None, None, 0, C.byref(n)))
+        m = n.value
+        z = np.zeros((max(m, 1), 36), np.float32)
+        y = np.zeros(max(m, 1), np.uint8)
+        vi = np.zeros(max(m, 1), np.uint32)
+        self._check(lib().gsc_reuse_collect(self.ctx, d, _p(z), _p(y), _p(vi), m, C.byref(n)))
+        return z[:m], y[:m], vi[:m]
+
+    def reuse_train(self, z, y, epochs: int, batch: int, lr: float, seed: int = 0, order=None) -> np.ndarray:
+        """Train on the GPU; returns the mean loss of each epoch."""
+        z = np.ascontiguousarray(z, np.float32)
+        y = np.ascontiguousarray(y, np.uint8)
+        n = z.shape[0]
+        assert z.shape == (n, 36) and y.shape == (n,)
+        o = None if order is None else np.ascontiguousarray(order, np.uint32)
+        if o is not None:
+            assert o.size == n * epochs
+        loss = np.zeros(epochs, np.float32)
+        self._check(lib().gsc_reuse_train(self.ctx, _p(z), _p(y), n, epochs, batch, float(lr), int(seed),
+                                          _p(o), _p(loss)))
+        return loss
+
+    def debug_reuse_grad(self, z, y):
+        z = np.ascontiguousarray(z, np.float32)
+        y = np.ascontiguousarray(y, np.uint8)
+        g = np.zeros(REUSE_NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(lib().gsc_debug_reuse_grad(self.ctx, _p(z), _p(y), z.shape[0], _p(g), _p(loss)))
+        return g, float(loss[0])
 
     def cache_reset(self):
         self._check(lib().gsc_cache_reset(self.ctx))

@@ -1,0 +1,160 @@
+"""The learned reuse predictor on the GPU against the oracle: training
+gradients and losses, the learned form's reuse decisions (bit-exact: the
+decision is an integer taken in pinned float32 on both sides) and the
+collected training samples (inputs bit-exact, labels equal away from their
+thresholds)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from oracle import predictor as P
+from oracle.cache import CacheSim, cached_derive, collect_samples, project_view
+from test_gpu_cache import CACHED_PIX_TOL, gpu_lines, set_cams
+from test_gpu_parity import check_image, make_renderer, render
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# A cached float16 value differs between the GPU (rounded from float32) and
+# the oracle (rounded from float64) by at most one float16 ulp, 4.9e-4 below
+# 1; labels are compared where every comparison is farther than that (plus
+# float32 slack) from its threshold.
+LABEL_MARGIN = 6e-4
+# The BF16 form's fresh attributes differ from the oracle's bf16-quantised
+# float64 ones by up to 1e-2 (a rounded hidden activation can flip), so its
+# labels are compared only away from that.
+LABEL_MARGIN_BF16 = 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def renderer_with_weights(theta, **kw):
+    import paper_2502_14938_b300 as pkg
+    m = gen.tiny_scene()
+    r = pkg.Renderer(max_views=1, **kw)
+    r.load_model(m)
+    r.reuse_set_weights(theta)
+    return r
+
+
+def tiny_frames(n=16):
+    cams = []
+    for f in range(n):
+        ang = 0.006 * f if f < 10 else 0.06 + 0.03 * (f - 10)
+        R = np.array([[np.cos(ang), 0, -np.sin(ang)], [0, 1, 0], [np.sin(ang), 0, np.cos(ang)]])
+        cams.append(gen.pinhole(R, np.array([0.04 * f, 0.01 * f, -15.0]), 256, 256, 60.0))
+    return cams
+
+
+def test_gradient_matches_oracle_backprop():
+    rs = np.random.default_rng(0)
+    theta = (rs.standard_normal(P.NPARAM) * 0.2).astype(np.float32)
+    Z = rs.standard_normal((4099, P.NZ)).astype(np.float32)   # ragged last block
+    y = (rs.uniform(size=4099) < 0.3).astype(np.uint8)
+    r = renderer_with_weights(theta)
+    g, loss = r.debug_reuse_grad(Z, y)
+    loss64, g64 = P.grad64(theta, Z, y)
+    assert abs(loss - loss64) <= 1e-5 * loss64
+    # float32 sums of <= 4099 terms: normwise relative error per tensor
+    cuts = [0, P.NZ * P.NH, P.NZ * P.NH + P.NH, P.NZ * P.NH + 2 * P.NH, P.NPARAM]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        err = np.linalg.norm(g[a:b] - g64[a:b]) / np.linalg.norm(g64[a:b])
+        assert err < 1e-4, (a, b, err)
+    r.close()
+
+
+def test_training_tracks_oracle_adam():
+    rs = np.random.default_rng(1)
+    n, epochs, batch = 3000, 4, 256
+    Z = rs.standard_normal((n, P.NZ)).astype(np.float32)
+    y = ((Z[:, 32] ** 2 + Z[:, 33] ** 2) < 1.0).astype(np.uint8)
+    theta0 = gen.reuse_mlp_init(7)
+    order = np.concatenate([rs.permutation(n) for _ in range(epochs)]).astype(np.uint32)
+    r = renderer_with_weights(theta0)
+    losses = r.reuse_train(Z, y, epochs, batch, 3e-3, order=order)
+    batches = [order[e * n + b: e * n + min(b + batch, n)] for e in range(epochs) for b in range(0, n, batch)]
+    th64, bl = P.train64(theta0, Z, y.astype(np.float64), batches, 3e-3)
+    sizes = np.array([len(b) for b in batches], np.float64)
+    nb = len(range(0, n, batch))
+    ref = [float(np.sum(np.array(bl[e * nb:(e + 1) * nb]) * sizes[e * nb:(e + 1) * nb]) / n) for e in range(epochs)]
+    assert np.all(np.abs(losses - ref) <= 2e-2 * np.array(ref)), (losses, ref)
+    assert np.all(np.diff(losses) < 0) and losses[-1] < 0.9 * losses[0]
+    th = r.reuse_get_weights()
+    assert np.linalg.norm(th - th64) <= 2e-2 * np.linalg.norm(th64)
+    r.close()
+
+
+def test_learned_decisions_match_oracle_simulation():
+    """Random weights (mixed decisions) on a panning path: hit / line sets
+    bit-exact every frame; images within the cached tolerance."""
+    rs = np.random.default_rng(2)
+    theta = (rs.standard_normal(P.NPARAM) * 0.2).astype(np.float32)
+    m = gen.tiny_scene()
+    r = make_renderer(m, [gen.tiny_camera()], reuse="learned", cache_gaussians=1500 * 10)
+    r.reuse_set_weights(theta)
+    sim = CacheSim(m.n, 1500, max_depth=10)
+    n_hit = n_valid_miss = 0
+    for f, cam in enumerate(tiny_frames()):
+        set_cams(r, [cam], [-1])
+        (img,), st = render(r, [cam])
+        valid, _, _ = sim.peek(oracle.cull(m, cam))
+        ids, attrs, kept, hit, line, used = cached_derive(m, cam, sim, theta=theta)
+        ghit, gline = gpu_lines(r.debug_cache(0)[0])
+        assert np.array_equal(ghit, hit), f
+        assert np.array_equal(gline, line), f
+        assert st["derived_anchors"] == int((~hit).sum())
+        n_hit += int(hit.sum())
+        n_valid_miss += int((valid & ~hit).sum())
+        vr = project_view(m, cam, ids, attrs, kept)
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height)
+        check_image(img, ref, mg, f"learned frame {f}", CACHED_PIX_TOL)
+    assert n_hit > 0 and n_valid_miss > 0  # the predictor both reused and refused
+    r.close()
+
+
+def test_learned_form_requires_weights():
+    import paper_2502_14938_b300 as pkg
+    m = gen.tiny_scene()
+    r = make_renderer(m, [gen.tiny_camera()], reuse="learned")
+    with pytest.raises(pkg.GscError):
+        render(r, [gen.tiny_camera()])
+    with pytest.raises(pkg.GscError):
+        r.reuse_set_weights(np.full(P.NPARAM, np.nan, np.float32))
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_collected_samples_match_oracle(precision):
+    import paper_2502_14938_b300 as pkg
+    m = gen.tiny_scene()
+    r = make_renderer(m, [gen.tiny_camera()], reuse="depth", cache_gaussians=1500 * 10, precision=precision,
+                      flags=pkg.FLAG_REUSE_COLLECT)
+    sim = CacheSim(m.n, 1500, max_depth=10)
+    quant = None
+    lm, max_flip = LABEL_MARGIN, 0.01
+    if precision == "bf16":
+        quant = oracle.OrcQuant()
+        quant.mode = 1
+        lm, max_flip = LABEL_MARGIN_BF16, 0.05
+    total = flipped = pos = 0
+    for f, cam in enumerate(tiny_frames()):
+        vi, z, lab, margin = collect_samples(m, cam, sim, quant)
+        set_cams(r, [cam], [-1])
+        render(r, [cam])
+        cached_derive(m, cam, sim, quant)
+        gz, gy, gvi = r.reuse_collect(0)
+        assert np.array_equal(gvi, vi.astype(np.uint32)), f
+        assert np.array_equal(gz, z), f
+        far = margin > lm
+        assert np.array_equal(gy[far].astype(bool), lab[far]), f
+        total += len(vi)
+        flipped += int((gy.astype(bool) != lab).sum())
+        pos += int(lab.sum())
+    assert total > 1000 and 0 < pos < total
+    assert flipped <= max_flip * total
+    r.close()
