@@ -134,6 +134,7 @@ def run_reference(args, rank, world):
         ts.append(oracle_frame_sample(model, *frames[f], phase=s))
     mean = float(np.mean(ts))
     batched = run_batched(args, flush) if args.batched else None
+    learned = run_learned(model, flush, args.steps) if args.learned else None
 
     cores = oracle.num_threads()
     sample = ("per step: one stereo frame of the path, full filtering/derivation/projection in float64, "
@@ -379,6 +380,56 @@ def run_batched(args, flush):
             "reuse_frac_mean": float(np.mean(reuse)), "tune_s": t_tune, "gen_s": t_gen}
 
 
+def run_learned(model, flush, steps):
+    """Cache + learned-reuse form on the look-around path (seed 12, 80-95%
+    frame-to-frame overlap): 100k labels collected on paths 20-29, GPU
+    training, then frame rate (label collection off) and quality of the
+    cached BF16 unified form with the depth rule and with the predictor."""
+    import torch
+    import gen
+    import paper_2502_14938_b300 as pkg
+    from paper_2502_14938_b300 import reuse
+    t0 = time.perf_counter()
+    Z, Y, st = reuse.collect(model, [gen.stereo_frames(gen.reuse_path(s)) for s in range(20, 30)], 100_000, seed=1)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    theta, losses = reuse.train(Z, Y, gen.reuse_mlp_init(7), epochs=40, batch=4096, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    path = gen.stereo_frames(gen.reuse_path(12))
+    out = {"path": "look-around path seed 12 (120 frames)", "collect_s": t_collect, "train_s": t_train,
+           "samples": st["samples"], "positive_frac": st["positive_frac"], "final_loss": float(losses[-1])}
+    for name, th in (("depth", None), ("learned", theta)):
+        r = pkg.Renderer(max_views=2, precision="bf16", reuse="depth" if th is None else "learned",
+                         stereo_unify=True)
+        mid = r.load_model(model)
+        if th is not None:
+            r.reuse_set_weights(th)
+        outs = [torch.empty((path[0][0].height, path[0][0].width, 3), dtype=torch.float32, device="cuda")
+                for _ in range(2)]
+        for L, R in path:
+            set_pair(r, mid, L, R)
+            r.render_frame(outs)
+        r.synchronize()
+        r.cache_reset()
+        n = min(steps, len(path))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        stream = torch.cuda.current_stream()
+        for f in range(n):
+            set_pair(r, mid, *path[f])
+            flush.fill_(f & 0xFF)
+            evs[f][0].record(stream)
+            r.render_frame(outs, stats=False)
+            evs[f][1].record(stream)
+        torch.cuda.synchronize()
+        r.close()
+        ms = np.array([a.elapsed_time(b) for a, b in evs])
+        ev = reuse.evaluate(model, path, th)
+        out[name] = {"fps": 1000.0 / float(ms.mean()), "ms_mean": float(ms.mean()),
+                     "p99_ms": float(np.percentile(ms, 99)), **{k: ev[k] for k in
+                     ("reuse_frac", "wrong_reuse_frac", "psnr_db_min", "psnr_db_mean")}}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -430,7 +481,7 @@ def run_ours(args, rank, world):
             (ref, _, _, _), _ = oracle.render_view(model, cam)
             got = outs[v].cpu().numpy().astype(np.float64)
             mse += float(np.mean((got - ref) ** 2)) / 2
-        psnrs.append(float("inf") if mse == 0 else 10 * np.log10(1.0 / mse))
+        psnrs.append(10 * np.log10(1.0 / max(mse, 1e-10)))  # identical images count as 100 dB
 
     # ---- end to end through the public API with host buffers
     host = [torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
@@ -445,6 +496,7 @@ def run_ours(args, rank, world):
 
     # ---- CPU baseline: the oracle on a bounded sample
     batched = run_batched(args, flush) if args.batched else None
+    learned = run_learned(model, flush, args.steps) if args.learned else None
 
     cores = oracle.num_threads()
     cts = [oracle_frame_sample(model, *frames[f], phase=i) for i, f in enumerate((0, 150))]
@@ -459,7 +511,7 @@ def run_ours(args, rank, world):
            "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
-           "compare": others, "batched": batched, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
+           "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+f32" if FORMS[form]["precision"] == "bf16" else "f32",
@@ -482,6 +534,8 @@ def main():
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the batched multi-viewer form (reported under config.batched)")
     ap.add_argument("--tiling-cache", default=None, help="JSON file the autotuner reads / writes")
+    ap.add_argument("--learned", action=argparse.BooleanOptionalAction, default=True,
+                    help="also train the reuse predictor and time the learned form (config.learned_reuse)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -3,6 +3,7 @@ exports every symbol its headers declare; the binding's structs match the
 C layout."""
 import ctypes as C
 import subprocess
+import numpy as np
 
 import pytest
 
@@ -73,3 +74,15 @@ def test_create_without_gpu_fails_cleanly():
     rc = pkg.lib().gsc_create(C.byref(ctx), None, None)
     assert rc in (-3, -2)  # GSC_ERR_CUDA / GSC_ERR_OOM, no context
     assert not ctx.value
+
+
+def test_predictor_file_roundtrip(tmp_path):
+    from paper_2502_14938_b300 import reuse
+    theta = np.random.default_rng(0).standard_normal(native.REUSE_NPARAM).astype(np.float32)
+    p = str(tmp_path / "w.gscr")
+    reuse.save(p, theta)
+    assert np.array_equal(reuse.load(p), theta)
+    with open(p, "r+b") as f:
+        f.write(b"XXXX")
+    with pytest.raises(ValueError):
+        reuse.load(p)

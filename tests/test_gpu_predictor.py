@@ -158,3 +158,25 @@ def test_collected_samples_match_oracle(precision):
     assert total > 1000 and 0 < pos < total
     assert flipped <= max_flip * total
     r.close()
+
+
+def test_learned_beats_depth_rule_on_held_out_path():
+    """Gain test: 100k labels from the look-around paths with seeds 20-29 on
+    the 2M-anchor city, GPU training, then the held-out path (seed 30):
+    against the depth rule of Eq. 4 the predictor must at least halve the
+    share of wrong reuses and raise the worst frame's PSNR (against the same
+    form without the cache) by >= 3 dB while still reusing more than half
+    the anchors."""
+    from paper_2502_14938_b300 import reuse
+    model, _ = gen.city_workload(n_frames=2)
+    train_paths = [gen.stereo_frames(gen.reuse_path(s)) for s in range(20, 30)]
+    Z, Y, st = reuse.collect(model, train_paths, 100_000, seed=1)
+    assert st["samples"] == 100_000 and 0.05 < st["positive_frac"] < 0.95
+    theta, losses = reuse.train(Z, Y, gen.reuse_mlp_init(7), epochs=40, batch=4096, lr=2e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    held = gen.stereo_frames(gen.reuse_path(30))
+    dep = reuse.evaluate(model, held, None)
+    lrn = reuse.evaluate(model, held, theta)
+    assert lrn["wrong_reuse_frac"] <= 0.5 * dep["wrong_reuse_frac"], (dep, lrn)
+    assert lrn["psnr_db_min"] >= dep["psnr_db_min"] + 3.0, (dep, lrn)
+    assert lrn["reuse_frac"] > 0.5, lrn
