@@ -323,6 +323,45 @@ def round_e4m3(x: float) -> float:
     return float(lib().orc_round_e4m3(float(x)))
 
 
+E4M3_MAX = 448.0
+
+
+def pow2_ceil(v: float) -> float:
+    """Smallest power of two >= v (v > 0); 1 for v <= 0."""
+    if not v > 0:
+        return 1.0
+    m, e = np.frexp(v)  # v = m 2^e, m in [0.5, 1)
+    return float(np.ldexp(1.0, int(e) - 1 if m == 0.5 else int(e)))
+
+
+def fp8_scales(model) -> OrcQuant:
+    """Per-tensor scales of the FP8-E4M3 form (a reading of "per-tensor
+    scales" with amax / 448, rounded up to a power of two so that scaling is
+    exact):
+      s_x     from max(amax of the anchor features, 1) (the unit view
+              direction shares the input tensor),
+      s_w1[h], s_w2[h] from amax of each head's weight matrices,
+      s_h[h]  from a bound on the head's hidden activations that holds for
+              every anchor and view direction:
+              max_o sum_c |W1[c,o]| amax_c + |b1[o]|, with amax_c the
+              largest |feature c| over the anchors and 1 for a direction
+              component."""
+    q = OrcQuant()
+    q.mode = 2
+    feat = np.abs(np.asarray(model.feat, np.float64))
+    amax_c = feat.max(axis=0) if feat.size else np.zeros(feat.shape[1])
+    q.s_x = pow2_ceil(max(float(amax_c.max()) if amax_c.size else 0.0, 1.0) / E4M3_MAX)
+    xb = np.concatenate([amax_c, np.ones(3)])
+    for h in range(3):
+        W1 = np.asarray(model.W1[h], np.float64)
+        W2 = np.asarray(model.W2[h], np.float64)
+        q.s_w1[h] = pow2_ceil(float(np.abs(W1).max()) / E4M3_MAX)
+        q.s_w2[h] = pow2_ceil(float(np.abs(W2).max()) / E4M3_MAX)
+        hb = (np.abs(W1) * xb[:, None]).sum(axis=0) + np.abs(np.asarray(model.b1[h], np.float64))
+        q.s_h[h] = pow2_ceil(float(hb.max()) / E4M3_MAX)
+    return q
+
+
 # ------------------------------------------------------------------ one view / one frame
 @dataclass
 class ViewResult:

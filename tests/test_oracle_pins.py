@@ -374,3 +374,38 @@ def test_e4m3_rounding_matches_torch():
     assert np.array_equal(got, ref)
     # reading: values beyond the largest finite e4m3 saturate to +-448
     assert oracle.round_e4m3(1e4) == 448.0 and oracle.round_e4m3(-900.0) == -448.0
+
+
+def test_fp8_scales_are_tight_powers_of_two_and_bound_the_hidden_layer():
+    """FP8 form: every scale a power of two with amax / s in (224, 448]; the
+    hidden-activation scale bounds every anchor's hidden layer for any view
+    direction (checked on all tiny-scene anchors x random directions)."""
+    m = gen.tiny_scene()
+    q = oracle.fp8_scales(m)
+    assert q.mode == 2
+
+    def tight(s, amax):
+        assert np.log2(s) == np.round(np.log2(s))
+        assert 224.0 < amax / s <= 448.0
+
+    tight(q.s_x, max(np.abs(m.feat).max(), 1.0))
+    rs = np.random.default_rng(0)
+    d = rs.standard_normal((m.n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    x = np.concatenate([m.feat.astype(np.float64), d], axis=1)
+    for h in range(3):
+        tight(q.s_w1[h], np.abs(m.W1[h]).max())
+        tight(q.s_w2[h], np.abs(m.W2[h]).max())
+        hid = np.maximum(x @ m.W1[h].astype(np.float64) + m.b1[h], 0.0)
+        assert hid.max() <= 448.0 * q.s_h[h]
+    assert oracle.pow2_ceil(1.0) == 1.0 and oracle.pow2_ceil(1.5) == 2.0 and oracle.pow2_ceil(0.25) == 0.25
+    assert oracle.pow2_ceil(3e-5) == 2.0 ** -15
+
+
+def test_e4m3_rounding_closed_forms():
+    """E4M3: 3 mantissa bits, bias 7, subnormal spacing 2^-9, largest finite 448, saturating."""
+    cases = {1.0: 1.0, 1.0625: 1.0, 1.1875: 1.25, 1.125: 1.125, 448.0: 448.0, 460.0: 448.0, 1e6: 448.0,
+             2.0 ** -9: 2.0 ** -9, 1.4 * 2.0 ** -10: 2.0 ** -9, 0.4 * 2.0 ** -9: 0.0, -3.3: -3.25,
+             2.0 ** -6 * 1.0625: 2.0 ** -6, 0.01: 0.009765625}
+    for x, want in cases.items():
+        assert oracle.round_e4m3(x) == want, (x, oracle.round_e4m3(x), want)
