@@ -157,6 +157,9 @@ FORMS = {
     "bf16_unified": dict(precision="bf16", stereo_unify=True, reuse="off"),
     "cached_unified": dict(precision="fp32", stereo_unify=True, reuse="depth"),
     "cached_bf16_unified": dict(precision="bf16", stereo_unify=True, reuse="depth"),
+    "fp8": dict(precision="fp8", stereo_unify=False, reuse="off"),
+    "fp8_unified": dict(precision="fp8", stereo_unify=True, reuse="off"),
+    "cached_fp8_unified": dict(precision="fp8", stereo_unify=True, reuse="depth"),
 }
 HEADLINE = "cached_bf16_unified"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP/FMA x max SM clock
@@ -257,7 +260,7 @@ def roofline(stage_ms, st, form, W, H, n_anchors):
     P, Rv, R, V = st["pairs"], st["valid_records"], st["records"], st["visible_anchors"]
     pixels = 2 * W * H
     dur = stage_ms[dom] / 1e3
-    feat_b = 64 if FORMS[form]["precision"] == "bf16" else 128
+    feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
     if dom == "blend":
         # FP32 lane work per (pixel, pair): 5 FMA quadratic, exp2, clamp, T update FMA, weight, 3 colour FMA
         flop = P * 256 * 20.0
@@ -504,7 +507,7 @@ def run_ours(args, rank, world):
            "sample": "2 stereo frames (0, 150): full float64 filtering/derivation/projection, "
                      "blending on every 16th pixel row scaled x16"}
 
-    derive_launches = 2 if FORMS[form]["precision"] == "bf16" else 1
+    derive_launches = 2 if FORMS[form]["precision"] != "fp32" else 1
     launches_per_frame = 1 + 1 + 1 + derive_launches + (1 + 4) + 1 + 2 + (1 + 2) + 1 + 1
     cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tile": "16x16",
            "l2": "flushed between frames (256 MB write, untimed)",
@@ -514,7 +517,7 @@ def run_ours(args, rank, world):
            "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16+f32" if FORMS[form]["precision"] == "bf16" else "f32",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[FORMS[form]["precision"]],
             "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": launches_per_frame * args.steps}
     print(json.dumps(line), flush=True)
@@ -527,7 +530,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default=HEADLINE, choices=sorted(FORMS))
-    ap.add_argument("--compare", nargs="*", default=["plain"], help="other forms timed for comparison")
+    ap.add_argument("--compare", nargs="*", default=["plain", "bf16_unified", "fp8_unified", "cached_fp8_unified"],
+                    help="other forms timed for comparison")
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 150, 299])
     ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
     ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")

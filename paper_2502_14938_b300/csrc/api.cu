@@ -29,7 +29,7 @@ struct DevBuf {
 
 struct ModelHost {
   uint32_t n = 0;
-  DevBuf px, py, pz, level, feat, offs, scale, w32, feat_bf16, w_tc;
+  DevBuf px, py, pz, level, feat, offs, scale, w32, feat_bf16, w_tc, feat_fp8, w_tc8;
   ModelDev dev{};
 };
 
@@ -345,11 +345,12 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
   const bool collect = caches && (ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && !replay;
+  const bool tc = ctx->cfg.precision != GSC_PREC_FP32, fp8 = ctx->cfg.precision == GSC_PREC_FP8;
   if (collect)  // fresh attributes of every visible anchor, for the labels
     for (int m : ctx->models_used)
-      if (ctx->cfg.precision == GSC_PREC_BF16)
+      if (tc)
         launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, &ctx->tmap_feat,
-                         ctx->compact, ctx->n_sm, s);
+                         ctx->compact, fp8, ctx->n_sm, s);
       else
         launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, ctx->n_sm, s);
   if (caches && !replay)
@@ -358,9 +359,9 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
                        ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
-    if (ctx->cfg.precision == GSC_PREC_BF16)
+    if (tc)
       launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, &ctx->tmap_feat,
-                       ctx->compact, ctx->n_sm, s);
+                       ctx->compact, fp8, ctx->n_sm, s);
     else
       launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->n_sm, s);
   launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->n_sm, s);
@@ -564,7 +565,6 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   if (!tiling_ok(cfg.tile_w, cfg.tile_h, cfg.blocks_per_sm)) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
-  if (cfg.precision == GSC_PREC_FP8) return GSC_ERR_UNIMPLEMENTED;
   if ((cfg.flags & GSC_FLAG_REUSE_COLLECT) && cfg.reuse == GSC_REUSE_OFF) return GSC_ERR_INVALID_ARG;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
 
@@ -610,7 +610,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   for (auto& m : ctx->models) {
     dfree(m.px.p); dfree(m.py.p); dfree(m.pz.p); dfree(m.level.p);
     dfree(m.feat.p); dfree(m.offs.p); dfree(m.scale.p); dfree(m.w32.p);
-    dfree(m.feat_bf16.p); dfree(m.w_tc.p);
+    dfree(m.feat_bf16.p); dfree(m.w_tc.p); dfree(m.feat_fp8.p); dfree(m.w_tc8.p);
   }
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
@@ -696,6 +696,23 @@ int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out
   }
   mh.dev.feat_bf16 = mh.feat_bf16.p;
   mh.dev.w_tc = mh.w_tc.p;
+  mh.dev.fp8_inv_sx = 1.f;
+  if (ctx->cfg.precision == GSC_PREC_FP8) {  // e4m3 features and weight image with per-tensor scales
+    const Fp8Scales sc = fp8_scales(d->feat, n, d->W1, d->b1, d->W2);
+    mh.dev.fp8_inv_sx = 1.0f / sc.sx;
+    mh.w_tc8.bytes = TC8_IMAGE_BYTES;
+    CK(cudaMalloc(&mh.w_tc8.p, mh.w_tc8.bytes));
+    CK(make_tc8_image(d->W1, d->b1, d->W2, d->b2, sc, mh.w_tc8.p, ctx->stream));
+    mh.feat_fp8.bytes = n * FDIM;
+    if (n) {
+      CK(cudaMalloc(&mh.feat_fp8.p, mh.feat_fp8.bytes));
+      launch_to_e4m3((const float*)mh.feat.p, 1.0f / sc.sx, mh.feat_fp8.p, n * FDIM, ctx->stream);
+      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaGetLastError());
+    }
+    mh.dev.feat_fp8 = mh.feat_fp8.p;
+    mh.dev.w_tc8 = mh.w_tc8.p;
+  }
   mh.dev.n = mh.n;
   mh.dev.n_levels = d->n_levels;
   mh.dev.lod_dmax = d->lod_dmax;
@@ -782,7 +799,7 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
     const uint64_t rows = (uint64_t)ctx->vis_cap * ctx->n_vis_slots;
     if (rows > ctx->compact_rows) {
       if ((r = dalloc(ctx, &ctx->compact, (size_t)rows * 4))) return r;  // 64 bytes = 4 x uint4 per row
-      if (encode_feat_tmap(&ctx->tmap_feat, ctx->compact, rows) != 0)
+      if (encode_feat_tmap(&ctx->tmap_feat, ctx->compact, rows, ctx->cfg.precision == GSC_PREC_FP8) != 0)
         return fail(ctx, GSC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
       ctx->compact_rows = rows;
       invalidate_graph(ctx);

@@ -1,6 +1,11 @@
-// Derivation on the 5th-generation tensor cores (tcgen05), BF16 inputs with
-// FP32 accumulation in tensor memory - the precision form of the decoder
-// MLPs (Eq. 3).  Covariance, projection and blending stay float32.
+// Derivation on the 5th-generation tensor cores (tcgen05), BF16 or FP8-E4M3
+// inputs with FP32 accumulation in tensor memory - the precision forms of
+// the decoder MLPs (Eq. 3).  Covariance, projection and blending stay float32.
+// FP8 uses per-tensor power-of-two scales (inputs, each head's W1 / W2 and
+// hidden layer): the accumulators are multiplied back by s_x s_w1 (layer 1)
+// and s_h s_w2 (layer 2), the hidden layer is divided by s_h before it is
+// rounded to E4M3.  Operand tiles are the same 16-byte core matrices either
+// way: 8 bf16 or 16 e4m3 per K-chunk, K = 16 or 32 per MMA.
 //
 // One CTA (8 warps) takes tiles of 128 visible anchors:
 //   TMA      features of the 128 anchors (a compact BF16 copy made by
@@ -20,7 +25,10 @@
 // drains its outstanding async work (bounded) and frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -30,19 +38,36 @@ namespace gsc {
 
 constexpr int TC_NT = 256;
 constexpr int TC_M = 128;
-// shared-memory image offsets (bytes)
-constexpr uint32_t TC_A = 0;                        // X: 6 K-chunks x 128 rows x 16 B
-constexpr uint32_t TC_W1 = TC_A + 6 * 2048;         // W1cat: 6 K-chunks x 96 rows x 16 B
-constexpr uint32_t TC_W2 = TC_W1 + 6 * 1536;        // W2bd: 12 K-chunks x 160 rows x 16 B
-constexpr uint32_t TC_H = TC_W2 + 12 * 2560;        // H: 12 K-chunks x 128 rows x 16 B
-constexpr uint32_t TC_B1 = TC_H + 12 * 2048;        // b1 fp32 [96]
-constexpr uint32_t TC_B2 = TC_B1 + 96 * 4;          // b2 fp32 [160] (Gaussian-major)
-constexpr uint32_t TC_META = TC_B2 + 160 * 4;
-constexpr uint32_t TC_BAR = TC_META + TC_M * 8 * 4;  // 2 mbarriers + TMEM address
+// Shared-memory image of one CTA (bytes).  X: XCH K-chunks x 128 rows x 16 B;
+// W1cat: XCH x 96 rows; W2bd: HCH x 160 rows; H: HCH x 128 rows; then fp32
+// b1 [96] (FP8: + s1 [96] dequant, r1 [96] 1/s_h), b2 [160] (FP8: + s2
+// [160] dequant), per-row metadata, 2 mbarriers and the TMEM address.
+template <bool FP8>
+struct TcL {
+  static constexpr int XCH = FP8 ? 4 : 6, HCH = FP8 ? 6 : 12;
+  static constexpr int K1 = FP8 ? 2 : 3, K2 = FP8 ? 3 : 6;  // MMA K-steps
+  static constexpr int FEAT_CH = FP8 ? 2 : 4;                 // chunks the TMA fills
+  static constexpr int DIR_CH = FP8 ? 2 : 4;                  // direction chunk
+  static constexpr int ZERO_CH = FP8 ? 3 : 5;                 // always-zero chunk
+  static constexpr uint32_t A = 0;
+  static constexpr uint32_t W1 = A + XCH * 2048;
+  static constexpr uint32_t W2 = W1 + XCH * 1536;
+  static constexpr uint32_t H = W2 + HCH * 2560;
+  static constexpr uint32_t B1 = H + HCH * 2048;
+  static constexpr uint32_t S1 = B1 + 96 * 4;
+  static constexpr uint32_t R1 = S1 + 96 * 4;
+  static constexpr uint32_t B2 = FP8 ? R1 + 96 * 4 : S1;
+  static constexpr uint32_t S2 = B2 + 160 * 4;
+  static constexpr uint32_t META = FP8 ? S2 + 160 * 4 : S2;
+  static constexpr uint32_t BAR = META + TC_M * 8 * 4;
+  static constexpr uint32_t IMG = META - W1;  // bytes of the weight image
+};
 // 84 KB (+ 9 KB static): two CTAs per SM, 2 x 256 = 512 TMEM columns, so a
 // CTA's allocation never waits
 constexpr uint32_t TC_SMEM = 84 * 1024;
-static_assert(TC_BAR + 32 <= TC_SMEM, "shared-memory image exceeds the allocation");
+static_assert(TcL<false>::BAR + 32 <= TC_SMEM && TcL<true>::BAR + 32 <= TC_SMEM,
+              "shared-memory image exceeds the allocation");
+static_assert(TcL<false>::IMG == 65536 && TcL<true>::IMG == 36224, "weight image sizes");
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_SPIN = 1u << 22;
 
@@ -88,17 +113,29 @@ __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uin
   d |= (uint64_t)1 << 46;
   return d;
 }
-// Instruction descriptor, kind::f16: D f32, A/B bf16, both K-major.
+// Instruction descriptors, D f32, A and B K-major: kind::f16 with A/B bf16
+// (format 1 at bits 7 and 10); kind::f8f6f4 with A/B e4m3 (format 0).
 __host__ __device__ constexpr uint32_t make_idesc_bf16(uint32_t M, uint32_t N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+__host__ __device__ constexpr uint32_t make_idesc_e4m3(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+template <bool FP8>
+__device__ __forceinline__ void mma_tc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  if constexpr (FP8)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -120,58 +157,72 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&p);
 }
+// Four floats -> four e4m3 bytes (round to nearest even, saturating), element 0 lowest.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
 
 // ------------------------------------------------------------------ gather
-// Compact BF16 features of this model's visible anchors, in the model-local
-// item order of the derivation kernel (rows of 64 bytes, the TMA source).
-__global__ void k_gather_bf16(const ModelDev* __restrict__ models, int model, const FrameDev* __restrict__ fd,
+// Compact BF16 (64-byte rows) or E4M3 (32-byte rows) features of this
+// model's visible anchors, in the model-local item order of the derivation
+// kernel: the TMA source.
+template <bool FP8>
+__global__ void k_gather_feat(const ModelDev* __restrict__ models, int model, const FrameDev* __restrict__ fd,
                               uint32_t* const* __restrict__ vis, uint4* __restrict__ out,
                               const CacheDev* __restrict__ caches) {
+  constexpr uint32_t PARTS = FP8 ? 2u : 4u;  // uint4 per row
   __shared__ DViewSet S;
   if (threadIdx.x == 0) build_dview_set(S, fd, model, caches);
   __syncthreads();
-  const uint4* src = reinterpret_cast<const uint4*>(models[model].feat_bf16);
+  const uint4* src = reinterpret_cast<const uint4*>(FP8 ? models[model].feat_fp8 : models[model].feat_bf16);
   const uint32_t total = S.base[S.nd];
-  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total * 4u; u += gridDim.x * blockDim.x) {
-    const uint32_t item = u >> 2, part = u & 3u;
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total * PARTS; u += gridDim.x * blockDim.x) {
+    const uint32_t item = u / PARTS, part = u % PARTS;
     int ld = 0;
     while (item >= S.base[ld + 1]) ++ld;
     const uint32_t w = item - S.base[ld];
     const uint32_t vi = S.miss[ld] ? S.miss[ld][w] : w;
     const uint32_t a = vis[S.d[ld]][vi];
-    out[u] = src[(size_t)a * 4 + part];
+    out[u] = src[(size_t)a * PARTS + part];
   }
 }
 
 // ------------------------------------------------------------------ derivation
+template <bool FP8>
 __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restrict__ models, int model,
                                                         FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
                                                         const CacheDev* __restrict__ caches,
                                                         const __grid_constant__ CUtensorMap tmap_feat) {
+  using L = TcL<FP8>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ DViewSet S;
-  uint32_t* m_anchor = reinterpret_cast<uint32_t*>(smem + TC_META);
+  uint32_t* m_anchor = reinterpret_cast<uint32_t*>(smem + L::META);
   uint32_t* m_vi = m_anchor + TC_M;
   int* m_ld = reinterpret_cast<int*>(m_vi + TC_M);
   float* m_pos = reinterpret_cast<float*>(m_ld + TC_M);  // [3][128]
   float* m_sa = m_pos + 3 * TC_M;
-  const float* s_b1 = reinterpret_cast<const float*>(smem + TC_B1);
-  const float* s_b2 = reinterpret_cast<const float*>(smem + TC_B2);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_BAR);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + TC_BAR + 16);
+  const float* s_b1 = reinterpret_cast<const float*>(smem + L::B1);
+  const float* s_s1 = reinterpret_cast<const float*>(smem + L::S1);
+  const float* s_r1 = reinterpret_cast<const float*>(smem + L::R1);
+  const float* s_b2 = reinterpret_cast<const float*>(smem + L::B2);
+  const float* s_s2 = reinterpret_cast<const float*>(smem + L::S2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR + 16);
   const uint32_t tma_bar = smem_u32(bars), mma_bar = smem_u32(bars + 1);
   const uint32_t sbase = smem_u32(smem);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const ModelDev md = models[model];
-  {  // weights image (bf16 operands, zeroed H staging area, fp32 biases), 65,536 bytes
-    const uint4* src = reinterpret_cast<const uint4*>(md.w_tc);
-    uint4* dst = reinterpret_cast<uint4*>(smem + TC_W1);
-    for (int i = t; i < (int)((TC_META - TC_W1) / 16); i += TC_NT) dst[i] = src[i];
-    // K-chunk 5 of X (K 40..47) is always zero; chunk 4 holds the direction
-    uint4* z5 = reinterpret_cast<uint4*>(smem + TC_A + 5 * 2048);
-    if (t < TC_M) z5[t] = make_uint4(0, 0, 0, 0);
+  {  // weights image (operands, zeroed H staging area, fp32 biases and scales)
+    const uint4* src = reinterpret_cast<const uint4*>(FP8 ? md.w_tc8 : md.w_tc);
+    uint4* dst = reinterpret_cast<uint4*>(smem + L::W1);
+    for (int i = t; i < (int)(L::IMG / 16); i += TC_NT) dst[i] = src[i];
+    // the last K-chunk of X is always zero; the one before holds the direction
+    uint4* zc = reinterpret_cast<uint4*>(smem + L::A + L::ZERO_CH * 2048);
+    if (t < TC_M) zc[t] = make_uint4(0, 0, 0, 0);
   }
   if (t == 0) {
     build_dview_set(S, fd, model, caches);
@@ -194,14 +245,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   const uint32_t total = S.base[nd];
   const uint32_t ntiles = (total + TC_M - 1) / TC_M;
   const uint32_t rec_cap = fd->n_records;
-  constexpr uint32_t IDESC1 = make_idesc_bf16(128, 96);
-  constexpr uint32_t IDESC2 = make_idesc_bf16(128, 160);
+  constexpr uint32_t IDESC1 = FP8 ? make_idesc_e4m3(128, 96) : make_idesc_bf16(128, 96);
+  constexpr uint32_t IDESC2 = FP8 ? make_idesc_e4m3(128, 160) : make_idesc_bf16(128, 160);
   uint32_t tma_phase = 0, mma_phase = 0;
   bool failed = false;
   bool tma_pending = false, mma_pending = false;
 
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    // ---- metadata, view direction (K-chunk 4), TMA of the features (K-chunks 0-3)
+    // ---- metadata, view direction chunk, TMA of the feature chunks
     if (t < TC_M) {
       const uint32_t item = tile * TC_M + t;
       int ld = -1;
@@ -224,13 +275,21 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         dx *= vn; dy *= vn; dz *= vn;
       }
       m_ld[t] = ld;
-      reinterpret_cast<uint4*>(smem + TC_A + 4 * 2048)[t] = make_uint4(pack_bf16x2(dx, dy), pack_bf16x2(dz, 0.f), 0u, 0u);
+      uint4 dirc;
+      if constexpr (FP8) {
+        const float ix = md.fp8_inv_sx;  // 1 / s_x, a power of two
+        dirc = make_uint4(pack_e4m3x4(dx * ix, dy * ix, dz * ix, 0.f), 0u, 0u, 0u);
+      } else {
+        dirc = make_uint4(pack_bf16x2(dx, dy), pack_bf16x2(dz, 0.f), 0u, 0u);
+      }
+      reinterpret_cast<uint4*>(smem + L::A + L::DIR_CH * 2048)[t] = dirc;
       fence_proxy_async();
     }
     if (t == 0) {
-      mbar_expect_tx(tma_bar, 4 * 2048);
+      mbar_expect_tx(tma_bar, L::FEAT_CH * 2048);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) tma_load_2d(sbase + TC_A + c * 2048, &tmap_feat, 8 * c, (int)(tile * TC_M), tma_bar);
+      for (int c = 0; c < L::FEAT_CH; ++c)  // x in elements: 8 bf16 or 16 e4m3 = 16 bytes per chunk
+        tma_load_2d(sbase + L::A + c * 2048, &tmap_feat, (FP8 ? 16 : 8) * c, (int)(tile * TC_M), tma_bar);
     }
     tma_pending = true;
     __syncthreads();
@@ -245,9 +304,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     // ---- MMA1
     if (t == 0) {
 #pragma unroll
-      for (int ks = 0; ks < 3; ++ks)
-        mma_bf16(tmem, make_sdesc(sbase + TC_A + ks * 4096, 2048, 128), make_sdesc(sbase + TC_W1 + ks * 3072, 1536, 128),
-                 IDESC1, ks > 0 ? 1u : 0u);
+      for (int ks = 0; ks < L::K1; ++ks)
+        mma_tc<FP8>(tmem, make_sdesc(sbase + L::A + ks * 4096, 2048, 128),
+                    make_sdesc(sbase + L::W1 + ks * 3072, 1536, 128), IDESC1, ks > 0 ? 1u : 0u);
       mma_commit(mma_bar);
     }
     mma_pending = true;
@@ -259,7 +318,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     }
     mma_pending = false;
     tc_fence_after();
-    // ---- epilogue 1: H = bf16(ReLU(D1 + b1)); warps w and w+4 share lanes 32(w%4).., 48 columns each
+    // ---- epilogue 1: H = ReLU(D1 + b1) (FP8: D1 s_x s_w1 + b1, then / s_h)
+    // rounded to the operand type; warps w and w+4 share lanes 32(w%4).., 48 columns each
     {
       const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(48 * half);
@@ -268,14 +328,23 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       for (int g = 0; g < 3; ++g) {
         tmem_ld16(taddr + 16 * g, v);
         const int c0 = 48 * half + 16 * g;
-        uint32_t pk[8];
+        if constexpr (FP8) {
+          float h[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          pk[u] = pack_bf16x2(fmaxf(v[2 * u] + s_b1[c0 + 2 * u], 0.f), fmaxf(v[2 * u + 1] + s_b1[c0 + 2 * u + 1], 0.f));
-        uint4* h0 = reinterpret_cast<uint4*>(smem + TC_H + (c0 / 8) * 2048 + row * 16);
-        uint4* h1 = reinterpret_cast<uint4*>(smem + TC_H + (c0 / 8 + 1) * 2048 + row * 16);
-        *h0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        *h1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          for (int u = 0; u < 16; ++u) h[u] = fmaxf(fmaf(v[u], s_s1[c0 + u], s_b1[c0 + u]), 0.f) * s_r1[c0 + u];
+          *reinterpret_cast<uint4*>(smem + L::H + (c0 / 16) * 2048 + row * 16) =
+              make_uint4(pack_e4m3x4(h[0], h[1], h[2], h[3]), pack_e4m3x4(h[4], h[5], h[6], h[7]),
+                         pack_e4m3x4(h[8], h[9], h[10], h[11]), pack_e4m3x4(h[12], h[13], h[14], h[15]));
+        } else {
+          uint32_t pk[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            pk[u] = pack_bf16x2(fmaxf(v[2 * u] + s_b1[c0 + 2 * u], 0.f), fmaxf(v[2 * u + 1] + s_b1[c0 + 2 * u + 1], 0.f));
+          uint4* h0 = reinterpret_cast<uint4*>(smem + L::H + (c0 / 8) * 2048 + row * 16);
+          uint4* h1 = reinterpret_cast<uint4*>(smem + L::H + (c0 / 8 + 1) * 2048 + row * 16);
+          *h0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *h1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
       }
     }
     fence_proxy_async();
@@ -285,9 +354,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     // ---- MMA2
     if (t == 0) {
 #pragma unroll
-      for (int ks = 0; ks < 6; ++ks)
-        mma_bf16(tmem + 96, make_sdesc(sbase + TC_H + ks * 4096, 2048, 128),
-                 make_sdesc(sbase + TC_W2 + ks * 5120, 2560, 128), IDESC2, ks > 0 ? 1u : 0u);
+      for (int ks = 0; ks < L::K2; ++ks)
+        mma_tc<FP8>(tmem + 96, make_sdesc(sbase + L::H + ks * 4096, 2048, 128),
+                    make_sdesc(sbase + L::W2 + ks * 5120, 2560, 128), IDESC2, ks > 0 ? 1u : 0u);
       mma_commit(mma_bar);
     }
     mma_pending = true;
@@ -312,7 +381,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         if (ld < 0) continue;
         float z[11];
 #pragma unroll
-        for (int u = 0; u < 11; ++u) z[u] = v[u] + s_b2[16 * j + u];
+        for (int u = 0; u < 11; ++u) z[u] = FP8 ? fmaf(v[u], s_s2[16 * j + u], s_b2[16 * j + u]) : v[u] + s_b2[16 * j + u];
         float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
         const size_t idx = (size_t)(S.gbase[ld] + m_vi[row]) * K + j;
         uint2* line = nullptr;
@@ -340,7 +409,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
 }
 
 cudaError_t prepare_derive_tc() {
-  return cudaFuncSetAttribute(k_derive_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_derive_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_derive_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
 }
 
 __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
@@ -352,9 +423,20 @@ void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s) {
   if (n) k_to_bf16<<<1024, 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst), n);
 }
 
-// Tensor map of the compact feature buffer: rows of 32 bf16, boxes of 8
-// columns x 128 rows (one K-chunk of core matrices per box).
-int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows) {
+// e4m3(x * inv_scale), round to nearest even, saturating.
+__global__ void k_to_e4m3(const float* __restrict__ src, float inv_scale, uint8_t* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (uint8_t)__nv_cvt_float_to_fp8(src[i] * inv_scale, __NV_SATFINITE, __NV_E4M3);
+}
+
+void launch_to_e4m3(const float* src, float inv_scale, void* dst, size_t n, cudaStream_t s) {
+  if (n) k_to_e4m3<<<1024, 256, 0, s>>>(src, inv_scale, static_cast<uint8_t*>(dst), n);
+}
+
+// Tensor map of the compact feature buffer: rows of 32 bf16 (64 bytes) with
+// boxes of 8 columns, or of 32 e4m3 (32 bytes) with boxes of 16 columns;
+// 128 rows per box, so a box is one K-chunk of core matrices.
+int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows, bool fp8) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -368,10 +450,11 @@ int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows) {
     fn = reinterpret_cast<EncodeFn>(p);
   }
   const cuuint64_t dims[2] = {32, rows};
-  const cuuint64_t strides[1] = {64};
-  const cuuint32_t box[2] = {8, 128};
+  const cuuint64_t strides[1] = {fp8 ? 32u : 64u};
+  const cuuint32_t box[2] = {fp8 ? 16u : 8u, 128};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+  const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+                        strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
@@ -393,11 +476,12 @@ static uint16_t host_bf16(float f) {
 // (zeros here), then b1 [96] and b2 [160] in fp32.
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img) {
-  img.assign(TC_META - TC_W1, 0);
+  using L = TcL<false>;
+  img.assign(L::IMG, 0);
   uint16_t* w1 = reinterpret_cast<uint16_t*>(img.data());
-  uint16_t* w2 = reinterpret_cast<uint16_t*>(img.data() + (TC_W2 - TC_W1));
-  float* fb1 = reinterpret_cast<float*>(img.data() + (TC_B1 - TC_W1));
-  float* fb2 = reinterpret_cast<float*>(img.data() + (TC_B2 - TC_W1));
+  uint16_t* w2 = reinterpret_cast<uint16_t*>(img.data() + (L::W2 - L::W1));
+  float* fb1 = reinterpret_cast<float*>(img.data() + (L::B1 - L::W1));
+  float* fb2 = reinterpret_cast<float*>(img.data() + (L::B2 - L::W1));
   for (int k = 0; k < IN; ++k)
     for (int n = 0; n < NH; ++n) w1[(k / 8) * (1536 / 2) + n * 8 + (k % 8)] = host_bf16(W1[n / HID][k * HID + n % HID]);
   for (int n = 0; n < NH; ++n) fb1[n] = b1[n / HID][n % HID];
@@ -415,11 +499,108 @@ void pack_tc_weights(const float* const W1[3], const float* const b1[3], const f
     }
 }
 
+// ------------------------------------------------------------------ FP8 form
+namespace {
+float pow2_at_least(double v) {  // smallest power of two >= v; 1 for v <= 0
+  if (!(v > 0.0)) return 1.f;
+  int e;
+  const double m = std::frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
+  return (float)std::ldexp(1.0, m == 0.5 ? e - 1 : e);
+}
+}  // namespace
+
+// Per-tensor scales: amax / 448 rounded up to a power of two (exact scaling).
+// Inputs: max(amax of the features, 1) (the unit direction shares the input
+// tensor); hidden layer: max over units o of sum_c |W1[c][o]| amax_c + |b1[o]|,
+// a bound over every anchor and view direction (amax_c: largest |feature c|,
+// 1 for a direction component).
+Fp8Scales fp8_scales(const float* feat, size_t n, const float* const W1[3], const float* const b1[3],
+                     const float* const W2[3]) {
+  Fp8Scales S{};
+  double amax_c[IN];
+  for (int c = 0; c < IN; ++c) amax_c[c] = c < FDIM ? 0.0 : 1.0;
+  for (size_t a = 0; a < n; ++a)
+    for (int c = 0; c < FDIM; ++c) amax_c[c] = std::max(amax_c[c], (double)std::fabs(feat[a * FDIM + c]));
+  double ax = 1.0;
+  for (int c = 0; c < FDIM; ++c) ax = std::max(ax, amax_c[c]);
+  S.sx = pow2_at_least(ax / 448.0);
+  const int outd[3] = {K, 3 * K, 7 * K};
+  for (int h = 0; h < 3; ++h) {
+    double a1 = 0.0, a2 = 0.0, hb = 0.0;
+    for (int i = 0; i < IN * HID; ++i) a1 = std::max(a1, (double)std::fabs(W1[h][i]));
+    for (int i = 0; i < HID * outd[h]; ++i) a2 = std::max(a2, (double)std::fabs(W2[h][i]));
+    for (int o = 0; o < HID; ++o) {
+      double b = std::fabs((double)b1[h][o]);
+      for (int c = 0; c < IN; ++c) b += std::fabs((double)W1[h][c * HID + o]) * amax_c[c];
+      hb = std::max(hb, b);
+    }
+    S.sw1[h] = pow2_at_least(a1 / 448.0);
+    S.sw2[h] = pow2_at_least(a2 / 448.0);
+    S.sh[h] = pow2_at_least(hb / 448.0);
+  }
+  return S;
+}
+
+// The 36,224-byte FP8 image (layout TcL<true>): e4m3 W1cat [96 x 64 K] and
+// block-diagonal W2bd [160 x 96 K] (each weight divided by its head's scale,
+// converted on the device), the zeroed H area, then fp32 b1, s1 = s_x s_w1,
+// r1 = 1 / s_h per hidden unit and b2, s2 = s_h s_w2 per output row.
+cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], const float* const W2[3],
+                           const float* const b2[3], const Fp8Scales& S, void* d_img, cudaStream_t s) {
+  using L = TcL<true>;
+  const size_t n_w1 = L::XCH * 1536, n_w2 = L::HCH * 2560;
+  std::vector<float> pre(n_w1 + n_w2, 0.f);
+  for (int k = 0; k < IN; ++k)
+    for (int n = 0; n < NH; ++n)
+      pre[(k / 16) * 1536 + n * 16 + (k % 16)] = W1[n / HID][k * HID + n % HID] / S.sw1[n / HID];
+  const int outd[3] = {K, 3 * K, 7 * K};
+  std::vector<float> tail((L::META - L::B1) / 4, 0.f);
+  float* fb1 = tail.data();
+  float* fs1 = tail.data() + (L::S1 - L::B1) / 4;
+  float* fr1 = tail.data() + (L::R1 - L::B1) / 4;
+  float* fb2 = tail.data() + (L::B2 - L::B1) / 4;
+  float* fs2 = tail.data() + (L::S2 - L::B1) / 4;
+  for (int n = 0; n < NH; ++n) {
+    fb1[n] = b1[n / HID][n % HID];
+    fs1[n] = S.sx * S.sw1[n / HID];
+    fr1[n] = 1.0f / S.sh[n / HID];
+  }
+  for (int j = 0; j < K; ++j)
+    for (int u = 0; u < 11; ++u) {
+      const int head = u == 0 ? 0 : (u < 4 ? 1 : 2);
+      const int out = u == 0 ? j : (u < 4 ? 3 * j + u - 1 : 7 * j + u - 4);
+      const int n = 16 * j + u;
+      for (int c = 0; c < HID; ++c) {
+        const int k = head * HID + c;
+        pre[n_w1 + (k / 16) * 2560 + n * 16 + (k % 16)] = W2[head][c * outd[head] + out] / S.sw2[head];
+      }
+      fb2[n] = b2[head][out];
+      fs2[n] = S.sh[head] * S.sw2[head];
+    }
+  float* d_pre = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_pre, pre.size() * 4);
+  if (e != cudaSuccess) return e;
+  uint8_t* img = static_cast<uint8_t*>(d_img);
+  if ((e = cudaMemcpy(d_pre, pre.data(), pre.size() * 4, cudaMemcpyHostToDevice)) == cudaSuccess) {
+    launch_to_e4m3(d_pre, 1.0f, img, pre.size(), s);
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFree(d_pre);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemset(img + (L::H - L::W1), 0, L::HCH * 2048)) != cudaSuccess) return e;
+  return cudaMemcpy(img + (L::B1 - L::W1), tail.data(), tail.size() * 4, cudaMemcpyHostToDevice);
+}
+
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                       float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
-                      int n_sm, cudaStream_t s) {
-  k_gather_bf16<<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
-  k_derive_tc<<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
+                      bool fp8, int n_sm, cudaStream_t s) {
+  if (fp8) {
+    k_gather_feat<true><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
+    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
+  } else {
+    k_gather_feat<false><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
+    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
+  }
 }
 
 }  // namespace gsc

@@ -114,7 +114,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
 struct ModelDev {
   uint32_t n, n_levels;
   float lod_dmax;
-  uint32_t pad;
+  float fp8_inv_sx;       // FP8 form: 1 / s_x (input scale, a power of two)
   const float* px;
   const float* py;
   const float* pz;
@@ -124,7 +124,9 @@ struct ModelDev {
   const float* scale;     // [N]
   const float* w32;       // packed weights, W_FLOATS
   const void* feat_bf16;  // [N][32] bf16 (tensor-core forms)
-  const void* w_tc;       // tensor-core weight image (65,536 bytes)
+  const void* w_tc;       // tensor-core weight image, bf16 (65,536 bytes)
+  const void* feat_fp8;   // [N][32] e4m3 of feature / s_x (FP8 form)
+  const void* w_tc8;      // tensor-core weight image, e4m3 + scales (36,224 bytes)
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
@@ -346,8 +348,18 @@ cudaError_t prepare_derive_tc();
 void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                       float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
-                      int n_sm, cudaStream_t s);
-int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows);
+                      bool fp8, int n_sm, cudaStream_t s);
+int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows, bool fp8);
+// FP8-E4M3 form: per-tensor power-of-two scales, the weight image, feature conversion
+struct Fp8Scales {
+  float sx, sw1[3], sw2[3], sh[3];
+};
+Fp8Scales fp8_scales(const float* feat, size_t n, const float* const W1[3], const float* const b1[3],
+                     const float* const W2[3]);
+constexpr size_t TC8_IMAGE_BYTES = 36224;
+cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], const float* const W2[3],
+                           const float* const b2[3], const Fp8Scales& S, void* d_img, cudaStream_t s);
+void launch_to_e4m3(const float* src, float inv_scale, void* dst, size_t n, cudaStream_t s);
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img);
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,

@@ -97,3 +97,64 @@ def test_bf16_and_fp32_agree_on_integer_stages(city):
         assert np.array_equal(r32.debug_visible(v), r16.debug_visible(v))
     r32.close()
     r16.close()
+
+
+# ------------------------------------------------------------------ FP8-E4M3
+# One E4M3 step is 2^-3 relative: an input or hidden value that lies near an
+# E4M3 rounding midpoint rounds one way from the GPU's float32 and the other
+# from the oracle's float64, and moves the outputs it feeds by up to a few
+# 1e-2.  Most attributes agree to float32 accuracy; the test bounds the share
+# that does not and the size of the rest.
+FP8_CLOSE = 1e-4      # scale-relative agreement of an attribute
+FP8_CLOSE_FRAC = 0.9  # share of attributes that must agree that closely
+FP8_MAX = 0.3         # bound on any attribute's scale-relative difference
+
+
+def check_attrs_fp8(got, ref, s_a, tag):
+    scale = np.ones(ref.shape, np.float64)
+    scale[..., 4:7] = np.asarray(s_a, np.float64)[:, None, None]
+    rel = np.abs(got.astype(np.float64) - ref) / scale
+    close = np.mean(rel <= FP8_CLOSE)
+    assert close >= FP8_CLOSE_FRAC and rel.max() <= FP8_MAX, f"{tag}: close {close:.3f}, worst {rel.max():.3e}"
+    return close, rel.max()
+
+
+def test_fp8_tiny_scene():
+    import paper_2502_14938_b300 as pkg
+    m, cam = gen.tiny_scene(), gen.tiny_camera()
+    r = make_renderer(m, [cam], flags=pkg.FLAG_DEBUG_ATTRS, precision="fp8")
+    (img,), st = render(r, [cam])
+    ids = oracle.cull(m, cam)
+    assert np.array_equal(r.debug_visible(0), ids)
+    attrs_q, _ = oracle.derive(m, oracle.camera_center(cam), ids, oracle.fp8_scales(m))
+    check_attrs_fp8(r.debug_attrs(0), attrs_q, m.scale[ids], "fp8 tiny")
+    check_keygen_and_sort(r, [cam])
+    (ref, T, mg, nc), _ = oracle.render_view(m, cam)
+    assert oracle.psnr(img, ref) >= 30.0
+    r.close()
+
+
+@pytest.mark.parametrize("frame", [0, 150, 299])
+def test_fp8_city_stereo(city, frame):
+    import paper_2502_14938_b300 as pkg
+    model, frames = city
+    L, R = frames[frame]
+    r = make_renderer(model, [L, R], partners=[1, 0], flags=pkg.FLAG_DEBUG_ATTRS, precision="fp8")
+    imgs, st = render(r, [L, R])
+    q = oracle.fp8_scales(model)
+    for v, cam in enumerate((L, R)):
+        ids = oracle.cull(model, cam)
+        assert np.array_equal(r.debug_visible(v), ids)
+        attrs_q, _ = oracle.derive(model, oracle.camera_center(cam), ids, q)
+        check_attrs_fp8(r.debug_attrs(v), attrs_q, model.scale[ids], f"fp8 city eye {v}")
+    check_keygen_and_sort(r, [L, R])
+    rs = np.random.default_rng(frame + 7)
+    for v, cam in enumerate((L, R)):
+        px = rs.integers(0, cam.width, 30000)
+        py = rs.integers(0, cam.height, 30000)
+        vr = oracle.view_gaussians(model, cam)
+        ref, _, _, _ = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        p = oracle.psnr(imgs[v][py, px], ref)
+        print(f"fp8 city frame {frame} eye {v}: {p:.2f} dB")
+        assert p >= 30.0, f"fp8 city frame {frame} eye {v}: {p:.2f} dB"
+    r.close()
