@@ -268,20 +268,23 @@ __global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ m
       if (threadIdx.x == 0) s_total[ld] = tot;
     }
     __syncthreads();
-    if (threadIdx.x < (uint32_t)nd) {
-      const int ld = threadIdx.x;
+    if ((int)(threadIdx.x >> 5) < nd) {  // warp ld publishes view ld's tile count and walks back
+      const int ld = (int)(threadIdx.x >> 5);
+      const bool l0 = (threadIdx.x & 31u) == 0;
       const uint32_t tot = s_total[ld];
       unsigned long long* w = status + (size_t)t * CULL_MAXD + ld;
       uint32_t pre = 0;
       if (t == 0) {
-        st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
       } else {
-        st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
-        pre = lb_exclusive(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
-        st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
+        pre = lb_exclusive_warp(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
       }
-      s_base[ld] = pre;
-      if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
+      if (l0) {
+        s_base[ld] = pre;
+        if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
+      }
     }
     __syncthreads();
 #pragma unroll

@@ -181,27 +181,81 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 // of the launch has timed out, the others give up at their next check, so
 // a failure costs one timeout, not one per tile.  The partial prefix is
 // never larger than the true one, so the writes it steers stay in bounds.
+// One thread per chain; LB_AHEAD predecessor words are loaded at once so a
+// walk over aggregates costs one memory round trip per LB_AHEAD tiles.
+constexpr int LB_AHEAD = 8;
 __device__ __forceinline__ uint32_t lb_exclusive(const unsigned long long* words, uint32_t stride, uint32_t t,
                                                  uint32_t epoch, uint32_t spin_limit, uint32_t* err) {
   uint32_t excl = 0;
   int j = (int)t - 1;
   uint32_t spins = 0;
   while (j >= 0) {
-    unsigned long long w = ld_relaxed_u64(words + (size_t)j * stride);
-    uint32_t ep = (uint32_t)(w >> 32);
-    uint32_t flag = (uint32_t)(w >> 30) & 3u;
-    if (ep != epoch || flag == 0) {
+    unsigned long long w[LB_AHEAD];
+#pragma unroll
+    for (int u = 0; u < LB_AHEAD; ++u) w[u] = j - u >= 0 ? ld_relaxed_u64(words + (size_t)(j - u) * stride) : 0ull;
+    int used = 0;
+    bool done = false, stalled = false;
+#pragma unroll
+    for (int u = 0; u < LB_AHEAD; ++u) {
+      if (done || stalled || j - u < 0) continue;
+      const uint32_t ep = (uint32_t)(w[u] >> 32);
+      const uint32_t flag = (uint32_t)(w[u] >> 30) & 3u;
+      if (ep != epoch || flag == 0) {
+        stalled = true;
+        continue;
+      }
+      excl += (uint32_t)(w[u] & 0x3FFFFFFFu);
+      ++used;
+      done = flag == 2;
+    }
+    if (done) break;
+    j -= used;
+    if (stalled) {
       if (++spins > spin_limit) {
         atomicOr(err, ERR_TIMEOUT);
         break;
       }
       if ((spins & 255u) == 0 && (*(volatile uint32_t*)err & ERR_TIMEOUT)) break;
-      __nanosleep(64);
-      continue;
+      __nanosleep(32);
     }
-    excl += (uint32_t)(w & 0x3FFFFFFFu);
-    if (flag == 2) break;
-    --j;
+  }
+  return excl;
+}
+
+// The same for one chain walked by a whole warp (all 32 lanes call it, the
+// result is returned in every lane): lane l reads predecessor j - l, so a
+// window of 32 words costs one round trip; the window is consumed up to the
+// first word that is not ready or through the first inclusive one.
+__device__ __forceinline__ uint32_t lb_exclusive_warp(const unsigned long long* words, uint32_t stride, uint32_t t,
+                                                      uint32_t epoch, uint32_t spin_limit, uint32_t* err) {
+  const int lane = (int)(threadIdx.x & 31u);
+  uint32_t excl = 0;
+  int j = (int)t - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const int k = j - lane;
+    const unsigned long long w = k >= 0 ? ld_relaxed_u64(words + (size_t)k * stride) : lb_pack(epoch, 2u, 0u);
+    const uint32_t flag = (uint32_t)(w >> 30) & 3u;
+    const bool ready = (uint32_t)(w >> 32) == epoch && flag != 0;
+    const unsigned not_ready = __ballot_sync(0xffffffffu, !ready);
+    const unsigned incl = __ballot_sync(0xffffffffu, ready && flag == 2);
+    const int first_nr = not_ready ? __ffs(not_ready) - 1 : 32;
+    const int first_inc = incl ? __ffs(incl) - 1 : 32;
+    const int take = first_inc < first_nr ? first_inc + 1 : first_nr;  // lanes [0, take) are summed
+    uint32_t v = lane < take ? (uint32_t)(w & 0x3FFFFFFFu) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (first_inc < first_nr) break;
+    j -= take;
+    if (take == 0) {
+      if (++spins > spin_limit) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      if ((spins & 255u) == 0 && (*(volatile uint32_t*)err & ERR_TIMEOUT)) break;
+      __nanosleep(32);
+    }
   }
   return excl;
 }

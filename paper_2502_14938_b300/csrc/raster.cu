@@ -45,18 +45,21 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
     }
     uint32_t tot;
     uint32_t ex = block_exclusive_scan<SCAN_NT>(sum, s_warp, &tot);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0 publishes the tile and walks back
+      const bool l0 = threadIdx.x == 0;
       unsigned long long* w = status + t;
       uint32_t pre = 0;
       if (t == 0) {
-        st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
       } else {
-        st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
-        pre = lb_exclusive(status, 1, t, epoch, spin, &fd->err);
-        st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
+        pre = lb_exclusive_warp(status, 1, t, epoch, spin, &fd->err);
+        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
       }
-      s_base = pre;
-      if (t == ntiles - 1) *total_out = pre + tot;
+      if (l0) {
+        s_base = pre;
+        if (t == ntiles - 1) *total_out = pre + tot;
+      }
     }
     __syncthreads();
     uint32_t run = s_base + ex;
@@ -203,13 +206,19 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 // with (X, Y) the pixel centre relative to the tile centre: the bracket in X
 // is per lane, so a pixel costs 2 FMA.  Each pixel walks the batch front to
 // back:
-//   skip if the power is below log2(1/255) (alpha < 1/255);
-//   alpha = min(0.99, 2^power);
+//   alpha = min(0.99, 2^power), taken as 0 when the power is below
+//   log2(1/255) (alpha < 1/255 is skipped: it then changes nothing);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
 //   C += c alpha T, T *= 1 - alpha;  out = C + T bg.
 // A warp skips a Gaussian whose opacity-aware box misses its band, and a
 // batch once all its pixels are finished; the block stops once all are.
 constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical)
+// 2^x by the hardware approximation (relative error ~2^-22; -inf -> 0).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 constexpr int BLEND_MAX_NT = 256;
 constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
@@ -246,13 +255,19 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
   const float wx0 = ((float)(tx * TW) + 0.5f) - ox, wx1 = wx0 + (float)(TW - 1);
   const float wy0 = ((float)(ty * TH + warp * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
   const uint2 rg = ranges[tile_key];
-  float T[BLEND_PPL], C0[BLEND_PPL], C1[BLEND_PPL], C2[BLEND_PPL];
-  unsigned live = 0;  // bit k: pixel k still blending
+  float T[BLEND_PPL], C0[BLEND_PPL], C1[BLEND_PPL], C2[BLEND_PPL], Yk[BLEND_PPL];
+  // kill[k]: 0 while pixel k blends, -inf once it has stopped (or lies
+  // outside the image): its power is then -inf, alpha 0, and T stays put
+  float kill[BLEND_PPL];
+  unsigned live = 0;  // bit k: pixel k still blending (for the early exit of the whole tile)
 #pragma unroll
   for (int k = 0; k < BLEND_PPL; ++k) {
     T[k] = 1.f;
     C0[k] = C1[k] = C2[k] = 0.f;
-    if (px < cd.W && py0 + k < cd.H) live |= 1u << k;
+    Yk[k] = Y0 + (float)k;
+    const bool in = px < cd.W && py0 + k < cd.H;
+    live |= (in ? 1u : 0u) << k;
+    kill[k] = in ? 0.f : -INFINITY;
   }
   for (uint32_t b = rg.x; b < rg.y; b += (uint32_t)nt) {
     if (__syncthreads_count(live != 0) == 0) break;
@@ -279,20 +294,18 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
     for (int u = 0; u < cnt; ++u) {
       const float4 bb = s_bb[u];
       if (bb.z < wx0 || bb.y > wx1 || bb.w > wy1 || s_ymax[u] < wy0) continue;  // box misses the band
-      if (!live) continue;
       const float4 q0 = s_q0[u];
       const float4 q1 = s_q1[u];
       const float pa = fmaf(X, fmaf(q0.w, X, q0.y), q0.x);  // F + X (D + A' X)
       const float pb = fmaf(q1.x, X, q0.z);                 // E + B' X
 #pragma unroll
       for (int k = 0; k < BLEND_PPL; ++k) {
-        if (!(live & (1u << k))) continue;
-        const float Y = Y0 + (float)k;
-        const float p = fmaf(Y, fmaf(q1.y, Y, pb), pa);
-        if (p < LOG2_MIN_ALPHA) continue;
-        const float alpha = fminf(0.99f, exp2f(p));
+        const float p = fmaf(Yk[k], fmaf(q1.y, Yk[k], pb), pa) + kill[k];
+        float alpha = fminf(0.99f, ex2_approx(p));
+        alpha = p >= LOG2_MIN_ALPHA ? alpha : 0.f;  // alpha < 1/255 contributes nothing
         const float tt = fmaf(-T[k], alpha, T[k]);
-        if (tt < 1e-4f) {
+        if (tt < 1e-4f) {  // stop before this Gaussian
+          kill[k] = -INFINITY;
           live &= ~(1u << k);
           continue;
         }
