@@ -184,11 +184,11 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096 (the
-  // cache scans run over visible anchors and over cache lines)
+  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096 (a
+  // cache's scan runs over its lines and the visible anchors)
   const uint32_t lines = std::max<uint32_t>(ctx->cfg.cache_gaussians / K, 1u);
   const uint32_t need = std::max({(ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 4095u) / 4096u,
-                                  (ctx->vis_cap + 4095u) / 4096u, (lines + 4095u) / 4096u}) + 1u;
+                                  (ctx->vis_cap + lines + 4095u) / 4096u}) + 1u;
   if (need > ctx->status_tiles) {
     int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
     if (r) return r;
@@ -263,8 +263,8 @@ int retile(gsc_ctx* ctx) {
 
 // ------------------------------------------------------------------ caches (Sec. 4)
 void free_cache(CacheDev& c) {
-  void* p[] = {c.slot_of, c.slot_anchor, c.slot_frame, c.slot_attr, c.vstat, c.new_flag, c.new_rank,
-               c.free_flag, c.free_rank, c.free_list, c.miss, c.state, c.slot_dir, c.cz, c.clab};
+  void* p[] = {c.slot_of, c.slot_anchor, c.slot_frame, c.slot_attr, c.vstat, c.flags, c.ranks,
+               c.free_list, c.miss, c.state, c.slot_dir, c.cz, c.clab};
   for (void* q : p) dfree(q);
   c = CacheDev{};
 }
@@ -311,9 +311,9 @@ int setup_caches(gsc_ctx* ctx) {
     int r;
     if ((r = dalloc(ctx, &c.slot_of, std::max(na, 1u))) || (r = dalloc(ctx, &c.slot_anchor, S)) ||
         (r = dalloc(ctx, &c.slot_frame, S)) || (r = dalloc(ctx, &c.slot_attr, (size_t)S * K * 3)) ||
-        (r = dalloc(ctx, &c.vstat, vcap)) || (r = dalloc(ctx, &c.new_flag, vcap)) ||
-        (r = dalloc(ctx, &c.new_rank, vcap)) || (r = dalloc(ctx, &c.free_flag, S)) ||
-        (r = dalloc(ctx, &c.free_rank, S)) || (r = dalloc(ctx, &c.free_list, S)) || (r = dalloc(ctx, &c.miss, vcap)) ||
+        (r = dalloc(ctx, &c.vstat, vcap)) || (r = dalloc(ctx, &c.flags, (size_t)S + vcap)) ||
+        (r = dalloc(ctx, &c.ranks, (size_t)S + vcap)) || (r = dalloc(ctx, &c.free_list, S)) ||
+        (r = dalloc(ctx, &c.miss, vcap)) ||
         (r = dalloc(ctx, &c.state, CS_WORDS)) || (r = dalloc(ctx, &c.slot_dir, S)))
       return r;
     if ((ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) &&
@@ -339,7 +339,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   FrameDev* fd = ctx->d_fd;
   const bool tm = ctx->timing;
   if (tm) cudaEventRecord(ctx->ev_stage[0], s);
-  launch_frame_begin(fd, ctx->d_fin, s);
+  launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
   for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
   launch_plan(fd, ctx->rec_cap, s);
@@ -365,7 +365,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     else
       launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->n_sm, s);
   launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->n_sm, s);
-  if (caches) launch_cache_policy(ctx->d_caches, ctx->n_caches, fd, replay, s);
+  if (caches && replay) launch_cache_replay_counts(ctx->d_caches, ctx->n_caches, fd, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
@@ -1085,8 +1085,9 @@ int gsc_debug_cache(gsc_ctx* ctx, uint32_t d, uint32_t* vstat, uint64_t cap, uin
   const CacheDev& c = ctx->h_caches[d];
   uint32_t st[CS_WORDS];
   CK(cudaMemcpy(st, c.state, sizeof st, cudaMemcpyDeviceToHost));
+  static_assert(CS_S == 7, "the 8 documented state words are CS_T .. CS_S");
   if (state8)
-    for (int i = 0; i < CS_WORDS; ++i) state8[i] = st[i];
+    for (int i = 0; i <= CS_S; ++i) state8[i] = st[i];
   *n = st[CS_VIS];
   return dbg_copy(ctx, vstat, c.vstat, st[CS_VIS], cap, 4);
 }

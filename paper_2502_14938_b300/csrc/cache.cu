@@ -5,16 +5,18 @@
 // the anchor id and the frame it was decoded in, plus a per-anchor line
 // index ("anchor indices are translated to the cache indices by index
 // mapping").  Per frame, all on the device:
-//   tick     t += 1
+//   tick     t += 1 (in the frame-setup kernel)
 //   probe    per visible anchor: hit (valid line with age <= depth), refresh
 //            (valid line, older than depth) or new (no valid line; lines past
 //            D_max are invalid); misses go to a work list for the decoder;
 //            per line: free iff unused or past D_max
-//   scans    ranks of new anchors (ascending) and of free lines (ascending)
+//   scan     one scan over [free flags of the S lines | new flags of the
+//            visible anchors]: ranks of free lines (and the free list, in
+//            ascending order) and of new anchors (ascending)
 //   assign   the i-th new anchor takes the i-th free line (none left: decoded
-//            but not cached); decoded lines are stamped with t
-//   policy   next depth = round(D_max (1 - misses / visible)) in [1, D_max]
-//            (Eq. 4, linear guiding function), computed in integers.
+//            but not cached); decoded lines are stamped with t; then the
+//            policy: next depth = round(D_max (1 - misses / visible)) in
+//            [1, D_max] (Eq. 4, linear guiding function), in integers.
 // The decoder writes fresh attributes of misses into their lines; the
 // projection reads hits from their lines.
 //
@@ -32,16 +34,6 @@ namespace gsc {
 __device__ __forceinline__ float anchor_dir(const ModelDev& md, const CamDev& cam, uint32_t a, float d[3]) {
   const float x[3] = {md.px[a], md.py[a], md.pz[a]};
   return pinned_dir(x, cam.pc, cam.pc_lo, d);
-}
-
-__global__ void k_cache_tick(CacheDev* caches, int n) {
-  const int c = threadIdx.x;
-  if (c >= n || !caches[c].active) return;
-  uint32_t* st = caches[c].state;
-  st[CS_T] += 1u;
-  st[CS_MISSES] = 0;
-  st[CS_NEW] = 0;
-  st[CS_FREE] = 0;
 }
 
 // rw: predictor weights (learned form), else unused.
@@ -82,34 +74,48 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
       hit = valid && age <= depth;
     }
     cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
-    cd.new_flag[vi] = valid ? 0u : 1u;
+    cd.flags[cd.S + vi] = valid ? 0u : 1u;
     if (!hit) cd.miss[atomicAdd(&cd.state[CS_MISSES], 1u)] = vi;
   }
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cd.S; s += stride)
-    cd.free_flag[s] = (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
+    cd.flags[s] = (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cd.state[CS_SCAN_N] = cd.S + V;
 }
 
-__global__ void k_cache_free_list(CacheDev* __restrict__ caches, int c) {
-  const CacheDev cd = caches[c];
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cd.S; s += gridDim.x * blockDim.x)
-    if (cd.free_flag[s]) cd.free_list[cd.free_rank[s]] = s;
+// Eq. 4 with the linear guide, from this frame's visible and decoded counts.
+__device__ __forceinline__ uint32_t next_depth(uint32_t depth, uint32_t V, uint32_t m, uint32_t D) {
+  if (V == 0) return depth;
+  const unsigned long long num = 2ull * D * (V - m) + V;
+  const uint32_t d = (uint32_t)(num / (2ull * V));
+  return d < 1u ? 1u : (d > D ? D : d);
 }
 
-__global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, const FrameDev* __restrict__ fd,
+__global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* __restrict__ fd,
                                uint32_t* const* __restrict__ vis, const ModelDev* __restrict__ models) {
   const CacheDev cd = caches[c];
   const CamDev& cam = fd->dcam[c];
   const ModelDev& md = models[cam.model];
   const uint32_t V = fd->vis_count[c];
-  const uint32_t t = cd.state[CS_T], n_free = cd.state[CS_FREE];
+  const uint32_t t = cd.state[CS_T];
+  const uint32_t n_free = V ? cd.ranks[cd.S] : cd.state[CS_SCAN_TOT];  // free lines precede the new flags
   const uint32_t* ids = vis[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // bookkeeping and the policy for the next frame
+    uint32_t* st = cd.state;
+    const uint32_t m = st[CS_MISSES];
+    st[CS_VIS] = V;
+    st[CS_FREE] = n_free;
+    st[CS_NEW] = st[CS_SCAN_TOT] - n_free;
+    st[CS_DEPTH] = next_depth(st[CS_DEPTH], V, m, st[CS_DMAX]);
+    atomicSub(&fd->n_derived, V - m);
+    if (c == 0) fd->cache_depth = st[CS_DEPTH];
+  }
   for (uint32_t vi = blockIdx.x * blockDim.x + threadIdx.x; vi < V; vi += gridDim.x * blockDim.x) {
     const uint32_t st = cd.vstat[vi];
     if (st & LINE_HIT) continue;
     const uint32_t a = ids[vi];
     uint32_t line = st;
-    if (cd.new_flag[vi]) {
-      const uint32_t rank = cd.new_rank[vi];
+    if (cd.flags[cd.S + vi]) {
+      const uint32_t rank = cd.ranks[cd.S + vi] - n_free;
       line = rank < n_free ? cd.free_list[rank] : LINE_NONE;
       cd.vstat[vi] = line;
     }
@@ -170,22 +176,15 @@ __global__ void k_reuse_label(CacheDev* __restrict__ caches, int c, const FrameD
   }
 }
 
-// replay != 0: the frame's decisions and the depth update were already made
-// by an earlier attempt at the same frame; only the frame counts are restated.
-__global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd, int replay) {
+// A frame rendered again after a buffer grew: its decisions and the depth
+// update were made by the first attempt; restate the frame's counts.
+__global__ void k_cache_replay_counts(CacheDev* caches, int n, FrameDev* fd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   uint32_t hits = 0;
   for (int c = 0; c < n; ++c) {
     if (!caches[c].active) continue;
-    uint32_t* st = caches[c].state;
-    const uint32_t V = fd->vis_count[c], m = st[CS_MISSES], D = st[CS_DMAX];
-    st[CS_VIS] = V;
-    hits += V - m;
-    if (!replay && V > 0) {
-      const unsigned long long num = 2ull * D * (V - m) + V;
-      uint32_t d = (uint32_t)(num / (2ull * V));
-      st[CS_DEPTH] = d < 1u ? 1u : (d > D ? D : d);
-    }
+    const uint32_t* st = caches[c].state;
+    hits += fd->vis_count[c] - st[CS_MISSES];
     if (c == 0) fd->cache_depth = st[CS_DEPTH];
   }
   fd->n_derived = fd->n_items - hits;
@@ -195,23 +194,19 @@ __global__ void k_cache_policy(CacheDev* caches, int n, FrameDev* fd, int replay
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s) {
-  k_cache_tick<<<1, 32, 0, s>>>(caches, n_caches);
   for (int c = 0; c < n_caches; ++c) {
     if (!host[c].active) continue;
     const CacheDev& h = host[c];
     k_cache_probe<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w, learned ? 1 : 0);
     if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
-    launch_scan_u32(h.new_flag, nullptr, &fd->vis_count[c], h.new_rank, h.state + CS_NEW, scan_status, fd,
-                    SLOT_CACHE + 2 * c, n_sm, s);
-    launch_scan_u32(h.free_flag, nullptr, h.state + CS_S, h.free_rank, h.state + CS_FREE, scan_status, fd,
-                    SLOT_CACHE + 2 * c + 1, n_sm, s);
-    k_cache_free_list<<<n_sm * 4, 256, 0, s>>>(caches, c);
+    launch_scan_u32(h.flags, nullptr, h.state + CS_SCAN_N, h.ranks, h.state + CS_SCAN_TOT, scan_status, fd,
+                    SLOT_CACHE + 2 * c, n_sm, s, h.free_list, h.S);
     k_cache_assign<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models);
   }
 }
 
-void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, bool replay, cudaStream_t s) {
-  k_cache_policy<<<1, 32, 0, s>>>(caches, n_caches, fd, replay ? 1 : 0);
+void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s) {
+  k_cache_replay_counts<<<1, 32, 0, s>>>(caches, n_caches, fd);
 }
 
 }  // namespace gsc

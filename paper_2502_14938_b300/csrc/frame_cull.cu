@@ -80,60 +80,93 @@ __device__ void unified_camera(const CamIn& L, const CamIn& Rr, CamIn& U) {
   }
 }
 
-__global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One warp: lane c sets up camera c, lane d derivation view d (the unified
+// camera of a stereo pair, Eq. 5-6, is float64 arithmetic with a long
+// dependency chain, so the views are set up side by side).
+// Lane c < n_caches also advances cache c's frame counter (Alg. 1 tick).
+__global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, CacheDev* __restrict__ caches,
+                              int n_caches) {
+  if (blockIdx.x != 0) return;
   const FrameIn& F = *fin;
-  fd->frame = fd->frame + 1;
-  fd->n_cams = F.n_cams;
-  fd->tile_w = F.tile_w;
-  fd->tile_h = F.tile_h;
-  fd->spin_limit = F.spin_limit;
-  uint32_t tb = 0;
-  for (uint32_t c = 0; c < F.n_cams; ++c) {
-    fill_camdev(fd->cam[c], F.cam[c], F);
-    fd->cam[c].tile_base = tb;
-    tb += (uint32_t)(fd->cam[c].ntx * fd->cam[c].nty);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nc = F.n_cams;
+  __shared__ int s_first[MAXV], s_second[MAXV];
+  __shared__ uint32_t s_nd;
+  // cameras: constants and tile bases (prefix of tile counts over lanes)
+  uint32_t ntiles = 0;
+  if (lane < nc) {
+    fill_camdev(fd->cam[lane], F.cam[lane], F);
+    ntiles = (uint32_t)(fd->cam[lane].ntx * fd->cam[lane].nty);
   }
-  fd->total_tiles = tb;
-  uint32_t bits = 1;
-  while ((1u << bits) < tb && bits < 31) ++bits;
-  fd->tile_bits = bits;
-  // derivation views
-  uint32_t nd = 0;
-  for (uint32_t c = 0; c < F.n_cams; ++c) fd->dview_of_cam[c] = -1;
-  for (uint32_t c = 0; c < F.n_cams; ++c) {
-    if (fd->dview_of_cam[c] >= 0) continue;
-    const int p = F.cam[c].partner;
-    const bool pair = F.unify && p > (int)c && p < (int)F.n_cams && F.cam[p].partner == (int)c;
-    if (pair) {
+  uint32_t incl = ntiles;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  if (lane < nc) fd->cam[lane].tile_base = incl - ntiles;
+  const uint32_t tb = __shfl_sync(0xffffffffu, incl, 31);
+  // derivation views: which cameras form each (integer bookkeeping, lane 0)
+  if (lane == 0) {
+    fd->frame = fd->frame + 1;
+    fd->n_cams = nc;
+    fd->tile_w = F.tile_w;
+    fd->tile_h = F.tile_h;
+    fd->spin_limit = F.spin_limit;
+    fd->total_tiles = tb;
+    uint32_t bits = 1;
+    while ((1u << bits) < tb && bits < 31) ++bits;
+    fd->tile_bits = bits;
+    int dof[MAXV];
+    for (uint32_t c = 0; c < nc; ++c) dof[c] = -1;
+    uint32_t nd = 0;
+    for (uint32_t c = 0; c < nc; ++c) {
+      if (dof[c] >= 0) continue;
+      const int p = F.cam[c].partner;
+      const bool pair = F.unify && p > (int)c && p < (int)nc && F.cam[p].partner == (int)c;
+      s_first[nd] = (int)c;
+      s_second[nd] = pair ? p : -1;
+      dof[c] = (int)nd;
+      if (pair) dof[p] = (int)nd;
+      ++nd;
+    }
+    for (uint32_t c = 0; c < nc; ++c) fd->dview_of_cam[c] = dof[c];
+    s_nd = nd;
+    fd->n_dviews = nd;
+    fd->n_valid = 0;
+    fd->n_pairs = 0;
+    fd->n_pairs_used = 0;
+    fd->n_big = 0;
+    fd->n_derived = 0;
+    fd->err = 0;
+  }
+  fd->ctr[lane] = 0;
+  fd->ctr[32 + lane] = 0;
+  if ((int)lane < n_caches && caches[lane].active) {
+    uint32_t* st = caches[lane].state;
+    st[CS_T] += 1u;
+    st[CS_MISSES] = 0;
+  }
+  __syncwarp();
+  __threadfence_block();
+  const uint32_t nd = s_nd;
+  if (lane < nd) {
+    const int c = s_first[lane], p = s_second[lane];
+    if (p >= 0) {
       CamIn U;
       unified_camera(F.cam[c], F.cam[p], U);
-      fill_camdev(fd->dcam[nd], U, F);
-      fd->dview_cam[nd][0] = (int)c;
-      fd->dview_cam[nd][1] = p;
-      fd->dview_of_cam[c] = (int)nd;
-      fd->dview_of_cam[p] = (int)nd;
+      fill_camdev(fd->dcam[lane], U, F);
     } else {
-      fd->dcam[nd] = fd->cam[c];
-      fd->dview_cam[nd][0] = (int)c;
-      fd->dview_cam[nd][1] = -1;
-      fd->dview_of_cam[c] = (int)nd;
+      fd->dcam[lane] = fd->cam[c];
     }
-    fd->vis_count[nd] = 0;
-    ++nd;
+    fd->dview_cam[lane][0] = c;
+    fd->dview_cam[lane][1] = p;
+    fd->vis_count[lane] = 0;
   }
-  fd->n_dviews = nd;
-  fd->n_valid = 0;
-  fd->n_pairs = 0;
-  fd->n_pairs_used = 0;
-  fd->n_big = 0;
-  fd->n_derived = 0;
-  fd->err = 0;
-  for (int i = 0; i < 64; ++i) fd->ctr[i] = 0;
 }
 
-void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s) {
-  k_frame_begin<<<1, 32, 0, s>>>(fd, fin);
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s) {
+  k_frame_begin<<<1, 32, 0, s>>>(fd, fin, caches, n_caches);
 }
 
 // New epoch for standalone uses of the look-back kernels (debug sort / scan).

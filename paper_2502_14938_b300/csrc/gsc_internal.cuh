@@ -130,7 +130,7 @@ struct ModelDev {
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
-enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_WORDS };
+enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_SCAN_N, CS_SCAN_TOT, CS_WORDS };
 constexpr uint32_t LINE_HIT = 0x80000000u;   // vstat: the anchor reuses its line
 constexpr uint32_t LINE_NONE = 0x7FFFFFFFu;  // vstat: decoded without a line
 struct CacheDev {
@@ -139,11 +139,9 @@ struct CacheDev {
   uint32_t* slot_frame;   // [S] frame of the line's last decode
   uint2* slot_attr;       // [S][K][3]: 12 float16 per Gaussian (alpha, c, s, q, 0)
   uint32_t* vstat;        // [visible] line | LINE_HIT, or LINE_NONE
-  uint32_t* new_flag;     // [visible]
-  uint32_t* new_rank;     // [visible]
-  uint32_t* free_flag;    // [S]
-  uint32_t* free_rank;    // [S]
-  uint32_t* free_list;    // [S]
+  uint32_t* flags;        // [S + visible]: line is free, then visible anchor is new
+  uint32_t* ranks;        // [S + visible]: exclusive prefix of flags (one scan)
+  uint32_t* free_list;    // [S] free lines in ascending order
   uint32_t* miss;         // [visible] visible indices to decode
   uint32_t* state;        // [CS_WORDS]
   float4* slot_dir;       // [S] unit direction camera -> anchor when the line was decoded
@@ -391,7 +389,7 @@ enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLO
              SLOT_CACHE = 32 };
 constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 
-void launch_frame_begin(FrameDev* fd, const FrameIn* fin, cudaStream_t s);
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
 void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
@@ -446,14 +444,14 @@ void launch_reuse_epoch_end(const ReuseTrain& T, cudaStream_t s);
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s);
-void launch_cache_policy(CacheDev* caches, int n_caches, FrameDev* fd, bool replay, cudaStream_t s);
+void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
                       uint32_t** vout, int ipt);
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
-                     cudaStream_t s);
+                     cudaStream_t s, uint32_t* scatter = nullptr, uint32_t scatter_n = 0);
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);

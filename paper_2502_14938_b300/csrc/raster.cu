@@ -8,6 +8,8 @@ namespace gsc {
 // ------------------------------------------------------------------ scan (K6)
 // Exclusive prefix sum of cnt[order[i]] (or cnt[i] without order) for
 // i < *n_ptr, one pass with a decoupled look-back; *total_out = the sum.
+// With scatter: for i < scatter_n with cnt[i] = 1, scatter[out[i]] = i (the
+// positions of the set flags, in ascending order).
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_IPT = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
@@ -15,7 +17,7 @@ constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ order,
                                                   const uint32_t* __restrict__ n_ptr, uint32_t* __restrict__ out,
                                                   uint32_t* total_out, unsigned long long* status, FrameDev* fd,
-                                                  int slot) {
+                                                  int slot, uint32_t* __restrict__ scatter, uint32_t scatter_n) {
   __shared__ uint32_t s_warp[SCAN_NT / 32 + 1];
   __shared__ uint32_t s_base;
   __shared__ uint32_t s_tile;
@@ -66,7 +68,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
 #pragma unroll
     for (int u = 0; u < SCAN_IPT; ++u) {
       const uint32_t i = i0 + u;
-      if (i < n) out[i] = run;
+      if (i < n) {
+        out[i] = run;
+        if (scatter && i < scatter_n && v[u]) scatter[run] = i;
+      }
       run += v[u];
     }
     __syncthreads();
@@ -75,8 +80,8 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
 
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
-                     cudaStream_t s) {
-  k_scan<<<n_sm * 2, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot);
+                     cudaStream_t s, uint32_t* scatter, uint32_t scatter_n) {
+  k_scan<<<n_sm * 2, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n);
 }
 
 // ------------------------------------------------------------------ key generation (K7)
