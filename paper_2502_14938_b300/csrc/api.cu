@@ -117,6 +117,9 @@ struct gsc_ctx {
   float* rw_w = nullptr;
   bool reuse_set = false;
   float4* attrs_fresh = nullptr;  // collection: every visible anchor derived afresh
+  // per-frame tables: decoder view set per model, projection table
+  DViewSet* d_tabs = nullptr;
+  ProjTab* d_ptab = nullptr;
 };
 
 namespace {
@@ -184,10 +187,10 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  // record sort tiles hold 2048 keys, pair sort and scan tiles 4096 (a
-  // cache's scan runs over its lines and the visible anchors)
+  // sort tiles hold 2048 keys, scan tiles 4096 (a cache's scan runs over
+  // its lines and the visible anchors)
   const uint32_t lines = std::max<uint32_t>(ctx->cfg.cache_gaussians / K, 1u);
-  const uint32_t need = std::max({(ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 4095u) / 4096u,
+  const uint32_t need = std::max({(ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 2047u) / 2048u,
                                   (ctx->vis_cap + lines + 4095u) / 4096u}) + 1u;
   if (need > ctx->status_tiles) {
     int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
@@ -349,22 +352,25 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (collect)  // fresh attributes of every visible anchor, for the labels
     for (int m : ctx->models_used)
       if (tc)
-        launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, &ctx->tmap_feat,
-                         ctx->compact, fp8, ctx->n_sm, s);
+        launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
+                         &ctx->tmap_feat, ctx->compact, fp8, ctx->n_sm, s);
       else
-        launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, ctx->n_sm, s);
+        launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
+                          ctx->n_sm, s);
   if (caches && !replay)
     launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
                        ctx->cfg.reuse == GSC_REUSE_LEARNED, collect ? ctx->attrs_fresh : nullptr, ctx->st_scan,
                        ctx->n_sm, s);
+  launch_tables(fd, caches, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
     if (tc)
-      launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, &ctx->tmap_feat,
-                       ctx->compact, fp8, ctx->n_sm, s);
+      launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
+                       &ctx->tmap_feat, ctx->compact, fp8, ctx->n_sm, s);
     else
-      launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->n_sm, s);
-  launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->n_sm, s);
+      launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
+                        ctx->n_sm, s);
+  launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->d_ptab, ctx->n_sm, s);
   if (caches && replay) launch_cache_replay_counts(ctx->d_caches, ctx->n_caches, fd, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
@@ -580,6 +586,9 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (prepare_derive_f32() != cudaSuccess || prepare_derive_tc() != cudaSuccess) return bail(GSC_ERR_CUDA);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cudaMalloc((void**)&ctx->d_tabs, dview_set_bytes() * MAX_MODELS) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_ptab, proj_tab_bytes()) != cudaSuccess)
+    return bail(GSC_ERR_OOM);
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
@@ -616,7 +625,7 @@ void gsc_destroy(gsc_ctx* ctx) {
                   ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
-                  ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w};
+                  ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
   dfree(ctx->d_caches);

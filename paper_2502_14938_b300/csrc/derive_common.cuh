@@ -33,8 +33,46 @@ struct DViewSet {
   ProjCam cam[MAXV][2];     // cameras fed by each view (cam = 0xFFFFFFFF unused)
 };
 
+// Per-frame tables in device memory, written once by k_tables so that the
+// derivation and projection kernels stage them with one block-wide copy
+// instead of each block walking the frame description serially.
+struct ProjTab {              // every derivation view, for the projection
+  uint32_t ibase[MAXV + 1];   // frame-wide item index of each view's first anchor; [n] = n_items
+  int model[MAXV];
+  const uint32_t* vstat[MAXV];
+  const uint2* lattr[MAXV];
+  ProjCam cam[MAXV][2];
+};
+
+// Block-wide copy of a table (sizes are multiples of 4 bytes).
+template <typename T>
+__device__ __forceinline__ void stage_table(T& dst, const T* __restrict__ src) {
+  static_assert(sizeof(T) % 4 == 0, "table size");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(&dst);
+  for (uint32_t i = threadIdx.x; i < sizeof(T) / 4; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ void fill_projcam(ProjCam& pc, const FrameDev* fd, int ci) {
+  pc.cam = ci < 0 ? 0xFFFFFFFFu : (uint32_t)ci;
+  if (ci < 0) return;
+  const CamDev& c = fd->cam[ci];
+  for (int i = 0; i < 9; ++i) pc.R[i] = c.R[i];
+  for (int i = 0; i < 3; ++i) {
+    pc.t[i] = c.t[i];
+    pc.pc[i] = c.pc[i];
+    pc.pc_lo[i] = c.pc_lo[i];
+    pc.dt[i] = c.dt[i];
+  }
+  pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
+  pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
+  pc.W = c.W; pc.H = c.H;
+  pc.rec_base = fd->rec_base[ci];
+}
+
 // Work of the decoder: every visible anchor of the model's views, or for a
-// view with a cache only its misses.
+// view with a cache only its misses.  (One thread; k_tables builds the same
+// sets for all models in parallel.)
 __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd, int model,
                                                 const CacheDev* caches) {
   int nd = 0;
@@ -53,28 +91,22 @@ __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd,
       S.pc[nd][u] = fd->dcam[d].pc[u];
       S.pc[nd][3 + u] = fd->dcam[d].pc_lo[u];
     }
-    for (int e = 0; e < 2; ++e) {
-      const int ci = fd->dview_cam[d][e];
-      ProjCam& pc = S.cam[nd][e];
-      pc.cam = ci < 0 ? 0xFFFFFFFFu : (uint32_t)ci;
-      if (ci < 0) continue;
-      const CamDev& c = fd->cam[ci];
-      for (int i = 0; i < 9; ++i) pc.R[i] = c.R[i];
-      for (int i = 0; i < 3; ++i) {
-        pc.t[i] = c.t[i];
-        pc.pc[i] = c.pc[i];
-        pc.pc_lo[i] = c.pc_lo[i];
-        pc.dt[i] = c.dt[i];
-      }
-      pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
-      pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
-      pc.W = c.W; pc.H = c.H;
-      pc.rec_base = fd->rec_base[ci];
-    }
+    for (int e = 0; e < 2; ++e) fill_projcam(S.cam[nd][e], fd, fd->dview_cam[d][e]);
     ++nd;
   }
   S.base[nd] = acc;
   S.nd = nd;
+}
+
+// The decoder's view set of `model`: staged from the frame table when there
+// is one, else built by thread 0.  Ends with a block barrier.
+__device__ __forceinline__ void load_dview_set(DViewSet& S, const DViewSet* __restrict__ tabs, const FrameDev* fd,
+                                               int model, const CacheDev* caches) {
+  if (tabs)
+    stage_table(S, tabs + model);
+  else if (threadIdx.x == 0)
+    build_dview_set(S, fd, model, caches);
+  __syncthreads();
 }
 
 // EWA projection of one Gaussian + opacity-aware exact tile count.

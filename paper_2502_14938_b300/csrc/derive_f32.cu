@@ -67,7 +67,8 @@ __device__ __forceinline__ void df_dots(const float (&h)[NH], const float* __res
 __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restrict__ models, int model,
                                                          FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                          float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
-                                                         const CacheDev* __restrict__ caches) {
+                                                         const CacheDev* __restrict__ caches,
+                                                         const DViewSet* __restrict__ tabs) {
   extern __shared__ __align__(16) float s_dyn[];
   float* s_w = s_dyn;
   float* s_h = s_dyn + DF_W;
@@ -76,16 +77,17 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
   __shared__ DFMeta M;
 
   const ModelDev md = models[model];
+  load_dview_set(S, tabs, fd, model, caches);
+  const int nd = S.nd;
+  const uint32_t total = S.base[nd];
+  const uint32_t ntiles = (total + DF_TA - 1) / DF_TA;
+  if (blockIdx.x >= ntiles) return;  // no tile for this block: skip the weight staging
   {
     const float4* src = reinterpret_cast<const float4*>(md.w32);
     for (int i = threadIdx.x; i < W_FLOATS / 4; i += DF_NT) reinterpret_cast<float4*>(s_w)[i] = src[i];
     for (int i = (W_FLOATS / 4) * 4 + threadIdx.x; i < W_FLOATS; i += DF_NT) s_w[i] = md.w32[i];
   }
-  if (threadIdx.x == 0) build_dview_set(S, fd, model, caches);
   __syncthreads();
-  const int nd = S.nd;
-  const uint32_t total = S.base[nd];
-  const uint32_t ntiles = (total + DF_TA - 1) / DF_TA;
   const uint32_t rec_cap = fd->n_records;
   const int t = threadIdx.x;
 
@@ -213,8 +215,9 @@ cudaError_t prepare_derive_f32() {
 }
 
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                       float* const* dbg_attrs, const CacheDev* caches, int n_sm, cudaStream_t s) {
-  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches);
+                       float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, int n_sm,
+                       cudaStream_t s) {
+  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
 }
 
 }  // namespace gsc

@@ -65,6 +65,8 @@ struct TcL {
 // 84 KB (+ 9 KB static): two CTAs per SM, 2 x 256 = 512 TMEM columns, so a
 // CTA's allocation never waits
 constexpr uint32_t TC_SMEM = 84 * 1024;
+// BAR: mbarriers for the features (+0) and the MMAs (+8), TMEM address (+16),
+// mbarrier for the weight image (+24)
 static_assert(TcL<false>::BAR + 32 <= TC_SMEM && TcL<true>::BAR + 32 <= TC_SMEM,
               "shared-memory image exceeds the allocation");
 static_assert(TcL<false>::IMG == 65536 && TcL<true>::IMG == 36224, "weight image sizes");
@@ -98,6 +100,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
+}
+// Untiled bulk copy global -> shared (both 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -171,11 +179,10 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
 template <bool FP8>
 __global__ void k_gather_feat(const ModelDev* __restrict__ models, int model, const FrameDev* __restrict__ fd,
                               uint32_t* const* __restrict__ vis, uint4* __restrict__ out,
-                              const CacheDev* __restrict__ caches) {
+                              const CacheDev* __restrict__ caches, const DViewSet* __restrict__ tabs) {
   constexpr uint32_t PARTS = FP8 ? 2u : 4u;  // uint4 per row
   __shared__ DViewSet S;
-  if (threadIdx.x == 0) build_dview_set(S, fd, model, caches);
-  __syncthreads();
+  load_dview_set(S, tabs, fd, model, caches);
   const uint4* src = reinterpret_cast<const uint4*>(FP8 ? models[model].feat_fp8 : models[model].feat_bf16);
   const uint32_t total = S.base[S.nd];
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total * PARTS; u += gridDim.x * blockDim.x) {
@@ -195,6 +202,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
                                                         FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
                                                         const CacheDev* __restrict__ caches,
+                                                        const DViewSet* __restrict__ tabs,
                                                         const __grid_constant__ CUtensorMap tmap_feat) {
   using L = TcL<FP8>;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -216,19 +224,21 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const ModelDev md = models[model];
-  {  // weights image (operands, zeroed H staging area, fp32 biases and scales)
-    const uint4* src = reinterpret_cast<const uint4*>(FP8 ? md.w_tc8 : md.w_tc);
-    uint4* dst = reinterpret_cast<uint4*>(smem + L::W1);
-    for (int i = t; i < (int)(L::IMG / 16); i += TC_NT) dst[i] = src[i];
-    // the last K-chunk of X is always zero; the one before holds the direction
+  load_dview_set(S, tabs, fd, model, caches);
+  if (blockIdx.x >= (S.base[S.nd] + TC_M - 1) / TC_M) return;  // no tile: skip weights, barriers and TMEM
+  const uint32_t w_bar = smem_u32(bars + 3);  // weight image barrier (after the TMEM address slot)
+  {  // the last K-chunk of X is always zero; the one before holds the direction
     uint4* zc = reinterpret_cast<uint4*>(smem + L::A + L::ZERO_CH * 2048);
     if (t < TC_M) zc[t] = make_uint4(0, 0, 0, 0);
   }
   if (t == 0) {
-    build_dview_set(S, fd, model, caches);
     mbar_init(tma_bar, 1);
     mbar_init(mma_bar, 1);
+    mbar_init(w_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // weights image (operands, zeroed H staging area, fp32 biases and scales): one bulk copy
+    mbar_expect_tx(w_bar, L::IMG);
+    bulk_load(sbase + L::W1, FP8 ? md.w_tc8 : md.w_tc, L::IMG, w_bar);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -250,8 +260,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   uint32_t tma_phase = 0, mma_phase = 0;
   bool failed = false;
   bool tma_pending = false, mma_pending = false;
+  bool w_pending = true;
+  if (__syncthreads_or(!mbar_wait(w_bar, 0)))
+    failed = true;
+  else
+    w_pending = false;
 
-  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (uint32_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     // ---- metadata, view direction chunk, TMA of the feature chunks
     if (t < TC_M) {
       const uint32_t item = tile * TC_M + t;
@@ -398,6 +413,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   if (failed) {
     if (t == 0) atomicOr(&fd->err, ERR_TIMEOUT);
     // drain what may still be in flight (bounded) before the memory goes away
+    if (w_pending) (void)mbar_wait(w_bar, 0);
     if (tma_pending) (void)mbar_wait(tma_bar, tma_phase ^ 1);
     if (mma_pending) (void)mbar_wait(mma_bar, mma_phase ^ 1);
   }
@@ -592,14 +608,15 @@ cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], c
 }
 
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
-                      bool fp8, int n_sm, cudaStream_t s) {
+                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, const CUtensorMap* tmap,
+                      uint4* compact, bool fp8, int n_sm, cudaStream_t s) {
   if (fp8) {
-    k_gather_feat<true><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
-    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
+    k_gather_feat<true><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches, tabs);
+    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs, *tmap);
   } else {
-    k_gather_feat<false><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches);
-    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, *tmap);
+    k_gather_feat<false><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches, tabs);
+    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs,
+                                                        *tmap);
   }
 }
 

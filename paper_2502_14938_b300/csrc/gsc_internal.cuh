@@ -398,9 +398,17 @@ void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();
 cudaError_t prepare_derive_tc();
 void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
+// Per-frame tables (defined in derive_common.cuh): the decoder's view set of
+// each model and the projection's per-view table, written by k_tables.
+struct DViewSet;
+struct ProjTab;
+size_t dview_set_bytes();
+size_t proj_tab_bytes();
+void launch_tables(const FrameDev* fd, const CacheDev* caches, DViewSet* tabs, ProjTab* ptab, int n_models,
+                   cudaStream_t s);
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CacheDev* caches, const CUtensorMap* tmap, uint4* compact,
-                      bool fp8, int n_sm, cudaStream_t s);
+                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, const CUtensorMap* tmap,
+                      uint4* compact, bool fp8, int n_sm, cudaStream_t s);
 int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows, bool fp8);
 // FP8-E4M3 form: per-tensor power-of-two scales, the weight image, feature conversion
 struct Fp8Scales {
@@ -415,11 +423,12 @@ void launch_to_e4m3(const float* src, float inv_scale, void* dst, size_t n, cuda
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img);
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                       float* const* dbg_attrs, const CacheDev* caches, int n_sm, cudaStream_t s);
+                       float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, int n_sm,
+                       cudaStream_t s);
 // derived attributes (3 float4 per Gaussian, frame-wide item order; cache
 // hits from their lines) -> records
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
-                    const CacheDev* caches, Records rec, int n_sm, cudaStream_t s);
+                    const CacheDev* caches, Records rec, const ProjTab* ptab, int n_sm, cudaStream_t s);
 // Reuse-predictor training buffers (device): samples, order, parameters,
 // Adam moments, gradient, per-block partials, per-epoch loss, counters
 // (ctl[0] Adam steps taken, ctl[1] epoch).

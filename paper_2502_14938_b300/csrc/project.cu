@@ -15,42 +15,29 @@ constexpr int PJ_NT = 256;
 
 __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ models, FrameDev* __restrict__ fd,
                                                    uint32_t* const* __restrict__ vis, const float4* __restrict__ attrs,
-                                                   const CacheDev* __restrict__ caches, Records rec) {
-  __shared__ uint32_t s_ibase[MAXV + 1];
-  __shared__ int s_model[MAXV];
-  __shared__ const uint32_t* s_vstat[MAXV];
-  __shared__ const uint2* s_lattr[MAXV];
-  __shared__ ProjCam s_cam[MAXV][2];
-  if (threadIdx.x == 0) {
+                                                   const CacheDev* __restrict__ caches, Records rec,
+                                                   const ProjTab* __restrict__ ptab) {
+  __shared__ ProjTab P;
+  if (ptab) {
+    stage_table(P, ptab);
+  } else if (threadIdx.x == 0) {
     const int nd = (int)fd->n_dviews;
     for (int d = 0; d < nd; ++d) {
-      s_ibase[d] = fd->item_base[d];
-      s_model[d] = fd->dcam[d].model;
+      P.ibase[d] = fd->item_base[d];
+      P.model[d] = fd->dcam[d].model;
       const bool cached = caches && d < MAX_CACHES && caches[d].active;
-      s_vstat[d] = cached ? caches[d].vstat : nullptr;
-      s_lattr[d] = cached ? caches[d].slot_attr : nullptr;
-      for (int e = 0; e < 2; ++e) {
-        const int ci = fd->dview_cam[d][e];
-        ProjCam& pc = s_cam[d][e];
-        pc.cam = ci < 0 ? 0xFFFFFFFFu : (uint32_t)ci;
-        if (ci < 0) continue;
-        const CamDev& c = fd->cam[ci];
-        for (int i = 0; i < 9; ++i) pc.R[i] = c.R[i];
-        for (int i = 0; i < 3; ++i) {
-          pc.t[i] = c.t[i];
-          pc.pc[i] = c.pc[i];
-          pc.pc_lo[i] = c.pc_lo[i];
-          pc.dt[i] = c.dt[i];
-        }
-        pc.fx = c.fx; pc.fy = c.fy; pc.cx = c.cx; pc.cy = c.cy;
-        pc.znear = c.znear; pc.gx = c.gx; pc.gy = c.gy;
-        pc.W = c.W; pc.H = c.H;
-        pc.rec_base = fd->rec_base[ci];
-      }
+      P.vstat[d] = cached ? caches[d].vstat : nullptr;
+      P.lattr[d] = cached ? caches[d].slot_attr : nullptr;
+      for (int e = 0; e < 2; ++e) fill_projcam(P.cam[d][e], fd, fd->dview_cam[d][e]);
     }
-    s_ibase[nd] = fd->n_items;
+    P.ibase[nd] = fd->n_items;
   }
   __syncthreads();
+  const uint32_t* s_ibase = P.ibase;
+  const int* s_model = P.model;
+  const uint32_t* const* s_vstat = P.vstat;
+  const uint2* const* s_lattr = P.lattr;
+  ProjCam (*s_cam)[2] = P.cam;
   const uint32_t n = fd->n_items * (uint32_t)K;
   const uint32_t rec_cap = fd->n_records;
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
@@ -105,8 +92,72 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
 }
 
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
-                    const CacheDev* caches, Records rec, int n_sm, cudaStream_t s) {
-  k_project<<<n_sm * 8, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec);
+                    const CacheDev* caches, Records rec, const ProjTab* ptab, int n_sm, cudaStream_t s) {
+  k_project<<<n_sm * 8, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec, ptab);
+}
+
+// ------------------------------------------------------------------ frame tables
+// One warp after the cache kernels: lane d fills derivation view d's entries
+// of the projection table and of its model's decoder view set (at its rank
+// among the model's views); lane m closes model m's set.
+__global__ void k_tables(const FrameDev* __restrict__ fd, const CacheDev* __restrict__ caches,
+                         DViewSet* __restrict__ tabs, ProjTab* __restrict__ ptab, int n_models) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const int nd = (int)fd->n_dviews;
+  auto work = [&](int d) -> uint32_t {
+    const bool cached = caches && d < MAX_CACHES && caches[d].active;
+    return cached ? caches[d].state[CS_MISSES] : fd->vis_count[d];
+  };
+  if (lane < nd) {
+    const int d = lane, m = fd->dcam[d].model;
+    const bool cached = caches && d < MAX_CACHES && caches[d].active;
+    ptab->ibase[d] = fd->item_base[d];
+    ptab->model[d] = m;
+    ptab->vstat[d] = cached ? caches[d].vstat : nullptr;
+    ptab->lattr[d] = cached ? caches[d].slot_attr : nullptr;
+    int r = 0;
+    uint32_t acc = 0;
+    for (int e = 0; e < d; ++e)
+      if (fd->dcam[e].model == m) {
+        ++r;
+        acc += work(e);
+      }
+    DViewSet& S = tabs[m];
+    S.d[r] = d;
+    S.base[r] = acc;
+    S.gbase[r] = fd->item_base[d];
+    S.miss[r] = cached ? caches[d].miss : nullptr;
+    S.vstat[r] = cached ? caches[d].vstat : nullptr;
+    S.lattr[r] = cached ? caches[d].slot_attr : nullptr;
+    for (int u = 0; u < 3; ++u) {
+      S.pc[r][u] = fd->dcam[d].pc[u];
+      S.pc[r][3 + u] = fd->dcam[d].pc_lo[u];
+    }
+    for (int e = 0; e < 2; ++e) {
+      fill_projcam(ptab->cam[d][e], fd, fd->dview_cam[d][e]);
+      fill_projcam(S.cam[r][e], fd, fd->dview_cam[d][e]);
+    }
+  }
+  if (lane == 0) ptab->ibase[nd] = fd->n_items;
+  if (lane < n_models) {
+    int c = 0;
+    uint32_t tot = 0;
+    for (int d = 0; d < nd; ++d)
+      if (fd->dcam[d].model == lane) {
+        ++c;
+        tot += work(d);
+      }
+    tabs[lane].nd = c;
+    tabs[lane].base[c] = tot;
+  }
+}
+
+size_t dview_set_bytes() { return sizeof(DViewSet); }
+size_t proj_tab_bytes() { return sizeof(ProjTab); }
+
+void launch_tables(const FrameDev* fd, const CacheDev* caches, DViewSet* tabs, ProjTab* ptab, int n_models,
+                   cudaStream_t s) {
+  k_tables<<<1, 32, 0, s>>>(fd, caches, tabs, ptab, n_models);
 }
 
 }  // namespace gsc
