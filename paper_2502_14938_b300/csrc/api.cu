@@ -286,7 +286,7 @@ int init_cache(gsc_ctx* ctx, CacheDev& c, uint32_t n_anchors) {
 }
 
 // One cache per derivation view of the current cameras (the views are found
-// as k_frame_begin finds them: a stereo pair under stereo_unify is one view).
+// as prepare_frame_cameras finds them: a stereo pair under stereo_unify is one view).
 int setup_caches(gsc_ctx* ctx) {
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
   ctx->n_caches = 0;
@@ -408,6 +408,143 @@ int build_graph(gsc_ctx* ctx) {
   return GSC_OK;
 }
 
+// ------------------------------------------------------------------ cameras (host, float64)
+// Camera constants and the unified camera of each stereo pair (Eq. 5-6) are
+// scalar float64 work per frame, done here rather than on the GPU, whose
+// float64 rate would put a long dependency chain at the head of every frame.
+// Every operation is written out in a fixed order and this file is compiled
+// without floating-point contraction, so the results are those of the same
+// sequence of IEEE double operations anywhere.
+
+// Camera centre p = -R^T t.
+void center64(const float* R, const float* t, double* p) {
+  for (int i = 0; i < 3; ++i) {
+    double s = (double)R[i] * (double)t[0];
+    s = s + (double)R[3 + i] * (double)t[1];
+    s = s + (double)R[6 + i] * (double)t[2];
+    p[i] = -s;
+  }
+}
+
+struct HostCam {
+  float R[9], t[3];
+  float fx, fy, cx, cy, znear;
+  int W, H, model;
+};
+
+HostCam host_cam(const gsc_camera& c) {
+  HostCam h;
+  std::memcpy(h.R, c.R, sizeof h.R);
+  std::memcpy(h.t, c.t, sizeof h.t);
+  h.fx = c.fx; h.fy = c.fy; h.cx = c.cx; h.cy = c.cy; h.znear = c.znear;
+  h.W = (int)c.width; h.H = (int)c.height; h.model = (int)c.model_id;
+  return h;
+}
+
+// Derived constants: double-float centre (pc, pc_lo), dt = t + R pc (what
+// R (x - pc) misses of R x + t when the float32 R is not exactly
+// orthonormal), guard-band tangents 1.3 (W/2)/fx and 1.3 (H/2)/fy in
+// float32, tile counts.
+void fill_camdev(CamDev& c, const HostCam& in, uint32_t tile_w, uint32_t tile_h) {
+  std::memset(&c, 0, sizeof c);
+  for (int i = 0; i < 9; ++i) c.R[i] = in.R[i];
+  for (int i = 0; i < 3; ++i) c.t[i] = in.t[i];
+  c.fx = in.fx; c.fy = in.fy; c.cx = in.cx; c.cy = in.cy;
+  c.W = in.W; c.H = in.H; c.znear = in.znear;
+  c.model = in.model;
+  double p[3];
+  center64(c.R, c.t, p);
+  for (int i = 0; i < 3; ++i) {
+    c.pc[i] = (float)p[i];
+    c.pc_lo[i] = (float)(p[i] - (double)c.pc[i]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    double s = (double)c.t[i];
+    for (int k = 0; k < 3; ++k) s = s + (double)c.R[3 * i + k] * p[k];
+    c.dt[i] = (float)s;
+  }
+  const float half_w = 0.5f * (float)c.W, half_h = 0.5f * (float)c.H;
+  c.gx = 1.3f * (half_w / c.fx);
+  c.gy = 1.3f * (half_h / c.fy);
+  c.ntx = (c.W + (int)tile_w - 1) / (int)tile_w;
+  c.nty = (c.H + (int)tile_h - 1) / (int)tile_h;
+}
+
+// Unified camera of a stereo pair (Eq. 5-6): d_u = normalised mean forward
+// axis; p_u = mean centre - d_u |p1 - p2| / (2 tan(theta/2)) with
+// 2 tan(theta/2) = W / fx (horizontal field of view); right/down axes from
+// the mean down axis orthogonalised against d_u; rounded once to float32.
+HostCam unified_camera(const HostCam& L, const HostCam& Rr) {
+  double p1[3], p2[3];
+  center64(L.R, L.t, p1);
+  center64(Rr.R, Rr.t, p2);
+  double d[3], y[3], pm[3];
+  for (int i = 0; i < 3; ++i) {
+    d[i] = ((double)L.R[6 + i] + (double)Rr.R[6 + i]) * 0.5;
+    y[i] = ((double)L.R[3 + i] + (double)Rr.R[3 + i]) * 0.5;
+    pm[i] = (p1[i] + p2[i]) * 0.5;
+  }
+  const double dn = std::sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  double du[3];
+  for (int i = 0; i < 3; ++i) du[i] = d[i] / dn;
+  const double bx = p1[0] - p2[0], by = p1[1] - p2[1], bz = p1[2] - p2[2];
+  const double b = std::sqrt((bx * bx + by * by) + bz * bz);
+  const double back = (b * (double)L.fx) / (double)L.W;
+  double pu[3];
+  for (int i = 0; i < 3; ++i) pu[i] = pm[i] - du[i] * back;
+  const double xr[3] = {y[1] * du[2] - y[2] * du[1], y[2] * du[0] - y[0] * du[2], y[0] * du[1] - y[1] * du[0]};
+  const double xn = std::sqrt((xr[0] * xr[0] + xr[1] * xr[1]) + xr[2] * xr[2]);
+  double xu[3];
+  for (int i = 0; i < 3; ++i) xu[i] = xr[i] / xn;
+  const double yu[3] = {du[1] * xu[2] - du[2] * xu[1], du[2] * xu[0] - du[0] * xu[2], du[0] * xu[1] - du[1] * xu[0]};
+  const double Ru[9] = {xu[0], xu[1], xu[2], yu[0], yu[1], yu[2], du[0], du[1], du[2]};
+  HostCam U = L;
+  for (int i = 0; i < 9; ++i) U.R[i] = (float)Ru[i];
+  for (int r = 0; r < 3; ++r) {
+    double s = Ru[r * 3 + 0] * pu[0];
+    s = s + Ru[r * 3 + 1] * pu[1];
+    s = s + Ru[r * 3 + 2] * pu[2];
+    U.t[r] = (float)(-s);
+  }
+  return U;
+}
+
+// Cameras, tile bases and derivation views of the current frame into F.
+void prepare_frame_cameras(const gsc_ctx* ctx, FrameIn& F) {
+  const uint32_t nc = (uint32_t)ctx->cams.size();
+  const uint32_t tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
+  F.n_cams = nc;
+  uint32_t tb = 0;
+  for (uint32_t c = 0; c < nc; ++c) {
+    fill_camdev(F.cam[c], host_cam(ctx->cams[c]), tw, th);
+    F.cam[c].tile_base = tb;
+    tb += (uint32_t)(F.cam[c].ntx * F.cam[c].nty);
+  }
+  F.total_tiles = tb;
+  uint32_t bits = 1;
+  while ((1u << bits) < tb && bits < 31) ++bits;
+  F.tile_bits = bits;
+  uint32_t nd = 0;
+  for (uint32_t c = 0; c < nc; ++c) F.dview_of_cam[c] = -1;
+  for (uint32_t c = 0; c < nc; ++c) {
+    if (F.dview_of_cam[c] >= 0) continue;
+    const int p = ctx->cams[c].stereo_partner;
+    const bool pair = ctx->cfg.stereo_unify && p > (int)c && p < (int)nc && ctx->cams[p].stereo_partner == (int)c;
+    if (pair) {
+      fill_camdev(F.dcam[nd], unified_camera(host_cam(ctx->cams[c]), host_cam(ctx->cams[p])), tw, th);
+      F.dcam[nd].tile_base = F.cam[c].tile_base;
+      F.dview_of_cam[p] = (int)nd;
+    } else {
+      F.dcam[nd] = F.cam[c];
+    }
+    F.dview_cam[nd][0] = (int)c;
+    F.dview_cam[nd][1] = pair ? p : -1;
+    F.dview_of_cam[c] = (int)nd;
+    ++nd;
+  }
+  F.n_dviews = nd;
+}
+
 // Upload the frame description into the next pinned slot and enqueue the
 // frame.  out_rgb / out_T are device pointers per camera.
 int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
@@ -416,22 +553,12 @@ int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
   CK(cudaEventSynchronize(ctx->ev_slot[sl]));
   FrameIn* F = ctx->h_fin[sl];
   std::memset(F, 0, sizeof(FrameIn));
-  F->n_cams = (uint32_t)ctx->cams.size();
-  F->unify = ctx->cfg.stereo_unify;
+  prepare_frame_cameras(ctx, *F);
   F->tile_w = ctx->cfg.tile_w;
   F->tile_h = ctx->cfg.tile_h;
   F->spin_limit = ctx->spin_limit;
   for (int i = 0; i < 3; ++i) F->bg[i] = ctx->cfg.bg[i];
   for (size_t i = 0; i < ctx->cams.size(); ++i) {
-    const gsc_camera& c = ctx->cams[i];
-    CamIn& d = F->cam[i];
-    std::memcpy(d.R, c.R, sizeof d.R);
-    std::memcpy(d.t, c.t, sizeof d.t);
-    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-    d.W = c.width; d.H = c.height; d.znear = c.znear;
-    d.partner = c.stereo_partner;
-    d.model = c.model_id;
-    d.viewer = c.viewer;
     F->out_rgb[i] = (unsigned long long)(uintptr_t)out_rgb[i];
     F->out_T[i] = (unsigned long long)(uintptr_t)(out_T ? out_T[i] : nullptr);
   }

@@ -4,135 +4,36 @@
 namespace gsc {
 
 // ------------------------------------------------------------------ frame setup
-// Camera centre p = -R^T t, float64 in a fixed order (each op rounded).
-__device__ void center64(const float* R, const float* t, double* p) {
-  for (int i = 0; i < 3; ++i) {
-    double s = __dmul_rn((double)R[i], (double)t[0]);
-    s = __dadd_rn(s, __dmul_rn((double)R[3 + i], (double)t[1]));
-    s = __dadd_rn(s, __dmul_rn((double)R[6 + i], (double)t[2]));
-    p[i] = -s;
-  }
-}
-
-__device__ void fill_camdev(CamDev& c, const CamIn& in, const FrameIn& fin) {
-  for (int i = 0; i < 9; ++i) c.R[i] = in.R[i];
-  for (int i = 0; i < 3; ++i) c.t[i] = in.t[i];
-  c.fx = in.fx; c.fy = in.fy; c.cx = in.cx; c.cy = in.cy;
-  c.W = (int)in.W; c.H = (int)in.H; c.znear = in.znear;
-  c.model = (int)in.model;
-  double p[3];
-  center64(c.R, c.t, p);
-  for (int i = 0; i < 3; ++i) {
-    c.pc[i] = __double2float_rn(p[i]);
-    c.pc_lo[i] = __double2float_rn(p[i] - (double)c.pc[i]);
-  }
-  for (int i = 0; i < 3; ++i) {
-    double s = (double)c.t[i];
-    for (int k = 0; k < 3; ++k) s = __dadd_rn(s, __dmul_rn((double)c.R[3 * i + k], p[k]));
-    c.dt[i] = __double2float_rn(s);
-  }
-  c.gx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.W), c.fx));
-  c.gy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)c.H), c.fy));
-  c.ntx = (c.W + (int)fin.tile_w - 1) / (int)fin.tile_w;
-  c.nty = (c.H + (int)fin.tile_h - 1) / (int)fin.tile_h;
-}
-
-// Unified camera of a stereo pair (Eq. 5-6): d_u = normalised mean forward
-// axis; p_u = mean centre - d_u |p1 - p2| / (2 tan(theta/2)) with
-// 2 tan(theta/2) = W / fx (horizontal field of view); right/down axes from
-// the mean down axis orthogonalised against d_u.  Float64, every operation
-// rounded explicitly (no contraction), result rounded once to float32.
-__device__ void unified_camera(const CamIn& L, const CamIn& Rr, CamIn& U) {
-  double p1[3], p2[3];
-  center64(L.R, L.t, p1);
-  center64(Rr.R, Rr.t, p2);
-  double d[3], y[3], pm[3];
-  for (int i = 0; i < 3; ++i) {
-    d[i] = __dmul_rn(__dadd_rn((double)L.R[6 + i], (double)Rr.R[6 + i]), 0.5);
-    y[i] = __dmul_rn(__dadd_rn((double)L.R[3 + i], (double)Rr.R[3 + i]), 0.5);
-    pm[i] = __dmul_rn(__dadd_rn(p1[i], p2[i]), 0.5);
-  }
-  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
-  double du[3];
-  for (int i = 0; i < 3; ++i) du[i] = __ddiv_rn(d[i], dn);
-  const double bx = __dsub_rn(p1[0], p2[0]), by = __dsub_rn(p1[1], p2[1]), bz = __dsub_rn(p1[2], p2[2]);
-  const double b = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)));
-  const double back = __ddiv_rn(__dmul_rn(b, (double)L.fx), (double)L.W);
-  double pu[3];
-  for (int i = 0; i < 3; ++i) pu[i] = __dsub_rn(pm[i], __dmul_rn(du[i], back));
-  double xr[3] = {__dsub_rn(__dmul_rn(y[1], du[2]), __dmul_rn(y[2], du[1])),
-                  __dsub_rn(__dmul_rn(y[2], du[0]), __dmul_rn(y[0], du[2])),
-                  __dsub_rn(__dmul_rn(y[0], du[1]), __dmul_rn(y[1], du[0]))};
-  const double xn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(xr[0], xr[0]), __dmul_rn(xr[1], xr[1])), __dmul_rn(xr[2], xr[2])));
-  double xu[3];
-  for (int i = 0; i < 3; ++i) xu[i] = __ddiv_rn(xr[i], xn);
-  double yu[3] = {__dsub_rn(__dmul_rn(du[1], xu[2]), __dmul_rn(du[2], xu[1])),
-                  __dsub_rn(__dmul_rn(du[2], xu[0]), __dmul_rn(du[0], xu[2])),
-                  __dsub_rn(__dmul_rn(du[0], xu[1]), __dmul_rn(du[1], xu[0]))};
-  double Ru[9] = {xu[0], xu[1], xu[2], yu[0], yu[1], yu[2], du[0], du[1], du[2]};
-  U = L;
-  for (int i = 0; i < 9; ++i) U.R[i] = __double2float_rn(Ru[i]);
-  for (int r = 0; r < 3; ++r) {
-    double s = __dmul_rn(Ru[r * 3 + 0], pu[0]);
-    s = __dadd_rn(s, __dmul_rn(Ru[r * 3 + 1], pu[1]));
-    s = __dadd_rn(s, __dmul_rn(Ru[r * 3 + 2], pu[2]));
-    U.t[r] = __double2float_rn(-s);
-  }
-}
-
-// One warp: lane c sets up camera c, lane d derivation view d (the unified
-// camera of a stereo pair, Eq. 5-6, is float64 arithmetic with a long
-// dependency chain, so the views are set up side by side).
-// Lane c < n_caches also advances cache c's frame counter (Alg. 1 tick).
+// The cameras' constants and the derivation views (with the unified camera
+// of each stereo pair, Eq. 5-6) are prepared in float64 by the library's host
+// code, which has fast float64; this warp copies them into the frame plan,
+// resets the per-frame counters and advances each cache's frame counter
+// (lane c < n_caches, Alg. 1 tick).
 __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, CacheDev* __restrict__ caches,
                               int n_caches) {
   if (blockIdx.x != 0) return;
   const FrameIn& F = *fin;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t nc = F.n_cams;
-  __shared__ int s_first[MAXV], s_second[MAXV];
-  __shared__ uint32_t s_nd;
-  // cameras: constants and tile bases (prefix of tile counts over lanes)
-  uint32_t ntiles = 0;
+  const uint32_t nc = F.n_cams, nd = F.n_dviews;
   if (lane < nc) {
-    fill_camdev(fd->cam[lane], F.cam[lane], F);
-    ntiles = (uint32_t)(fd->cam[lane].ntx * fd->cam[lane].nty);
+    fd->cam[lane] = F.cam[lane];
+    fd->dview_of_cam[lane] = F.dview_of_cam[lane];
   }
-  uint32_t incl = ntiles;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
+  if (lane < nd) {
+    fd->dcam[lane] = F.dcam[lane];
+    fd->dview_cam[lane][0] = F.dview_cam[lane][0];
+    fd->dview_cam[lane][1] = F.dview_cam[lane][1];
+    fd->vis_count[lane] = 0;
   }
-  if (lane < nc) fd->cam[lane].tile_base = incl - ntiles;
-  const uint32_t tb = __shfl_sync(0xffffffffu, incl, 31);
-  // derivation views: which cameras form each (integer bookkeeping, lane 0)
   if (lane == 0) {
     fd->frame = fd->frame + 1;
     fd->n_cams = nc;
+    fd->n_dviews = nd;
     fd->tile_w = F.tile_w;
     fd->tile_h = F.tile_h;
     fd->spin_limit = F.spin_limit;
-    fd->total_tiles = tb;
-    uint32_t bits = 1;
-    while ((1u << bits) < tb && bits < 31) ++bits;
-    fd->tile_bits = bits;
-    int dof[MAXV];
-    for (uint32_t c = 0; c < nc; ++c) dof[c] = -1;
-    uint32_t nd = 0;
-    for (uint32_t c = 0; c < nc; ++c) {
-      if (dof[c] >= 0) continue;
-      const int p = F.cam[c].partner;
-      const bool pair = F.unify && p > (int)c && p < (int)nc && F.cam[p].partner == (int)c;
-      s_first[nd] = (int)c;
-      s_second[nd] = pair ? p : -1;
-      dof[c] = (int)nd;
-      if (pair) dof[p] = (int)nd;
-      ++nd;
-    }
-    for (uint32_t c = 0; c < nc; ++c) fd->dview_of_cam[c] = dof[c];
-    s_nd = nd;
-    fd->n_dviews = nd;
+    fd->total_tiles = F.total_tiles;
+    fd->tile_bits = F.tile_bits;
     fd->n_valid = 0;
     fd->n_pairs = 0;
     fd->n_pairs_used = 0;
@@ -146,22 +47,6 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
     uint32_t* st = caches[lane].state;
     st[CS_T] += 1u;
     st[CS_MISSES] = 0;
-  }
-  __syncwarp();
-  __threadfence_block();
-  const uint32_t nd = s_nd;
-  if (lane < nd) {
-    const int c = s_first[lane], p = s_second[lane];
-    if (p >= 0) {
-      CamIn U;
-      unified_camera(F.cam[c], F.cam[p], U);
-      fill_camdev(fd->dcam[lane], U, F);
-    } else {
-      fd->dcam[lane] = fd->cam[c];
-    }
-    fd->dview_cam[lane][0] = c;
-    fd->dview_cam[lane][1] = p;
-    fd->vis_count[lane] = 0;
   }
 }
 

@@ -45,18 +45,7 @@ enum : uint32_t { ERR_PAIR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_CACHE_FULL = 4u,
 constexpr uint32_t INVALID_KEY = 0xFFFFFFFFu;
 constexpr uint32_t REC_VALID_BIT = 0x80000000u;
 
-struct CamIn {  // host-provided camera, uploaded each frame
-  float R[9];
-  float t[3];
-  float fx, fy, cx, cy;
-  uint32_t W, H;
-  float znear;
-  int32_t partner;
-  uint32_t model;
-  uint32_t viewer;
-};
-
-struct CamDev {  // camera with derived constants (computed on device)
+struct CamDev {  // camera with derived constants (prepared by the library's host code each frame)
   float R[9];
   float t[3];
   float fx, fy, cx, cy;
@@ -73,15 +62,18 @@ struct CamDev {  // camera with derived constants (computed on device)
 };
 
 struct FrameIn {  // host -> device per frame
-  uint32_t n_cams;
-  uint32_t unify;
+  uint32_t n_cams, n_dviews;
   uint32_t tile_w, tile_h;
   uint32_t spin_limit;
-  uint32_t pad[3];
+  uint32_t total_tiles, tile_bits;
+  uint32_t pad;
   float bg[4];
   unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
   unsigned long long out_T[MAXV];    // float* [H][W] per camera or 0
-  CamIn cam[MAXV];
+  CamDev cam[MAXV];                  // cameras with their constants
+  CamDev dcam[MAXV];                 // derivation views (unified camera of a stereo pair, Eq. 5-6)
+  int32_t dview_of_cam[MAXV];
+  int32_t dview_cam[MAXV][2];
 };
 
 struct FrameDev {  // device-resident per-frame plan and counters
