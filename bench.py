@@ -120,6 +120,24 @@ def oracle_frame_sample(model, L, R, subsample=16, phase=0):
     return t_fixed + t_blend * subsample
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, total_ms: float) -> float:
+    """Frames per second of the whole job: every rank renders `steps` frames
+    (weak scaling, independent replicas) within the slowest rank's time."""
+    return world * steps / (total_ms / 1e3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -133,9 +151,6 @@ def run_reference(args, rank, world):
         f = (args.warmup + s * 37) % len(frames)
         ts.append(oracle_frame_sample(model, *frames[f], phase=s))
     mean = float(np.mean(ts))
-    batched = run_batched(args, flush) if args.batched else None
-    learned = run_learned(model, flush, args.steps) if args.learned else None
-
     cores = oracle.num_threads()
     sample = ("per step: one stereo frame of the path, full filtering/derivation/projection in float64, "
               "blending on every 16th pixel row, blend time x16")
@@ -195,8 +210,10 @@ def run_profile(args):
           flush=True)
 
 
-def time_form(model, frames, form, steps, warmup, flush, world, clk=None):
-    """Per-frame CUDA-event times (ms) of `steps` frames of the path; L2 flushed between frames."""
+def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=False):
+    """Per-frame CUDA-event times (ms) of `steps` frames of the path; L2 flushed between frames.
+    tune: pick the blend tiling (tile shape, blocks/SM) with the project's autotuner on the
+    middle frame of the path first."""
     import torch
     W, H = frames[0][0].width, frames[0][0].height
     r, mid = make_renderer(model, form)
@@ -204,6 +221,15 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None):
     for f in range(len(frames)):  # one pass over the path with stats grows buffers to its needs
         set_pair(r, mid, *frames[f])
         r.render_frame(outs)
+    r.tiling = {"tile_w": 16, "tile_h": 16, "blocks_per_sm": 0, "source": "default"}
+    if tune:
+        from paper_2502_14938_b300 import autotune
+        set_pair(r, mid, *frames[len(frames) // 2])
+        best = autotune.tune(r, outs, None, reps=3)
+        r.tiling = {k: best[k] for k in ("tile_w", "tile_h", "blocks_per_sm", "source")}
+        for f in range(len(frames)):  # regrow for the chosen tiling
+            set_pair(r, mid, *frames[f])
+            r.render_frame(outs)
     for w in range(warmup):
         set_pair(r, mid, *frames[w % len(frames)])
         r.render_frame(outs, stats=False)
@@ -224,6 +250,8 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None):
         r.render_frame(outs, stats=False)
         evs[s][1].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     wall = time.perf_counter() - wall0
     if clk:
         clk.__exit__()
@@ -232,12 +260,15 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None):
     return r, mid, outs, ms, wall
 
 
-def stage_profile(model, frames, form, n, flush):
-    """Per-stage CUDA-event times on the library's stream (eager launches)."""
+def stage_profile(model, frames, form, n, flush, tiling=None):
+    """Per-stage CUDA-event times on the library's stream (eager launches), with the timed run's tiling."""
     import paper_2502_14938_b300 as pkg
     import torch
     W, H = frames[0][0].width, frames[0][0].height
     rt, mid = make_renderer(model, form, flags=pkg.FLAG_TIMING, use_graph=False)
+    set_pair(rt, mid, *frames[0])
+    if tiling:
+        rt.set_tiling(tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
     outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     stage = np.zeros(8)
     acc = {"visible_anchors": 0, "derived_anchors": 0, "records": 0, "valid_records": 0, "pairs": 0}
@@ -253,7 +284,7 @@ def stage_profile(model, frames, form, n, flush):
     return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, {k: v / n for k, v in acc.items()}
 
 
-def roofline(stage_ms, st, form, W, H, n_anchors):
+def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
     """Dominant stage: algorithmic work per launch / its event time, against a peak."""
     pk = peaks()
     dom = max(stage_ms, key=stage_ms.get)
@@ -263,7 +294,10 @@ def roofline(stage_ms, st, form, W, H, n_anchors):
     feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
     if dom == "blend":
         # FP32 lane work per (pixel, pair): 5 FMA quadratic, exp2, clamp, T update FMA, weight, 3 colour FMA
-        flop = P * 256 * 20.0
+        # per (pixel, pair) of the inner loop: quadratic 2 FMA, stop bias add, ex2, min, select,
+        # T update FMA, weight mul, 3 colour FMA = 17 flop, plus the per-lane quadratic prefix
+        # (3 FMA per 4 pixels) -> ~20 flop; every pixel of the tile for every pair
+        flop = P * tiling["tile_w"] * tiling["tile_h"] * 20.0
         ach = flop / dur / 1e12
         return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "peak_src": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
@@ -445,26 +479,23 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     form = args.form
     clk = ClockSampler(dev)
-    r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, world, clk)
-    total_ms = float(ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, world, clk,
+                                       tune=args.autotune)
+    total_ms = max_over_ranks(float(ms.sum()), world)
     others = {}
     for f2 in args.compare:
         if f2 == form:
             continue
-        r2, _, _, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1)
+        r2, _, _, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1, tune=args.autotune)
         others[f2] = {"fps": 1000.0 / float(ms2.mean()), "ms_mean": float(ms2.mean()),
-                      "p99_ms": float(np.percentile(ms2, 99))}
+                      "p99_ms": float(np.percentile(ms2, 99)), "tiling": r2.tiling}
         r2.close()
     if rank != 0:
         return
     mean_ms = total_ms / args.steps
-    fps = world * args.steps / (total_ms / 1e3)
-    stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush)
-    roof = roofline(stage_ms, per_frame, form, W, H, model.n)
+    fps = job_rate(world, args.steps, total_ms)
+    stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush, r.tiling)
+    roof = roofline(stage_ms, per_frame, form, W, H, model.n, r.tiling)
 
     # ---- quality: PSNR of sampled frames against the float64 oracle (plain
     # method), rendered in path order from an empty cache so reuse is live
@@ -509,7 +540,7 @@ def run_ours(args, rank, world):
 
     derive_launches = 2 if FORMS[form]["precision"] != "fp32" else 1
     launches_per_frame = 1 + 1 + 1 + derive_launches + (1 + 4) + 1 + 2 + (1 + 2) + 1 + 1
-    cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tile": "16x16",
+    cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tiling": r.tiling,
            "l2": "flushed between frames (256 MB write, untimed)",
            "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "psnr_frames": args.psnr_frames,
@@ -538,6 +569,8 @@ def main():
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the batched multi-viewer form (reported under config.batched)")
     ap.add_argument("--tiling-cache", default=None, help="JSON file the autotuner reads / writes")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="tune the headline form's blend tiling before timing it")
     ap.add_argument("--learned", action=argparse.BooleanOptionalAction, default=True,
                     help="also train the reuse predictor and time the learned form (config.learned_reuse)")
     args = ap.parse_args()
