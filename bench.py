@@ -193,10 +193,8 @@ def set_pair(r, mid, L, R):
 
 
 def run_profile(args):
-    """Minimal run for profilers: W + K frames from --frame, no extras.
-    Per frame: 17 library kernels (frame setup, cull, plan, derive - two for
-    the tensor-core forms - depth sort histogram + 4 passes, scan, keygen x2,
-    tile sort histogram + 2 passes, ranges, blend)."""
+    """Minimal run for profilers: W + K frames from --frame, no extras, default
+    16x16 tiling (launches per frame: launches_per_frame_of)."""
     import torch
     model, frames, _ = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
@@ -224,8 +222,9 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
     r.tiling = {"tile_w": 16, "tile_h": 16, "blocks_per_sm": 0, "source": "default"}
     if tune:
         from paper_2502_14938_b300 import autotune
-        set_pair(r, mid, *frames[len(frames) // 2])
-        best = autotune.tune(r, outs, None, reps=3)
+        picks = [frames[i] for i in np.linspace(0, len(frames) - 1, 6).astype(int)]
+        setups = [lambda fr=fr: set_pair(r, mid, *fr) for fr in picks]
+        best = autotune.tune(r, outs, None, reps=5, setups=setups)
         r.tiling = {k: best[k] for k in ("tile_w", "tile_h", "blocks_per_sm", "source")}
         for f in range(len(frames)):  # regrow for the chosen tiling
             set_pair(r, mid, *frames[f])
@@ -467,6 +466,49 @@ def run_learned(model, flush, steps):
     return out
 
 
+def form_quality(r, mid, outs, frames, refs):
+    """PSNR / max-abs against the oracle images `refs` {frame: [left, right]},
+    rendering the path from frame 0 in order (from an empty cache); also the
+    reused share of visible anchors per frame."""
+    r.cache_reset()
+    psnr, maxabs, reuse = [], [], []
+    for f in range(max(refs) + 1):
+        set_pair(r, mid, *frames[f])
+        st = r.render_frame(outs)
+        reuse.append(1.0 - st["derived_anchors"] / max(st["visible_anchors"], 1))
+        if f not in refs:
+            continue
+        mse, mx = 0.0, 0.0
+        for v in range(2):
+            got = outs[v].cpu().numpy().astype(np.float64)
+            mse += float(np.mean((got - refs[f][v]) ** 2)) / 2
+            mx = max(mx, float(np.abs(got - refs[f][v]).max()))
+        psnr.append(10 * np.log10(1.0 / max(mse, 1e-10)))  # identical images count as 100 dB
+        maxabs.append(mx)
+    return {"psnr_db": psnr, "max_abs": maxabs, "frames": sorted(refs)}, reuse
+
+
+def per_frame_tile_bits(W, H, tiling):
+    tiles = 2 * ((W + tiling["tile_w"] - 1) // tiling["tile_w"]) * ((H + tiling["tile_h"] - 1) // tiling["tile_h"])
+    bits = 1
+    while (1 << bits) < tiles and bits < 31:
+        bits += 1
+    return bits
+
+
+def launches_per_frame_of(form, tile_bits):
+    """Library kernels per stereo frame of one model: frame setup, cull, plan,
+    [cache probe, scan, assign], tables, derivation (+ feature gather on the
+    tensor-core forms), projection, depth sort (histogram + 4 passes), scan,
+    key generation (2), tile sort (histogram + one pass per 8 tile-key bits),
+    ranges, blend."""
+    f = FORMS[form]
+    n = 1 + 1 + 1 + 1 + (2 if f["precision"] != "fp32" else 1) + 1 + 5 + 1 + 2 + (1 + (tile_bits + 7) // 8) + 1 + 1
+    if f["reuse"] != "off":
+        n += 3
+    return n
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -483,13 +525,15 @@ def run_ours(args, rank, world):
                                        tune=args.autotune)
     total_ms = max_over_ranks(float(ms.sum()), world)
     others = {}
+    compare_renderers = {}
     for f2 in args.compare:
         if f2 == form:
             continue
-        r2, _, _, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1, tune=args.autotune)
+        r2, mid2, outs2, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1, tune=args.autotune)
         others[f2] = {"fps": 1000.0 / float(ms2.mean()), "ms_mean": float(ms2.mean()),
                       "p99_ms": float(np.percentile(ms2, 99)), "tiling": r2.tiling}
-        r2.close()
+        r2.mid, r2.outs = mid2, outs2
+        compare_renderers[f2] = r2
     if rank != 0:
         return
     mean_ms = total_ms / args.steps
@@ -497,25 +541,16 @@ def run_ours(args, rank, world):
     stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush, r.tiling)
     roof = roofline(stage_ms, per_frame, form, W, H, model.n, r.tiling)
 
-    # ---- quality: PSNR of sampled frames against the float64 oracle (plain
-    # method), rendered in path order from an empty cache so reuse is live
+    # ---- quality: PSNR and max-abs of sampled frames against the float64
+    # oracle (plain method), each form rendered in path order from an empty
+    # cache so reuse is live; the oracle images are made once
     import oracle
-    psnrs = []
-    r.cache_reset()
-    reuse_frac = []
-    for f in range(max(args.psnr_frames) + 1):
-        L, R = frames[f]
-        set_pair(r, mid, L, R)
-        st = r.render_frame(outs)
-        reuse_frac.append(1.0 - st["derived_anchors"] / max(st["visible_anchors"], 1))
-        if f not in args.psnr_frames:
-            continue
-        mse = 0.0
-        for v, cam in enumerate((L, R)):
-            (ref, _, _, _), _ = oracle.render_view(model, cam)
-            got = outs[v].cpu().numpy().astype(np.float64)
-            mse += float(np.mean((got - ref) ** 2)) / 2
-        psnrs.append(10 * np.log10(1.0 / max(mse, 1e-10)))  # identical images count as 100 dB
+    refs = {f: [oracle.render_view(model, cam)[0][0] for cam in frames[f]] for f in args.psnr_frames}
+    q, reuse_frac = form_quality(r, mid, outs, frames, refs)
+    for f2, r2 in compare_renderers.items():
+        others[f2]["quality"], _ = form_quality(r2, r2.mid, r2.outs, frames, refs)
+        r2.close()
+    psnrs = q["psnr_db"]
 
     # ---- end to end through the public API with host buffers
     host = [torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
@@ -538,12 +573,12 @@ def run_ours(args, rank, world):
            "sample": "2 stereo frames (0, 150): full float64 filtering/derivation/projection, "
                      "blending on every 16th pixel row scaled x16"}
 
-    derive_launches = 2 if FORMS[form]["precision"] != "fp32" else 1
-    launches_per_frame = 1 + 1 + 1 + derive_launches + (1 + 4) + 1 + 2 + (1 + 2) + 1 + 1
+    launches_per_frame = launches_per_frame_of(form, per_frame_tile_bits(W, H, r.tiling))
     cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tiling": r.tiling,
            "l2": "flushed between frames (256 MB write, untimed)",
            "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
-           "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "psnr_frames": args.psnr_frames,
+           "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "max_abs": q["max_abs"],
+           "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
            "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,

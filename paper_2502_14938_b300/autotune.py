@@ -29,35 +29,42 @@ def workload_key(renderer, extra: str = "") -> str:
     return f"{torch.cuda.get_device_name()}|{form}|{cams}|{extra}"
 
 
-def time_frames(renderer, outs, reps: int = 5, warmup: int = 2) -> float:
-    """Median ms of one rendered frame (device time on the renderer's stream)."""
+def time_frames(renderer, outs, reps: int = 5, warmup: int = 2, setups: Optional[Sequence] = None) -> float:
+    """Mean over `setups` (callables that set the renderer's cameras; default:
+    the current cameras) of the median ms of one rendered frame (device time
+    on the renderer's stream)."""
     import torch
-    for _ in range(warmup):
-        renderer.render_frame(outs, stats=False)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        renderer.render_frame(outs, stats=False)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ts.sort()
-    return ts[len(ts) // 2]
+    per_setup = []
+    for setup in (setups or [None]):
+        if setup is not None:
+            setup()
+        for _ in range(warmup):
+            renderer.render_frame(outs, stats=False)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            renderer.render_frame(outs, stats=False)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        per_setup.append(ts[len(ts) // 2])
+    return float(sum(per_setup) / len(per_setup))
 
 
 def sweep(renderer, outs, shapes: Iterable[Tuple[int, int]] = TILE_SHAPES,
-          blocks: Iterable[int] = BLOCKS_PER_SM, reps: int = 5) -> List[Dict]:
+          blocks: Iterable[int] = BLOCKS_PER_SM, reps: int = 5, setups: Optional[Sequence] = None) -> List[Dict]:
     """Every (shape, blocks/SM) candidate timed on the renderer's current
-    cameras; returns the table sorted fastest first.  The renderer keeps the
-    fastest tiling when this returns."""
+    cameras (or on each of `setups`, averaged); returns the table sorted
+    fastest first.  The renderer keeps the fastest tiling when this returns."""
     rows = []
     for tw, th in shapes:
         for bps in blocks:
             renderer.set_tiling(tw, th, bps)
             rows.append({"tile_w": tw, "tile_h": th, "blocks_per_sm": bps,
-                         "ms": time_frames(renderer, outs, reps)})
+                         "ms": time_frames(renderer, outs, reps, setups=setups)})
     rows.sort(key=lambda r: r["ms"])
     best = rows[0]
     renderer.set_tiling(best["tile_w"], best["tile_h"], best["blocks_per_sm"])
