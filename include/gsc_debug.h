@@ -37,7 +37,8 @@ GSC_API int gsc_debug_attrs(gsc_ctx* ctx, uint32_t d, float* attrs, uint64_t cap
  * threshold on q), depth, colour(3), and the bits of a uint32 word
  * (camera index in bits 0-15, bit 31 = record passed the projection tests);
  * plus the sort key (depth bits, 0xFFFFFFFF when unused) and tile count.
- * Unit: records. */
+ * A record that covers no tile is reported as zeros with its camera index
+ * and a tile count of 0 (the device keeps only its key).  Unit: records. */
 GSC_API int gsc_debug_records(gsc_ctx* ctx, float* rec12, uint32_t* depth_key, uint32_t* tile_count,
                       uint64_t cap, uint64_t* n);
 

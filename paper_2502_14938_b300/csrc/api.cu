@@ -375,15 +375,17 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
-                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov, 8);
+                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov, 8, fd->hist_depth);
   ctx->order_out = ov;
   if (tm) cudaEventRecord(ctx->ev_stage[3], s);
-  launch_scan_u32(ctx->rec.cnt, ov, &fd->n_valid, ctx->offs, &fd->n_pairs, ctx->st_scan, fd, SLOT_SCAN, ctx->n_sm, s);
+  launch_scan_u32(ctx->rec.cnt, ov, &fd->n_valid, ctx->offs, &fd->n_pairs, ctx->st_scan, fd, SLOT_SCAN, ctx->n_sm, s,
+                  nullptr, 0, ctx->big, &fd->n_big, KG_SMALL);
   launch_keygen(fd, ctx->rec, ov, ctx->offs, ctx->pk0, ctx->pv0, ctx->pair_cap, ctx->big, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[4], s);
   uint32_t *pk = nullptr, *pv = nullptr;
   launch_sort_impl(ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->pk0, ctx->pv0, &fd->n_pairs_used, nullptr,
-                   (int)ctx->tile_bits, 0, SLOT_SORT2, fd, ctx->sb, ctx->n_sm, s, &pk, &pv, 16);
+                   (int)ctx->tile_bits, 0, SLOT_SORT2, fd, ctx->sb, ctx->n_sm, s, &pk, &pv, 16,
+                   fd->hist_tile);
   ctx->pkeys_out = pk;
   ctx->pvals_out = pv;
   if (tm) cudaEventRecord(ctx->ev_stage[5], s);
@@ -1295,6 +1297,16 @@ int gsc_debug_records(gsc_ctx* ctx, float* rec12, uint32_t* depth_key, uint32_t*
   *n = cnt;
   const uint64_t m = std::min<uint64_t>(cnt, cap);
   if (m == 0) return GSC_OK;
+  // records that cover no tile hold only their (invalid) key on the device:
+  // report them with zero geometry, their camera and a count of 0
+  std::vector<uint32_t> keys(m);
+  CK(cudaMemcpy(keys.data(), ctx->rec.key, m * 4, cudaMemcpyDeviceToHost));
+  const Counters& hc = *ctx->h_cnt;
+  auto camera_of = [&](uint64_t i) {
+    uint32_t c = 0;
+    while (c + 1 < ctx->cams.size() && i >= hc.rec_base[c + 1]) ++c;
+    return c;
+  };
   if (rec12) {
     std::vector<float4> g(m), c(m), o(m);
     CK(cudaMemcpy(g.data(), ctx->rec.geo, m * 16, cudaMemcpyDeviceToHost));
@@ -1302,13 +1314,23 @@ int gsc_debug_records(gsc_ctx* ctx, float* rec12, uint32_t* depth_key, uint32_t*
     CK(cudaMemcpy(o.data(), ctx->rec.col, m * 16, cudaMemcpyDeviceToHost));
     for (uint64_t i = 0; i < m; ++i) {
       float* q = rec12 + i * 12;
+      if (keys[i] == INVALID_KEY) {
+        for (int u = 0; u < 11; ++u) q[u] = 0.f;
+        const uint32_t bits = camera_of(i);
+        std::memcpy(&q[11], &bits, 4);
+        continue;
+      }
       q[0] = g[i].x; q[1] = g[i].y; q[2] = g[i].z; q[3] = g[i].w;
       q[4] = c[i].x; q[5] = c[i].y; q[6] = c[i].z; q[7] = c[i].w;
       q[8] = o[i].x; q[9] = o[i].y; q[10] = o[i].z; q[11] = o[i].w;
     }
   }
-  if (depth_key) CK(cudaMemcpy(depth_key, ctx->rec.key, m * 4, cudaMemcpyDeviceToHost));
-  if (tile_count) CK(cudaMemcpy(tile_count, ctx->rec.cnt, m * 4, cudaMemcpyDeviceToHost));
+  if (depth_key) std::memcpy(depth_key, keys.data(), m * 4);
+  if (tile_count) {
+    CK(cudaMemcpy(tile_count, ctx->rec.cnt, m * 4, cudaMemcpyDeviceToHost));
+    for (uint64_t i = 0; i < m; ++i)
+      if (keys[i] == INVALID_KEY) tile_count[i] = 0;
+  }
   return GSC_OK;
 }
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ void load_dview_set(DViewSet& S, const DViewSet* __re
 // the oracle uses for its ordering depth).  The geometry uses camera-relative
 // coordinates rel = ((x_a - c_hi) - c_lo) + o, which avoid the cancellation of
 // R x + t at city scale.
-__device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3],
+__device__ __forceinline__ uint32_t project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3],
                                               const float rel[3], float alpha, bool kept, const float col[3],
                                               const float s[3], const float q[4], int TW, int TH) {
   const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mu[0]), __fmul_rn(c.R[7], mu[1])),
@@ -169,12 +169,17 @@ __device__ __forceinline__ void project_write(const ProjCam& c, Records rec, uin
       flag |= REC_VALID_BIT;
     }
   }
-  colv.w = __uint_as_float(flag);
-  rec.geo[r] = geo;
-  rec.cop[r] = cop;
-  rec.col[r] = colv;
-  rec.key[r] = cnt > 0 ? __float_as_uint(tz) : INVALID_KEY;
-  rec.cnt[r] = cnt;
+  // a record that covers no tile is only its invalid key: nothing reads the rest
+  const uint32_t key = cnt > 0 ? __float_as_uint(tz) : INVALID_KEY;
+  rec.key[r] = key;
+  if (cnt > 0) {
+    colv.w = __uint_as_float(flag);
+    rec.geo[r] = geo;
+    rec.cop[r] = cop;
+    rec.col[r] = colv;
+    rec.cnt[r] = cnt;
+  }
+  return key;
 }
 
 // Activations of Eq. 3 for Gaussian j of one anchor from its 11 head

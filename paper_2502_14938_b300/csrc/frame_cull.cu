@@ -43,6 +43,14 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
   }
   fd->ctr[lane] = 0;
   fd->ctr[32 + lane] = 0;
+  {  // the two sorts' digit histograms (filled by the key producers)
+    uint4* h = reinterpret_cast<uint4*>(fd->hist_depth);
+    uint4* h2 = reinterpret_cast<uint4*>(fd->hist_tile);
+    for (uint32_t i = lane; i < 256; i += 32) {
+      h[i] = make_uint4(0, 0, 0, 0);
+      h2[i] = make_uint4(0, 0, 0, 0);
+    }
+  }
   if ((int)lane < n_caches && caches[lane].active) {
     uint32_t* st = caches[lane].state;
     st[CS_T] += 1u;

@@ -101,6 +101,11 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t n_derived;           // anchors decoded this frame (visible minus cache hits)
   uint32_t cache_depth;         // reuse depth of derivation view 0 for the next frame
   uint32_t ctr[64];             // dynamic tile counters of look-back kernels
+  // digit histograms (4 passes x 256) of the two sorts, accumulated by the
+  // kernels that produce their keys (projection: depth keys of valid
+  // records; key generation: tile keys of the written pairs)
+  alignas(16) uint32_t hist_depth[4 * 256];
+  alignas(16) uint32_t hist_tile[4 * 256];
 };
 
 struct ModelDev {
@@ -446,13 +451,21 @@ void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, Fr
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s);
 void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s);
+// hist: digit histograms already accumulated by the key producer (the
+// histogram kernel is skipped; with drop_invalid, *n_valid_out must hold the
+// kept count too), or null.
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
-                      uint32_t** vout, int ipt);
+                      uint32_t** vout, int ipt, const uint32_t* hist = nullptr);
+// Records covering more than KG_SMALL tiles get their pairs from a warp each.
+constexpr uint32_t KG_SMALL = 32;
+// big / n_big: indices i with cnt > big_above are appended (the large
+// records of key generation), else null.
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
-                     cudaStream_t s, uint32_t* scatter = nullptr, uint32_t scatter_n = 0);
+                     cudaStream_t s, uint32_t* scatter = nullptr, uint32_t scatter_n = 0, uint32_t* big = nullptr,
+                     uint32_t* n_big = nullptr, uint32_t big_above = 0);
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);

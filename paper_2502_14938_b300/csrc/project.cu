@@ -18,6 +18,10 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
                                                    const CacheDev* __restrict__ caches, Records rec,
                                                    const ProjTab* __restrict__ ptab) {
   __shared__ ProjTab P;
+  __shared__ uint32_t s_h[4][256];  // digit histograms of this block's valid depth keys
+  __shared__ uint32_t s_nv;
+  for (int i = threadIdx.x; i < 4 * 256; i += PJ_NT) (&s_h[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_nv = 0;
   if (ptab) {
     stage_table(P, ptab);
   } else if (threadIdx.x == 0) {
@@ -86,9 +90,20 @@ __global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ 
       if (r >= rec_cap) continue;
       const float rel[3] = {((xa - pc.pc[0]) - pc.pc_lo[0]) + o3[0], ((ya - pc.pc[1]) - pc.pc_lo[1]) + o3[1],
                             ((za - pc.pc[2]) - pc.pc_lo[2]) + o3[2]};
-      project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
+      const uint32_t key = project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
+      if (key != INVALID_KEY) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xFFu], 1u);
+        atomicAdd(&s_nv, 1u);
+      }
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 256; i += PJ_NT) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(&fd->hist_depth[i], c);
+  }
+  if (threadIdx.x == 0 && s_nv) atomicAdd(&fd->n_valid, s_nv);
 }
 
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,

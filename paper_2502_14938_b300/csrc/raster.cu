@@ -9,7 +9,8 @@ namespace gsc {
 // Exclusive prefix sum of cnt[order[i]] (or cnt[i] without order) for
 // i < *n_ptr, one pass with a decoupled look-back; *total_out = the sum.
 // With scatter: for i < scatter_n with cnt[i] = 1, scatter[out[i]] = i (the
-// positions of the set flags, in ascending order).
+// positions of the set flags, in ascending order).  With big: every i whose
+// count exceeds big_above is appended to big (order unspecified).
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_IPT = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
@@ -17,7 +18,9 @@ constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ order,
                                                   const uint32_t* __restrict__ n_ptr, uint32_t* __restrict__ out,
                                                   uint32_t* total_out, unsigned long long* status, FrameDev* fd,
-                                                  int slot, uint32_t* __restrict__ scatter, uint32_t scatter_n) {
+                                                  int slot, uint32_t* __restrict__ scatter, uint32_t scatter_n,
+                                                  uint32_t* __restrict__ big, uint32_t* __restrict__ n_big,
+                                                  uint32_t big_above) {
   __shared__ uint32_t s_warp[SCAN_NT / 32 + 1];
   __shared__ uint32_t s_base;
   __shared__ uint32_t s_tile;
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
       if (i < n) {
         out[i] = run;
         if (scatter && i < scatter_n && v[u]) scatter[run] = i;
+        if (big && v[u] > big_above) big[atomicAdd(n_big, 1u)] = i;
       }
       run += v[u];
     }
@@ -80,61 +84,46 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
 
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
-                     cudaStream_t s, uint32_t* scatter, uint32_t scatter_n) {
-  k_scan<<<n_sm * 2, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n);
+                     cudaStream_t s, uint32_t* scatter, uint32_t scatter_n, uint32_t* big, uint32_t* n_big,
+                     uint32_t big_above) {
+  k_scan<<<n_sm * 2, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n, big,
+                                      n_big, big_above);
 }
 
 // ------------------------------------------------------------------ key generation (K7)
 // For the i-th record in depth order, emit (tile_base(camera) + tile, record)
 // at offs[i] .. offs[i] + cnt - 1, tiles in row-major order of the exact
 // coverage.  Pairs beyond the capacity are not written and flag an overflow.
-// A record covering at most KG_SMALL tiles is emitted by its own thread.
-// Larger ones (near-camera Gaussians, up to thousands of tiles) cluster at
-// the front of the depth order, so they go to a work list that a second
-// kernel spreads over all warps, one record per warp: lane l computes the
-// range of tile row ty0 + l (32 rows at once), a warp scan gives each row's
-// offset, and the lanes write the tiles of each row.  The float32 row ranges
-// are the ones the count pass used, so the pairs and their order are the same.
-constexpr uint32_t KG_SMALL = 32;
+// Records covering more than KG_SMALL tiles (near-camera Gaussians, up to
+// thousands of tiles, clustered at the front of the depth order) were listed
+// by the offset scan; each warp first takes such records one at a time: lane
+// l computes the range of tile row ty0 + l (32 rows at once), a warp scan
+// gives each row's offset, and the lanes write the tiles of each row.  Then
+// every thread emits the small records of a grid-stride range itself.  The
+// float32 row ranges are the ones the count pass used, so the pairs and their
+// order are the same either way.  Each block also accumulates the digit
+// histograms of the written tile keys for the tile sort.
+__device__ __forceinline__ void tile_hist_add(uint32_t (*s_h)[256], int npass, uint32_t key) {
+  for (int p = 0; p < npass; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xFFu], 1u);
+}
 
 __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Records rec, const uint32_t* __restrict__ order,
                                                 const uint32_t* __restrict__ offs, uint32_t* __restrict__ pkeys,
-                                                uint32_t* __restrict__ pvals, uint32_t cap, uint32_t* __restrict__ big) {
+                                                uint32_t* __restrict__ pvals, uint32_t cap,
+                                                const uint32_t* __restrict__ big) {
+  __shared__ uint32_t s_h[4][256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
   const uint32_t n = fd->n_valid;
+  const int npass = (int)((fd->tile_bits + 7u) / 8u);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const uint32_t np = fd->n_pairs;
     fd->n_pairs_used = np < cap ? np : cap;
     if (np > cap) atomicOr(&fd->err, ERR_PAIR_OVERFLOW);
   }
+  __syncthreads();
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t r = order[i];
-    const uint32_t c = rec.cnt[r];
-    if (c > KG_SMALL) {
-      big[atomicAdd(&fd->n_big, 1u)] = i;
-      continue;
-    }
-    uint32_t o = offs[i];
-    const float4 g = rec.geo[r];
-    const float4 cp = rec.cop[r];
-    const CamDev& cd = fd->cam[__float_as_uint(rec.col[r].w) & 0xFFFFu];
-    const uint32_t tb = cd.tile_base;
-    cover_tiles_f32(g.x, g.y, g.z, g.w, cp.x, cp.z, cd.W, cd.H, TW, TH, [&](int tile) {
-      if (o < cap) {
-        pkeys[o] = tb + (uint32_t)tile;
-        pvals[o] = r;
-      }
-      ++o;
-    });
-  }
-}
-
-__global__ void __launch_bounds__(256) k_keygen_big(FrameDev* __restrict__ fd, Records rec,
-                                                    const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
-                                                    uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
-                                                    uint32_t cap, const uint32_t* __restrict__ big) {
+  // large records: one warp each
   const uint32_t nb = fd->n_big;
-  const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t e = 0;
@@ -174,18 +163,41 @@ __global__ void __launch_bounds__(256) k_keygen_big(FrameDev* __restrict__ fd, R
           if (oi < cap) {
             pkeys[oi] = kb + u;
             pvals[oi] = r;
+            tile_hist_add(s_h, npass, kb + u);
           }
         }
       }
       o += chunk;
     }
   }
+  // small records: one thread each
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t r = order[i];
+    if (rec.cnt[r] > KG_SMALL) continue;
+    uint32_t o = offs[i];
+    const float4 g = rec.geo[r];
+    const float4 cp = rec.cop[r];
+    const CamDev& cd = fd->cam[__float_as_uint(rec.col[r].w) & 0xFFFFu];
+    const uint32_t tb = cd.tile_base;
+    cover_tiles_f32(g.x, g.y, g.z, g.w, cp.x, cp.z, cd.W, cd.H, TW, TH, [&](int tile) {
+      if (o < cap) {
+        pkeys[o] = tb + (uint32_t)tile;
+        pvals[o] = r;
+        tile_hist_add(s_h, npass, tb + (uint32_t)tile);
+      }
+      ++o;
+    });
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(&fd->hist_tile[i], c);
+  }
 }
 
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s) {
   k_keygen<<<n_sm * 8, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap, big);
-  k_keygen_big<<<n_sm * 4, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap, big);
 }
 
 // ------------------------------------------------------------------ tile ranges (K9)

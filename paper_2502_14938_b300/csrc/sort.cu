@@ -149,10 +149,13 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
-                      uint32_t** vout, int ipt) {
+                      uint32_t** vout, int ipt, const uint32_t* hist) {
   const int npass = (bits + 7) / 8;
-  cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * 4 * 256, s);
-  k_sort_hist<<<n_sm * 4, 256, 0, s>>>(kin, n_in, npass, drop_invalid, sb.hist, n_valid_out);
+  if (!hist) {
+    cudaMemsetAsync(sb.hist, 0, sizeof(uint32_t) * 4 * 256, s);
+    k_sort_hist<<<n_sm * 4, 256, 0, s>>>(kin, n_in, npass, drop_invalid, sb.hist, n_valid_out);
+    hist = sb.hist;
+  }
   const uint32_t* ci = kin;
   const uint32_t* cv = vin;
   for (int p = 0; p < npass; ++p) {
@@ -160,10 +163,10 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
     if (ipt == 8)
-      k_sort_pass<8><<<n_sm * 4, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256,
+      k_sort_pass<8><<<n_sm * 4, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
                                                   p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     else
-      k_sort_pass<16><<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, sb.hist + p * 256,
+      k_sort_pass<16><<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
                                                    p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     ci = ok;
     cv = ov;
