@@ -178,6 +178,10 @@ FORMS = {
 }
 HEADLINE = "cached_bf16_unified"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP/FMA x max SM clock
+# DRAM bytes (read + write) of one launch from an ncu capture of the same
+# kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
+# reported as the roofline's traffic only when the timed run uses that tiling.
+NCU_TRAFFIC = {"k_blend": {"bytes": 15.695e6 + 2.284e6, "tiling": (16, 32, 0), "frame": 151}}
 
 
 def make_renderer(model, form, flags=0, use_graph=True):
@@ -193,13 +197,15 @@ def set_pair(r, mid, L, R):
 
 
 def run_profile(args):
-    """Minimal run for profilers: W + K frames from --frame, no extras, default
-    16x16 tiling (launches per frame: launches_per_frame_of)."""
+    """Minimal run for profilers: W + K frames from --frame, no extras, with
+    the tiling of --tile (launches per frame: launches_per_frame_of)."""
     import torch
     model, frames, _ = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     r, mid = make_renderer(model, args.form)
     outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    set_pair(r, mid, *frames[args.frame % len(frames)])
+    r.set_tiling(*args.tile)
     for s in range(args.warmup + args.steps):
         set_pair(r, mid, *frames[(args.frame + s) % len(frames)])
         st = r.render_frame(outs)
@@ -298,9 +304,12 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
         # (3 FMA per 4 pixels) -> ~20 flop; every pixel of the tile for every pair
         flop = P * tiling["tile_w"] * tiling["tile_h"] * 20.0
         ach = flop / dur / 1e12
+        cap = NCU_TRAFFIC["k_blend"]
+        same = tuple(cap["tiling"]) == (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
         return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "peak_src": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
-                "traffic": None, "alg_flop_per_launch": flop, "ms_per_launch": stage_ms[dom],
+                "traffic": cap["bytes"] if same else None,
+                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {cap['tiling']}" if same else None, "alg_flop_per_launch": flop, "ms_per_launch": stage_ms[dom],
                 "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
     if dom == "sort_tile":
         b = P * 4 + 2 * P * 16
@@ -499,11 +508,10 @@ def per_frame_tile_bits(W, H, tiling):
 def launches_per_frame_of(form, tile_bits):
     """Library kernels per stereo frame of one model: frame setup, cull, plan,
     [cache probe, scan, assign], tables, derivation (+ feature gather on the
-    tensor-core forms), projection, depth sort (histogram + 4 passes), scan,
-    key generation (2), tile sort (histogram + one pass per 8 tile-key bits),
-    ranges, blend."""
+    tensor-core forms), projection, depth sort (4 passes), scan, key
+    generation, tile sort (one pass per 8 tile-key bits), ranges, blend."""
     f = FORMS[form]
-    n = 1 + 1 + 1 + 1 + (2 if f["precision"] != "fp32" else 1) + 1 + 5 + 1 + 2 + (1 + (tile_bits + 7) // 8) + 1 + 1
+    n = 1 + 1 + 1 + 1 + (2 if f["precision"] != "fp32" else 1) + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
     if f["reuse"] != "off":
         n += 3
     return n
@@ -601,6 +609,8 @@ def main():
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 150, 299])
     ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
     ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")
+    ap.add_argument("--tile", type=int, nargs=3, default=[16, 16, 0], metavar=("W", "H", "BPS"),
+                    help="blend tiling of a --profile run (tile width, height, blocks per SM)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the batched multi-viewer form (reported under config.batched)")
     ap.add_argument("--tiling-cache", default=None, help="JSON file the autotuner reads / writes")
