@@ -63,6 +63,12 @@ typedef enum {
 
 typedef enum { GSC_PREC_FP32 = 0, GSC_PREC_BF16 = 1, GSC_PREC_FP8 = 2 } gsc_precision;
 
+/* Image format of the outputs.  F32: float [H][W][3], the blended colour
+ * C + T bg.  RGBA8: uint8 [H][W][4], round-to-nearest-even of 255 x the same
+ * colour clamped to [0, 1], and alpha = that of 1 - T (the display format:
+ * 4 bytes per pixel instead of 12). */
+typedef enum { GSC_OUT_F32 = 0, GSC_OUT_RGBA8 = 1 } gsc_out_format;
+
 typedef enum {
   GSC_REUSE_OFF = 0,      /* decode every visible anchor every frame */
   GSC_REUSE_DEPTH = 1,    /* Alg. 1 dynamic cache depth (Eq. 4, linear guide) */
@@ -90,7 +96,8 @@ typedef struct {
   uint32_t flags;            /* GSC_FLAG_* */
   uint32_t blocks_per_sm;    /* blend: 0 = one block per tile; n = persistent grid of n blocks per SM
                                 taking the tiles of all cameras from one counter */
-  uint32_t reserved[7];
+  uint32_t out_format;       /* gsc_out_format of the images */
+  uint32_t reserved[6];
 } gsc_config;
 
 /* Model description: host pointers, float32, row-major.  Copied by
@@ -162,12 +169,28 @@ GSC_API int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n);
  * fills *stats.  With stats == NULL the call only enqueues work; a pair
  * overflow or a wait timeout of such a frame is reported by the next
  * synchronising call (GSC_ERR_CAPACITY / GSC_ERR_TIMEOUT). */
-GSC_API int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats);
+GSC_API int gsc_render_frame(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats);
 
 /* Same as gsc_render_frame, but out_rgb[i] are HOST pointers (pinned or
  * pageable); the device->host copies are part of the call, which returns
  * when the images are in host memory. */
-GSC_API int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats);
+GSC_API int gsc_render_frame_host(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats);
+
+/* Pipelined host rendering for a stream of frames: enqueues the frame and
+ * the copy of its images into out[i] (HOST pointers, pinned for the copy to
+ * overlap, valid until gsc_wait_host returns) and returns at once.  The
+ * device renders into one of two internal image sets while the previous
+ * frame's images are still being copied to the host on a copy stream, so a
+ * frame costs max(render, copy) rather than their sum.  The images of a
+ * frame are complete when gsc_wait_host returns (or after two more frames
+ * have been enqueued).  Buffer growth cannot re-render an asynchronous
+ * frame: run one synchronous frame first; a later overflow or timeout is
+ * reported by gsc_wait_host (GSC_ERR_CAPACITY / GSC_ERR_TIMEOUT, the
+ * affected images invalid). */
+GSC_API int gsc_render_frame_host_async(gsc_ctx* ctx, void* const* out);
+
+/* Wait for all pipelined host frames; returns the first deferred error. */
+GSC_API int gsc_wait_host(gsc_ctx* ctx);
 
 /* Change the blend tiling of a context in place (models and cameras stay):
  * tile_w x tile_h as for gsc_config, blocks_per_sm as for gsc_config.  Used

@@ -83,6 +83,10 @@ GSC_API int gsc_debug_wait_timeout(gsc_ctx* ctx, uint32_t spin_limit);
  * library's decoupled look-back scan kernel; *total receives the sum. */
 GSC_API int gsc_debug_scan(gsc_ctx* ctx, uint32_t* vals, uint64_t n, uint64_t* total);
 
+/* Bytes of the per-frame description uploaded host -> device by every
+ * render call (cameras with their constants, output pointers). */
+GSC_API int gsc_debug_frame_upload_bytes(void);
+
 /* Gradient of the predictor's mean binary cross-entropy over n samples (host
  * z [n][36], label [n]) at the current weights (bfloat16-rounded, as in
  * training), one forward/backward through the training kernels: grad

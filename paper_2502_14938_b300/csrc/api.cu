@@ -90,8 +90,6 @@ struct gsc_ctx {
   uint32_t* pkeys_out = nullptr;
   uint32_t* pvals_out = nullptr;
   // host-output images
-  float* d_img[MAXV] = {};
-  size_t d_img_bytes[MAXV] = {};
   float* d_T[MAXV] = {};
   size_t d_T_bytes[MAXV] = {};
   // graph
@@ -120,6 +118,14 @@ struct gsc_ctx {
   // per-frame tables: decoder view set per model, projection table
   DViewSet* d_tabs = nullptr;
   ProjTab* d_ptab = nullptr;
+  // pipelined host frames: two device image sets, a copy stream
+  void* d_hbuf[2][MAXV] = {};
+  size_t d_hbuf_bytes[2][MAXV] = {};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rendered[2] = {}, ev_copied[2] = {};
+  int hslot = 0;
+  bool hpending[2] = {false, false};
+  bool keep_err = false;  // the frame being enqueued is a pipelined host frame
 };
 
 namespace {
@@ -549,7 +555,7 @@ void prepare_frame_cameras(const gsc_ctx* ctx, FrameIn& F) {
 
 // Upload the frame description into the next pinned slot and enqueue the
 // frame.  out_rgb / out_T are device pointers per camera.
-int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
+int enqueue_frame(gsc_ctx* ctx, void* const* out_rgb, float* const* out_T) {
   const int sl = ctx->slot;
   ctx->slot = (ctx->slot + 1) % NSLOT;
   CK(cudaEventSynchronize(ctx->ev_slot[sl]));
@@ -558,6 +564,8 @@ int enqueue_frame(gsc_ctx* ctx, float* const* out_rgb, float* const* out_T) {
   prepare_frame_cameras(ctx, *F);
   F->tile_w = ctx->cfg.tile_w;
   F->tile_h = ctx->cfg.tile_h;
+  F->out_format = ctx->cfg.out_format;
+  F->keep_err = ctx->keep_err ? 1u : 0u;
   F->spin_limit = ctx->spin_limit;
   for (int i = 0; i < 3; ++i) F->bg[i] = ctx->cfg.bg[i];
   for (size_t i = 0; i < ctx->cams.size(); ++i) {
@@ -640,7 +648,7 @@ void fill_stats(gsc_ctx* ctx, gsc_frame_stats* st) {
   }
 }
 
-int render_impl(gsc_ctx* ctx, float* const* out_dev, float* const* out_T, gsc_frame_stats* stats, bool sync) {
+int render_impl(gsc_ctx* ctx, void* const* out_dev, float* const* out_T, gsc_frame_stats* stats, bool sync) {
   if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
   if (ctx->cfg.reuse == GSC_REUSE_LEARNED && !ctx->reuse_set)
     return fail(ctx, GSC_ERR_STATE, "the learned reuse form needs predictor weights (gsc_reuse_set_weights)");
@@ -699,6 +707,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.pair_capacity == 0) cfg.pair_capacity = 16u << 20;
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   if (!tiling_ok(cfg.tile_w, cfg.tile_h, cfg.blocks_per_sm)) return GSC_ERR_INVALID_ARG;
+  if (cfg.out_format > GSC_OUT_RGBA8) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
   if ((cfg.flags & GSC_FLAG_REUSE_COLLECT) && cfg.reuse == GSC_REUSE_OFF) return GSC_ERR_INVALID_ARG;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
@@ -718,7 +727,13 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cudaMalloc((void**)&ctx->d_tabs, dview_set_bytes() * MAX_MODELS) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_ptab, proj_tab_bytes()) != cudaSuccess)
     return bail(GSC_ERR_OOM);
-  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(GSC_ERR_CUDA);
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(GSC_ERR_CUDA);
   if (cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return bail(GSC_ERR_CUDA);
@@ -759,7 +774,6 @@ void gsc_destroy(gsc_ctx* ctx) {
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
   dfree(ctx->d_caches);
   for (int i = 0; i < MAXV; ++i) {
-    dfree(ctx->d_img[i]);
     dfree(ctx->d_T[i]);
   }
   for (int i = 0; i < NSLOT; ++i) {
@@ -771,6 +785,15 @@ void gsc_destroy(gsc_ctx* ctx) {
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_rendered[i]) cudaEventDestroy(ctx->ev_rendered[i]);
+    if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+    for (int v = 0; v < MAXV; ++v) dfree(ctx->d_hbuf[i][v]);
+  }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -958,7 +981,7 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
   return GSC_OK;
 }
 
-int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats) {
+int gsc_render_frame(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats) {
   if (!ctx) return GSC_ERR_INVALID_ARG;
   if (!out_rgb) return fail(ctx, GSC_ERR_INVALID_ARG, "null output table");
   for (size_t i = 0; i < ctx->cams.size(); ++i)
@@ -979,31 +1002,101 @@ int gsc_render_frame(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats
   return render_impl(ctx, out_rgb, (ctx->cfg.flags & GSC_FLAG_DEBUG_T) ? Ts : nullptr, stats, stats != nullptr);
 }
 
-int gsc_render_frame_host(gsc_ctx* ctx, float* const* out_rgb, gsc_frame_stats* stats) {
+namespace {
+size_t image_bytes(const gsc_ctx* ctx, size_t i) {
+  const size_t px = (size_t)ctx->cams[i].width * ctx->cams[i].height;
+  return px * (ctx->cfg.out_format == GSC_OUT_RGBA8 ? 4 : 12);
+}
+
+// Device image set `set` sized for the current cameras.
+int ensure_host_images(gsc_ctx* ctx, int set, void** outs) {
+  for (size_t i = 0; i < ctx->cams.size(); ++i) {
+    const size_t b = image_bytes(ctx, i);
+    if (ctx->d_hbuf_bytes[set][i] < b) {
+      dfree(ctx->d_hbuf[set][i]);
+      ctx->d_hbuf[set][i] = nullptr;
+      CK(cudaMalloc(&ctx->d_hbuf[set][i], b));
+      ctx->d_hbuf_bytes[set][i] = b;
+    }
+    outs[i] = ctx->d_hbuf[set][i];
+  }
+  return GSC_OK;
+}
+
+// Error bits of all frames since the last read (asynchronous frames).
+int take_sticky_error(gsc_ctx* ctx) {
+  uint32_t e = 0;
+  CK(cudaMemcpy(&e, &ctx->d_fd->err_sticky, 4, cudaMemcpyDeviceToHost));
+  if (!e) return GSC_OK;
+  CK(cudaMemset(&ctx->d_fd->err_sticky, 0, 4));
+  if (e & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up in a pipelined frame");
+  return fail(ctx, GSC_ERR_CAPACITY, "a pipelined frame overflowed a buffer; render a synchronous frame to grow it");
+}
+}  // namespace
+
+int gsc_render_frame_host(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats) {
   if (!ctx) return GSC_ERR_INVALID_ARG;
   if (!out_rgb) return fail(ctx, GSC_ERR_INVALID_ARG, "null output table");
   if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
-  float* outs[MAXV] = {};
-  for (size_t i = 0; i < ctx->cams.size(); ++i) {
+  for (size_t i = 0; i < ctx->cams.size(); ++i)
     if (!out_rgb[i]) return fail(ctx, GSC_ERR_INVALID_ARG, "null output image %zu", i);
-    const size_t b = (size_t)ctx->cams[i].width * ctx->cams[i].height * 3 * 4;
-    if (ctx->d_img_bytes[i] < b) {
-      dfree(ctx->d_img[i]);
-      ctx->d_img[i] = nullptr;
-      CK(cudaMalloc((void**)&ctx->d_img[i], b));
-      ctx->d_img_bytes[i] = b;
-    }
-    outs[i] = ctx->d_img[i];
-  }
-  gsc_frame_stats tmp;
-  int r = render_impl(ctx, outs, nullptr, stats ? stats : &tmp, true);
+  int r = gsc_wait_host(ctx);
   if (r) return r;
-  for (size_t i = 0; i < ctx->cams.size(); ++i) {
-    const size_t b = (size_t)ctx->cams[i].width * ctx->cams[i].height * 3 * 4;
-    CK(cudaMemcpyAsync(out_rgb[i], outs[i], b, cudaMemcpyDeviceToHost, ctx->stream));
-  }
+  void* outs[MAXV] = {};
+  if ((r = ensure_host_images(ctx, 0, outs))) return r;
+  gsc_frame_stats tmp;
+  r = render_impl(ctx, outs, nullptr, stats ? stats : &tmp, true);
+  if (r) return r;
+  for (size_t i = 0; i < ctx->cams.size(); ++i)
+    CK(cudaMemcpyAsync(out_rgb[i], outs[i], image_bytes(ctx, i), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return GSC_OK;
+}
+
+int gsc_render_frame_host_async(gsc_ctx* ctx, void* const* out) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  if (!out) return fail(ctx, GSC_ERR_INVALID_ARG, "null output table");
+  if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
+  for (size_t i = 0; i < ctx->cams.size(); ++i)
+    if (!out[i]) return fail(ctx, GSC_ERR_INVALID_ARG, "null output image %zu", i);
+  if (ctx->cfg.reuse == GSC_REUSE_LEARNED && !ctx->reuse_set)
+    return fail(ctx, GSC_ERR_STATE, "the learned reuse form needs predictor weights (gsc_reuse_set_weights)");
+  const int set = ctx->hslot;
+  ctx->hslot ^= 1;
+  if (ctx->hpending[set]) {  // the copy of the frame two back still reads this set
+    CK(cudaEventSynchronize(ctx->ev_copied[set]));
+    ctx->hpending[set] = false;
+  }
+  void* outs[MAXV] = {};
+  int r = ensure_host_images(ctx, set, outs);
+  if (r) return r;
+  ctx->pending = false;  // errors of pipelined frames are collected by gsc_wait_host
+  ctx->keep_err = true;
+  r = enqueue_frame(ctx, outs, nullptr);
+  ctx->keep_err = false;
+  if (r) return r;
+  CK(cudaEventRecord(ctx->ev_rendered[set], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[set], 0));
+  for (size_t i = 0; i < ctx->cams.size(); ++i)
+    CK(cudaMemcpyAsync(out[i], outs[i], image_bytes(ctx, i), cudaMemcpyDeviceToHost, ctx->copy_stream));
+  CK(cudaEventRecord(ctx->ev_copied[set], ctx->copy_stream));
+  ctx->hpending[set] = true;
+  ctx->pending = false;
+  return GSC_OK;
+}
+
+int gsc_wait_host(gsc_ctx* ctx) {
+  if (!ctx) return GSC_ERR_INVALID_ARG;
+  bool any = false;
+  for (int set = 0; set < 2; ++set)
+    if (ctx->hpending[set]) {
+      CK(cudaEventSynchronize(ctx->ev_copied[set]));
+      ctx->hpending[set] = false;
+      any = true;
+    }
+  if (!any) return GSC_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return take_sticky_error(ctx);
 }
 
 static int dbg_sync(gsc_ctx* ctx);
@@ -1185,6 +1278,8 @@ int gsc_reuse_train(gsc_ctx* ctx, const float* z, const uint8_t* y, uint64_t n, 
   ctx->err.clear();
   return GSC_OK;
 }
+
+int gsc_debug_frame_upload_bytes(void) { return (int)sizeof(FrameIn); }
 
 int gsc_debug_reuse_grad(gsc_ctx* ctx, const float* z, const uint8_t* y, uint64_t n, float* grad, float* loss) {
   if (!ctx) return GSC_ERR_INVALID_ARG;

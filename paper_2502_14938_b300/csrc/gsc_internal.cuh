@@ -66,7 +66,9 @@ struct FrameIn {  // host -> device per frame
   uint32_t tile_w, tile_h;
   uint32_t spin_limit;
   uint32_t total_tiles, tile_bits;
-  uint32_t pad;
+  uint32_t out_format;               // gsc_out_format
+  uint32_t keep_err;                 // 1: OR the frame's error bits into err_sticky (pipelined host frames)
+  uint32_t pad[3];
   float bg[4];
   unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
   unsigned long long out_T[MAXV];    // float* [H][W] per camera or 0
@@ -106,6 +108,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
   // records; key generation: tile keys of the written pairs)
   alignas(16) uint32_t hist_depth[4 * 256];
   alignas(16) uint32_t hist_tile[4 * 256];
+  uint32_t err_sticky;          // error bits of all frames since the host last read them
 };
 
 struct ModelDev {

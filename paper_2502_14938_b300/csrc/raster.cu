@@ -334,25 +334,46 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
       }
     }
   }
-  float* out = reinterpret_cast<float*>(fin->out_rgb[cam]);
-  float* outT = reinterpret_cast<float*>(fin->out_T[cam]);
+  if (fin->out_format == 0) {
+    float* out = reinterpret_cast<float*>(fin->out_rgb[cam]);
 #pragma unroll
-  for (int k = 0; k < BLEND_PPL; ++k) {
-    const int py = py0 + k;
-    if (px >= cd.W || py >= cd.H) continue;
-    const size_t p = ((size_t)py * cd.W + px) * 3;
-    out[p + 0] = C0[k] + T[k] * fin->bg[0];
-    out[p + 1] = C1[k] + T[k] * fin->bg[1];
-    out[p + 2] = C2[k] + T[k] * fin->bg[2];
-    if (outT) outT[(size_t)py * cd.W + px] = T[k];
+    for (int k = 0; k < BLEND_PPL; ++k) {
+      const int py = py0 + k;
+      if (px >= cd.W || py >= cd.H) continue;
+      const size_t p = ((size_t)py * cd.W + px) * 3;
+      out[p + 0] = C0[k] + T[k] * fin->bg[0];
+      out[p + 1] = C1[k] + T[k] * fin->bg[1];
+      out[p + 2] = C2[k] + T[k] * fin->bg[2];
+    }
+  } else {  // RGBA8: round-to-nearest-even of 255 x clamp(colour), alpha 1 - T
+    uchar4* out = reinterpret_cast<uchar4*>(fin->out_rgb[cam]);
+#pragma unroll
+    for (int k = 0; k < BLEND_PPL; ++k) {
+      const int py = py0 + k;
+      if (px >= cd.W || py >= cd.H) continue;
+      out[(size_t)py * cd.W + px] =
+          make_uchar4((unsigned char)__float2uint_rn(__saturatef(C0[k] + T[k] * fin->bg[0]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(C1[k] + T[k] * fin->bg[1]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(C2[k] + T[k] * fin->bg[2]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(1.f - T[k]) * 255.f));
+    }
+  }
+  float* outT = reinterpret_cast<float*>(fin->out_T[cam]);
+  if (outT) {
+#pragma unroll
+    for (int k = 0; k < BLEND_PPL; ++k) {
+      const int py = py0 + k;
+      if (px < cd.W && py < cd.H) outT[(size_t)py * cd.W + px] = T[k];
+    }
   }
 }
 
 // One block per tile of every camera.
-__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(const FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && fin->keep_err && fd->err) atomicOr(&fd->err_sticky, fd->err);
   blend_tile(blockIdx.x, sm, fd, ranges, vals, rec, fin);
 }
 
@@ -365,6 +386,7 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend_persistent(FrameDev* __r
                                                                    const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
   __shared__ uint32_t s_tile;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && fin->keep_err && fd->err) atomicOr(&fd->err_sticky, fd->err);
   const uint32_t total = fd->total_tiles;
   for (;;) {
     __syncthreads();

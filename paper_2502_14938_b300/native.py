@@ -23,6 +23,7 @@ STATUS = {0: "GSC_OK", -1: "GSC_ERR_INVALID_ARG", -2: "GSC_ERR_OOM", -3: "GSC_ER
           -4: "GSC_ERR_CAPACITY", -5: "GSC_ERR_TIMEOUT", -6: "GSC_ERR_STATE",
           -7: "GSC_ERR_UNIMPLEMENTED", -8: "GSC_ERR_INTERNAL"}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+OUT_FORMAT = {"f32": 0, "rgba8": 1}
 REUSE = {"off": 0, "depth": 1, "learned": 2}
 FLAG_DEBUG_ATTRS = 0x1
 FLAG_DEBUG_T = 0x2
@@ -42,7 +43,7 @@ class Config(C.Structure):
                 ("stereo_unify", C.c_uint32), ("cache_gaussians", C.c_uint32), ("max_depth", C.c_uint32),
                 ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("pair_capacity", C.c_uint64),
                 ("bg", C.c_float * 3), ("use_graph", C.c_uint32), ("flags", C.c_uint32),
-                ("blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+                ("blocks_per_sm", C.c_uint32), ("out_format", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class ModelDesc(C.Structure):
@@ -109,6 +110,9 @@ def lib():
             "gsc_scan_u32_noalloc": (I, [P, P, U64, P, P]),
             "gsc_debug_cache": (I, [P, U32, P, U64, P, P]),
             "gsc_set_tiling": (I, [P, U32, U32, U32]),
+            "gsc_render_frame_host_async": (I, [P, P]),
+            "gsc_wait_host": (I, [P]),
+            "gsc_debug_frame_upload_bytes": (I, []),
             "gsc_reuse_set_weights": (I, [P, P, U32]),
             "gsc_reuse_get_weights": (I, [P, P, U32]),
             "gsc_reuse_collect": (I, [P, U32, P, P, P, U64, P]),
@@ -180,7 +184,7 @@ class Renderer:
     def __init__(self, max_views: int = 2, precision: str = "fp32", reuse: str = "off",
                  stereo_unify: bool = False, tile: tuple = (16, 16), pair_capacity: int = 0,
                  bg=(0.0, 0.0, 0.0), use_graph: bool = True, flags: int = 0, stream=None,
-                 cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0):
+                 cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0, out_format: str = "f32"):
         cfg = default_config()
         cfg.max_views = max_views
         cfg.precision = PREC[precision]
@@ -195,7 +199,9 @@ class Renderer:
         cfg.cache_gaussians = cache_gaussians
         cfg.max_depth = max_depth
         cfg.blocks_per_sm = blocks_per_sm
+        cfg.out_format = OUT_FORMAT[out_format]
         self.cfg = cfg
+        self.out_format = out_format
         self.ctx = C.c_void_p()
         if stream is None:
             try:
@@ -251,7 +257,8 @@ class Renderer:
         self.cams = list(cams)
 
     def render_frame(self, outs, stats: bool = True) -> Optional[dict]:
-        """outs: list of device pointers or CUDA tensors [H,W,3] float32, one per camera."""
+        """outs: list of device pointers or CUDA tensors, one per camera: [H,W,3]
+        float32 (out_format "f32") or [H,W,4] uint8 ("rgba8")."""
         ptrs = (C.c_void_p * MAX_VIEWS)()
         for i, o in enumerate(outs):
             ptrs[i] = o.data_ptr() if hasattr(o, "data_ptr") else int(o)
@@ -262,14 +269,28 @@ class Renderer:
         self._check(lib().gsc_render_frame(self.ctx, ptrs, None))
         return None
 
-    def render_frame_host(self, outs: Sequence[np.ndarray], stats: bool = True) -> Optional[dict]:
+    def _host_ptrs(self, outs):
+        want = np.float32 if self.out_format == "f32" else np.uint8
         ptrs = (C.c_void_p * MAX_VIEWS)()
         for i, o in enumerate(outs):
-            assert o.dtype == np.float32 and o.flags.c_contiguous
-            ptrs[i] = o.ctypes.data if isinstance(o, np.ndarray) else o.data_ptr()
+            assert o.dtype == want and o.flags.c_contiguous
+            ptrs[i] = o.ctypes.data
+        return ptrs
+
+    def render_frame_host(self, outs: Sequence[np.ndarray], stats: bool = True) -> Optional[dict]:
+        """outs: host arrays [H,W,3] float32 or [H,W,4] uint8 per camera."""
+        ptrs = self._host_ptrs(outs)
         st = FrameStats()
         self._check(lib().gsc_render_frame_host(self.ctx, ptrs, C.byref(st) if stats else None))
         return st.as_dict() if stats else None
+
+    def render_frame_host_async(self, outs: Sequence[np.ndarray]):
+        """Pipelined host frame: the images land in outs (keep them alive,
+        preferably pinned) by the time wait_host() returns."""
+        self._check(lib().gsc_render_frame_host_async(self.ctx, self._host_ptrs(outs)))
+
+    def wait_host(self):
+        self._check(lib().gsc_wait_host(self.ctx))
 
     def set_tiling(self, tile_w: int, tile_h: int, blocks_per_sm: int = 0):
         """Blend tiling of this context (the autotuner's knob)."""
