@@ -207,7 +207,7 @@ int ensure_status(gsc_ctx* ctx) {
     CK(cudaMemset(ctx->st_scan, 0, (size_t)need * sizeof(unsigned long long)));
     ctx->status_tiles = need;
   }
-  const uint32_t cw = ((models_max_n(ctx) + 2047u) / 2048u + 1u) * 8u;
+  const uint32_t cw = ((models_max_n(ctx) + 2047u) / 2048u + 1u) * (uint32_t)MAXV;  // a look-back word per view
   if (cw > ctx->st_cull_words) {
     int r = dalloc(ctx, &ctx->st_cull, (size_t)cw);
     if (r) return r;
@@ -919,8 +919,6 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
     const bool second_eye = ctx->cfg.stereo_unify && c.stereo_partner >= 0 && (uint32_t)c.stereo_partner < i;
     if (!second_eye) per_model[c.model_id]++;
   }
-  for (uint32_t m = 0; m < MAX_MODELS; ++m)
-    if (per_model[m] > 8) return fail(ctx, GSC_ERR_INVALID_ARG, "more than 8 derivation views of model %u", m);
   // shape of the frame
   bool shape_same = ctx->cams.size() == n;
   for (uint32_t i = 0; shape_same && i < n; ++i) {

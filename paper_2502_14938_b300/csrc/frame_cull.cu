@@ -100,7 +100,8 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) 
 constexpr int CULL_NT = 256;
 constexpr int CULL_IPT = 8;
 constexpr int CULL_TILE = CULL_NT * CULL_IPT;
-constexpr int CULL_MAXD = 8;
+constexpr int CULL_MAXD = MAXV;  // derivation views of one model (look-back words per tile)
+constexpr int CULL_GROUP = 8;    // views tested together (one warp walks back per view)
 
 __global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
                                                   uint32_t* const* __restrict__ vis, unsigned long long* status) {
@@ -117,14 +118,14 @@ __global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ m
     int nd = 0;
     for (uint32_t d = 0; d < fd->n_dviews; ++d) {
       if (fd->dcam[d].model != model) continue;
-      if (nd < CULL_MAXD) s_d[nd++] = (int)d;  // the host admits at most 8 views per model
+      if (nd < CULL_MAXD) s_d[nd++] = (int)d;
     }
     s_nd = nd;
   }
   __syncthreads();
   const int nd = s_nd;
-  if (threadIdx.x < nd * 20) {
-    const int ld = threadIdx.x / 20, f = threadIdx.x % 20;
+  for (int i = threadIdx.x; i < nd * 20; i += CULL_NT) {
+    const int ld = i / 20, f = i % 20;
     const CamDev& c = fd->dcam[s_d[ld]];
     float v;
     if (f < 9) v = c.R[f];
@@ -165,67 +166,71 @@ __global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ m
         lv[i] = -1;
       }
     }
-    uint32_t excl[CULL_MAXD], mask[CULL_MAXD];
+    for (int g0 = 0; g0 < nd; g0 += CULL_GROUP) {  // views g0 .. g0 + 7 of this model
+      uint32_t excl[CULL_GROUP], mask[CULL_GROUP];
 #pragma unroll
-    for (int ld = 0; ld < CULL_MAXD; ++ld) {
-      excl[ld] = 0;
-      mask[ld] = 0;
-      if (ld >= nd) continue;
-      const float* c = s_cam[ld];
-      uint32_t m = 0;
+      for (int u = 0; u < CULL_GROUP; ++u) {
+        const int ld = g0 + u;
+        excl[u] = 0;
+        mask[u] = 0;
+        if (ld >= nd) continue;
+        const float* c = s_cam[ld];
+        uint32_t m = 0;
 #pragma unroll
-      for (int i = 0; i < CULL_IPT; ++i) {
-        if (lv[i] < 0) continue;
-        const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
-        const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
-        const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
-        bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-        if (v && lv[i] >= 1) {
-          const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
-          const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-          const float thr = ldexpf(md.lod_dmax, -lv[i]);
-          v = d2 <= __fmul_rn(thr, thr);
+        for (int i = 0; i < CULL_IPT; ++i) {
+          if (lv[i] < 0) continue;
+          const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
+          const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
+          const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
+          bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
+          if (v && lv[i] >= 1) {
+            const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
+            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const float thr = ldexpf(md.lod_dmax, -lv[i]);
+            v = d2 <= __fmul_rn(thr, thr);
+          }
+          if (v) m |= 1u << i;
         }
-        if (v) m |= 1u << i;
+        mask[u] = m;
+        uint32_t tot;
+        excl[u] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m), s_warp, &tot);
+        if (threadIdx.x == 0) s_total[ld] = tot;
       }
-      mask[ld] = m;
-      uint32_t tot;
-      excl[ld] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m), s_warp, &tot);
-      if (threadIdx.x == 0) s_total[ld] = tot;
-    }
-    __syncthreads();
-    if ((int)(threadIdx.x >> 5) < nd) {  // warp ld publishes view ld's tile count and walks back
-      const int ld = (int)(threadIdx.x >> 5);
-      const bool l0 = (threadIdx.x & 31u) == 0;
-      const uint32_t tot = s_total[ld];
-      unsigned long long* w = status + (size_t)t * CULL_MAXD + ld;
-      uint32_t pre = 0;
-      if (t == 0) {
-        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
-      } else {
-        if (l0) st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
-        pre = lb_exclusive_warp(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
-        if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
+      __syncthreads();
+      const int ld = g0 + (int)(threadIdx.x >> 5);
+      if (ld < nd && (int)(threadIdx.x >> 5) < CULL_GROUP) {  // warp u publishes view g0 + u's count, walks back
+        const bool l0 = (threadIdx.x & 31u) == 0;
+        const uint32_t tot = s_total[ld];
+        unsigned long long* w = status + (size_t)t * CULL_MAXD + ld;
+        uint32_t pre = 0;
+        if (t == 0) {
+          if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
+        } else {
+          if (l0) st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
+          pre = lb_exclusive_warp(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
+          if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
+        }
+        if (l0) {
+          s_base[ld] = pre;
+          if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
+        }
       }
-      if (l0) {
-        s_base[ld] = pre;
-        if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
-      }
-    }
-    __syncthreads();
+      __syncthreads();
 #pragma unroll
-    for (int ld = 0; ld < CULL_MAXD; ++ld) {
-      if (ld >= nd) continue;
-      uint32_t* out = vis[s_d[ld]];
-      uint32_t o = s_base[ld] + excl[ld];
-      uint32_t m = mask[ld];
-      while (m) {
-        const int i = __ffs(m) - 1;
-        m &= m - 1;
-        out[o++] = a0 + (uint32_t)i;
+      for (int u = 0; u < CULL_GROUP; ++u) {
+        const int lw = g0 + u;
+        if (lw >= nd) continue;
+        uint32_t* out = vis[s_d[lw]];
+        uint32_t o = s_base[lw] + excl[u];
+        uint32_t m = mask[u];
+        while (m) {
+          const int i = __ffs(m) - 1;
+          m &= m - 1;
+          out[o++] = a0 + (uint32_t)i;
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
