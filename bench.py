@@ -177,11 +177,16 @@ FORMS = {
     "cached_fp8_unified": dict(precision="fp8", stereo_unify=True, reuse="depth"),
 }
 HEADLINE = "cached_bf16_unified"
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 FLOP/FMA x max SM clock
+FP32_LANE_OPS = 148 * 128 * 2.032e9  # SMs x FP32 lanes x max SM clock: FP32 lane operations / s
+SFU_EXP2 = 148 * 16 * 2.032e9        # SMs x exp2 results per clock (SFU) x max SM clock
+# FP32-pipe lane operations of one evaluation besides its exp2: quadratic 2 FMA,
+# T update FMA, weight MUL, 3 colour FMA, and the per-lane prefix (3 FMA per
+# 4 pixels); the compare / min / select ops run on the ALU pipe
+FP32_OPS_PER_EVAL = 7.75
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
 # reported as the roofline's traffic only when the timed run uses that tiling.
-NCU_TRAFFIC = {"k_blend": {"bytes": 15.695e6 + 2.284e6, "tiling": (16, 32, 0), "frame": 151}}
+NCU_TRAFFIC = {"k_blend": {"bytes": 15.700e6 + 2.030e6, "tiling": (16, 32, 0), "frame": 151}}
 
 
 def make_renderer(model, form, flags=0, use_graph=True):
@@ -285,6 +290,19 @@ def stage_profile(model, frames, form, n, flush, tiling=None):
         for k in acc:
             acc[k] += st[k]
     rt.close()
+    # the same frames (from an empty cache) through the blend's counting
+    # variant: its (pixel, Gaussian) evaluations per frame
+    rw, mid = make_renderer(model, form, flags=pkg.FLAG_BLEND_WORK, use_graph=False)
+    if tiling:
+        rw.set_tiling(tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
+    acc["blend_walk"] = acc["blend_issued"] = 0
+    for s in range(n):
+        set_pair(rw, mid, *frames[s % len(frames)])
+        rw.render_frame(outs, stats=False)
+        w, i = rw.debug_blend_work()
+        acc["blend_walk"] += w
+        acc["blend_issued"] += i
+    rw.close()
     names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
     return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, {k: v / n for k, v in acc.items()}
 
@@ -298,18 +316,21 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
     dur = stage_ms[dom] / 1e3
     feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
     if dom == "blend":
-        # FP32 lane work per (pixel, pair): 5 FMA quadratic, exp2, clamp, T update FMA, weight, 3 colour FMA
-        # per (pixel, pair) of the inner loop: quadratic 2 FMA, stop bias add, ex2, min, select,
-        # T update FMA, weight mul, 3 colour FMA = 17 flop, plus the per-lane quadratic prefix
-        # (3 FMA per 4 pixels) -> ~20 flop; every pixel of the tile for every pair
-        flop = P * tiling["tile_w"] * tiling["tile_h"] * 20.0
-        ach = flop / dur / 1e12
+        # unit: one (pixel, Gaussian) evaluation, counted in the kernel (the
+        # counting variant on the same frames): every evaluation the blend
+        # issues takes one exp2 on the SFU, whose rate bounds the kernel
+        ev, walk = st["blend_issued"], st["blend_walk"]
+        ach = ev / dur / 1e9
+        peak = SFU_EXP2 / 1e9
         cap = NCU_TRAFFIC["k_blend"]
-        same = tuple(cap["tiling"]) == (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
-        return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "peak_src": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+        same = cap["bytes"] is not None and \
+            tuple(cap["tiling"]) == (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
+        return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Geval/s",
+                "frac": ach / peak, "peak_src": "148 SMs x 16 exp2/clk (SFU) x 2.032 GHz; one exp2 per evaluation",
                 "traffic": cap["bytes"] if same else None,
-                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {cap['tiling']}" if same else None, "alg_flop_per_launch": flop, "ms_per_launch": stage_ms[dom],
+                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {cap['tiling']}" if same else None,
+                "evals_per_launch": ev, "walk_evals_per_launch": walk, "walk_geval_s": walk / dur / 1e9,
+                "fp32_pipe_frac": ev * FP32_OPS_PER_EVAL / dur / FP32_LANE_OPS, "ms_per_launch": stage_ms[dom],
                 "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
     if dom == "sort_tile":
         b = P * 4 + 2 * P * 16

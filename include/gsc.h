@@ -80,6 +80,7 @@ typedef enum {
 #define GSC_FLAG_DEBUG_T 0x2u      /* keep per-pixel final transmittance */
 #define GSC_FLAG_TIMING 0x4u       /* per-stage CUDA-event timing into gsc_frame_stats */
 #define GSC_FLAG_REUSE_COLLECT 0x8u /* reuse forms: record predictor inputs + labels (gsc_reuse_collect) */
+#define GSC_FLAG_BLEND_WORK 0x10u  /* blend counts its work per frame (gsc_debug_blend_work); slower */
 
 typedef struct {
   uint32_t max_views;        /* cameras per frame, 1..GSC_MAX_VIEWS */

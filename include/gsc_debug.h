@@ -94,6 +94,15 @@ GSC_API int gsc_debug_frame_upload_bytes(void);
 GSC_API int gsc_debug_reuse_grad(gsc_ctx* ctx, const float* z, const uint8_t* label, uint64_t n, float* grad,
                                  float* loss);
 
+/* Blend work of the last rendered frame, needs GSC_FLAG_BLEND_WORK (host
+ * work[2]): work[0] = (pixel, Gaussian) evaluations of the front-to-back
+ * walk of every pixel - each Gaussian of its tile's list up to and including
+ * the one at which the pixel stops (T would fall below 1e-4), or all of
+ * them; work[1] = pixel evaluations the blend issued: 4 per lane of each
+ * warp for every Gaussian whose opacity-aware box meets the warp's rows
+ * (each one exp2, whether or not its pixel still blends).  Synchronises. */
+GSC_API int gsc_debug_blend_work(gsc_ctx* ctx, uint64_t* work);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,7 +84,7 @@ def lib():
         L.orc_keygen_f32.argtypes = [C.c_int64] + [P] * 8 + [C.c_int] * 4 + [P, P, P, C.c_int64]
         L.orc_keygen_f32.restype = C.c_int64
         L.orc_render.argtypes = [P, P, P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                 C.c_int64, P, P, P, P, P, P, P]
+                                 C.c_int64, P, P, P, P, P, P, P, P]
         L.orc_render.restype = C.c_int
         L.orc_blend_trace.argtypes = [P, P, C.c_int64, P, P]
         L.orc_blend_trace.restype = C.c_int64
@@ -280,9 +280,11 @@ def keygen_f32(mx, my, A, B, Cc, tau, view, valid, W, H, TW=16, TH=16):
 
 def render(rec: np.ndarray, depth32: np.ndarray, gid: np.ndarray, W: int, H: int, tiled: bool = True,
            px: Optional[np.ndarray] = None, py: Optional[np.ndarray] = None, bg=(0.0, 0.0, 0.0),
-           TW: int = 16, TH: int = 16):
+           TW: int = 16, TH: int = 16, walk: bool = False):
     """Alpha-blend the records.  Returns rgb, final T, decision margin, contributor count
-    (per listed pixel, or [H,W,...] images when no pixel list is given)."""
+    (per listed pixel, or [H,W,...] images when no pixel list is given), and with
+    walk=True also the walk length: how many Gaussians of its list each pixel
+    evaluated (all, or up to and including the one at which it stops)."""
     rec = np.ascontiguousarray(rec, np.float64)
     depth32 = np.ascontiguousarray(depth32, np.float32)
     gid = np.ascontiguousarray(gid, np.int64)
@@ -298,12 +300,14 @@ def render(rec: np.ndarray, depth32: np.ndarray, gid: np.ndarray, W: int, H: int
     T = np.zeros(NP, np.float64)
     mg = np.zeros(NP, np.float64)
     nc = np.zeros(NP, np.int32)
+    wk = np.zeros(NP, np.int32) if walk else None
     bgv = np.ascontiguousarray(bg, np.float64)
     assert lib().orc_render(_p(rec), _p(depth32), _p(gid), n, W, H, 1 if tiled else 0, TW, TH, npix,
-                            _p(px), _p(py), _p(bgv), _p(rgb), _p(T), _p(mg), _p(nc)) == 0
+                            _p(px), _p(py), _p(bgv), _p(rgb), _p(T), _p(mg), _p(nc), _p(wk)) == 0
     if px is None:
-        return rgb.reshape(H, W, 3), T.reshape(H, W), mg.reshape(H, W), nc.reshape(H, W)
-    return rgb, T, mg, nc
+        out = (rgb.reshape(H, W, 3), T.reshape(H, W), mg.reshape(H, W), nc.reshape(H, W))
+        return out + (wk.reshape(H, W),) if walk else out
+    return (rgb, T, mg, nc, wk) if walk else (rgb, T, mg, nc)
 
 
 def blend_trace(alpha_raw: np.ndarray, colour: np.ndarray):

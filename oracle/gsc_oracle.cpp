@@ -560,10 +560,12 @@ int64_t orc_keygen_f32(int64_t n, const float* mx, const float* my, const float*
 // Pixel list px/py (npix >= 0) or all pixels (npix < 0, row-major output).
 // margin: per pixel, the smallest |ln(alpha_raw * 255)| and |ln(T(1-alpha) 1e4)|
 // over the Gaussians the pixel evaluated (how close a threshold decision was).
+// walk (optional): per pixel, how many Gaussians of its list it evaluated -
+// all of them, or up to and including the one at which it stops.
 int orc_render(const double* rec, const float* depth32, const int64_t* gid, int64_t n, int W, int H,
                int mode, int TW, int TH, int64_t npix, const int32_t* px, const int32_t* py,
                const double* bg, double* out_rgb, double* out_T, double* out_margin,
-               int32_t* out_ncontrib) {
+               int32_t* out_ncontrib, int32_t* out_walk) {
   if (!rec || !depth32 || !gid || !out_rgb) return -1;
   // order of all valid records
   std::vector<int64_t> order;
@@ -621,6 +623,7 @@ int orc_render(const double* rec, const float* depth32, const int64_t* gid, int6
       lst = order.data();
       len = (int64_t)order.size();
     }
+    int64_t walk = len;
     for (int64_t u = 0; u < len; ++u) {
       const double* g = rec + lst[u] * 16;
       const double dx = X - g[1], dy = Y - g[2];
@@ -633,7 +636,10 @@ int orc_render(const double* rec, const float* depth32, const int64_t* gid, int6
       const double tt = T * (1.0 - al);
       const double ms = std::fabs(std::log(tt * 1e4));
       if (ms < mg) mg = ms;
-      if (tt < 1e-4) break;
+      if (tt < 1e-4) {
+        walk = u + 1;
+        break;
+      }
       for (int c = 0; c < 3; ++c) Cc[c] += g[7 + c] * al * T;
       T = tt;
       ++nc;
@@ -642,6 +648,7 @@ int orc_render(const double* rec, const float* depth32, const int64_t* gid, int6
     if (out_T) out_T[i] = T;
     if (out_margin) out_margin[i] = mg;
     if (out_ncontrib) out_ncontrib[i] = nc;
+    if (out_walk) out_walk[i] = (int32_t)walk;
   }
   return 0;
 }

@@ -4,7 +4,9 @@ The compute lives in libgsc.so (hand-written sm_103a CUDA behind a C ABI,
 include/gsc.h); `native` is the ctypes binding with the same call names.
 """
 from .native import (GscError, Renderer, default_config, exported_symbols, lib, to_camera,
-                     FLAG_DEBUG_ATTRS, FLAG_DEBUG_T, FLAG_TIMING, FLAG_REUSE_COLLECT, REUSE_NPARAM)
+                     FLAG_DEBUG_ATTRS, FLAG_DEBUG_T, FLAG_TIMING, FLAG_REUSE_COLLECT, FLAG_BLEND_WORK,
+                     REUSE_NPARAM)
 
 __all__ = ["GscError", "Renderer", "default_config", "exported_symbols", "lib", "to_camera",
-           "FLAG_DEBUG_ATTRS", "FLAG_DEBUG_T", "FLAG_TIMING", "FLAG_REUSE_COLLECT", "REUSE_NPARAM"]
+           "FLAG_DEBUG_ATTRS", "FLAG_DEBUG_T", "FLAG_TIMING", "FLAG_REUSE_COLLECT", "FLAG_BLEND_WORK",
+           "REUSE_NPARAM"]

@@ -398,7 +398,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   launch_ranges(fd, pk, ctx->ranges, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[6], s);
   launch_blend(fd, ctx->ranges, pv, ctx->rec, ctx->d_fin, ctx->total_tiles, ctx->cfg.tile_w * ctx->cfg.tile_h,
-               ctx->cfg.blocks_per_sm, ctx->n_sm, s);
+               ctx->cfg.blocks_per_sm, (ctx->cfg.flags & GSC_FLAG_BLEND_WORK) != 0, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[7], s);
 }
 
@@ -1462,6 +1462,18 @@ int gsc_debug_final_T(gsc_ctx* ctx, uint32_t v, float* T, uint64_t cap, uint64_t
   const uint64_t cnt = (uint64_t)ctx->cams[v].width * ctx->cams[v].height;
   *n = cnt;
   return dbg_copy(ctx, T, ctx->d_T[v], cnt, cap, 4);
+}
+
+int gsc_debug_blend_work(gsc_ctx* ctx, uint64_t* work) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (!(ctx->cfg.flags & GSC_FLAG_BLEND_WORK)) return fail(ctx, GSC_ERR_STATE, "context was created without GSC_FLAG_BLEND_WORK");
+  if (!work) return fail(ctx, GSC_ERR_INVALID_ARG, "null output");
+  unsigned long long w[2];
+  CK(cudaMemcpy(w, ctx->d_fd->blend_work, sizeof(w), cudaMemcpyDeviceToHost));
+  work[0] = w[0];
+  work[1] = w[1];
+  return GSC_OK;
 }
 
 int gsc_debug_set_spin_limit(gsc_ctx* ctx, uint32_t limit) {

@@ -40,6 +40,8 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
     fd->n_big = 0;
     fd->n_derived = 0;
     fd->err = 0;
+    fd->blend_work[0] = 0;
+    fd->blend_work[1] = 0;
   }
   fd->ctr[lane] = 0;
   fd->ctr[32 + lane] = 0;

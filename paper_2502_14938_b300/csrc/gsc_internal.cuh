@@ -109,6 +109,12 @@ struct FrameDev {  // device-resident per-frame plan and counters
   alignas(16) uint32_t hist_depth[4 * 256];
   alignas(16) uint32_t hist_tile[4 * 256];
   uint32_t err_sticky;          // error bits of all frames since the host last read them
+  // blend work of the frame, counted only by the counting blend variant:
+  // [0] (pixel, Gaussian) evaluations of the front-to-back walk (every
+  //     Gaussian of the tile's list up to and including the one a pixel
+  //     stops at), [1] pixel slots issued through the inner loop (4 per lane
+  //     for each Gaussian whose box meets the warp's band; one exp2 each)
+  unsigned long long blend_work[2];
 };
 
 struct ModelDev {
@@ -473,6 +479,7 @@ void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint3
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
-                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, int n_sm, cudaStream_t s);
+                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, bool count, int n_sm,
+                  cudaStream_t s);
 
 }  // namespace gsc

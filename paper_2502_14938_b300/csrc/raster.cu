@@ -227,9 +227,17 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 //   log2(1/255) (alpha < 1/255 is skipped: it then changes nothing);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
 //   C += c alpha T, T *= 1 - alpha;  out = C + T bg.
-// A warp skips a Gaussian whose opacity-aware box misses its band, and a
-// batch once all its pixels are finished; the block stops once all are.
-constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical)
+// A lane's 4 vertical pixels run as two pairs on the packed FP32x2 pipe
+// (FFMA2/FMUL2: one issue slot for two pixels); every packed op is the
+// round-to-nearest op of the scalar form element by element, so the image
+// is the one the scalar loop gives.  The staged coefficients are stored
+// twice ({a, a}) so they feed packed operands directly, and opacity and
+// colour are carried negated (-alpha, -c) so that T (1 - alpha) and
+// C + c alpha T stay single FMAs.  The staging thread also tests the
+// record's opacity-aware box against each warp's band of rows (a bit per
+// warp); a warp skips records whose bit is clear, and a batch once all its
+// pixels are finished; the block stops once all are.
+constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical): two packed pairs
 // 2^x by the hardware approximation (relative error ~2^-22; -inf -> 0).
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -241,21 +249,24 @@ constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
 
 struct BlendSmem {
-  float4 q0[BLEND_MAX_NT];   // F, D, E, A'
-  float4 q1[BLEND_MAX_NT];   // B', C', r, g
-  float4 bb[BLEND_MAX_NT];   // b, xmin, xmax, ymin
-  float ymax[BLEND_MAX_NT];
+  float4 fd[BLEND_MAX_NT];   // F, F, D, D
+  float4 ea[BLEND_MAX_NT];   // E, E, A', A'
+  float4 bc[BLEND_MAX_NT];   // B', B', C', C'
+  float4 rg[BLEND_MAX_NT];   // -r, -r, -g, -g
+  float4 bm[BLEND_MAX_NT];   // -b, -b, band mask (bits), unused
 };
 
-__device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, const FrameDev* __restrict__ fd,
+__device__ __forceinline__ float2 dup2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float half_of(float2 v, int i) { return i ? v.y : v.x; }
+
+template <bool COUNT>
+__device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, FrameDev* __restrict__ fd,
                                            const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                            const Records& rec, const FrameIn* __restrict__ fin) {
-  float4* s_q0 = sm.q0;
-  float4* s_q1 = sm.q1;
-  float4* s_bb = sm.bb;
-  float* s_ymax = sm.ymax;
+  static_assert(BLEND_PPL == 4, "the packed loop handles two pairs per lane");
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
   const int nt = (int)blockDim.x;  // TW * TH / BLEND_PPL
+  const int n_warps = nt >> 5;
   uint32_t cam = 0;
   while (cam + 1 < fd->n_cams && fd->cam[cam + 1].tile_base <= tile_key) ++cam;
   const CamDev& cd = fd->cam[cam];
@@ -270,21 +281,26 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
   const float X = ((float)px + 0.5f) - ox;
   const float Y0 = ((float)py0 + 0.5f) - oy;
   const float wx0 = ((float)(tx * TW) + 0.5f) - ox, wx1 = wx0 + (float)(TW - 1);
-  const float wy0 = ((float)(ty * TH + warp * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
   const uint2 rg = ranges[tile_key];
-  float T[BLEND_PPL], C0[BLEND_PPL], C1[BLEND_PPL], C2[BLEND_PPL], Yk[BLEND_PPL];
-  // kill[k]: 0 while pixel k blends, -inf once it has stopped (or lies
-  // outside the image): its power is then -inf, alpha 0, and T stays put
-  float kill[BLEND_PPL];
+  const float2 X2 = dup2(X, X);
+  const float2 Y2[2] = {dup2(Y0, Y0 + 1.f), dup2(Y0 + 2.f, Y0 + 3.f)};
+  float2 T2[2], C0[2], C1[2], C2[2];
+  // thr[k]: the power pixel k needs to take a Gaussian - log2(1/255) while it
+  // blends, +inf once it has stopped (or lies outside the image), so that
+  // every later alpha of that pixel is 0 and its T stays put
+  float thr[BLEND_PPL];
   unsigned live = 0;  // bit k: pixel k still blending (for the early exit of the whole tile)
+  uint32_t n_walk = 0, n_issued = 0;  // counting variant only
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    T2[j] = dup2(1.f, 1.f);
+    C0[j] = C1[j] = C2[j] = dup2(0.f, 0.f);
+  }
 #pragma unroll
   for (int k = 0; k < BLEND_PPL; ++k) {
-    T[k] = 1.f;
-    C0[k] = C1[k] = C2[k] = 0.f;
-    Yk[k] = Y0 + (float)k;
     const bool in = px < cd.W && py0 + k < cd.H;
     live |= (in ? 1u : 0u) << k;
-    kill[k] = in ? 0.f : -INFINITY;
+    thr[k] = in ? LOG2_MIN_ALPHA : INFINITY;
   }
   for (uint32_t b = rg.x; b < rg.y; b += (uint32_t)nt) {
     if (__syncthreads_count(live != 0) == 0) break;
@@ -297,40 +313,75 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
       const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
-      s_q0[threadIdx.x] = make_float4(__log2f(c.y) - LOG2E_HALF * q0, 2.f * LOG2E_HALF * (A * mxl + B * myl),
-                                      2.f * LOG2E_HALF * (B * mxl + Cc * myl), -LOG2E_HALF * A);
-      s_q1[threadIdx.x] = make_float4(-2.f * LOG2E_HALF * B, -LOG2E_HALF * Cc, cl.x, cl.y);
+      const float F = __log2f(c.y) - LOG2E_HALF * q0;
+      const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
+      const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
+      const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
+      sm.fd[threadIdx.x] = make_float4(F, F, D, D);
+      sm.ea[threadIdx.x] = make_float4(E, E, Ap, Ap);
+      sm.bc[threadIdx.x] = make_float4(Bp, Bp, Cp, Cp);
+      sm.rg[threadIdx.x] = make_float4(-cl.x, -cl.x, -cl.y, -cl.y);
       const float idet = 1.f / (A * Cc - B * B);
       const float ex = sqrtf(c.z * Cc * idet), ey = sqrtf(c.z * A * idet);
-      s_bb[threadIdx.x] = make_float4(cl.z, mxl - ex, mxl + ex, myl - ey);
-      s_ymax[threadIdx.x] = myl + ey;
+      const float xmin = mxl - ex, xmax = mxl + ex, ymin = myl - ey, ymax = myl + ey;
+      uint32_t mask = 0;
+      if (!(xmax < wx0 || xmin > wx1)) {
+        for (int w = 0; w < n_warps; ++w) {
+          const float wy0 = ((float)(ty * TH + w * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
+          mask |= (ymin > wy1 || ymax < wy0 ? 0u : 1u) << w;
+        }
+      }
+      sm.bm[threadIdx.x] = make_float4(-cl.z, -cl.z, __uint_as_float(mask), 0.f);
     }
     __syncthreads();
     const int cnt = min(nt, (int)(rg.y - b));
     if (!__any_sync(0xffffffffu, live != 0)) continue;
     for (int u = 0; u < cnt; ++u) {
-      const float4 bb = s_bb[u];
-      if (bb.z < wx0 || bb.y > wx1 || bb.w > wy1 || s_ymax[u] < wy0) continue;  // box misses the band
-      const float4 q0 = s_q0[u];
-      const float4 q1 = s_q1[u];
-      const float pa = fmaf(X, fmaf(q0.w, X, q0.y), q0.x);  // F + X (D + A' X)
-      const float pb = fmaf(q1.x, X, q0.z);                 // E + B' X
+      const float4 bm = sm.bm[u];
+      if (COUNT) n_walk += __popc(live);
+      if (!((__float_as_uint(bm.z) >> warp) & 1u)) continue;  // box misses the band
+      if (COUNT) n_issued += BLEND_PPL;
+      const float4 s0 = sm.fd[u], s1 = sm.ea[u], s2 = sm.bc[u], s3 = sm.rg[u];
+      const float2 pa = __ffma2_rn(X2, __ffma2_rn(dup2(s1.z, s1.w), X2, dup2(s0.z, s0.w)), dup2(s0.x, s0.y));
+      const float2 pb = __ffma2_rn(dup2(s2.x, s2.y), X2, dup2(s1.x, s1.y));  // E + B' X
+      const float2 cq = dup2(s2.z, s2.w);
+      float2 na[2], tt[2];
+      bool stop = false;
 #pragma unroll
-      for (int k = 0; k < BLEND_PPL; ++k) {
-        const float p = fmaf(Yk[k], fmaf(q1.y, Yk[k], pb), pa) + kill[k];
-        float alpha = fminf(0.99f, ex2_approx(p));
-        alpha = p >= LOG2_MIN_ALPHA ? alpha : 0.f;  // alpha < 1/255 contributes nothing
-        const float tt = fmaf(-T[k], alpha, T[k]);
-        if (tt < 1e-4f) {  // stop before this Gaussian
-          kill[k] = -INFINITY;
-          live &= ~(1u << k);
-          continue;
+      for (int j = 0; j < 2; ++j) {
+        const float2 p = __ffma2_rn(Y2[j], __ffma2_rn(cq, Y2[j], pb), pa);
+        float a0 = fmaxf(-0.99f, -ex2_approx(p.x));  // -alpha
+        float a1 = fmaxf(-0.99f, -ex2_approx(p.y));
+        a0 = p.x >= thr[2 * j] ? a0 : 0.f;            // alpha < 1/255 contributes nothing
+        a1 = p.y >= thr[2 * j + 1] ? a1 : 0.f;
+        na[j] = dup2(a0, a1);
+        tt[j] = __ffma2_rn(na[j], T2[j], T2[j]);      // T (1 - alpha)
+        stop |= (tt[j].x < 1e-4f) | (tt[j].y < 1e-4f);
+      }
+      if (stop) {  // a pixel stops before this Gaussian: it takes nothing from it, nor after
+#pragma unroll
+        for (int k = 0; k < BLEND_PPL; ++k) {
+          const int j = k >> 1;
+          if (half_of(tt[j], k & 1) < 1e-4f) {
+            thr[k] = INFINITY;
+            live &= ~(1u << k);
+            if (k & 1) {
+              na[j].y = 0.f;
+              tt[j].y = T2[j].y;
+            } else {
+              na[j].x = 0.f;
+              tt[j].x = T2[j].x;
+            }
+          }
         }
-        const float w = alpha * T[k];
-        C0[k] = fmaf(q1.z, w, C0[k]);
-        C1[k] = fmaf(q1.w, w, C1[k]);
-        C2[k] = fmaf(bb.x, w, C2[k]);
-        T[k] = tt;
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float2 nw = __fmul2_rn(na[j], T2[j]);  // -alpha T
+        C0[j] = __ffma2_rn(dup2(s3.x, s3.y), nw, C0[j]);
+        C1[j] = __ffma2_rn(dup2(s3.z, s3.w), nw, C1[j]);
+        C2[j] = __ffma2_rn(dup2(bm.x, bm.y), nw, C2[j]);
+        T2[j] = tt[j];
       }
     }
   }
@@ -341,9 +392,10 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
       const int py = py0 + k;
       if (px >= cd.W || py >= cd.H) continue;
       const size_t p = ((size_t)py * cd.W + px) * 3;
-      out[p + 0] = C0[k] + T[k] * fin->bg[0];
-      out[p + 1] = C1[k] + T[k] * fin->bg[1];
-      out[p + 2] = C2[k] + T[k] * fin->bg[2];
+      const float T = half_of(T2[k >> 1], k & 1);
+      out[p + 0] = half_of(C0[k >> 1], k & 1) + T * fin->bg[0];
+      out[p + 1] = half_of(C1[k >> 1], k & 1) + T * fin->bg[1];
+      out[p + 2] = half_of(C2[k >> 1], k & 1) + T * fin->bg[2];
     }
   } else {  // RGBA8: round-to-nearest-even of 255 x clamp(colour), alpha 1 - T
     uchar4* out = reinterpret_cast<uchar4*>(fin->out_rgb[cam]);
@@ -351,11 +403,12 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
     for (int k = 0; k < BLEND_PPL; ++k) {
       const int py = py0 + k;
       if (px >= cd.W || py >= cd.H) continue;
+      const float T = half_of(T2[k >> 1], k & 1);
       out[(size_t)py * cd.W + px] =
-          make_uchar4((unsigned char)__float2uint_rn(__saturatef(C0[k] + T[k] * fin->bg[0]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(C1[k] + T[k] * fin->bg[1]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(C2[k] + T[k] * fin->bg[2]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(1.f - T[k]) * 255.f));
+          make_uchar4((unsigned char)__float2uint_rn(__saturatef(half_of(C0[k >> 1], k & 1) + T * fin->bg[0]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(half_of(C1[k >> 1], k & 1) + T * fin->bg[1]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(half_of(C2[k >> 1], k & 1) + T * fin->bg[2]) * 255.f),
+                      (unsigned char)__float2uint_rn(__saturatef(1.f - T) * 255.f));
     }
   }
   float* outT = reinterpret_cast<float*>(fin->out_T[cam]);
@@ -363,23 +416,32 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, con
 #pragma unroll
     for (int k = 0; k < BLEND_PPL; ++k) {
       const int py = py0 + k;
-      if (px < cd.W && py < cd.H) outT[(size_t)py * cd.W + px] = T[k];
+      if (px < cd.W && py < cd.H) outT[(size_t)py * cd.W + px] = half_of(T2[k >> 1], k & 1);
+    }
+  }
+  if (COUNT) {
+    const uint32_t w = __reduce_add_sync(0xffffffffu, n_walk), i = __reduce_add_sync(0xffffffffu, n_issued);
+    if (lane == 0) {
+      atomicAdd(&fd->blend_work[0], (unsigned long long)w);
+      atomicAdd(&fd->blend_work[1], (unsigned long long)i);
     }
   }
 }
 
 // One block per tile of every camera.
+template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
   if (blockIdx.x == 0 && threadIdx.x == 0 && fin->keep_err && fd->err) atomicOr(&fd->err_sticky, fd->err);
-  blend_tile(blockIdx.x, sm, fd, ranges, vals, rec, fin);
+  blend_tile<COUNT>(blockIdx.x, sm, fd, ranges, vals, rec, fin);
 }
 
 // Persistent form: a fixed grid (blocks per SM x SMs) whose blocks take the
 // tiles of all cameras - of every viewer in a batched frame - from one
 // counter, so long and short tiles balance across the machine.
+template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend_persistent(FrameDev* __restrict__ fd,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ vals, Records rec,
@@ -394,16 +456,25 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend_persistent(FrameDev* __r
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= total) break;
-    blend_tile(tile, sm, fd, ranges, vals, rec, fin);
+    blend_tile<COUNT>(tile, sm, fd, ranges, vals, rec, fin);
   }
 }
 
 void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Records rec, const FrameIn* fin,
-                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, int n_sm, cudaStream_t s) {
-  if (blocks_per_sm == 0)
-    k_blend<<<total_tiles, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
-  else
-    k_blend_persistent<<<n_sm * blocks_per_sm, tile_threads / BLEND_PPL, 0, s>>>(fd, ranges, vals, rec, fin);
+                  uint32_t total_tiles, uint32_t tile_threads, uint32_t blocks_per_sm, bool count, int n_sm,
+                  cudaStream_t s) {
+  const uint32_t nt = tile_threads / BLEND_PPL, grid = n_sm * blocks_per_sm;
+  if (blocks_per_sm == 0) {
+    if (count)
+      k_blend<true><<<total_tiles, nt, 0, s>>>(fd, ranges, vals, rec, fin);
+    else
+      k_blend<false><<<total_tiles, nt, 0, s>>>(fd, ranges, vals, rec, fin);
+  } else {
+    if (count)
+      k_blend_persistent<true><<<grid, nt, 0, s>>>(fd, ranges, vals, rec, fin);
+    else
+      k_blend_persistent<false><<<grid, nt, 0, s>>>(fd, ranges, vals, rec, fin);
+  }
 }
 
 }  // namespace gsc

@@ -29,6 +29,7 @@ FLAG_DEBUG_ATTRS = 0x1
 FLAG_DEBUG_T = 0x2
 FLAG_TIMING = 0x4
 FLAG_REUSE_COLLECT = 0x8
+FLAG_BLEND_WORK = 0x10
 REUSE_NPARAM = 2433
 
 
@@ -103,6 +104,7 @@ def lib():
             "gsc_debug_depth_order": (I, [P, P, U64, P]),
             "gsc_debug_ranges": (I, [P, P, U64, P]),
             "gsc_debug_final_T": (I, [P, U32, P, U64, P]),
+            "gsc_debug_blend_work": (I, [P, P]),
             "gsc_debug_set_spin_limit": (I, [P, U32]),
             "gsc_debug_sort_pairs": (I, [P, P, P, U64, U32]),
             "gsc_debug_scan": (I, [P, P, U64, P]),
@@ -406,6 +408,14 @@ class Renderer:
         T = np.zeros(max(n.value, 1), np.float32)
         self._check(lib().gsc_debug_final_T(self.ctx, v, _p(T), n.value, C.byref(n)))
         return T[: n.value]
+
+    def debug_blend_work(self) -> tuple:
+        """(walk, issued) pixel evaluations of the last frame's blend (needs FLAG_BLEND_WORK):
+        walk = the front-to-back walk of every pixel up to its stop; issued = pixel
+        slots run through the inner loop after the warp-band box test."""
+        w = np.zeros(2, np.uint64)
+        self._check(lib().gsc_debug_blend_work(self.ctx, _p(w)))
+        return int(w[0]), int(w[1])
 
     def debug_cache(self, d: int):
         """(line status per visible anchor, state dict) of derivation view d's cache."""

@@ -409,3 +409,38 @@ def test_e4m3_rounding_closed_forms():
              2.0 ** -6 * 1.0625: 2.0 ** -6, 0.01: 0.009765625}
     for x, want in cases.items():
         assert oracle.round_e4m3(x) == want, (x, oracle.round_e4m3(x), want)
+
+
+# ---------------------------------------------------------------- walk length
+def stacked_records(n, opacity, mx, my, sigma=2.0):
+    """n identical isotropic Gaussians at (mx, my), depths 1..n (front to back)."""
+    rec = np.zeros((n, 16))
+    A = 1.0 / sigma ** 2
+    tau = 2 * np.log(255 * opacity)
+    for i in range(n):
+        rec[i, :12] = [1, mx, my, A, 0, A, opacity, 0.5, 0.5, 0.5, 1.0 + i, tau]
+    return rec, np.arange(1, n + 1, dtype=np.float32), np.arange(n, dtype=np.int64)
+
+
+def test_walk_length_closed_form():
+    """At the common centre alpha = o exactly: T after k Gaussians is (1-o)^k,
+    so with o = 0.95 the 4th Gaussian would bring T to 6.25e-6 < 1e-4 and the
+    pixel stops there (walk 4, 3 contributors); with o = 0.5 T = 2^-k stays
+    above 1e-4 up to k = 13 and the pixel stops at the 14th; a pixel of a tile
+    the Gaussians do not cover walks nothing; far from the centre (alpha <
+    1/255 for all) a pixel of a covered tile walks the whole list."""
+    W, H = 64, 32
+    for o, want_walk, want_nc in [(0.95, 4, 3), (0.5, 14, 13)]:
+        rec, d32, gid = stacked_records(20, o, 8.5, 8.5)
+        px = np.array([8, 60, 15])
+        py = np.array([8, 30, 0])
+        rgb, T, mg, nc, wk = oracle.render(rec, d32, gid, W, H, True, px, py, walk=True)
+        assert wk[0] == want_walk and nc[0] == want_nc
+        assert np.isclose(T[0], (1 - o) ** want_nc)
+        assert wk[1] == 0 and nc[1] == 0 and T[1] == 1.0   # tile (3, 1): not covered
+        a15 = o * np.exp(-0.5 * (6.5 ** 2 + 8.0 ** 2) / 4.0)  # pixel (15, 0), same tile as the centre
+        assert a15 < 1 / 255 and wk[2] == 20 and nc[2] == 0
+    # brute-force form (one list for every pixel) walks the same way at the centre
+    rec, d32, gid = stacked_records(20, 0.95, 8.5, 8.5)
+    _, _, _, _, wk = oracle.render(rec, d32, gid, W, H, False, np.array([8, 60]), np.array([8, 30]), walk=True)
+    assert wk[0] == 4 and wk[1] == 20
