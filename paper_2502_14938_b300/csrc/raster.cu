@@ -217,26 +217,25 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 // ------------------------------------------------------------------ blend (K10)
 // One block per (camera, tile); each lane owns a vertical strip of 4 pixels
 // (lanes of a warp cover the tile's columns, so a warp owns a band of rows).
-// The tile's records are staged into shared memory one batch at a time,
-// each turned into the tile-local quadratic of its power in the exp2 domain,
+// Each warp of a tile's block owns a band of the tile's rows and walks the
+// tile's record list on its own, 32 records at a time: lane l loads record
+// l of the chunk, tests its opacity-aware box against the warp's band, and
+// for a hit stages the tile-local quadratic of its power in the exp2 domain,
 //   log2(o) - (log2 e / 2) q(D) = [F + X (D + A' X)] + Y [(E + B' X) + C' Y],
-// with (X, Y) the pixel centre relative to the tile centre: the bracket in X
-// is per lane, so a pixel costs 2 FMA.  Each pixel walks the batch front to
-// back:
+// with (X, Y) the pixel centre relative to the tile centre (the bracket in
+// X is per lane, so a pixel costs 2 FMA).  The ballot of hits is the
+// chunk's work list: the warp visits only those records, in list order.
+// Each pixel walks them front to back:
 //   alpha = min(0.99, 2^power), taken as 0 when the power is below
 //   log2(1/255) (alpha < 1/255 is skipped: it then changes nothing);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
-//   C += c alpha T, T *= 1 - alpha;  out = C + T bg.
+//   C += c w, T -= w with w = alpha T;  out = C + T bg.
 // A lane's 4 vertical pixels run as two pairs on the packed FP32x2 pipe
-// (FFMA2/FMUL2: one issue slot for two pixels); every packed op is the
-// round-to-nearest op of the scalar form element by element, so the image
-// is the one the scalar loop gives.  The staged coefficients are stored
-// twice ({a, a}) so they feed packed operands directly, and opacity and
-// colour are carried negated (-alpha, -c) so that T (1 - alpha) and
-// C + c alpha T stay single FMAs.  The staging thread also tests the
-// record's opacity-aware box against each warp's band of rows (a bit per
-// warp); a warp skips records whose bit is clear, and a batch once all its
-// pixels are finished; the block stops once all are.
+// (FFMA2/FMUL2: one issue slot for two pixels); staged coefficients are
+// stored twice ({a, a}) so they feed packed operands directly.  The clamp
+// to 0.99 is only applied for records whose opacity can reach it (a warp-
+// uniform branch; below opacity 0.985 the approximated 2^power stays under
+// 0.99).  A warp stops once all its pixels have; no block-wide barrier.
 constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical): two packed pairs
 // 2^x by the hardware approximation (relative error ~2^-22; -inf -> 0).
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -244,20 +243,93 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {  // a - b, round to nearest, per element
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 constexpr int BLEND_MAX_NT = 256;
+constexpr int BLEND_MAX_WARPS = BLEND_MAX_NT / 32;
 constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
+constexpr float CLAMP_OPACITY = 0.985f;                  // records at or above it take the 0.99 clamp
 
-struct BlendSmem {
-  float4 fd[BLEND_MAX_NT];   // F, F, D, D
-  float4 ea[BLEND_MAX_NT];   // E, E, A', A'
-  float4 bc[BLEND_MAX_NT];   // B', B', C', C'
-  float4 rg[BLEND_MAX_NT];   // -r, -r, -g, -g
-  float4 bm[BLEND_MAX_NT];   // -b, -b, band mask (bits), unused
+struct BlendSmem {  // per warp, one slot per lane of the current chunk
+  float4 fd[BLEND_MAX_WARPS][32];   // F, F, D, D
+  float4 ea[BLEND_MAX_WARPS][32];   // E, E, A', A'
+  float4 bc[BLEND_MAX_WARPS][32];   // B', B', C', C'
+  float4 rg[BLEND_MAX_WARPS][32];   // r, r, g, g
+  float2 bl[BLEND_MAX_WARPS][32];   // b, b
 };
 
 __device__ __forceinline__ float2 dup2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float half_of(float2 v, int i) { return i ? v.y : v.x; }
+
+struct PixState {
+  float2 T2[2], C0[2], C1[2], C2[2];
+  float thr[BLEND_PPL];  // log2(1/255) while pixel k blends, +inf once it has stopped (or is off-image)
+  unsigned live;         // bit k: pixel k still blending
+};
+
+// One staged record through the lane's 4 pixels.  Returns the chunk-relative
+// stop mask (bit k: pixel k stopped at this record).
+template <bool CLAMP>
+__device__ __forceinline__ unsigned blend_record(PixState& ps, const BlendSmem& sm, int warp, int u, float2 X2,
+                                                 const float2 (&Y2)[2]) {
+  const float4 s0 = sm.fd[warp][u], s1 = sm.ea[warp][u], s2 = sm.bc[warp][u], s3 = sm.rg[warp][u];
+  const float2 s4 = sm.bl[warp][u];
+  const float2 pa = __ffma2_rn(X2, __ffma2_rn(dup2(s1.z, s1.w), X2, dup2(s0.z, s0.w)), dup2(s0.x, s0.y));
+  const float2 pb = __ffma2_rn(dup2(s2.x, s2.y), X2, dup2(s1.x, s1.y));  // E + B' X
+  const float2 cq = dup2(s2.z, s2.w);
+  float2 w[2], tt[2];
+  bool stop = false;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float2 p = __ffma2_rn(Y2[j], __ffma2_rn(cq, Y2[j], pb), pa);
+    float a0 = p.x >= ps.thr[2 * j] ? ex2_approx(p.x) : 0.f;  // alpha < 1/255 contributes nothing
+    float a1 = p.y >= ps.thr[2 * j + 1] ? ex2_approx(p.y) : 0.f;
+    if (CLAMP) {
+      a0 = fminf(0.99f, a0);
+      a1 = fminf(0.99f, a1);
+    }
+    w[j] = __fmul2_rn(dup2(a0, a1), ps.T2[j]);  // alpha T
+    tt[j] = fsub2(ps.T2[j], w[j]);              // T (1 - alpha)
+    stop |= (tt[j].x < 1e-4f) | (tt[j].y < 1e-4f);
+  }
+  unsigned stopped = 0;
+  if (stop) {  // a pixel stops before this Gaussian: it takes nothing from it, nor after
+#pragma unroll
+    for (int k = 0; k < BLEND_PPL; ++k) {
+      const int j = k >> 1;
+      if (half_of(tt[j], k & 1) < 1e-4f) {
+        ps.thr[k] = INFINITY;
+        ps.live &= ~(1u << k);
+        stopped |= 1u << k;
+        if (k & 1) {
+          w[j].y = 0.f;
+          tt[j].y = ps.T2[j].y;
+        } else {
+          w[j].x = 0.f;
+          tt[j].x = ps.T2[j].x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    ps.C0[j] = __ffma2_rn(dup2(s3.x, s3.y), w[j], ps.C0[j]);
+    ps.C1[j] = __ffma2_rn(dup2(s3.z, s3.w), w[j], ps.C1[j]);
+    ps.C2[j] = __ffma2_rn(s4, w[j], ps.C2[j]);
+    ps.T2[j] = tt[j];
+  }
+  return stopped;
+}
 
 template <bool COUNT>
 __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, FrameDev* __restrict__ fd,
@@ -265,8 +337,6 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
                                            const Records& rec, const FrameIn* __restrict__ fin) {
   static_assert(BLEND_PPL == 4, "the packed loop handles two pairs per lane");
   const int TW = (int)fd->tile_w, TH = (int)fd->tile_h;
-  const int nt = (int)blockDim.x;  // TW * TH / BLEND_PPL
-  const int n_warps = nt >> 5;
   uint32_t cam = 0;
   while (cam + 1 < fd->n_cams && fd->cam[cam + 1].tile_base <= tile_key) ++cam;
   const CamDev& cd = fd->cam[cam];
@@ -281,109 +351,68 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
   const float X = ((float)px + 0.5f) - ox;
   const float Y0 = ((float)py0 + 0.5f) - oy;
   const float wx0 = ((float)(tx * TW) + 0.5f) - ox, wx1 = wx0 + (float)(TW - 1);
+  const float wy0 = ((float)(ty * TH + warp * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
   const uint2 rg = ranges[tile_key];
   const float2 X2 = dup2(X, X);
   const float2 Y2[2] = {dup2(Y0, Y0 + 1.f), dup2(Y0 + 2.f, Y0 + 3.f)};
-  float2 T2[2], C0[2], C1[2], C2[2];
-  // thr[k]: the power pixel k needs to take a Gaussian - log2(1/255) while it
-  // blends, +inf once it has stopped (or lies outside the image), so that
-  // every later alpha of that pixel is 0 and its T stays put
-  float thr[BLEND_PPL];
-  unsigned live = 0;  // bit k: pixel k still blending (for the early exit of the whole tile)
-  uint32_t n_walk = 0, n_issued = 0;  // counting variant only
+  PixState ps;
+  ps.live = 0;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    T2[j] = dup2(1.f, 1.f);
-    C0[j] = C1[j] = C2[j] = dup2(0.f, 0.f);
+    ps.T2[j] = dup2(1.f, 1.f);
+    ps.C0[j] = ps.C1[j] = ps.C2[j] = dup2(0.f, 0.f);
   }
 #pragma unroll
   for (int k = 0; k < BLEND_PPL; ++k) {
     const bool in = px < cd.W && py0 + k < cd.H;
-    live |= (in ? 1u : 0u) << k;
-    thr[k] = in ? LOG2_MIN_ALPHA : INFINITY;
+    ps.live |= (in ? 1u : 0u) << k;
+    ps.thr[k] = in ? LOG2_MIN_ALPHA : INFINITY;
   }
-  for (uint32_t b = rg.x; b < rg.y; b += (uint32_t)nt) {
-    if (__syncthreads_count(live != 0) == 0) break;
-    const uint32_t idx = b + threadIdx.x;
+  uint32_t n_walk = 0, n_issued = 0;  // counting variant only
+  for (uint32_t b = rg.x; b < rg.y; b += 32u) {
+    if (!__any_sync(0xffffffffu, ps.live != 0)) break;  // every pixel of the warp has stopped
+    const uint32_t idx = b + (uint32_t)lane;
+    bool hit = false, clamp = false;
     if (idx < rg.y) {
       const uint32_t r = vals[idx];
       const float4 g = rec.geo[r];   // mean x, mean y, A, B
       const float4 c = rec.cop[r];   // C, opacity, tau, depth
-      const float4 cl = rec.col[r];
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
-      const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
-      const float F = __log2f(c.y) - LOG2E_HALF * q0;
-      const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
-      const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
-      const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
-      sm.fd[threadIdx.x] = make_float4(F, F, D, D);
-      sm.ea[threadIdx.x] = make_float4(E, E, Ap, Ap);
-      sm.bc[threadIdx.x] = make_float4(Bp, Bp, Cp, Cp);
-      sm.rg[threadIdx.x] = make_float4(-cl.x, -cl.x, -cl.y, -cl.y);
       const float idet = 1.f / (A * Cc - B * B);
       const float ex = sqrtf(c.z * Cc * idet), ey = sqrtf(c.z * A * idet);
-      const float xmin = mxl - ex, xmax = mxl + ex, ymin = myl - ey, ymax = myl + ey;
-      uint32_t mask = 0;
-      if (!(xmax < wx0 || xmin > wx1)) {
-        for (int w = 0; w < n_warps; ++w) {
-          const float wy0 = ((float)(ty * TH + w * band) + 0.5f) - oy, wy1 = wy0 + (float)(band - 1);
-          mask |= (ymin > wy1 || ymax < wy0 ? 0u : 1u) << w;
-        }
-      }
-      sm.bm[threadIdx.x] = make_float4(-cl.z, -cl.z, __uint_as_float(mask), 0.f);
-    }
-    __syncthreads();
-    const int cnt = min(nt, (int)(rg.y - b));
-    if (!__any_sync(0xffffffffu, live != 0)) continue;
-    for (int u = 0; u < cnt; ++u) {
-      const float4 bm = sm.bm[u];
-      if (COUNT) n_walk += __popc(live);
-      if (!((__float_as_uint(bm.z) >> warp) & 1u)) continue;  // box misses the band
-      if (COUNT) n_issued += BLEND_PPL;
-      const float4 s0 = sm.fd[u], s1 = sm.ea[u], s2 = sm.bc[u], s3 = sm.rg[u];
-      const float2 pa = __ffma2_rn(X2, __ffma2_rn(dup2(s1.z, s1.w), X2, dup2(s0.z, s0.w)), dup2(s0.x, s0.y));
-      const float2 pb = __ffma2_rn(dup2(s2.x, s2.y), X2, dup2(s1.x, s1.y));  // E + B' X
-      const float2 cq = dup2(s2.z, s2.w);
-      float2 na[2], tt[2];
-      bool stop = false;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const float2 p = __ffma2_rn(Y2[j], __ffma2_rn(cq, Y2[j], pb), pa);
-        float a0 = fmaxf(-0.99f, -ex2_approx(p.x));  // -alpha
-        float a1 = fmaxf(-0.99f, -ex2_approx(p.y));
-        a0 = p.x >= thr[2 * j] ? a0 : 0.f;            // alpha < 1/255 contributes nothing
-        a1 = p.y >= thr[2 * j + 1] ? a1 : 0.f;
-        na[j] = dup2(a0, a1);
-        tt[j] = __ffma2_rn(na[j], T2[j], T2[j]);      // T (1 - alpha)
-        stop |= (tt[j].x < 1e-4f) | (tt[j].y < 1e-4f);
-      }
-      if (stop) {  // a pixel stops before this Gaussian: it takes nothing from it, nor after
-#pragma unroll
-        for (int k = 0; k < BLEND_PPL; ++k) {
-          const int j = k >> 1;
-          if (half_of(tt[j], k & 1) < 1e-4f) {
-            thr[k] = INFINITY;
-            live &= ~(1u << k);
-            if (k & 1) {
-              na[j].y = 0.f;
-              tt[j].y = T2[j].y;
-            } else {
-              na[j].x = 0.f;
-              tt[j].x = T2[j].x;
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const float2 nw = __fmul2_rn(na[j], T2[j]);  // -alpha T
-        C0[j] = __ffma2_rn(dup2(s3.x, s3.y), nw, C0[j]);
-        C1[j] = __ffma2_rn(dup2(s3.z, s3.w), nw, C1[j]);
-        C2[j] = __ffma2_rn(dup2(bm.x, bm.y), nw, C2[j]);
-        T2[j] = tt[j];
+      hit = !(mxl + ex < wx0 || mxl - ex > wx1 || myl + ey < wy0 || myl - ey > wy1);  // box meets the band
+      if (hit) {
+        const float4 cl = rec.col[r];
+        const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
+        const float F = __log2f(c.y) - LOG2E_HALF * q0;
+        const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
+        const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
+        const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
+        sm.fd[warp][lane] = make_float4(F, F, D, D);
+        sm.ea[warp][lane] = make_float4(E, E, Ap, Ap);
+        sm.bc[warp][lane] = make_float4(Bp, Bp, Cp, Cp);
+        sm.rg[warp][lane] = make_float4(cl.x, cl.x, cl.y, cl.y);
+        sm.bl[warp][lane] = make_float2(cl.z, cl.z);
+        clamp = c.y >= CLAMP_OPACITY;
       }
     }
+    unsigned todo = __ballot_sync(0xffffffffu, hit);
+    const unsigned cmask = __ballot_sync(0xffffffffu, clamp);
+    __syncwarp();
+    const uint32_t cnt = min(32u, rg.y - b);
+    if (COUNT) {
+      n_walk += (uint32_t)__popc(ps.live) * cnt;
+      n_issued += (uint32_t)__popc(todo) * BLEND_PPL;
+    }
+    while (todo) {
+      const int u = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const unsigned st = ((cmask >> u) & 1u) ? blend_record<true>(ps, sm, warp, u, X2, Y2)
+                                              : blend_record<false>(ps, sm, warp, u, X2, Y2);
+      if (COUNT && st) n_walk -= (uint32_t)__popc(st) * (cnt - 1u - (uint32_t)u);
+    }
+    __syncwarp();  // the slots are rewritten by the next chunk
   }
   if (fin->out_format == 0) {
     float* out = reinterpret_cast<float*>(fin->out_rgb[cam]);
@@ -392,10 +421,10 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
       const int py = py0 + k;
       if (px >= cd.W || py >= cd.H) continue;
       const size_t p = ((size_t)py * cd.W + px) * 3;
-      const float T = half_of(T2[k >> 1], k & 1);
-      out[p + 0] = half_of(C0[k >> 1], k & 1) + T * fin->bg[0];
-      out[p + 1] = half_of(C1[k >> 1], k & 1) + T * fin->bg[1];
-      out[p + 2] = half_of(C2[k >> 1], k & 1) + T * fin->bg[2];
+      const float T = half_of(ps.T2[k >> 1], k & 1);
+      out[p + 0] = half_of(ps.C0[k >> 1], k & 1) + T * fin->bg[0];
+      out[p + 1] = half_of(ps.C1[k >> 1], k & 1) + T * fin->bg[1];
+      out[p + 2] = half_of(ps.C2[k >> 1], k & 1) + T * fin->bg[2];
     }
   } else {  // RGBA8: round-to-nearest-even of 255 x clamp(colour), alpha 1 - T
     uchar4* out = reinterpret_cast<uchar4*>(fin->out_rgb[cam]);
@@ -403,12 +432,12 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
     for (int k = 0; k < BLEND_PPL; ++k) {
       const int py = py0 + k;
       if (px >= cd.W || py >= cd.H) continue;
-      const float T = half_of(T2[k >> 1], k & 1);
-      out[(size_t)py * cd.W + px] =
-          make_uchar4((unsigned char)__float2uint_rn(__saturatef(half_of(C0[k >> 1], k & 1) + T * fin->bg[0]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(half_of(C1[k >> 1], k & 1) + T * fin->bg[1]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(half_of(C2[k >> 1], k & 1) + T * fin->bg[2]) * 255.f),
-                      (unsigned char)__float2uint_rn(__saturatef(1.f - T) * 255.f));
+      const float T = half_of(ps.T2[k >> 1], k & 1);
+      out[(size_t)py * cd.W + px] = make_uchar4(
+          (unsigned char)__float2uint_rn(__saturatef(half_of(ps.C0[k >> 1], k & 1) + T * fin->bg[0]) * 255.f),
+          (unsigned char)__float2uint_rn(__saturatef(half_of(ps.C1[k >> 1], k & 1) + T * fin->bg[1]) * 255.f),
+          (unsigned char)__float2uint_rn(__saturatef(half_of(ps.C2[k >> 1], k & 1) + T * fin->bg[2]) * 255.f),
+          (unsigned char)__float2uint_rn(__saturatef(1.f - T) * 255.f));
     }
   }
   float* outT = reinterpret_cast<float*>(fin->out_T[cam]);
@@ -416,7 +445,7 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
 #pragma unroll
     for (int k = 0; k < BLEND_PPL; ++k) {
       const int py = py0 + k;
-      if (px < cd.W && py < cd.H) outT[(size_t)py * cd.W + px] = half_of(T2[k >> 1], k & 1);
+      if (px < cd.W && py < cd.H) outT[(size_t)py * cd.W + px] = half_of(ps.T2[k >> 1], k & 1);
     }
   }
   if (COUNT) {
@@ -430,7 +459,7 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
 
 // One block per tile of every camera.
 template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend(FrameDev* __restrict__ fd, const uint2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
@@ -442,7 +471,7 @@ __global__ void __launch_bounds__(BLEND_MAX_NT) k_blend(FrameDev* __restrict__ f
 // tiles of all cameras - of every viewer in a batched frame - from one
 // counter, so long and short tiles balance across the machine.
 template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_MAX_NT) k_blend_persistent(FrameDev* __restrict__ fd,
+__global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend_persistent(FrameDev* __restrict__ fd,
                                                                    const uint2* __restrict__ ranges,
                                                                    const uint32_t* __restrict__ vals, Records rec,
                                                                    const FrameIn* __restrict__ fin) {
