@@ -178,11 +178,10 @@ FORMS = {
 }
 HEADLINE = "cached_bf16_unified"
 FP32_LANE_OPS = 148 * 128 * 2.032e9  # SMs x FP32 lanes x max SM clock: FP32 lane operations / s
-SFU_EXP2 = 148 * 16 * 2.032e9        # SMs x exp2 results per clock (SFU) x max SM clock
-# FP32-pipe lane operations of one evaluation besides its exp2: quadratic 2 FMA,
-# T update FMA, weight MUL, 3 colour FMA, and the per-lane prefix (3 FMA per
-# 4 pixels); the compare / min / select ops run on the ALU pipe
-FP32_OPS_PER_EVAL = 7.75
+# Algorithmic work of one (pixel, Gaussian) evaluation of the blend: ~20 FP32
+# operations (offset, quadratic form, opacity product and clamp, the two
+# thresholds, T update, colour accumulation) and one exponential
+OPS_PER_EVAL = 20
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
 # reported as the roofline's traffic only when the timed run uses that tiling.
@@ -316,21 +315,27 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
     dur = stage_ms[dom] / 1e3
     feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
     if dom == "blend":
-        # unit: one (pixel, Gaussian) evaluation, counted in the kernel (the
-        # counting variant on the same frames): every evaluation the blend
-        # issues takes one exp2 on the SFU, whose rate bounds the kernel
-        ev, walk = st["blend_issued"], st["blend_walk"]
-        ach = ev / dur / 1e9
-        peak = SFU_EXP2 / 1e9
+        # unit: one (pixel, Gaussian) evaluation of the front-to-back walk
+        # (every Gaussian of the pixel's tile list up to the one it stops at),
+        # counted in the kernel by its counting variant on the same frames;
+        # 20 FP32 ops + 1 exp2 each.  The kernel issues fewer (a warp skips
+        # records whose box misses its rows): issued_evals_per_launch.
+        import paper_2502_14938_b300 as pkg
+        walk, ev = st["blend_walk"], st["blend_issued"]
+        ach = walk * OPS_PER_EVAL / dur / 1e12
+        peak = FP32_LANE_OPS / 1e12
+        rates = pkg.native.pipe_rates()
         cap = NCU_TRAFFIC["k_blend"]
         same = cap["bytes"] is not None and \
             tuple(cap["tiling"]) == (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
-        return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Geval/s",
-                "frac": ach / peak, "peak_src": "148 SMs x 16 exp2/clk (SFU) x 2.032 GHz; one exp2 per evaluation",
+        return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32-op/s",
+                "frac": ach / peak,
+                "peak_src": "nominal: 148 SMs x 128 FP32 lanes x 2.032 GHz; work = 20 FP32 ops per evaluation",
                 "traffic": cap["bytes"] if same else None,
                 "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {cap['tiling']}" if same else None,
-                "evals_per_launch": ev, "walk_evals_per_launch": walk, "walk_geval_s": walk / dur / 1e9,
-                "fp32_pipe_frac": ev * FP32_OPS_PER_EVAL / dur / FP32_LANE_OPS, "ms_per_launch": stage_ms[dom],
+                "evals_per_launch": walk, "issued_evals_per_launch": ev, "evals_per_s": walk / dur,
+                "exp2_frac_of_measured": walk / dur / rates["exp2_per_s"],
+                "measured_rates": rates, "ms_per_launch": stage_ms[dom],
                 "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
     if dom == "sort_tile":
         b = P * 4 + 2 * P * 16

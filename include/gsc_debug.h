@@ -103,6 +103,14 @@ GSC_API int gsc_debug_reuse_grad(gsc_ctx* ctx, const float* z, const uint8_t* la
  * (each one exp2, whether or not its pixel still blends).  Synchronises. */
 GSC_API int gsc_debug_blend_work(gsc_ctx* ctx, uint64_t* work);
 
+/* Measured throughput of the current device's arithmetic units (host
+ * rates[3], per second): [0] exp2 results (ex2.approx, the special function
+ * unit), [1] FP32 FMA lane operations (scalar), [2] FP32 FMA lane operations
+ * of the packed FP32x2 form (two per instruction).  Runs three short probe
+ * kernels (a few ms) on a stream of its own; allocates and frees a small
+ * buffer.  Returns GSC_ERR_CUDA / GSC_ERR_OOM on failure. */
+GSC_API int gsc_debug_pipe_rates(double* rates);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,7 @@ def lib():
             "gsc_debug_ranges": (I, [P, P, U64, P]),
             "gsc_debug_final_T": (I, [P, U32, P, U64, P]),
             "gsc_debug_blend_work": (I, [P, P]),
+            "gsc_debug_pipe_rates": (I, [P]),
             "gsc_debug_set_spin_limit": (I, [P, U32]),
             "gsc_debug_sort_pairs": (I, [P, P, P, U64, U32]),
             "gsc_debug_scan": (I, [P, P, U64, P]),
@@ -158,6 +159,16 @@ def scan_u32_noalloc(d_in: int, d_out: int, n: int, d_total: int = 0, stream: in
                                     C.c_void_p(d_total or None), C.c_void_p(stream or None))
     if rc != GSC_OK:
         raise GscError(rc, "gsc_scan_u32_noalloc failed")
+
+
+def pipe_rates() -> dict:
+    """Measured unit throughputs of the current device (per second): exp2
+    results, scalar FP32 FMA lane ops, packed FP32x2 FMA lane ops."""
+    r = np.zeros(3, np.float64)
+    code = lib().gsc_debug_pipe_rates(_p(r))
+    if code:
+        raise GscError(code, "gsc_debug_pipe_rates failed")
+    return {"exp2_per_s": float(r[0]), "ffma_lane_ops_per_s": float(r[1]), "ffma2_lane_ops_per_s": float(r[2])}
 
 
 def default_config() -> Config:

@@ -109,3 +109,16 @@ def test_walk_brackets_the_oracle_stops(tiling):
     hi = int(per_pix.sum())
     assert lo <= walk <= hi
     assert hi - walk > 0  # the stopped pixels walked less than their lists
+
+
+def test_pipe_rates_are_plausible():
+    """The unit-throughput probe returns rates within the device's reach:
+    below SMs x clock x (32 exp2 | 128 FMA lanes) and not absurdly low."""
+    import paper_2502_14938_b300 as pkg
+    r = pkg.native.pipe_rates()
+    p = torch.cuda.get_device_properties(0)
+    clk = 2.2e9  # above any B300 SM clock
+    n = p.multi_processor_count
+    assert 0.1 * n * 16 * 1e9 < r["exp2_per_s"] <= n * 32 * clk
+    assert 0.1 * n * 128 * 1e9 < r["ffma_lane_ops_per_s"] <= n * 128 * clk
+    assert 0.1 * n * 128 * 1e9 < r["ffma2_lane_ops_per_s"] <= n * 128 * clk
