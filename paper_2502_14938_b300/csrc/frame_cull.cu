@@ -155,17 +155,30 @@ __global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ m
     const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
     float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
     int lv[CULL_IPT];
+    static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
+    if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
+      const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
+      const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
+      const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
+      const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
+      x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+      y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
+      z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
 #pragma unroll
-    for (int i = 0; i < CULL_IPT; ++i) {
-      const uint32_t a = a0 + i;
-      if (a < n) {
-        x[i] = __ldg(md.px + a);
-        y[i] = __ldg(md.py + a);
-        z[i] = __ldg(md.pz + a);
-        lv[i] = md.level[a];
-      } else {
-        x[i] = y[i] = z[i] = 0.f;
-        lv[i] = -1;
+      for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
+    } else {
+#pragma unroll
+      for (int i = 0; i < CULL_IPT; ++i) {
+        const uint32_t a = a0 + i;
+        if (a < n) {
+          x[i] = __ldg(md.px + a);
+          y[i] = __ldg(md.py + a);
+          z[i] = __ldg(md.pz + a);
+          lv[i] = md.level[a];
+        } else {
+          x[i] = y[i] = z[i] = 0.f;
+          lv[i] = -1;
+        }
       }
     }
     for (int g0 = 0; g0 < nd; g0 += CULL_GROUP) {  // views g0 .. g0 + 7 of this model
