@@ -185,7 +185,7 @@ OPS_PER_EVAL = 20
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
 # reported as the roofline's traffic only when the timed run uses that tiling.
-NCU_TRAFFIC = {"k_blend": {"bytes": 15.700e6 + 2.030e6, "tiling": (16, 32, 0), "frame": 151}}
+NCU_TRAFFIC = {"k_blend": {"bytes": 13.502e6 + 2.388e6, "tiling": (16, 32, 0), "frame": 151}}
 
 
 def make_renderer(model, form, flags=0, use_graph=True):
