@@ -13,7 +13,7 @@ namespace gsc {
 
 constexpr int PJ_NT = 256;
 
-__global__ void __launch_bounds__(PJ_NT) k_project(const ModelDev* __restrict__ models, FrameDev* __restrict__ fd,
+__global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict__ models, FrameDev* __restrict__ fd,
                                                    uint32_t* const* __restrict__ vis, const float4* __restrict__ attrs,
                                                    const CacheDev* __restrict__ caches, Records rec,
                                                    const ProjTab* __restrict__ ptab) {
