@@ -81,7 +81,8 @@ struct gsc_ctx {
   uint32_t ranges_cap = 0;
   uint2* ranges = nullptr;
   SortBufs sb{};
-  uint32_t status_tiles = 0;
+  uint32_t status_tiles = 0;  // sort look-back tiles allocated
+  uint32_t scan_tiles = 0;    // scan look-back words allocated
   unsigned long long* st_cull = nullptr;
   uint32_t st_cull_words = 0;
   unsigned long long* st_scan = nullptr;
@@ -193,19 +194,25 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  // sort tiles hold 2048 keys, scan tiles 4096 (a cache's scan runs over
-  // its lines and the visible anchors)
+  // sort tiles hold 2048 or 4096 keys (256 digit words each); scan tiles
+  // 1024 elements (the pair offsets run over records, a cache's scan over
+  // its lines and the visible anchors, the standalone scan over up to the
+  // pair capacity)
   const uint32_t lines = std::max<uint32_t>(ctx->cfg.cache_gaussians / K, 1u);
-  const uint32_t need = std::max({(ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 2047u) / 2048u,
-                                  (ctx->vis_cap + lines + 4095u) / 4096u}) + 1u;
+  const uint32_t need = std::max((ctx->rec_cap + 2047u) / 2048u, (ctx->pair_cap + 2047u) / 2048u) + 1u;
+  const uint32_t need_scan = std::max({(ctx->rec_cap + 1023u) / 1024u, (ctx->pair_cap + 1023u) / 1024u,
+                                       (ctx->vis_cap + lines + 1023u) / 1024u}) + 1u;
   if (need > ctx->status_tiles) {
     int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
     if (r) return r;
     CK(cudaMemset(ctx->sb.status, 0, (size_t)need * 256 * sizeof(unsigned long long)));
-    r = dalloc(ctx, &ctx->st_scan, (size_t)need);
-    if (r) return r;
-    CK(cudaMemset(ctx->st_scan, 0, (size_t)need * sizeof(unsigned long long)));
     ctx->status_tiles = need;
+  }
+  if (need_scan > ctx->scan_tiles) {
+    int r = dalloc(ctx, &ctx->st_scan, (size_t)need_scan);
+    if (r) return r;
+    CK(cudaMemset(ctx->st_scan, 0, (size_t)need_scan * sizeof(unsigned long long)));
+    ctx->scan_tiles = need_scan;
   }
   const uint32_t cw = ((models_max_n(ctx) + 2047u) / 2048u + 1u) * (uint32_t)MAXV;  // a look-back word per view
   if (cw > ctx->st_cull_words) {

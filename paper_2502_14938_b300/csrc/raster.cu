@@ -12,7 +12,7 @@ namespace gsc {
 // positions of the set flags, in ascending order).  With big: every i whose
 // count exceeds big_above is appended to big (order unspecified).
 constexpr int SCAN_NT = 256;
-constexpr int SCAN_IPT = 16;
+constexpr int SCAN_IPT = 4;  // 1024-element tiles: a frame's ~0.5M counts spread over every SM
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 
 __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ order,
@@ -86,7 +86,7 @@ void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t*
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
                      cudaStream_t s, uint32_t* scatter, uint32_t scatter_n, uint32_t* big, uint32_t* n_big,
                      uint32_t big_above) {
-  k_scan<<<n_sm * 2, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n, big,
+  k_scan<<<n_sm * 4, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n, big,
                                       n_big, big_above);
 }
 
