@@ -391,7 +391,7 @@ struct SortBufs {
 };
 
 // counter / epoch slots of the look-back kernels within one frame
-enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28, SLOT_BLEND = 29,
+enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLOT_AUX = 28, SLOT_BLEND = 29, SLOT_KEYGEN = 30,
              SLOT_CACHE = 32 };
 constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 

@@ -101,8 +101,11 @@ void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t*
 // gives each row's offset, and the lanes write the tiles of each row.  Then
 // every thread emits the small records of a grid-stride range itself.  The
 // float32 row ranges are the ones the count pass used, so the pairs and their
-// order are the same either way.  Each block also accumulates the digit
-// histograms of the written tile keys for the tile sort.
+// order are the same either way.  Then the warps take the small records in
+// chunks of 32 (one per lane) from a counter, so warps that spent long on
+// large records take fewer.  Each block also accumulates the digit
+// histograms of the written tile keys for the tile sort (a row of a large
+// record shares its upper digits: one atomic per distinct digit of a warp).
 __device__ __forceinline__ void tile_hist_add(uint32_t (*s_h)[256], int npass, uint32_t key) {
   for (int p = 0; p < npass; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xFFu], 1u);
 }
@@ -158,20 +161,32 @@ __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Recor
         const uint32_t ex = __shfl_sync(0xffffffffu, excl, rr);
         const int x0 = __shfl_sync(0xffffffffu, tx0, rr);
         const uint32_t kb = tb + (uint32_t)((c0 + rr) * cv.ntx + x0);
-        for (uint32_t u = lane; u < l; u += 32u) {
-          const uint32_t oi = o + ex + u;
-          if (oi < cap) {
-            pkeys[oi] = kb + u;
+        for (uint32_t u0 = 0; u0 < l; u0 += 32u) {  // warp-uniform bounds: every lane takes part
+          const uint32_t u = u0 + lane, oi = o + ex + u, key = kb + u;
+          const bool w = u < l && oi < cap;
+          if (w) {
+            pkeys[oi] = key;
             pvals[oi] = r;
-            tile_hist_add(s_h, npass, kb + u);
+            atomicAdd(&s_h[0][key & 0xFFu], 1u);
+          }
+          for (int p = 1; p < npass; ++p) {
+            const uint32_t d = (key >> (8 * p)) & 0xFFu;
+            const unsigned peers = __match_any_sync(0xffffffffu, w ? d : 0x100u);
+            if (w && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
           }
         }
       }
       o += chunk;
     }
   }
-  // small records: one thread each
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  // small records: one thread each, chunks of 32 per warp from a counter
+  for (;;) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(&fd->ctr[SLOT_KEYGEN], 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c * 32u >= n) break;
+    const uint32_t i = c * 32u + lane;
+    if (i >= n) continue;
     const uint32_t r = order[i];
     if (rec.cnt[r] > KG_SMALL) continue;
     uint32_t o = offs[i];
