@@ -8,6 +8,11 @@
 // yields the (tile, depth, Gaussian id) order of the key definition.
 // Tiles are taken from an atomic counter in increasing order: a block only
 // waits on tiles already held by running blocks, and every wait is bounded.
+// The grid is two blocks per SM: when every tile of a pass is in flight at
+// once, tile t walks back over ~t/16 aggregate windows and the look-back
+// traffic grows with the square of the tiles in flight; fewer resident
+// blocks let earlier tiles finish their prefixes first (measured: 4 or 3
+// blocks per SM and a 16- or 32-word window were slower).
 #include "gsc_internal.cuh"
 
 namespace gsc {
@@ -163,10 +168,10 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
     if (ipt == 8)
-      k_sort_pass<8><<<n_sm * 4, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
+      k_sort_pass<8><<<n_sm * 2, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
                                                   p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     else
-      k_sort_pass<16><<<n_sm * 3, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
+      k_sort_pass<16><<<n_sm * 2, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
                                                    p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     ci = ok;
     cv = ov;
