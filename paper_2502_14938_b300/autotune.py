@@ -54,18 +54,38 @@ def time_frames(renderer, outs, reps: int = 5, warmup: int = 2, setups: Optional
     return float(sum(per_setup) / len(per_setup))
 
 
+PERSISTENT_MARGIN = 0.02  # a persistent grid must beat one block per tile by 2% to be chosen
+
+
+def order_candidates(rows: List[Dict]) -> List[Dict]:
+    """Timed candidates fastest first, except that one block per tile of the
+    fastest shape goes first when the fastest (a persistent grid) beats it
+    by less than PERSISTENT_MARGIN."""
+    rows = sorted(rows, key=lambda r: r["ms"])
+    if rows and rows[0]["blocks_per_sm"] != 0:
+        same = [r for r in rows if (r["tile_w"], r["tile_h"]) == (rows[0]["tile_w"], rows[0]["tile_h"])
+                and r["blocks_per_sm"] == 0]
+        if same and same[0]["ms"] <= rows[0]["ms"] * (1.0 + PERSISTENT_MARGIN):
+            rows.remove(same[0])
+            rows.insert(0, same[0])
+    return rows
+
+
 def sweep(renderer, outs, shapes: Iterable[Tuple[int, int]] = TILE_SHAPES,
           blocks: Iterable[int] = BLOCKS_PER_SM, reps: int = 5, setups: Optional[Sequence] = None) -> List[Dict]:
     """Every (shape, blocks/SM) candidate timed on the renderer's current
     cameras (or on each of `setups`, averaged); returns the table sorted
-    fastest first.  The renderer keeps the fastest tiling when this returns."""
+    fastest first.  When the fastest is a persistent grid within
+    PERSISTENT_MARGIN of one block per tile of the same shape, the latter
+    (the simpler launch; the two differ by noise) is moved to the front.
+    The renderer keeps the first tiling of the table when this returns."""
     rows = []
     for tw, th in shapes:
         for bps in blocks:
             renderer.set_tiling(tw, th, bps)
             rows.append({"tile_w": tw, "tile_h": th, "blocks_per_sm": bps,
                          "ms": time_frames(renderer, outs, reps, setups=setups)})
-    rows.sort(key=lambda r: r["ms"])
+    rows = order_candidates(rows)
     best = rows[0]
     renderer.set_tiling(best["tile_w"], best["tile_h"], best["blocks_per_sm"])
     return rows

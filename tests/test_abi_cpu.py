@@ -86,3 +86,16 @@ def test_predictor_file_roundtrip(tmp_path):
         f.write(b"XXXX")
     with pytest.raises(ValueError):
         reuse.load(p)
+
+
+def test_autotuner_prefers_one_block_per_tile_within_margin():
+    from paper_2502_14938_b300.autotune import order_candidates
+    rows = [{"tile_w": 16, "tile_h": 32, "blocks_per_sm": 16, "ms": 0.500},
+            {"tile_w": 16, "tile_h": 32, "blocks_per_sm": 0, "ms": 0.505},
+            {"tile_w": 16, "tile_h": 16, "blocks_per_sm": 0, "ms": 0.503}]
+    assert order_candidates(rows)[0] == rows[1]           # within 2% of the persistent grid
+    rows[1]["ms"] = 0.520
+    assert order_candidates(rows)[0] == rows[0]           # 4% slower: the persistent grid stays
+    only = [{"tile_w": 8, "tile_h": 32, "blocks_per_sm": 4, "ms": 0.4}]
+    assert order_candidates(only) == only
+    assert order_candidates([]) == []
