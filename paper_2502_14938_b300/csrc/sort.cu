@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
 // output; *n_valid_out receives the kept count).  Ping-pongs between
 // (k0, v0) and (k1, v1); *kout / *vout get the buffers holding the result.
 // Uses counter / epoch slots slot_base .. slot_base + passes - 1.  ipt 8
-// (2048-key tiles, for the smaller record sort) or 16 (4096-key tiles).
+// (the record sort: its first pass runs over every record, invalid ones
+// included, in 4096-key tiles; the later passes over the valid ones in
+// 2048-key tiles) or 16 (4096-key tiles throughout).
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,
@@ -167,7 +169,7 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ok = (p % 2 == 0) ? k0 : k1;
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
-    if (ipt == 8)
+    if (ipt == 8 && p > 0)
       k_sort_pass<8><<<n_sm * 2, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
                                                   p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
     else
