@@ -16,7 +16,8 @@ import json
 import os
 from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
-TILE_SHAPES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (8, 32))
+TILE_SHAPES: Tuple[Tuple[int, int], ...] = ((16, 16), (32, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (8, 32),
+                                         (16, 64), (8, 64))
 BLOCKS_PER_SM: Tuple[int, ...] = (0, 4, 8, 16, 32)  # 0 = one block per tile
 
 

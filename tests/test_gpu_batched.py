@@ -105,7 +105,8 @@ def test_batched_frame_every_image_matches_oracle(small):
     r.close()
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (8, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (16, 8), (8, 16), (32, 16), (16, 32), (32, 32), (8, 32),
+                                  (16, 64), (8, 64), (8, 128)])
 def test_batched_tilings_and_persistent_blend(small, tile):
     """Every tile shape, one block per tile and persistent: each image within
     tolerance of the oracle; persistent and per-tile blends bit-identical
