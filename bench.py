@@ -185,7 +185,11 @@ OPS_PER_EVAL = 20
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
 # reported as the roofline's traffic only when the timed run uses that tiling.
-NCU_TRAFFIC = {"k_blend": {"bytes": 13.502e6 + 2.388e6, "tiling": (16, 32, 0), "frame": 151}}
+NCU_TRAFFIC = {"k_blend": {(16, 32, 0): {"bytes": 13.502e6 + 2.388e6, "frame": 151},
+                           (16, 64, 0): {"bytes": 12.791e6 + 2.363e6, "frame": 151}}}
+# The blend's algorithmic work is counted on the paper's rasteriser tiling
+# (16x16 tiles, one block per tile), so it does not depend on the tuned shape
+WORK_TILING = (16, 16, 0)
 
 
 def make_renderer(model, form, flags=0, use_graph=True):
@@ -290,18 +294,24 @@ def stage_profile(model, frames, form, n, flush, tiling=None):
             acc[k] += st[k]
     rt.close()
     # the same frames (from an empty cache) through the blend's counting
-    # variant: its (pixel, Gaussian) evaluations per frame
-    rw, mid = make_renderer(model, form, flags=pkg.FLAG_BLEND_WORK, use_graph=False)
-    if tiling:
-        rw.set_tiling(tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
-    acc["blend_walk"] = acc["blend_issued"] = 0
-    for s in range(n):
-        set_pair(rw, mid, *frames[s % len(frames)])
-        rw.render_frame(outs, stats=False)
-        w, i = rw.debug_blend_work()
-        acc["blend_walk"] += w
-        acc["blend_issued"] += i
-    rw.close()
+    # variant: its (pixel, Gaussian) evaluations per frame, on the timed
+    # tiling (walk and issued) and on 16x16 tiles (the algorithmic walk)
+    acc["blend_walk"] = acc["blend_issued"] = acc["blend_walk16"] = 0
+    timed = (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"]) if tiling else None
+    for pass_, t in enumerate((timed, WORK_TILING)):
+        rw, mid = make_renderer(model, form, flags=pkg.FLAG_BLEND_WORK, use_graph=False)
+        if t:
+            rw.set_tiling(*t)
+        for s in range(n):
+            set_pair(rw, mid, *frames[s % len(frames)])
+            rw.render_frame(outs, stats=False)
+            w, i = rw.debug_blend_work()
+            if pass_ == 0:
+                acc["blend_walk"] += w
+                acc["blend_issued"] += i
+            else:
+                acc["blend_walk16"] += w
+        rw.close()
     names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
     return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, {k: v / n for k, v in acc.items()}
 
@@ -316,25 +326,27 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
     feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
     if dom == "blend":
         # unit: one (pixel, Gaussian) evaluation of the front-to-back walk
-        # (every Gaussian of the pixel's tile list up to the one it stops at),
-        # counted in the kernel by its counting variant on the same frames;
-        # 20 FP32 ops + 1 exp2 each.  The kernel issues fewer (a warp skips
-        # records whose box misses its rows): issued_evals_per_launch.
+        # over 16x16 tile lists (every Gaussian of the pixel's tile list up
+        # to the one it stops at: the paper's rasteriser), counted in the
+        # kernel by its counting variant on the same frames; 20 FP32 ops +
+        # 1 exp2 each.  On the timed tiling the kernel's own walk and the
+        # evaluations it issued (a warp skips records whose box misses its
+        # rows) are reported beside it.
         import paper_2502_14938_b300 as pkg
-        walk, ev = st["blend_walk"], st["blend_issued"]
-        ach = walk * OPS_PER_EVAL / dur / 1e12
+        walk16, walk, ev = st["blend_walk16"], st["blend_walk"], st["blend_issued"]
+        ach = walk16 * OPS_PER_EVAL / dur / 1e12
         peak = FP32_LANE_OPS / 1e12
         rates = pkg.native.pipe_rates()
-        cap = NCU_TRAFFIC["k_blend"]
-        same = cap["bytes"] is not None and \
-            tuple(cap["tiling"]) == (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
+        key = (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
+        cap = NCU_TRAFFIC["k_blend"].get(key)
         return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32-op/s",
                 "frac": ach / peak,
-                "peak_src": "nominal: 148 SMs x 128 FP32 lanes x 2.032 GHz; work = 20 FP32 ops per evaluation",
-                "traffic": cap["bytes"] if same else None,
-                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {cap['tiling']}" if same else None,
-                "evals_per_launch": walk, "issued_evals_per_launch": ev, "evals_per_s": walk / dur,
-                "exp2_frac_of_measured": walk / dur / rates["exp2_per_s"],
+                "peak_src": "nominal: 148 SMs x 128 FP32 lanes x 2.032 GHz; work = 20 FP32 ops per evaluation "
+                            "of the walk over 16x16 tile lists",
+                "traffic": cap["bytes"] if cap else None,
+                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {key}" if cap else None,
+                "evals_per_launch": walk16, "walk_evals_timed_tiling": walk, "issued_evals_per_launch": ev,
+                "evals_per_s": walk16 / dur, "exp2_frac_of_measured": walk16 / dur / rates["exp2_per_s"],
                 "measured_rates": rates, "ms_per_launch": stage_ms[dom],
                 "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
     if dom == "sort_tile":

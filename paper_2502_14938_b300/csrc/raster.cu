@@ -235,10 +235,10 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 // Each warp of a tile's block owns a band of the tile's rows and walks the
 // tile's record list on its own, 32 records at a time: lane l loads record
 // l of the chunk, tests its opacity-aware box against the warp's band, and
-// for a hit stages the tile-local quadratic of its power in the exp2 domain,
+// for a hit stages the band-local quadratic of its power in the exp2 domain,
 //   log2(o) - (log2 e / 2) q(D) = [F + X (D + A' X)] + Y [(E + B' X) + C' Y],
-// with (X, Y) the pixel centre relative to the tile centre (the bracket in
-// X is per lane, so a pixel costs 2 FMA).  The ballot of hits is the
+// with (X, Y) the pixel centre relative to the band's centre (the bracket
+// in X is per lane, so a pixel costs 2 FMA).  The ballot of hits is the
 // chunk's work list: the warp visits only those records, in list order.
 // Each pixel walks them front to back:
 //   alpha = min(0.99, 2^power), taken as 0 when the power is below
@@ -362,7 +362,10 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
   const int band = groups * BLEND_PPL;              // rows per warp
   const int lx = lane % TW, ly0 = warp * band + (lane / TW) * BLEND_PPL;
   const int px = tx * TW + lx, py0 = ty * TH + ly0;
-  const float ox = (float)(tx * TW) + 0.5f * (float)TW, oy = (float)(ty * TH) + 0.5f * (float)TH;
+  // origin of the quadratic: the centre of the warp's band (|X| <= TW/2,
+  // |Y| <= band/2 whatever the tile height, which bounds the float32
+  // rounding of the expanded power)
+  const float ox = (float)(tx * TW) + 0.5f * (float)TW, oy = (float)(ty * TH + warp * band) + 0.5f * (float)band;
   const float X = ((float)px + 0.5f) - ox;
   const float Y0 = ((float)py0 + 0.5f) - oy;
   const float wx0 = ((float)(tx * TW) + 0.5f) - ox, wx1 = wx0 + (float)(TW - 1);
