@@ -227,7 +227,8 @@ int ensure_status(gsc_ctx* ctx) {
 int alloc_records(gsc_ctx* ctx, uint32_t cap) {
   int r;
   if ((r = dalloc(ctx, &ctx->rec.geo, cap)) || (r = dalloc(ctx, &ctx->rec.cop, cap)) ||
-      (r = dalloc(ctx, &ctx->rec.col, cap)) || (r = dalloc(ctx, &ctx->rec.key, cap)) ||
+      (r = dalloc(ctx, &ctx->rec.col, cap)) || (r = dalloc(ctx, &ctx->rec.aux, cap)) ||
+      (r = dalloc(ctx, &ctx->rec.key, cap)) ||
       (r = dalloc(ctx, &ctx->rec.cnt, cap)) || (r = dalloc(ctx, &ctx->s1k0, cap)) ||
       (r = dalloc(ctx, &ctx->s1v0, cap)) || (r = dalloc(ctx, &ctx->s1k1, cap)) ||
       (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)) ||
@@ -773,7 +774,7 @@ void gsc_destroy(gsc_ctx* ctx) {
     dfree(m.feat_bf16.p); dfree(m.w_tc.p); dfree(m.feat_fp8.p); dfree(m.w_tc8.p);
   }
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
-                  ctx->rec.cop, ctx->rec.col, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
+                  ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
                   ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab};

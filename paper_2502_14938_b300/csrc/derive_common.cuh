@@ -178,6 +178,13 @@ __device__ __forceinline__ uint32_t project_write(const ProjCam& c, Records rec,
     rec.cop[r] = cop;
     rec.col[r] = colv;
     rec.cnt[r] = cnt;
+    // what every warp of every tile the record reaches would otherwise
+    // recompute: the opacity in the exp2 domain and the half extents of the
+    // opacity-aware box (q <= tau reaches x_mean +- sqrt(tau C / det) and
+    // y_mean +- sqrt(tau A / det), det the conic's determinant)
+    const float A = geo.z, B = geo.w, C = cop.x, tau = cop.z;
+    const float idet = 1.f / (A * C - B * B);
+    rec.aux[r] = make_float4(C, __log2f(alpha), sqrtf(tau * C * idet), sqrtf(tau * A * idet));
   }
   return key;
 }

@@ -161,6 +161,7 @@ struct Records {
   float4* geo;    // mean x, mean y, A, B
   float4* cop;    // C, opacity, tau_cov, depth
   float4* col;    // r, g, b, bits(view | valid bit)
+  float4* aux;    // for the blend: C, log2(opacity), box half-width, box half-height
   uint32_t* key;  // depth bits or INVALID_KEY
   uint32_t* cnt;  // covered tiles
 };

@@ -273,7 +273,7 @@ constexpr int BLEND_MAX_NT = 256;
 constexpr int BLEND_MAX_WARPS = BLEND_MAX_NT / 32;
 constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
-constexpr float CLAMP_OPACITY = 0.985f;                  // records at or above it take the 0.99 clamp
+constexpr float LOG2_CLAMP_OPACITY = -0.02180437f;      // log2(0.985): records at or above it take the 0.99 clamp
 
 struct BlendSmem {  // per warp, one slot per lane of the current chunk
   float4 fd[BLEND_MAX_WARPS][32];   // F, F, D, D
@@ -394,16 +394,14 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
     if (idx < rg.y) {
       const uint32_t r = vals[idx];
       const float4 g = rec.geo[r];   // mean x, mean y, A, B
-      const float4 c = rec.cop[r];   // C, opacity, tau, depth
+      const float4 c = rec.aux[r];   // C, log2(opacity), box half-width, box half-height
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
-      const float idet = 1.f / (A * Cc - B * B);
-      const float ex = sqrtf(c.z * Cc * idet), ey = sqrtf(c.z * A * idet);
-      hit = !(mxl + ex < wx0 || mxl - ex > wx1 || myl + ey < wy0 || myl - ey > wy1);  // box meets the band
+      hit = !(mxl + c.z < wx0 || mxl - c.z > wx1 || myl + c.w < wy0 || myl - c.w > wy1);  // box meets the band
       if (hit) {
         const float4 cl = rec.col[r];
         const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
-        const float F = __log2f(c.y) - LOG2E_HALF * q0;
+        const float F = c.y - LOG2E_HALF * q0;
         const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
         const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
         const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
@@ -412,7 +410,7 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
         sm.bc[warp][lane] = make_float4(Bp, Bp, Cp, Cp);
         sm.rg[warp][lane] = make_float4(cl.x, cl.x, cl.y, cl.y);
         sm.bl[warp][lane] = make_float2(cl.z, cl.z);
-        clamp = c.y >= CLAMP_OPACITY;
+        clamp = c.y >= LOG2_CLAMP_OPACITY;
       }
     }
     unsigned todo = __ballot_sync(0xffffffffu, hit);
