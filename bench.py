@@ -400,20 +400,40 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
                 "evals_per_s": walk16 / dur, "exp2_frac_of_measured": walk16 / dur / rates["exp2_per_s"],
                 "measured_rates": rates, "ms_per_launch": stage_ms[dom],
                 "hbm_gbs": (P * 52 + pixels * 12) / dur / 1e9}
-    if dom == "sort_tile":
-        b = P * 4 + 2 * P * 16
-    elif dom == "sort_depth":
-        b = R * 8 + Rv * 8 + 3 * Rv * 16
-    elif dom == "derive+project":
-        b = V * (feat_b + 16 + 120) + R * 56
-    elif dom == "scan+keygen":
-        b = Rv * 16 + P * 8
-    else:
-        b = n_anchors * 13 + V * 4
+    b = stage_bytes(dom, st, form, n_anchors)
     ach = b / dur / 1e9
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": ach / pk["hbm_gbs"], "peak_src": pk["src"], "traffic": None, "alg_bytes_per_launch": b,
             "ms_per_launch": stage_ms[dom]}
+
+
+def stage_bytes(stage, st, form, n_anchors):
+    """Algorithmic HBM bytes of one frame's stage (each datum read or written once)."""
+    P, Rv, R, V = st["pairs"], st["valid_records"], st["records"], st["visible_anchors"]
+    feat_b = {"fp32": 128, "bf16": 64, "fp8": 32}[FORMS[form]["precision"]]
+    if stage == "sort_tile":      # 2 passes: key + value in and out; tile ranges
+        return P * 4 + 2 * P * 16
+    if stage == "sort_depth":     # pass 1 reads every record's key, 4 passes move the valid (key, value)
+        return R * 8 + Rv * 8 + 3 * Rv * 16
+    if stage == "derive+project":  # features + directions + attributes of visible anchors; records out
+        return V * (feat_b + 16 + 120) + R * 56
+    if stage == "scan+keygen":    # counts and offsets of valid records; pairs out
+        return Rv * 16 + P * 8
+    if stage == "ranges":
+        return P * 4
+    if stage == "blend":          # pairs and records of every pair in; the images out
+        return P * 52
+    return n_anchors * 13 + V * 4  # cull + cache + tables: positions and levels in, visible ids out
+
+
+def stage_hbm(stage_ms, st, form, W, H, n_anchors):
+    """Every stage's algorithmic bytes over its (eagerly timed) duration, against the HBM peak."""
+    pk = peaks()
+    out = {}
+    for s, ms in stage_ms.items():
+        b = stage_bytes(s, st, form, n_anchors) + (2 * W * H * 12 if s == "blend" else 0)
+        out[s] = {"alg_bytes": b, "gbs": b / (ms / 1e3) / 1e9, "frac": b / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    return out
 
 
 BATCHED_FORM = dict(stereo_unify=True, precision="bf16", reuse="depth")
@@ -637,6 +657,7 @@ def run_ours(args, rank, world):
     fps = job_rate(world, args.steps, total_ms)
     stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush, r.tiling)
     roof = roofline(stage_ms, per_frame, form, W, H, model.n, r.tiling)
+    stage_gbs = stage_hbm(stage_ms, per_frame, form, W, H, model.n)
 
     # ---- quality: PSNR and max-abs of sampled frames against the float64
     # oracle (plain method), each form rendered in path order from an empty
@@ -700,7 +721,7 @@ def run_ours(args, rank, world):
            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "max_abs": q["max_abs"],
            "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
-           "e2e_sync_f32": e2e_sync_f32, "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "per_frame": per_frame, "gen_s": t_gen}
+           "e2e_sync_f32": e2e_sync_f32, "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "stage_hbm": stage_gbs, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[FORMS[form]["precision"]],
