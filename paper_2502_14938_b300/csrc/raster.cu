@@ -398,6 +398,17 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
       hit = !(mxl + c.z < wx0 || mxl - c.z > wx1 || myl + c.w < wy0 || myl - c.w > wy1);  // box meets the band
+      if (hit) {  // the ellipse itself: its x-extent over the band's rows against the band's columns
+        // on the row dy (from the mean) the ellipse spans dx = (-B dy +- sqrt(det) sqrt(ey^2 - dy^2)) / A;
+        // its right- and leftmost points lie on dy = -+B ex / C, clamped to the band's rows
+        const float ya = fmaxf(wy0 - myl, -c.w), yb = fminf(wy1 - myl, c.w);
+        const float iA = 1.f / A, sd = sqrtf(fmaxf(0.f, A * Cc - B * B)) * iA, bxc = B * c.z / Cc;
+        const float dr = fminf(fmaxf(-bxc, ya), yb), dl = fminf(fmaxf(bxc, ya), yb);
+        const float xr = mxl - B * dr * iA + sd * sqrtf(fmaxf(0.f, c.w * c.w - dr * dr));
+        const float xl = mxl - B * dl * iA - sd * sqrtf(fmaxf(0.f, c.w * c.w - dl * dl));
+        const float slack = 1e-3f * (c.z + 1.f);  // float32 rounding; the box's tau is already enlarged
+        hit = xr + slack >= wx0 && xl - slack <= wx1;
+      }
       if (hit) {
         const float4 cl = rec.col[r];
         const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
