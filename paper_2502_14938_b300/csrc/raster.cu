@@ -230,12 +230,14 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 }
 
 // ------------------------------------------------------------------ blend (K10)
-// One block per (camera, tile); each lane owns a vertical strip of 4 pixels
-// (lanes of a warp cover the tile's columns, so a warp owns a band of rows).
-// Each warp of a tile's block owns a band of the tile's rows and walks the
-// tile's record list on its own, 32 records at a time: lane l loads record
-// l of the chunk, tests its opacity-aware box against the warp's band, and
-// for a hit stages the band-local quadratic of its power in the exp2 domain,
+// One block per (camera, tile) (or a persistent grid taking tiles from a
+// counter); each lane owns a vertical strip of 4 pixels (lanes of a warp
+// cover the tile's columns, so a warp owns a band of rows).
+// Each warp walks the tile's record list on its own, 32 records at a time:
+// lane l loads record l of the chunk (with the blend view the projection
+// wrote for it: C, log2 opacity, box half extents), tests its opacity-aware
+// box and then the ellipse itself against the warp's band, and for a hit
+// stages the band-local quadratic of its power in the exp2 domain,
 //   log2(o) - (log2 e / 2) q(D) = [F + X (D + A' X)] + Y [(E + B' X) + C' Y],
 // with (X, Y) the pixel centre relative to the band's centre (the bracket
 // in X is per lane, so a pixel costs 2 FMA).  The ballot of hits is the
