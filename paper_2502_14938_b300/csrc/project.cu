@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
 
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,
                     const CacheDev* caches, Records rec, const ProjTab* ptab, int n_sm, cudaStream_t s) {
-  k_project<<<n_sm * 8, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec, ptab);
+  // one wave of resident blocks (four per SM) striding over the Gaussians:
+  // half the per-block histogram flushes of two waves
+  k_project<<<n_sm * 4, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec, ptab);
 }
 
 // ------------------------------------------------------------------ frame tables
