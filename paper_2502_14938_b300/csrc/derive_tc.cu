@@ -260,11 +260,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   uint32_t tma_phase = 0, mma_phase = 0;
   bool failed = false;
   bool tma_pending = false, mma_pending = false;
-  bool w_pending = true;
-  if (__syncthreads_or(!mbar_wait(w_bar, 0)))
-    failed = true;
-  else
-    w_pending = false;
+  bool w_pending = true;  // the weight image is waited for just before the first MMA, so that its
+                          // copy overlaps the first tile's metadata loads and feature copy
 
   for (uint32_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     // ---- metadata, view direction chunk, TMA of the feature chunks
@@ -315,6 +312,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       break;
     }
     tma_pending = false;
+    if (w_pending) {
+      if (__syncthreads_or(!mbar_wait(w_bar, 0))) {
+        failed = true;
+        break;
+      }
+      w_pending = false;
+    }
     tc_fence_after();
     // ---- MMA1
     if (t == 0) {
