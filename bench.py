@@ -221,6 +221,7 @@ FORMS = {
     "plain": dict(precision="fp32", stereo_unify=False, reuse="off"),
     "unified": dict(precision="fp32", stereo_unify=True, reuse="off"),
     "bf16": dict(precision="bf16", stereo_unify=False, reuse="off"),
+    "cached_bf16": dict(precision="bf16", stereo_unify=False, reuse="depth"),
     "bf16_unified": dict(precision="bf16", stereo_unify=True, reuse="off"),
     "cached_unified": dict(precision="fp32", stereo_unify=True, reuse="depth"),
     "cached_bf16_unified": dict(precision="bf16", stereo_unify=True, reuse="depth"),
@@ -255,6 +256,49 @@ def set_pair(r, mid, L, R):
     r.set_cameras([pkg.to_camera(L, partner=1, model_id=mid), pkg.to_camera(R, partner=0, model_id=mid)])
 
 
+# Synthetic ablation in the manner of the paper's Tables 5-6: the headline
+# form with one optimisation removed at a time (the paper's "w/o kernels",
+# its PyTorch op-by-op pipeline, has no counterpart here: every stage is a
+# kernel of this library).
+ABLATION = (("full: cached + BF16 + unified stereo", "cached_bf16_unified"),
+            ("w/o de-redundancy (per-eye derivation)", "cached_bf16"),
+            ("w/o reuse", "bf16_unified"),
+            ("w/o BF16 (FP32 MLPs)", "cached_unified"),
+            ("none: plain FP32, per eye, no cache", "plain"))
+
+
+def run_ablation(args):
+    """AVG and 1%-low FPS, decoding / rasterisation stage times, device
+    memory of each ablated form on the timed frames of the path, at one tiling."""
+    import torch
+    model, frames, t_gen = build_workload()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tiling = tuple(args.tile)
+    rows = []
+    for name, form in ABLATION:
+        torch.cuda.synchronize()
+        free0, res0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+        r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, 1, tiling=tiling)
+        torch.cuda.synchronize()
+        lib_bytes = (free0 - torch.cuda.mem_get_info()[0]) - (torch.cuda.memory_reserved() - res0)
+        r.close()
+        stage, _ = stage_profile(model, frames, form, min(args.steps, len(frames)), flush,
+                                 {"tile_w": tiling[0], "tile_h": tiling[1], "blocks_per_sm": tiling[2]}, count=False)
+        dec = stage["cull+plan"] + stage["derive+project"]
+        mean, p99 = float(np.mean(ms)), float(np.percentile(ms, 99))
+        rows.append({"method": name, "form": form, "avg_fps": 1e3 / mean, "fps_1pct_low": 1e3 / p99,
+                     "ms_mean": mean, "decoding_ms": dec, "rasterization_ms": sum(stage.values()) - dec,
+                     "device_gib": lib_bytes / 2 ** 30})
+    for row in rows:
+        row["speedup_loss"] = rows[0]["avg_fps"] / row["avg_fps"]
+    print(json.dumps({"ablation": rows, "workload": "city 2M anchors, stereo 1920x1080, 300-frame ascending path",
+                      "steps": args.steps, "warmup": args.warmup, "tiling": list(tiling),
+                      "stages": "decoding = culling, cache, tables, derivation and projection; rasterisation = "
+                                "sorts, pair offsets, key generation, ranges, blend (eager CUDA events)",
+                      "memory": "device memory the library allocated (free-memory drop minus torch's own)"}),
+          flush=True)
+
+
 def run_profile(args):
     """Minimal run for profilers: W + K frames from --frame, no extras, with
     the tiling of --tile (launches per frame: launches_per_frame_of)."""
@@ -273,10 +317,10 @@ def run_profile(args):
           flush=True)
 
 
-def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=False):
+def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=False, tiling=None):
     """Per-frame CUDA-event times (ms) of `steps` frames of the path; L2 flushed between frames.
     tune: pick the blend tiling (tile shape, blocks/SM) with the project's autotuner on the
-    middle frame of the path first."""
+    middle frame of the path first; tiling: a fixed (W, H, blocks/SM) instead."""
     import torch
     W, H = frames[0][0].width, frames[0][0].height
     r, mid = make_renderer(model, form)
@@ -285,7 +329,13 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
         set_pair(r, mid, *frames[f])
         r.render_frame(outs)
     r.tiling = {"tile_w": 16, "tile_h": 16, "blocks_per_sm": 0, "source": "default"}
-    if tune:
+    if tiling is not None:
+        r.set_tiling(*tiling)
+        r.tiling = {"tile_w": tiling[0], "tile_h": tiling[1], "blocks_per_sm": tiling[2], "source": "fixed"}
+        for f in range(len(frames)):  # regrow for the tiling
+            set_pair(r, mid, *frames[f])
+            r.render_frame(outs)
+    elif tune:
         from paper_2502_14938_b300 import autotune
         picks = [frames[i] for i in np.linspace(0, len(frames) - 1, 6).astype(int)]
         setups = [lambda fr=fr: set_pair(r, mid, *fr) for fr in picks]
@@ -324,7 +374,7 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
     return r, mid, outs, ms, wall
 
 
-def stage_profile(model, frames, form, n, flush, tiling=None):
+def stage_profile(model, frames, form, n, flush, tiling=None, count=True):
     """Per-stage CUDA-event times on the library's stream (eager launches), with the timed run's tiling."""
     import paper_2502_14938_b300 as pkg
     import torch
@@ -349,7 +399,7 @@ def stage_profile(model, frames, form, n, flush, tiling=None):
     # tiling (walk and issued) and on 16x16 tiles (the algorithmic walk)
     acc["blend_walk"] = acc["blend_issued"] = acc["blend_walk16"] = 0
     timed = (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"]) if tiling else None
-    for pass_, t in enumerate((timed, WORK_TILING)):
+    for pass_, t in enumerate((timed, WORK_TILING) if count else ()):
         rw, mid = make_renderer(model, form, flags=pkg.FLAG_BLEND_WORK, use_graph=False)
         if t:
             rw.set_tiling(*t)
@@ -633,6 +683,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     if args.profile:
         return run_profile(args)
+    if args.ablation:
+        return run_ablation(args) if rank == 0 else None
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -751,6 +803,8 @@ def main():
                     help="tune the headline form's blend tiling before timing it")
     ap.add_argument("--learned", action=argparse.BooleanOptionalAction, default=True,
                     help="also train the reuse predictor and time the learned form (config.learned_reuse)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead of the bench line: the ablation table (one JSON line) at the --tile tiling")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))
