@@ -69,6 +69,18 @@ typedef enum { GSC_PREC_FP32 = 0, GSC_PREC_BF16 = 1, GSC_PREC_FP8 = 2 } gsc_prec
  * 4 bytes per pixel instead of 12). */
 typedef enum { GSC_OUT_F32 = 0, GSC_OUT_RGBA8 = 1 } gsc_out_format;
 
+/* Guiding function H of Eq. 4: the reuse depth of the next frame from this
+ * frame's update rate u = misses / visible anchors of a derivation view
+ * (depth reuse form; D = max_depth; the result is clamped to [1, D]).
+ * LINEAR (the paper's experiments): round(D (1 - u)), in integers, halves up.
+ * EXP (for accelerating motion): round(D^(1 - u)), in float64; it falls
+ *   faster than the linear one as u grows and meets it at u = 0 and u = 1.
+ * STAGED (for staged speed changes): D for u < 0.1, ceil(D / 2) for
+ *   u < 0.3, 1 otherwise, in integers.
+ * The paper names the exponential and staged responses without a formula;
+ * these are this library's forms of them. */
+typedef enum { GSC_GUIDE_LINEAR = 0, GSC_GUIDE_EXP = 1, GSC_GUIDE_STAGED = 2 } gsc_depth_guide;
+
 typedef enum {
   GSC_REUSE_OFF = 0,      /* decode every visible anchor every frame */
   GSC_REUSE_DEPTH = 1,    /* Alg. 1 dynamic cache depth (Eq. 4, linear guide) */
@@ -98,7 +110,8 @@ typedef struct {
   uint32_t blocks_per_sm;    /* blend: 0 = one block per tile; n = persistent grid of n blocks per SM
                                 taking the tiles of all cameras from one counter */
   uint32_t out_format;       /* gsc_out_format of the images */
-  uint32_t reserved[6];
+  uint32_t depth_guide;      /* gsc_depth_guide of the depth reuse form */
+  uint32_t reserved[5];
 } gsc_config;
 
 /* Model description: host pointers, float32, row-major.  Copied by

@@ -30,26 +30,45 @@ Readings (the paper gives the algorithm's branches, not its data layout):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 ATTR = 11
 
 
-def next_depth(depth: int, visible: int, misses: int, d_max: int) -> int:
-    """Linear guiding function of Eq. 4 (integer rounding, half up)."""
+GUIDES = ("linear", "exp", "staged")
+
+
+def next_depth(depth: int, visible: int, misses: int, d_max: int, guide: str = "linear") -> int:
+    """Guiding function H of Eq. 4, u = misses / visible, result in [1, d_max]:
+    linear  round(d_max (1 - u)) (integer rounding, half up; the paper's
+            experiments);
+    exp     round(d_max ** (1 - u)) in float64 (the paper's "exponential
+            response" for accelerating motion; its formula is this reading);
+    staged  d_max for u < 0.1, ceil(d_max / 2) for u < 0.3, else 1 (the
+            paper's "staged response"; thresholds are this reading)."""
     if visible <= 0:
         return depth
     v, m = int(visible), int(misses)
-    d = (2 * d_max * (v - m) + v) // (2 * v)
+    if guide == "exp":
+        d = int(math.floor(float(d_max) ** (1.0 - m / v) + 0.5))
+    elif guide == "staged":
+        d = d_max if 10 * m < v else ((d_max + 1) // 2 if 10 * m < 3 * v else 1)
+    elif guide == "linear":
+        d = (2 * d_max * (v - m) + v) // (2 * v)
+    else:
+        raise ValueError(guide)
     return int(min(max(d, 1), d_max))
 
 
 class CacheSim:
     """Alg. 1 for one derivation view."""
 
-    def __init__(self, n_anchors: int, slots: int, k: int = 10, max_depth: int = 10):
+    def __init__(self, n_anchors: int, slots: int, k: int = 10, max_depth: int = 10, guide: str = "linear"):
         self.k = k
         self.D = int(max_depth)
+        self.guide = guide
         self.slot_of = np.full(n_anchors, -1, np.int64)
         self.slot_anchor = np.full(slots, -1, np.int64)
         self.slot_frame = np.zeros(slots, np.int64)
@@ -104,7 +123,7 @@ class CacheSim:
         used = self.depth
         self.last = dict(visible=len(ids), misses=int((~hit).sum()), hits=int(hit.sum()),
                          new=len(new_idx), cached_new=n)
-        self.depth = next_depth(self.depth, len(ids), int((~hit).sum()), self.D)
+        self.depth = next_depth(self.depth, len(ids), int((~hit).sum()), self.D, self.guide)
         return hit, line, used
 
     def store(self, line: np.ndarray, decoded: np.ndarray, attrs: np.ndarray):

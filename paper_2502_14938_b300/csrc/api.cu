@@ -294,6 +294,7 @@ int init_cache(gsc_ctx* ctx, CacheDev& c, uint32_t n_anchors) {
   uint32_t st[CS_WORDS] = {0};
   st[CS_DEPTH] = ctx->cfg.max_depth;
   st[CS_DMAX] = ctx->cfg.max_depth;
+  st[CS_GUIDE] = ctx->cfg.depth_guide;
   st[CS_S] = c.S;
   CK(cudaMemcpy(c.state, st, sizeof st, cudaMemcpyHostToDevice));
   return GSC_OK;
@@ -716,6 +717,7 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.max_views == 0 || cfg.max_views > GSC_MAX_VIEWS) return GSC_ERR_INVALID_ARG;
   if (!tiling_ok(cfg.tile_w, cfg.tile_h, cfg.blocks_per_sm)) return GSC_ERR_INVALID_ARG;
   if (cfg.out_format > GSC_OUT_RGBA8) return GSC_ERR_INVALID_ARG;
+  if (cfg.depth_guide > GSC_GUIDE_STAGED) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
   if ((cfg.flags & GSC_FLAG_REUSE_COLLECT) && cfg.reuse == GSC_REUSE_OFF) return GSC_ERR_INVALID_ARG;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;

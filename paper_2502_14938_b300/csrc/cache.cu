@@ -15,8 +15,8 @@
 //            ascending order) and of new anchors (ascending)
 //   assign   the i-th new anchor takes the i-th free line (none left: decoded
 //            but not cached); decoded lines are stamped with t; then the
-//            policy: next depth = round(D_max (1 - misses / visible)) in
-//            [1, D_max] (Eq. 4, linear guiding function), in integers.
+//            policy: next depth = H(misses / visible) in [1, D_max] (Eq. 4;
+//            H linear, exponential or staged, gsc_depth_guide).
 // The decoder writes fresh attributes of misses into their lines; the
 // projection reads hits from their lines.
 //
@@ -83,10 +83,19 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
 }
 
 // Eq. 4 with the linear guide, from this frame's visible and decoded counts.
-__device__ __forceinline__ uint32_t next_depth(uint32_t depth, uint32_t V, uint32_t m, uint32_t D) {
+// Eq. 4 with the guiding function of the configuration (gsc_depth_guide).
+__device__ __forceinline__ uint32_t next_depth(uint32_t depth, uint32_t V, uint32_t m, uint32_t D, uint32_t guide) {
   if (V == 0) return depth;
-  const unsigned long long num = 2ull * D * (V - m) + V;
-  const uint32_t d = (uint32_t)(num / (2ull * V));
+  uint32_t d;
+  if (guide == GSC_GUIDE_EXP) {
+    const double e = exp((1.0 - (double)m / (double)V) * log((double)D));
+    d = (uint32_t)floor(e + 0.5);
+  } else if (guide == GSC_GUIDE_STAGED) {
+    d = 10ull * m < V ? D : (10ull * m < 3ull * V ? (D + 1u) / 2u : 1u);
+  } else {
+    const unsigned long long num = 2ull * D * (V - m) + V;
+    d = (uint32_t)(num / (2ull * V));
+  }
   return d < 1u ? 1u : (d > D ? D : d);
 }
 
@@ -105,7 +114,7 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* _
     st[CS_VIS] = V;
     st[CS_FREE] = n_free;
     st[CS_NEW] = st[CS_SCAN_TOT] - n_free;
-    st[CS_DEPTH] = next_depth(st[CS_DEPTH], V, m, st[CS_DMAX]);
+    st[CS_DEPTH] = next_depth(st[CS_DEPTH], V, m, st[CS_DMAX], st[CS_GUIDE]);
     atomicSub(&fd->n_derived, V - m);
     if (c == 0) fd->cache_depth = st[CS_DEPTH];
   }

@@ -136,7 +136,8 @@ struct ModelDev {
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
-enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_SCAN_N, CS_SCAN_TOT, CS_WORDS };
+enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_SCAN_N, CS_SCAN_TOT, CS_GUIDE,
+             CS_WORDS };
 constexpr uint32_t LINE_HIT = 0x80000000u;   // vstat: the anchor reuses its line
 constexpr uint32_t LINE_NONE = 0x7FFFFFFFu;  // vstat: decoded without a line
 struct CacheDev {

@@ -24,6 +24,7 @@ STATUS = {0: "GSC_OK", -1: "GSC_ERR_INVALID_ARG", -2: "GSC_ERR_OOM", -3: "GSC_ER
           -7: "GSC_ERR_UNIMPLEMENTED", -8: "GSC_ERR_INTERNAL"}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 OUT_FORMAT = {"f32": 0, "rgba8": 1}
+DEPTH_GUIDE = {"linear": 0, "exp": 1, "staged": 2}
 REUSE = {"off": 0, "depth": 1, "learned": 2}
 FLAG_DEBUG_ATTRS = 0x1
 FLAG_DEBUG_T = 0x2
@@ -44,7 +45,8 @@ class Config(C.Structure):
                 ("stereo_unify", C.c_uint32), ("cache_gaussians", C.c_uint32), ("max_depth", C.c_uint32),
                 ("tile_w", C.c_uint32), ("tile_h", C.c_uint32), ("pair_capacity", C.c_uint64),
                 ("bg", C.c_float * 3), ("use_graph", C.c_uint32), ("flags", C.c_uint32),
-                ("blocks_per_sm", C.c_uint32), ("out_format", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+                ("blocks_per_sm", C.c_uint32), ("out_format", C.c_uint32), ("depth_guide", C.c_uint32),
+                ("reserved", C.c_uint32 * 5)]
 
 
 class ModelDesc(C.Structure):
@@ -197,7 +199,8 @@ class Renderer:
     def __init__(self, max_views: int = 2, precision: str = "fp32", reuse: str = "off",
                  stereo_unify: bool = False, tile: tuple = (16, 16), pair_capacity: int = 0,
                  bg=(0.0, 0.0, 0.0), use_graph: bool = True, flags: int = 0, stream=None,
-                 cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0, out_format: str = "f32"):
+                 cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0, out_format: str = "f32",
+                 depth_guide: str = "linear"):
         cfg = default_config()
         cfg.max_views = max_views
         cfg.precision = PREC[precision]
@@ -213,6 +216,7 @@ class Renderer:
         cfg.max_depth = max_depth
         cfg.blocks_per_sm = blocks_per_sm
         cfg.out_format = OUT_FORMAT[out_format]
+        cfg.depth_guide = DEPTH_GUIDE[depth_guide]
         self.cfg = cfg
         self.out_format = out_format
         self.ctx = C.c_void_p()

@@ -132,3 +132,29 @@ def test_cache_reset_decodes_everything_again(city):
     hit, _ = gpu_lines(r.debug_cache(0)[0])
     assert not hit.any() and st["derived_anchors"] == st["visible_anchors"]
     r.close()
+
+
+@pytest.mark.parametrize("guide", ["linear", "exp", "staged"])
+def test_guiding_functions_match_oracle_simulation(guide):
+    """Eq. 4 with each guiding function on an accelerating pan of the tiny
+    scene: the depth chosen after every frame and the hit / line decisions
+    are bit-exact with the oracle simulation using the same guide."""
+    m = gen.tiny_scene()
+    lines = 4000
+    r = make_renderer(m, [gen.tiny_camera()], reuse="depth", cache_gaussians=lines * 10, depth_guide=guide)
+    sim = CacheSim(m.n, lines, max_depth=10, guide=guide)
+    depths = []
+    for f in range(30):
+        ang = 0.0009 * f * f  # accelerating pan from inside the scene: anchors leave and enter the view
+        Ry = np.array([[np.cos(ang), 0, -np.sin(ang)], [0, 1, 0], [np.sin(ang), 0, np.cos(ang)]])
+        cam = gen.pinhole(Ry, np.array([0.0, 0.0, -4.0]), 256, 256, 30.0)
+        set_cams(r, [cam], [-1])
+        (img,), st = render(r, [cam])
+        ids, attrs, kept, hit, line, used = cached_derive(m, cam, sim)
+        vstat, cst = r.debug_cache(0)
+        ghit, gline = gpu_lines(vstat)
+        assert np.array_equal(ghit, hit) and np.array_equal(gline, line), f"{guide} frame {f}"
+        assert cst["depth"] == sim.depth, f"{guide} frame {f}: depth {cst['depth']} vs {sim.depth}"
+        depths.append(sim.depth)
+    assert len(set(depths)) > 2, f"{guide}: the depth hardly moved"
+    r.close()

@@ -119,3 +119,32 @@ def test_view_independent_model_cached_equals_fp16_uncached():
         assert np.array_equal(img, ref)
         if f == 1:
             assert hit.all()
+
+
+def test_guiding_functions_closed_forms():
+    """Eq. 4 guides: all three give D at u = 0 and 1 at u = 1; the exponential
+    one is D^(1-u) rounded (10^0.5 = 3.16 -> 3 at u = 1/2, 10^0.9 = 7.94 -> 8
+    at u = 1/10); the staged one switches at u = 0.1 and u = 0.3; the
+    exponential one never exceeds the linear one by more than rounding
+    (D^(1-u) <= 1 + (D-1)(1-u) by convexity), so it reuses less under
+    accelerating motion."""
+    for g in ("linear", "exp", "staged"):
+        assert next_depth(10, 100, 0, 10, g) == 10
+        assert next_depth(10, 100, 100, 10, g) == 1
+        assert next_depth(4, 0, 0, 10, g) == 4
+    assert next_depth(10, 100, 50, 10, "exp") == 3
+    assert next_depth(10, 100, 10, 10, "exp") == 8
+    assert next_depth(10, 1000, 99, 10, "staged") == 10
+    assert next_depth(10, 1000, 100, 10, "staged") == 5
+    assert next_depth(9, 1000, 299, 9, "staged") == 5
+    assert next_depth(10, 1000, 300, 10, "staged") == 1
+    for v in (7, 100, 997):
+        for m in range(0, v + 1, max(1, v // 50)):
+            e, l = next_depth(10, v, m, 10, "exp"), next_depth(10, v, m, 10, "linear")
+            assert e <= l + 1
+            assert e == max(1, min(10, round(10 ** (1 - m / v))))
+    for g in ("linear", "exp", "staged"):  # monotone non-increasing in the update rate
+        ds = [next_depth(10, 500, m, 10, g) for m in range(0, 501)]
+        assert all(a >= b for a, b in zip(ds, ds[1:]))
+    with pytest.raises(ValueError):
+        next_depth(10, 100, 5, 10, "cubic")
