@@ -299,6 +299,56 @@ def run_ablation(args):
           flush=True)
 
 
+def run_guides(args):
+    """Eq. 4 guiding functions on an accelerating camera: the ascending city
+    path with frame k taken at path index k^2 / 30 (speed growing linearly),
+    cached BF16 unified form with each guide; per frame the reuse depth
+    chosen, the update rate (misses / visible), the device time and the PSNR
+    against the same form without the cache."""
+    import torch
+    import paper_2502_14938_b300 as pkg
+    model, frames, _ = build_workload()
+    path = [frames[min(len(frames) - 1, k * k // 30)] for k in range(95)]
+    W, H = path[0][0].width, path[0][0].height
+    ref_r, ref_mid = make_renderer(model, "bf16_unified")
+    ref_r.set_tiling(*args.tile)
+    ref = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    res = {}
+    for guide in ("linear", "exp", "staged"):
+        r = pkg.Renderer(max_views=2, depth_guide=guide, **FORMS[HEADLINE])
+        mid = r.load_model(model)
+        r.set_tiling(*args.tile)
+        for fr in path:  # grow the buffers, then start from an empty cache
+            set_pair(r, mid, *fr)
+            r.render_frame(outs)
+        r.cache_reset()
+        depth, rate, psnr, ms = [], [], [], []
+        for fr in path:
+            set_pair(r, mid, *fr)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = r.render_frame(outs)
+            e1.record()
+            set_pair(ref_r, ref_mid, *fr)
+            ref_r.render_frame(ref, stats=False)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            depth.append(int(st["cache_depth"]))
+            rate.append(st["derived_anchors"] / max(1, st["visible_anchors"]))
+            mse = max(float(sum(torch.mean((o - q) ** 2) for o, q in zip(outs, ref)) / 2), 1e-10)
+            psnr.append(10.0 * np.log10(1.0 / mse))
+        r.close()
+        res[guide] = {"psnr_db_min": min(psnr), "psnr_db_mean": float(np.mean(psnr)),
+                      "update_rate_mean": float(np.mean(rate)), "depth_mean": float(np.mean(depth)),
+                      "ms_mean_with_stats": float(np.mean(ms)), "depth": depth,
+                      "update_rate": [round(x, 4) for x in rate], "psnr_db": [round(x, 2) for x in psnr]}
+    ref_r.close()
+    print(json.dumps({"guides": res, "path": "city ascending path, frame k at index k^2/30 (95 frames)",
+                      "form": HEADLINE, "tiling": list(args.tile),
+                      "psnr": "against the same form without the cache, whole images"}), flush=True)
+
+
 def run_profile(args):
     """Minimal run for profilers: W + K frames from --frame, no extras, with
     the tiling of --tile (launches per frame: launches_per_frame_of)."""
@@ -685,6 +735,8 @@ def run_ours(args, rank, world):
         return run_profile(args)
     if args.ablation:
         return run_ablation(args) if rank == 0 else None
+    if args.guides:
+        return run_guides(args) if rank == 0 else None
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -805,6 +857,8 @@ def main():
                     help="also train the reuse predictor and time the learned form (config.learned_reuse)")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the bench line: the ablation table (one JSON line) at the --tile tiling")
+    ap.add_argument("--guides", action="store_true",
+                    help="instead of the bench line: Eq. 4 guiding functions on an accelerating path (one JSON line)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))
