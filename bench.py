@@ -349,6 +349,58 @@ def run_guides(args):
                       "psnr": "against the same form without the cache, whole images"}), flush=True)
 
 
+def run_sched(args):
+    """Frames displayed per second by the single-host elastic schedule
+    (paper_2502_14938_b300.sched, Alg. 2) with 1-4 fixed workers, each a
+    context of its own on its own stream, rendering the city path's stereo
+    frames (headline form, device images, one synchronize per frame) from a
+    queue that is never empty."""
+    import torch
+    import paper_2502_14938_b300 as pkg
+    from paper_2502_14938_b300.sched import CameraQueue, DisplaySink, ElasticPool
+    model, frames, _ = build_workload()
+    W, H = frames[0][0].width, frames[0][0].height
+
+    ready = []
+
+    def make(wid):
+        r = pkg.Renderer(max_views=2, **FORMS[HEADLINE])
+        mid = r.load_model(model)
+        r.set_tiling(*args.tile)
+        outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+        for fr in frames[:40]:
+            set_pair(r, mid, *fr)
+            r.render_frame(outs)
+        r.synchronize()
+        ready.append(wid)
+
+        def render(fr):
+            set_pair(r, mid, *fr)
+            r.render_frame(outs, stats=False)
+            r.synchronize()
+        return render
+
+    res = {}
+    n_frames = max(400, 20 * args.steps)
+    for n in (1, 2, 3, 4):
+        q, sink = CameraQueue(timeout_s=60.0), DisplaySink()
+        ready.clear()
+        pool = ElasticPool(make, q, sink, min_fps=1, max_fps=1e12, max_workers=n, start_workers=n,
+                           window_s=10.0, period_s=1.0)
+        while len(ready) < n and pool.failed == 0:  # workers load the model and warm up
+            time.sleep(0.01)
+        t0 = time.monotonic()
+        for k in range(n_frames):
+            q.put(frames[k % len(frames)])
+        while len(q) > 0 or len(sink.written) + sink.discarded < n_frames:
+            time.sleep(0.002)
+        dt = time.monotonic() - t0
+        pool.close()
+        res[str(n)] = {"frames_per_s": len(sink.written) / dt, "discarded": sink.discarded, "failed": pool.failed}
+    print(json.dumps({"sched_workers": res, "form": HEADLINE, "tiling": list(args.tile), "frames": n_frames,
+                      "note": "device images; the queue is filled at once, so no camera times out"}), flush=True)
+
+
 def run_profile(args):
     """Minimal run for profilers: W + K frames from --frame, no extras, with
     the tiling of --tile (launches per frame: launches_per_frame_of)."""
@@ -737,6 +789,8 @@ def run_ours(args, rank, world):
         return run_ablation(args) if rank == 0 else None
     if args.guides:
         return run_guides(args) if rank == 0 else None
+    if args.sched:
+        return run_sched(args) if rank == 0 else None
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -859,6 +913,8 @@ def main():
                     help="instead of the bench line: the ablation table (one JSON line) at the --tile tiling")
     ap.add_argument("--guides", action="store_true",
                     help="instead of the bench line: Eq. 4 guiding functions on an accelerating path (one JSON line)")
+    ap.add_argument("--sched", action="store_true",
+                    help="instead of the bench line: frames/s of the elastic schedule with 1-4 workers (one JSON line)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
     world = int(os.environ.get("WORLD_SIZE", "1"))
