@@ -44,6 +44,52 @@ def peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "src": "fallback"}
 
 
+class _CtypesNvml:
+    """The few read-only NVML queries the clock sampler makes, through the
+    driver's libnvidia-ml (for hosts without the Python NVML binding)."""
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, r):
+        if r != 0:
+            raise RuntimeError(f"NVML error {r}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self.C.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(self.C.c_char_p(uuid.encode()), self.C.byref(h)))
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.C.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.C.c_uint(i), self.C.byref(h)))
+        return h
+
+    def _clock(self, fn, h, kind):
+        v = self.C.c_uint()
+        self._ok(fn(h, self.C.c_int(kind), self.C.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.C.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.C.byref(v)))
+        return v.value
+
+
 class ClockSampler:
     """SM clocks and clock-event (throttle) reasons sampled during the timed
     region: read in-process through NVML every millisecond (the timed region
@@ -63,11 +109,14 @@ class ClockSampler:
         self.stop = threading.Event()
 
     def _nvml_handle(self):
-        import pynvml
         import torch
-        pynvml.nvmlInit()
         uuid = str(torch.cuda.get_device_properties(self.idx).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        try:
+            import pynvml
+        except ImportError:
+            pynvml = _CtypesNvml()  # the driver's libnvidia-ml through its C API
+        pynvml.nvmlInit()
         try:
             return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
         except Exception:
