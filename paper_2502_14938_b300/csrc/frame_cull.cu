@@ -105,7 +105,7 @@ constexpr int CULL_TILE = CULL_NT * CULL_IPT;
 constexpr int CULL_MAXD = MAXV;  // derivation views of one model (look-back words per tile)
 constexpr int CULL_GROUP = 8;    // views tested together (one warp walks back per view)
 
-__global__ void __launch_bounds__(CULL_NT) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
+__global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
                                                   uint32_t* const* __restrict__ vis, unsigned long long* status) {
   __shared__ int s_d[CULL_MAXD];
   __shared__ int s_nd;
