@@ -36,18 +36,20 @@ __device__ __forceinline__ float anchor_dir(const ModelDev& md, const CamDev& ca
   return pinned_dir(x, cam.pc, cam.pc_lo, d);
 }
 
-// rw: predictor weights (learned form), else unused.
+// rw: predictor weights (learned form), else unused.  The depth-rule form is
+// its own instantiation so it does not carry the predictor's registers.
+template <bool LEARNED>
 __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ caches, int c,
                                                      const FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                      const ModelDev* __restrict__ models,
-                                                     const float* __restrict__ rw, int learned) {
-  __shared__ float s_w[RPARAM];
+                                                     const float* __restrict__ rw) {
+  __shared__ float s_w[LEARNED ? RPARAM : 1];
   const CacheDev cd = caches[c];
   const uint32_t V = fd->vis_count[c];
   const uint32_t t = cd.state[CS_T], depth = cd.state[CS_DEPTH], D = cd.state[CS_DMAX];
   const uint32_t* ids = vis[c];
   const uint32_t stride = gridDim.x * blockDim.x;
-  if (learned) {
+  if (LEARNED) {
     for (int i = threadIdx.x; i < RPARAM; i += blockDim.x) s_w[i] = rw[i];
     __syncthreads();
   }
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
     const uint32_t age = valid ? t - cd.slot_frame[s] : 0xFFFFFFFFu;
     valid = valid && age <= D;
     bool hit;
-    if (learned) {
+    if (LEARNED) {
       hit = false;
       if (valid) {
         float dn[3], z[RZ];
@@ -82,7 +84,6 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
   if (blockIdx.x == 0 && threadIdx.x == 0) cd.state[CS_SCAN_N] = cd.S + V;
 }
 
-// Eq. 4 with the linear guide, from this frame's visible and decoded counts.
 // Eq. 4 with the guiding function of the configuration (gsc_depth_guide).
 __device__ __forceinline__ uint32_t next_depth(uint32_t depth, uint32_t V, uint32_t m, uint32_t D, uint32_t guide) {
   if (V == 0) return depth;
@@ -206,7 +207,10 @@ void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, Fr
   for (int c = 0; c < n_caches; ++c) {
     if (!host[c].active) continue;
     const CacheDev& h = host[c];
-    k_cache_probe<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w, learned ? 1 : 0);
+    if (learned)
+      k_cache_probe<true><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
+    else
+      k_cache_probe<false><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
     if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
     launch_scan_u32(h.flags, nullptr, h.state + CS_SCAN_N, h.ranks, h.state + CS_SCAN_TOT, scan_status, fd,
                     SLOT_CACHE + 2 * c, n_sm, s, h.free_list, h.S);
