@@ -732,7 +732,8 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
     return code;
   };
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(GSC_ERR_CUDA);
-  if (prepare_derive_f32() != cudaSuccess || prepare_derive_tc() != cudaSuccess) return bail(GSC_ERR_CUDA);
+  if (prepare_derive_f32() != cudaSuccess || prepare_derive_tc() != cudaSuccess || prepare_sort() != cudaSuccess)
+    return bail(GSC_ERR_CUDA);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (cudaMalloc((void**)&ctx->d_tabs, dview_set_bytes() * MAX_MODELS) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_ptab, proj_tab_bytes()) != cudaSuccess)

@@ -405,6 +405,7 @@ void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* v
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();
 cudaError_t prepare_derive_tc();
+cudaError_t prepare_sort();
 void launch_to_bf16(const float* src, void* dst, size_t n, cudaStream_t s);
 // Per-frame tables (defined in derive_common.cuh): the decoder's view set of
 // each model and the projection's per-view table, written by k_tables.

@@ -1,6 +1,6 @@
 // LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits,
 // "onesweep" style: one kernel computes the digit histograms of every pass;
-// each pass is then one kernel in which a block ranks a 4096-key tile
+// each pass is then one kernel in which a block ranks a tile of keys
 // (warp match + per-warp digit counters, stable), obtains its per-digit
 // global offsets by a decoupled look-back over the preceding tiles, and
 // scatters through shared memory so that global writes are mostly
@@ -12,13 +12,13 @@
 // once, tile t walks back over ~t/16 aggregate windows and the look-back
 // traffic grows with the square of the tiles in flight; fewer resident
 // blocks let earlier tiles finish their prefixes first (measured: 4 or 3
-// blocks per SM and a 16- or 32-word window were slower).
+// blocks per SM and a 16- or 32-word window were slower).  4096-key tiles
+// are ranked by 512 threads (16 warps of 8 keys each: half the serial
+// match rounds of 256 threads x 16 keys), 2048-key tiles by 256 threads.
 #include "gsc_internal.cuh"
 
 namespace gsc {
 
-constexpr int SORT_NT = 256;
-constexpr int SORT_WARPS = SORT_NT / 32;
 
 __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_ptr,
                                                    int npass, int drop_invalid, uint32_t* __restrict__ hist,
@@ -45,43 +45,51 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ 
   }
 }
 
-template <int SORT_IPT>
-__global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                       uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                       const uint32_t* __restrict__ n_ptr, int shift,
-                                                       const uint32_t* __restrict__ hist_p, int drop_invalid,
-                                                       unsigned long long* status, FrameDev* fd, int slot) {
-  constexpr int SORT_TILE = SORT_NT * SORT_IPT;
+// NT threads per block (NT / 32 warps each ranking 32 x IPT keys), tiles of
+// NT x IPT keys; the keys and values of a tile are staged in dynamic shared
+// memory.  Threads 0..255 own one digit each for the histograms, scans and
+// the look-back.
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                  const uint32_t* __restrict__ n_ptr, int shift,
+                                                  const uint32_t* __restrict__ hist_p, int drop_invalid,
+                                                  unsigned long long* status, FrameDev* fd, int slot) {
+  constexpr int TILE = NT * IPT, WARPS = NT / 32;
+  static_assert(NT >= 256, "one thread per digit");
   __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_whist[SORT_WARPS][256];
+  __shared__ uint32_t s_whist[WARPS][256];
   __shared__ uint32_t s_dstart[256];
   __shared__ uint32_t s_gofs[256];
-  __shared__ uint32_t s_keys[SORT_TILE];
-  __shared__ uint32_t s_vals[SORT_TILE];
-  __shared__ uint32_t s_warp[SORT_NT / 32 + 1];
+  __shared__ uint32_t s_warp[NT / 32 + 1];
   __shared__ uint32_t s_tile;
+  extern __shared__ uint32_t s_kv[];  // keys [TILE], values [TILE]
+  uint32_t* s_keys = s_kv;
+  uint32_t* s_vals = s_kv + TILE;
 
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const bool dig = tid < 256u;
   {
     uint32_t tot;
-    s_gbase[tid] = block_exclusive_scan<SORT_NT>(hist_p[tid], s_warp, &tot);
+    const uint32_t g = block_exclusive_scan<NT>(dig ? hist_p[tid] : 0u, s_warp, &tot);
+    if (dig) s_gbase[tid] = g;
   }
   const uint32_t n = *n_ptr;
-  const uint32_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+  const uint32_t ntiles = (n + TILE - 1) / TILE;
   const uint32_t epoch = fd->frame * 64u + (uint32_t)slot;
   const uint32_t spin = fd->spin_limit;
   const uint32_t lt_mask = (1u << lane) - 1u;
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&fd->ctr[slot], 1u);
-    for (int i = tid; i < SORT_WARPS * 256; i += SORT_NT) (&s_whist[0][0])[i] = 0;
+    for (int i = tid; i < WARPS * 256; i += NT) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= ntiles) break;
-    const uint32_t base = t * SORT_TILE + warp * 32u * SORT_IPT;
-    uint32_t key[SORT_IPT], val[SORT_IPT], rank[SORT_IPT];
+    const uint32_t base = t * TILE + warp * 32u * IPT;
+    uint32_t key[IPT], val[IPT], rank[IPT];
 #pragma unroll
-    for (int i = 0; i < SORT_IPT; ++i) {
+    for (int i = 0; i < IPT; ++i) {
       const uint32_t idx = base + (uint32_t)i * 32u + lane;
       bool valid = idx < n;
       uint32_t k = valid ? kin[idx] : INVALID_KEY;
@@ -100,18 +108,21 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
     __syncthreads();
     // per digit: warp-exclusive offsets, tile total
     uint32_t tot_d = 0;
-    {
+    if (dig) {
       const uint32_t d = tid;
 #pragma unroll
-      for (int w = 0; w < SORT_WARPS; ++w) {
+      for (int w = 0; w < WARPS; ++w) {
         const uint32_t c = s_whist[w][d];
         s_whist[w][d] = tot_d;
         tot_d += c;
       }
     }
     uint32_t tile_total;
-    s_dstart[tid] = block_exclusive_scan<SORT_NT>(tot_d, s_warp, &tile_total);
     {
+      const uint32_t ds = block_exclusive_scan<NT>(tot_d, s_warp, &tile_total);
+      if (dig) s_dstart[tid] = ds;
+    }
+    if (dig) {
       const uint32_t d = tid;
       unsigned long long* w = status + (size_t)t * 256 + d;
       uint32_t pre = 0;
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < SORT_IPT; ++i) {
+    for (int i = 0; i < IPT; ++i) {
       if (rank[i] == 0xFFFFFFFFu) continue;
       const uint32_t d = (key[i] >> shift) & 0xFFu;
       const uint32_t p = s_dstart[d] + s_whist[warp][d] + rank[i];
@@ -134,7 +145,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
       s_vals[p] = val[i];
     }
     __syncthreads();
-    for (uint32_t p = tid; p < tile_total; p += SORT_NT) {
+    for (uint32_t p = tid; p < tile_total; p += NT) {
       const uint32_t k = s_keys[p];
       const uint32_t d = (k >> shift) & 0xFFu;
       const uint32_t o = s_gofs[d] + (p - s_dstart[d]);
@@ -143,6 +154,19 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_pass(const uint32_t* __restric
     }
     __syncthreads();
   }
+}
+
+template <int NT, int IPT>
+void sort_pass(int blocks, cudaStream_t s, const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
+               const uint32_t* n_ptr, int shift, const uint32_t* hist_p, int drop_invalid, unsigned long long* status,
+               FrameDev* fd, int slot) {
+  k_sort_pass<NT, IPT><<<blocks, NT, 2 * NT * IPT * sizeof(uint32_t), s>>>(kin, vin, kout, vout, n_ptr, shift, hist_p,
+                                                                           drop_invalid, status, fd, slot);
+}
+
+cudaError_t prepare_sort() {
+  return cudaFuncSetAttribute(k_sort_pass<512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * 512 * 8 * sizeof(uint32_t)));
 }
 
 // Sort n_in (from device memory) pairs on bits [0, bits).  drop_invalid:
@@ -170,11 +194,10 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
     if (ipt == 8 && p > 0)
-      k_sort_pass<8><<<n_sm * 2, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
-                                                  p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
+      sort_pass<256, 8>(n_sm * 2, s, ci, cv, ok, ov, np, 8 * p, hist + p * 256, 0, sb.status, fd, slot_base + p);
     else
-      k_sort_pass<16><<<n_sm * 2, SORT_NT, 0, s>>>(ci, cv, ok, ov, np, 8 * p, hist + p * 256,
-                                                   p == 0 ? drop_invalid : 0, sb.status, fd, slot_base + p);
+      sort_pass<512, 8>(n_sm * 2, s, ci, cv, ok, ov, np, 8 * p, hist + p * 256, p == 0 ? drop_invalid : 0, sb.status, fd,
+                        slot_base + p);
     ci = ok;
     cv = ov;
   }
