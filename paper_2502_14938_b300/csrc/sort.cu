@@ -14,7 +14,8 @@
 // blocks let earlier tiles finish their prefixes first (measured: 4 or 3
 // blocks per SM and a 16- or 32-word window were slower).  4096-key tiles
 // are ranked by 512 threads (16 warps of 8 keys each: half the serial
-// match rounds of 256 threads x 16 keys), 2048-key tiles by 256 threads.
+// match rounds of 256 threads x 16 keys), 2048-key tiles by 512 threads of
+// 4 keys (1024 threads of 4 keys for 4096-key tiles were slower).
 #include "gsc_internal.cuh"
 
 namespace gsc {
@@ -194,7 +195,7 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
     uint32_t* ov = (p % 2 == 0) ? v0 : v1;
     const uint32_t* np = (p == 0 || !drop_invalid) ? n_in : n_valid_out;
     if (ipt == 8 && p > 0)
-      sort_pass<256, 8>(n_sm * 2, s, ci, cv, ok, ov, np, 8 * p, hist + p * 256, 0, sb.status, fd, slot_base + p);
+      sort_pass<512, 4>(n_sm * 2, s, ci, cv, ok, ov, np, 8 * p, hist + p * 256, 0, sb.status, fd, slot_base + p);
     else
       sort_pass<512, 8>(n_sm * 2, s, ci, cv, ok, ov, np, 8 * p, hist + p * 256, p == 0 ? drop_invalid : 0, sb.status, fd,
                         slot_base + p);
