@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
         tot_d += c;
       }
     }
+    if (dig)  // publish this tile's counts before the block scan
+      st_relaxed_u64(status + (size_t)t * 256 + tid, lb_pack(epoch, t == 0 ? 2u : 1u, tot_d));
     uint32_t tile_total;
     {
       const uint32_t ds = block_exclusive_scan<NT>(tot_d, s_warp, &tile_total);
@@ -125,14 +127,10 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
     }
     if (dig) {
       const uint32_t d = tid;
-      unsigned long long* w = status + (size_t)t * 256 + d;
       uint32_t pre = 0;
-      if (t == 0) {
-        st_relaxed_u64(w, lb_pack(epoch, 2u, tot_d));
-      } else {
-        st_relaxed_u64(w, lb_pack(epoch, 1u, tot_d));
+      if (t > 0) {
         pre = lb_exclusive(status + d, 256, t, epoch, spin, &fd->err);
-        st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot_d));
+        st_relaxed_u64(status + (size_t)t * 256 + d, lb_pack(epoch, 2u, pre + tot_d));
       }
       s_gofs[d] = s_gbase[d] + pre;
     }
