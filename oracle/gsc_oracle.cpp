@@ -630,7 +630,13 @@ int orc_render(const double* rec, const float* depth32, const int64_t* gid, int6
       const double q = g[3] * dx * dx + 2.0 * g[4] * dx * dy + g[5] * dy * dy;
       const double araw = g[6] * std::exp(-0.5 * q);
       const double al = std::min(0.99, araw);
-      const double ma = std::fabs(std::log(araw * 255.0));
+      // distance of the 1/255 decision from its threshold in log-opacity,
+      // less what float32 pixel coordinates of the mean can move it: an
+      // error e in the mean shifts q/2 by up to |grad_mean(q/2)|_1 e, and a
+      // float32 projection places the mean within a few ulps of its value
+      const double grad = std::fabs(g[3] * dx + g[4] * dy) + std::fabs(g[4] * dx + g[5] * dy);
+      const double epos = std::ldexp(std::max(std::max(std::fabs(g[1]), std::fabs(g[2])), 16.0), -21);
+      const double ma = std::fabs(std::log(araw * 255.0)) - grad * epos;
       if (ma < mg) mg = ma;
       if (al < 1.0 / 255.0) continue;
       const double tt = T * (1.0 - al);
