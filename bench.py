@@ -348,6 +348,41 @@ def run_ablation(args):
           flush=True)
 
 
+def run_octree(args):
+    """Octree-GS level selection (per-anchor level offsets and the level
+    fade) against the plain distance rule on the same city model: frames/s,
+    the culling stage and visible anchors, and each form's PSNR against the
+    float64 oracle of the octree model (frames rendered in path order)."""
+    import torch
+    import gen
+    import oracle
+    model, frames, t_gen = build_workload()
+    sigma, beta = 0.5, 0.5
+    octree = gen.with_level_offsets(model, sigma=sigma, beta=beta)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tiling = tuple(args.tile)
+    tl = {"tile_w": tiling[0], "tile_h": tiling[1], "blocks_per_sm": tiling[2]}
+    refs = {f: [oracle.render_view(octree, cam)[0][0] for cam in frames[f]] for f in args.psnr_frames}
+    rows = []
+    for name, m in (("distance LOD (plain rule)", model), ("Octree-GS offsets + fade", octree)):
+        for form in (HEADLINE, "plain"):
+            r, mid, outs, ms, wall = time_form(m, frames, form, args.steps, args.warmup, flush, 1, tiling=tiling)
+            row = {"model": name, "form": form, "fps": 1e3 / float(ms.mean()), "ms_mean": float(ms.mean()),
+                   "p99_ms": float(np.percentile(ms, 99))}
+            if m is octree:
+                row["quality_vs_octree_oracle"], _ = form_quality(r, mid, outs, frames, refs)
+            r.close()
+            stage, per_frame = stage_profile(m, frames, form, min(args.steps, len(frames)), flush, tl, count=False)
+            row["cull+plan_ms"] = stage["cull+plan"]
+            row["derive+project_ms"] = stage["derive+project"]
+            row["visible_anchors"] = per_frame["visible_anchors"]
+            rows.append(row)
+    print(json.dumps({"octree": rows, "workload": "city 2M anchors, stereo 1920x1080, 300-frame ascending path",
+                      "level_offsets": f"N(0, {sigma}^2) clipped to 3 sigma (synthetic: no trained offsets)",
+                      "lod_blend_levels": beta, "steps": args.steps, "warmup": args.warmup, "tiling": list(tiling),
+                      "psnr_frames": sorted(refs)}), flush=True)
+
+
 def run_guides(args):
     """Eq. 4 guiding functions on an accelerating camera: the ascending city
     path with frame k taken at path index k^2 / 30 (speed growing linearly),
@@ -840,6 +875,8 @@ def run_ours(args, rank, world):
         return run_guides(args) if rank == 0 else None
     if args.sched:
         return run_sched(args) if rank == 0 else None
+    if args.octree:
+        return run_octree(args) if rank == 0 else None
     model, frames, t_gen = build_workload()
     W, H = frames[0][0].width, frames[0][0].height
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -962,6 +999,8 @@ def main():
                     help="instead of the bench line: the ablation table (one JSON line) at the --tile tiling")
     ap.add_argument("--guides", action="store_true",
                     help="instead of the bench line: Eq. 4 guiding functions on an accelerating path (one JSON line)")
+    ap.add_argument("--octree", action="store_true",
+                    help="instead of the bench line: Octree-GS level offsets + fade vs the plain LOD rule (one JSON line)")
     ap.add_argument("--sched", action="store_true",
                     help="instead of the bench line: frames/s of the elastic schedule with 1-4 workers (one JSON line)")
     args = ap.parse_args()

@@ -7,7 +7,7 @@ import numpy as np
 
 from .rng import Stream, splitmix64, stream_seed
 from .scenes import (FEAT_DIM, HIDDEN, IN_DIM, K_GAUSS, Model, city_scene,
-                     glorot_mlps, head_out_dims, reuse_mlp_init, tiny_scene)
+                     glorot_mlps, head_out_dims, reuse_mlp_init, tiny_scene, with_level_offsets)
 from .cameras import (Camera, HeadPose, city_path, look_rotation, path_extent,
                       pinhole, reuse_path, stereo_frames, stereo_pair, tiny_camera)
 
@@ -26,7 +26,7 @@ __all__ = [
     "Stream", "splitmix64", "stream_seed", "FEAT_DIM", "HIDDEN", "IN_DIM", "K_GAUSS",
     "Model", "city_scene", "glorot_mlps", "head_out_dims", "reuse_mlp_init", "tiny_scene", "Camera",
     "HeadPose", "city_path", "look_rotation", "path_extent", "pinhole", "stereo_frames",
-    "stereo_pair", "tiny_camera", "city_workload", "reuse_path", "multiviewer_workload", "MV_SCENES", "MV_VIEWERS",
+    "stereo_pair", "tiny_camera", "with_level_offsets", "city_workload", "reuse_path", "multiviewer_workload", "MV_SCENES", "MV_VIEWERS",
 ]
 
 

@@ -11,8 +11,8 @@ All values are drawn in float64 from `gen.rng` and cast to float32 once.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
-from typing import List
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
 
 import numpy as np
 
@@ -44,6 +44,8 @@ class Model:
     b2: List[np.ndarray] = field(default_factory=list)   # 3 x float32 [out_h]
     k: int = K_GAUSS
     name: str = ""
+    level_offset: Optional[np.ndarray] = None  # float32 [N] per-anchor level offsets (Octree-GS), or None
+    lod_blend: float = 0.0     # level fade width beta in levels (0: levels switch on at once)
 
     @property
     def n(self) -> int:
@@ -56,11 +58,22 @@ class Model:
         assert self.offs.shape == (n, k, 3) and self.offs.dtype == np.float32
         assert self.scale.shape == (n,) and self.scale.dtype == np.float32
         assert self.level.shape == (n,) and self.level.dtype == np.uint8
+        if self.level_offset is not None:
+            assert self.level_offset.shape == (n,) and self.level_offset.dtype == np.float32
         for h, od in enumerate(head_out_dims(k)):
             assert self.W1[h].shape == (IN_DIM, HIDDEN)
             assert self.b1[h].shape == (HIDDEN,)
             assert self.W2[h].shape == (HIDDEN, od)
             assert self.b2[h].shape == (od,)
+
+
+def with_level_offsets(m: Model, sigma: float = 0.3, beta: float = 0.5, seed: int = 21) -> Model:
+    """A copy of `m` with Octree-GS style per-anchor level offsets.  Trained
+    offsets are not available; these are drawn N(0, sigma^2), clipped to
+    [-3 sigma, 3 sigma], with fade width `beta` levels."""
+    st = Stream(seed, "level_offset")
+    d = np.clip(st.normal(m.n) * sigma, -3.0 * sigma, 3.0 * sigma).astype(np.float32)
+    return replace(m, level_offset=d, lod_blend=float(beta), name=(m.name + "+octree") if m.name else "octree")
 
 
 def glorot_mlps(seed: int, k: int = K_GAUSS):

@@ -132,6 +132,23 @@ typedef struct {
   const float* b1[3];        /* per head [32] */
   const float* W2[3];        /* per head [32][out_h], out_h = k, 3k, 7k */
   const float* b2[3];        /* per head [out_h] */
+  /* Octree-GS level selection (Sec. 2: the octree's levels of detail chosen
+   * by distance).  Optional; NULL / 0 keep the plain distance rule above.
+   * level_offset: [N] learned per-anchor level offsets Delta_a, finite,
+   *   |Delta_a| <= 8.  An anchor of level l >= 1 is drawn iff
+   *   l <= log2(lod_dmax / d) + Delta_a, i.e. d <= r_a with the float32
+   *   radius r_a = (float)ldexp((double)lod_dmax * exp2((double)Delta_a), -l),
+   *   evaluated once at load in float64 (so the decision is a float32
+   *   comparison d^2 <= r_a^2, taken in the same order as the plain rule).
+   * lod_blend: beta >= 0, in levels.  beta > 0 fades in an anchor of level
+   *   l >= 1 as the camera approaches: its Gaussians' opacities are scaled by
+   *   w = min(1, u / beta), u = log2(r_a / d) >= 0 (its margin in levels
+   *   inside the switching distance; d^2 is the culling test's float32
+   *   squared distance), so an anchor does not pop in when its level is
+   *   switched on.  Applied after derivation and the cache. */
+  const float* level_offset;
+  float lod_blend;
+  uint32_t reserved0;
 } gsc_model_desc;
 
 /* Pinhole camera: camera coords c = R x + t (x right, y down, z forward),

@@ -50,7 +50,8 @@ class OrcModel(C.Structure):
                 ("pos", C.c_void_p), ("feat", C.c_void_p), ("offs", C.c_void_p),
                 ("scale", C.c_void_p), ("level", C.c_void_p), ("lod_dmax", C.c_float),
                 ("pad1", C.c_int32), ("W1", C.c_void_p * 3), ("b1", C.c_void_p * 3),
-                ("W2", C.c_void_p * 3), ("b2", C.c_void_p * 3)]
+                ("W2", C.c_void_p * 3), ("b2", C.c_void_p * 3),
+                ("level_offset", C.c_void_p), ("lod_blend", C.c_float), ("pad2", C.c_int32)]
 
 
 class OrcQuant(C.Structure):
@@ -71,6 +72,8 @@ def lib():
         L.orc_unified_camera.restype = C.c_int
         L.orc_cull.argtypes = [P, P, P, C.c_int64]
         L.orc_cull.restype = C.c_int64
+        L.orc_lod_weight.argtypes = [P, P, P, C.c_int64, C.c_double, P]
+        L.orc_lod_weight.restype = C.c_int
         L.orc_derive.argtypes = [P, P, P, C.c_int64, P, P, P, P]
         L.orc_derive.restype = C.c_int
         L.orc_quat_to_rot.argtypes = [P, P]
@@ -170,6 +173,9 @@ class ModelRef:
         s.pos, s.feat, s.offs = arr(m.pos, np.float32), arr(m.feat, np.float32), arr(m.offs, np.float32)
         s.scale, s.level = arr(m.scale, np.float32), arr(m.level, np.uint8)
         s.lod_dmax = float(m.lod_dmax)
+        lo = getattr(m, "level_offset", None)
+        s.level_offset = arr(lo, np.float32) if lo is not None else None
+        s.lod_blend = float(getattr(m, "lod_blend", 0.0))
         for h in range(3):
             s.W1[h], s.b1[h] = arr(m.W1[h], np.float32), arr(m.b1[h], np.float32)
             s.W2[h], s.b2[h] = arr(m.W2[h], np.float32), arr(m.b2[h], np.float32)
@@ -224,11 +230,33 @@ def derive(model, view_pos: np.ndarray, ids: np.ndarray, quant: Optional[OrcQuan
     return (attrs, kept, raw) if want_raw else (attrs, kept)
 
 
-def project_records(model, cam, ids: np.ndarray, attrs: np.ndarray, kept: Optional[np.ndarray]):
-    """Projected records [n*k, 16] and pinned float32 depths [n*k]."""
+def lod_weight(model, derive_cam, ids: np.ndarray) -> np.ndarray:
+    """Octree-GS level fade per anchor (orc_lod_weight): w = clamp(u / beta,
+    0, 1) with u = log2(r_a / d) the anchor's levels inside its switching
+    distance, from the culling radius and the culling test's float32 d^2;
+    level 0 and beta = 0 give w = 1."""
+    ids = np.ascontiguousarray(ids, np.uint32)
+    w = np.ones(ids.shape[0], np.float64)
+    beta = float(getattr(model, "lod_blend", 0.0))
+    if beta > 0.0 and ids.shape[0]:
+        c = to_cam(derive_cam)
+        assert lib().orc_lod_weight(mref(model).ref, C.byref(c), _p(ids), ids.shape[0], beta, _p(w)) == 0
+    return w
+
+
+def project_records(model, cam, ids: np.ndarray, attrs: np.ndarray, kept: Optional[np.ndarray], derive_cam=None):
+    """Projected records [n*k, 16] and pinned float32 depths [n*k].  With a
+    level fade (model.lod_blend > 0) the opacities are first scaled by
+    lod_weight of the derivation camera `derive_cam` (default: `cam`)."""
     mr = mref(model)
     ids = np.ascontiguousarray(ids, np.uint32)
     n, k = ids.shape[0], model.k
+    if float(getattr(model, "lod_blend", 0.0)) > 0.0:
+        w = lod_weight(model, cam if derive_cam is None else derive_cam, ids)
+        attrs = np.array(attrs, np.float64).reshape(n, k, -1)
+        attrs[:, :, 0] *= w[:, None]
+        if kept is not None:
+            kept = (np.asarray(kept).reshape(n, k) != 0) & (w[:, None] > 0.0)
     rec = np.zeros((n * k, REC), np.float64)
     d32 = np.zeros(n * k, np.float32)
     c = to_cam(cam)
@@ -387,7 +415,7 @@ def view_gaussians(model, cam, derive_cam=None, quant=None, attrs_override=None)
         attrs, kept = attrs_override(ids)
     else:
         attrs, kept = derive(model, camera_center(dc), ids, quant)
-    rec, d32 = project_records(model, cam, ids, attrs, kept)
+    rec, d32 = project_records(model, cam, ids, attrs, kept, derive_cam=dc)
     gid = (ids.astype(np.int64)[:, None] * model.k + np.arange(model.k)[None, :]).reshape(-1)
     return ViewResult(ids=ids, attrs=attrs, kept=kept, rec=rec, depth32=d32, gid=gid)
 

@@ -189,9 +189,10 @@ def collect_samples(model, dcam, sim: CacheSim, quant=None):
     return v, z, P.label(cached, fresh), P.label_margin(cached, fresh)
 
 
-def project_view(model, cam, ids, attrs, kept):
-    """Records of one camera from attributes of the visible anchors."""
+def project_view(model, cam, ids, attrs, kept, derive_cam=None):
+    """Records of one camera from attributes of the visible anchors (of the
+    derivation camera `derive_cam`, which a level fade measures from)."""
     import oracle
-    rec, d32 = oracle.project_records(model, cam, ids, attrs, kept)
+    rec, d32 = oracle.project_records(model, cam, ids, attrs, kept, derive_cam=derive_cam)
     gid = (np.asarray(ids, np.int64)[:, None] * model.k + np.arange(model.k)[None, :]).reshape(-1)
     return oracle.ViewResult(ids=ids, attrs=attrs, kept=kept, rec=rec, depth32=d32, gid=gid)

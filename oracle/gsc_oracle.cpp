@@ -55,6 +55,9 @@ struct orc_model {
   const float* b1[3];     // [32]
   const float* W2[3];     // [32][out_h]
   const float* b2[3];     // [out_h]
+  const float* level_offset;  // [n] Octree-GS per-anchor level offsets, or null
+  float lod_blend;            // level fade width (applied by the Python layer)
+  int32_t pad2;
 };
 
 // Quantisation of the decoder MLPs (precision forms).  mode 0: none (fp64);
@@ -180,7 +183,12 @@ int orc_unified_camera(const orc_camera* L, const orc_camera* Rr, orc_camera* ou
 // Anchor filtering (Sec. 3.2, Alg. 1 "anchors indexing and filtering"):
 // frustum test with a 1.3 guard band and the distance LOD rule (an anchor of
 // level l >= 1 is drawn iff its distance d to the camera satisfies
-// d <= d_max 2^-l; level 0 is always drawn).  Decision-pinned float32:
+// d <= d_max 2^-l; level 0 is always drawn).  With Octree-GS level offsets
+// (reading of Sec. 2's distance-chosen octree levels) level l >= 1 is drawn
+// iff l <= log2(d_max / d) + Delta_a, i.e. d <= d_max 2^(Delta_a - l); the
+// threshold is that radius taken once in float64 and rounded to float32,
+//   thr = (float) ldexp(d_max * exp2(Delta_a), -l).
+// Decision-pinned float32:
 //   c = ((R0 x + R1 y) + R2 z) + t0   (and likewise for rows 1, 2)
 //   c.z > znear  and |c.x| <= (1.3 tan_x) c.z  and |c.y| <= (1.3 tan_y) c.z,
 //   tan_x = (0.5 W) / fx;   d^2 = (dx dx + dy dy) + dz dz <= (d_max 2^-l)^2.
@@ -208,7 +216,11 @@ int64_t orc_cull(const orc_model* m, const orc_camera* c, uint32_t* ids, int64_t
       float d2 = dx * dx;
       d2 = d2 + dy * dy;
       d2 = d2 + dz * dz;
-      float thr = std::ldexp(m->lod_dmax, -l);
+      float thr;
+      if (m->level_offset)
+        thr = (float)std::ldexp((double)m->lod_dmax * std::exp2((double)m->level_offset[a]), -l);
+      else
+        thr = std::ldexp(m->lod_dmax, -l);
       v = d2 <= thr * thr;
     }
     vis[a] = v ? 1 : 0;
@@ -220,6 +232,40 @@ int64_t orc_cull(const orc_model* m, const orc_camera* c, uint32_t* ids, int64_t
       ++cnt;
     }
   return cnt;
+}
+
+// Octree-GS level fade (reading: a level is switched on gradually).  For a
+// visible anchor of level l >= 1, u = log2(r_a / d) is how many levels it
+// lies inside its switching distance; its Gaussians' opacities are scaled by
+// w = clamp(u / beta, 0, 1); level 0 (and beta = 0) give w = 1.  r_a is the
+// culling radius and d^2 the culling test's pinned float32 squared distance
+// (so u >= 0 for every kept anchor); u itself is float64:
+//   u = log1p((r_a^2 - d^2) / d^2) / (2 ln 2).
+int orc_lod_weight(const orc_model* m, const orc_camera* c, const uint32_t* ids, int64_t n, double beta,
+                   double* w) {
+  if (!m || !c || (n > 0 && (!ids || !w))) return -1;
+  double p64[3];
+  center64(c, p64);
+  const float pcx = (float)p64[0], pcy = (float)p64[1], pcz = (float)p64[2];
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t a = ids[i];
+    const int l = m->level[a];
+    if (!(beta > 0.0) || l == 0) {
+      w[i] = 1.0;
+      continue;
+    }
+    const double delta = m->level_offset ? (double)m->level_offset[a] : 0.0;
+    const float r = (float)std::ldexp((double)m->lod_dmax * std::exp2(delta), -l);
+    const float x = m->pos[3 * (size_t)a], y = m->pos[3 * (size_t)a + 1], z = m->pos[3 * (size_t)a + 2];
+    float dx = x - pcx, dy = y - pcy, dz = z - pcz;
+    float d2 = dx * dx;
+    d2 = d2 + dy * dy;
+    d2 = d2 + dz * dz;
+    const double r2 = (double)r * (double)r;  // exact
+    const double u = std::log1p((r2 - (double)d2) / (double)d2) / (2.0 * std::log(2.0));
+    w[i] = std::min(1.0, std::max(0.0, u / beta));
+  }
+  return 0;
 }
 
 // Derivation, Eq. 3 (Sec. 3.1): for each anchor a,

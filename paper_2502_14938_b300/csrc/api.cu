@@ -29,7 +29,7 @@ struct DevBuf {
 
 struct ModelHost {
   uint32_t n = 0;
-  DevBuf px, py, pz, level, feat, offs, scale, w32, feat_bf16, w_tc, feat_fp8, w_tc8;
+  DevBuf px, py, pz, level, lod_r, feat, offs, scale, w32, feat_bf16, w_tc, feat_fp8, w_tc8;
   ModelDev dev{};
 };
 
@@ -359,7 +359,9 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (tm) cudaEventRecord(ctx->ev_stage[0], s);
   launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
-  for (int m : ctx->models_used) launch_cull(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm, s);
+  for (int m : ctx->models_used)
+    launch_cull(ctx->d_models, m, ctx->models[m].dev.lod_r != nullptr, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm,
+                s);
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
   const bool collect = caches && (ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && !replay;
@@ -772,7 +774,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   invalidate_graph(ctx);
   for (auto& m : ctx->models) {
-    dfree(m.px.p); dfree(m.py.p); dfree(m.pz.p); dfree(m.level.p);
+    dfree(m.px.p); dfree(m.py.p); dfree(m.pz.p); dfree(m.level.p); dfree(m.lod_r.p);
     dfree(m.feat.p); dfree(m.offs.p); dfree(m.scale.p); dfree(m.w32.p);
     dfree(m.feat_bf16.p); dfree(m.w_tc.p); dfree(m.feat_fp8.p); dfree(m.w_tc8.p);
   }
@@ -828,6 +830,11 @@ int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out
   if (!(d->lod_dmax >= 0.f) || !std::isfinite(d->lod_dmax)) return fail(ctx, GSC_ERR_INVALID_ARG, "bad lod_dmax");
   for (size_t i = 0; i < n; ++i)
     if (d->level[i] >= d->n_levels) return fail(ctx, GSC_ERR_INVALID_ARG, "level >= n_levels at anchor %zu", i);
+  if (!(d->lod_blend >= 0.f) || !(d->lod_blend <= 32.f)) return fail(ctx, GSC_ERR_INVALID_ARG, "bad lod_blend");
+  if (d->level_offset)
+    for (size_t i = 0; i < n; ++i)
+      if (!(std::fabs(d->level_offset[i]) <= 8.f))
+        return fail(ctx, GSC_ERR_INVALID_ARG, "level offset not finite or beyond 8 levels at anchor %zu", i);
   ModelHost mh;
   mh.n = (uint32_t)n;
   std::vector<float> xs(n), ys(n), zs(n);
@@ -850,6 +857,18 @@ int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out
     }
   }
   int r;
+  // Octree-GS level selection: per-anchor switching radius r_a, level 0
+  // always drawn (+inf), r_a = d_max 2^(Delta_a - l) rounded once to float32.
+  const bool octree = d->level_offset != nullptr || d->lod_blend > 0.f;
+  if (octree) {
+    std::vector<float> rad(n);
+    for (size_t i = 0; i < n; ++i) {
+      const int l = d->level[i];
+      const double delta = d->level_offset ? (double)d->level_offset[i] : 0.0;
+      rad[i] = l == 0 ? INFINITY : (float)std::ldexp((double)d->lod_dmax * std::exp2(delta), -l);
+    }
+    if ((r = upload(ctx, mh.lod_r, rad.data(), n * 4))) return r;
+  }
   if ((r = upload(ctx, mh.px, xs.data(), n * 4)) || (r = upload(ctx, mh.py, ys.data(), n * 4)) ||
       (r = upload(ctx, mh.pz, zs.data(), n * 4)) || (r = upload(ctx, mh.level, d->level, n)) ||
       (r = upload(ctx, mh.feat, d->feat, n * FDIM * 4)) || (r = upload(ctx, mh.offs, d->offset, n * K * 3 * 4)) ||
@@ -892,6 +911,8 @@ int gsc_load_model(gsc_ctx* ctx, const gsc_model_desc* d, uint32_t* model_id_out
   mh.dev.py = (const float*)mh.py.p;
   mh.dev.pz = (const float*)mh.pz.p;
   mh.dev.level = (const uint8_t*)mh.level.p;
+  mh.dev.lod_r = octree ? (const float*)mh.lod_r.p : nullptr;
+  mh.dev.lod_beta = d->lod_blend;
   mh.dev.feat = (const float4*)mh.feat.p;
   mh.dev.offs = (const float*)mh.offs.p;
   mh.dev.scale = (const float*)mh.scale.p;

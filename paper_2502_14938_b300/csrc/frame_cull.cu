@@ -95,7 +95,9 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) 
 // Anchor filtering (Sec. 3.2; Alg. 1 "anchors indexing and filtering"): for
 // every derivation view of this model, frustum test with a 1.3 guard band and
 // the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max 2^-l)^2,
-// level 0 always).  Float32 with an explicit operation order.  Each thread
+// level 0 always; with Octree-GS level offsets the threshold is the anchor's
+// own radius r_a = d_max 2^(Delta_a - l), rounded to float32 at load: the
+// RADIUS instantiation).  Float32 with an explicit operation order.  Each thread
 // owns CULL_IPT consecutive anchors; a block scan of per-thread counts plus a
 // decoupled look-back across tiles gives an order-preserving compaction
 // (ascending anchor ids), one pass over the positions.
@@ -105,6 +107,7 @@ constexpr int CULL_TILE = CULL_NT * CULL_IPT;
 constexpr int CULL_MAXD = MAXV;  // derivation views of one model (look-back words per tile)
 constexpr int CULL_GROUP = 8;    // views tested together (one warp walks back per view)
 
+template <bool RADIUS>
 __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
                                                   uint32_t* const* __restrict__ vis, unsigned long long* status) {
   __shared__ int s_d[CULL_MAXD];
@@ -154,18 +157,26 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
     if (t >= ntiles) break;
     const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
     float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
-    int lv[CULL_IPT];
+    int lv[CULL_IPT];     // plain rule: level, -1 past the end
+    float rr[CULL_IPT];   // radius rule: the anchor's switching radius (+inf at level 0);
+                          // past the end the position is NaN, which fails the frustum test
     static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
     if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
       const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
       const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
       const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
-      const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
       x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
       y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
       z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
+      if (RADIUS) {
+        const float4 r0 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0));
+        const float4 r1 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0) + 1);
+        rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w; rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
+      } else {
+        const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
 #pragma unroll
-      for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
+        for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < CULL_IPT; ++i) {
@@ -174,7 +185,13 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
           x[i] = __ldg(md.px + a);
           y[i] = __ldg(md.py + a);
           z[i] = __ldg(md.pz + a);
-          lv[i] = md.level[a];
+          if (RADIUS)
+            rr[i] = __ldg(md.lod_r + a);
+          else
+            lv[i] = md.level[a];
+        } else if (RADIUS) {
+          x[i] = y[i] = z[i] = __int_as_float(0x7fffffff);
+          rr[i] = 0.f;
         } else {
           x[i] = y[i] = z[i] = 0.f;
           lv[i] = -1;
@@ -193,15 +210,15 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
         uint32_t m = 0;
 #pragma unroll
         for (int i = 0; i < CULL_IPT; ++i) {
-          if (lv[i] < 0) continue;
+          if (!RADIUS && lv[i] < 0) continue;
           const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
           const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
           const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
           bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-          if (v && lv[i] >= 1) {
+          if (v && (RADIUS || lv[i] >= 1)) {
             const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
             const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            const float thr = ldexpf(md.lod_dmax, -lv[i]);
+            const float thr = RADIUS ? rr[i] : ldexpf(md.lod_dmax, -lv[i]);
             v = d2 <= __fmul_rn(thr, thr);
           }
           if (v) m |= 1u << i;
@@ -249,9 +266,12 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
   }
 }
 
-void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
+void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
                  unsigned long long* status, int n_sm, cudaStream_t s) {
-  k_cull<<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
+  if (radius)
+    k_cull<true><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
+  else
+    k_cull<false><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
 }
 
 // ------------------------------------------------------------------ plan

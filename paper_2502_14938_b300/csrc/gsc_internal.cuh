@@ -125,6 +125,8 @@ struct ModelDev {
   const float* py;
   const float* pz;
   const uint8_t* level;
+  const float* lod_r;     // [N] Octree-GS switching radius (+inf at level 0), or null: plain distance rule
+  float lod_beta;         // level fade width in levels (0: none; needs lod_r)
   const float4* feat;     // [N][8]
   const float* offs;      // [N][K][3]
   const float* scale;     // [N]
@@ -400,7 +402,7 @@ constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
-void launch_cull(const ModelDev* md, int model, FrameDev* fd, uint32_t* const* vis_dev,
+void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
                  unsigned long long* status, int n_sm, cudaStream_t s);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();

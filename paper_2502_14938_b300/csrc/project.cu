@@ -1,4 +1,6 @@
 // Projection (K5): derived attributes -> one record per (camera, Gaussian).
+// With an Octree-GS level fade (beta > 0) a Gaussian's opacity is first
+// scaled by min(1, log2(r_a / d) / beta) of its anchor (level >= 1).
 //
 // One thread per (visible anchor item, Gaussian j) of the whole frame, in
 // item order, so the records of consecutive threads are consecutive and the
@@ -73,12 +75,25 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
       a1 = attrs[3 * (size_t)g + 1];
       a2 = attrs[3 * (size_t)g + 2];
     }
-    const float alpha = a0.x;
+    const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
+    float alpha = a0.x;
+    if (md.lod_beta > 0.f) {  // Octree-GS level fade, from this frame's distance (so after the cache)
+      const float ra = __ldg(md.lod_r + a);
+      if (ra < INFINITY) {  // level >= 1: u = log2(r_a / d) levels inside the switching distance
+        // d^2 is the cull's float32 squared distance (same operations), so u >= 0 exactly for
+        // every anchor the cull kept; u = log1p((r^2 - d^2) / d^2) / (2 ln 2), with r^2 - d^2
+        // rounded once, keeps u accurate relative to itself as the anchor nears its switch
+        const float* pc = fd->dcam[d].pc;  // the derivation camera, as in the cull
+        const float dx = __fsub_rn(xa, pc[0]), dy = __fsub_rn(ya, pc[1]), dz = __fsub_rn(za, pc[2]);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        const float u = 0.72134752f * log1pf(__fdiv_rn(fmaf(ra, ra, -d2), d2));
+        alpha = alpha * fminf(1.f, fmaxf(0.f, __fdiv_rn(u, md.lod_beta)));
+      }
+    }
     const bool kept = alpha > 0.f;
     const float col[3] = {a0.y, a0.z, a0.w};
     const float s[3] = {a1.x, a1.y, a1.z};
     const float q[4] = {a1.w, a2.x, a2.y, a2.z};
-    const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
     const float* op = md.offs + ((size_t)a * K + j) * 3;
     const float o3[3] = {__ldg(op), __ldg(op + 1), __ldg(op + 2)};
     const float mu[3] = {__fadd_rn(xa, o3[0]), __fadd_rn(ya, o3[1]), __fadd_rn(za, o3[2])};

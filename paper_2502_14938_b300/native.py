@@ -54,7 +54,8 @@ class ModelDesc(C.Structure):
                 ("hidden", C.c_uint32), ("n_levels", C.c_uint32), ("lod_dmax", C.c_float),
                 ("pos", C.c_void_p), ("feat", C.c_void_p), ("offset", C.c_void_p), ("scale", C.c_void_p),
                 ("level", C.c_void_p), ("W1", C.c_void_p * 3), ("b1", C.c_void_p * 3),
-                ("W2", C.c_void_p * 3), ("b2", C.c_void_p * 3)]
+                ("W2", C.c_void_p * 3), ("b2", C.c_void_p * 3),
+                ("level_offset", C.c_void_p), ("lod_blend", C.c_float), ("reserved0", C.c_uint32)]
 
 
 class Camera(C.Structure):
@@ -264,6 +265,9 @@ class Renderer:
         for h in range(3):
             d.W1[h], d.b1[h] = arr(m.W1[h], np.float32), arr(m.b1[h], np.float32)
             d.W2[h], d.b2[h] = arr(m.W2[h], np.float32), arr(m.b2[h], np.float32)
+        lo = getattr(m, "level_offset", None)
+        d.level_offset = arr(lo, np.float32) if lo is not None else None
+        d.lod_blend = float(getattr(m, "lod_blend", 0.0))
         mid = C.c_uint32()
         self._check(lib().gsc_load_model(self.ctx, C.byref(d), C.byref(mid)))
         return int(mid.value)

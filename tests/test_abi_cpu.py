@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     checks = [("gsc_config", native.Config, ["pair_capacity", "bg", "flags", "blocks_per_sm", "out_format",
                                              "depth_guide"]),
-              ("gsc_model_desc", native.ModelDesc, ["pos", "W1", "b2"]),
+              ("gsc_model_desc", native.ModelDesc, ["pos", "W1", "b2", "level_offset", "lod_blend"]),
               ("gsc_camera", native.Camera, ["fx", "znear", "viewer"]),
               ("gsc_frame_stats", native.FrameStats, ["cache_depth", "ms_stage"])]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsc.h"', "int main(void){"]
