@@ -487,9 +487,14 @@ def run_sched(args):
 
 def run_profile(args):
     """Minimal run for profilers: W + K frames from --frame, no extras, with
-    the tiling of --tile (launches per frame: launches_per_frame_of)."""
+    the tiling of --tile (launches per frame: launches_per_frame_of); with
+    --octree the model carries the synthetic Octree-GS level offsets and fade
+    of run_octree."""
     import torch
     model, frames, _ = build_workload()
+    if args.octree:
+        import gen
+        model = gen.with_level_offsets(model, sigma=0.5, beta=0.5)
     W, H = frames[0][0].width, frames[0][0].height
     r, mid = make_renderer(model, args.form)
     outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
@@ -499,7 +504,8 @@ def run_profile(args):
         set_pair(r, mid, *frames[(args.frame + s) % len(frames)])
         st = r.render_frame(outs)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_run": True, "form": args.form, "frames": args.warmup + args.steps, "last": st}),
+    print(json.dumps({"profile_run": True, "form": args.form, "octree": bool(args.octree),
+                      "frames": args.warmup + args.steps, "last": st}),
           flush=True)
 
 
