@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
   __shared__ int s_d[CULL_MAXD];
   __shared__ int s_nd;
   __shared__ float s_cam[CULL_MAXD][20];
+  __shared__ float s_thr2[32];  // plain rule: (d_max 2^-l)^2 per level, +inf at level 0
   __shared__ uint32_t s_warp[CULL_NT / 32 + 1];
   __shared__ uint32_t s_total[CULL_MAXD];
   __shared__ uint32_t s_base[CULL_MAXD];
@@ -141,6 +142,10 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
     else if (f == 17) v = c.gy;
     else v = 0.f;
     s_cam[ld][f] = v;
+  }
+  if (!RADIUS && threadIdx.x < 32) {
+    const float thr = ldexpf(md.lod_dmax, -(int)threadIdx.x);
+    s_thr2[threadIdx.x] = threadIdx.x == 0 ? INFINITY : __fmul_rn(thr, thr);
   }
   __syncthreads();
   if (nd == 0) return;
@@ -215,11 +220,10 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
           const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
           const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
           bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-          if (v && (RADIUS || lv[i] >= 1)) {
+          if (v) {
             const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
             const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            const float thr = RADIUS ? rr[i] : ldexpf(md.lod_dmax, -lv[i]);
-            v = d2 <= __fmul_rn(thr, thr);
+            v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : s_thr2[lv[i]]);
           }
           if (v) m |= 1u << i;
         }
