@@ -51,7 +51,9 @@ __global__ void k_noalloc_begin(unsigned long long* scratch) {
   *err = 0;
 }
 
-__global__ void __launch_bounds__(NA_NT) k_noalloc_scan(const uint32_t* __restrict__ in, uint32_t* out, uint32_t n,
+// `in` may equal `out` (in place: a tile reads all its inputs before it
+// writes), so neither pointer is declared __restrict__.
+__global__ void __launch_bounds__(NA_NT) k_noalloc_scan(const uint32_t* in, uint32_t* out, uint32_t n,
                                                         uint32_t* total_out, unsigned long long* scratch) {
   __shared__ uint32_t s_warp[NA_NT / 32 + 1];
   __shared__ unsigned long long s_sum64[NA_NT / 32];

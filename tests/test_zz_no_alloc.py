@@ -34,6 +34,12 @@ def test_noalloc_scan_matches_allocating_scan_on_two_calls():
         got = d_out.cpu().numpy().view(np.uint32)
         assert np.array_equal(got, ref)
         assert int(d_tot.cpu().numpy().view(np.uint32)[0]) == ref_total
+    # in place (d_out == d_in), which the header allows
+    vals = rs.integers(0, 50, 300_001).astype(np.uint32)
+    ref, ref_total = r.debug_scan(vals)
+    d_io = torch.from_numpy(vals.view(np.int32)).cuda()
+    native.scan_u32_noalloc(d_io.data_ptr(), d_io.data_ptr(), vals.size, 0, stream)
+    assert np.array_equal(d_io.cpu().numpy().view(np.uint32), ref)
     r.close()
 
 
