@@ -90,98 +90,113 @@ class _CtypesNvml:
         return v.value
 
 
+def _nvml_open(uuid: str, index: int):
+    """(nvml module, device handle): the Python NVML binding, else the
+    driver's libnvidia-ml through its C API."""
+    try:
+        import pynvml
+    except ImportError:
+        pynvml = _CtypesNvml()
+    pynvml.nvmlInit()
+    try:
+        return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
+    except Exception:
+        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(index)
+
+
+def clock_sampler_main(uuid: str, index: int, period_ms: float) -> None:
+    """Child process of ClockSampler: prints "ready", then one line per
+    sample (SM MHz, max SM MHz, clock-event reason bits) every period_ms
+    until its standard input closes.  Reads only; nothing is set."""
+    nv, h = _nvml_open(uuid, index)
+    mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+    stop = threading.Event()
+
+    def wait_eof():
+        sys.stdin.read()
+        stop.set()
+
+    threading.Thread(target=wait_eof, daemon=True).start()
+    print("ready", flush=True)
+    while True:
+        sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
+        bits = int(nv.nvmlDeviceGetCurrentClocksEventReasons(h))
+        print(f"{sm} {mx} {bits}", flush=True)
+        if stop.wait(period_ms / 1e3):
+            break
+
+
 class ClockSampler:
     """SM clocks and clock-event (throttle) reasons sampled during the timed
-    region: read in-process through NVML every millisecond (the timed region
-    of a default run is only ~20 ms), else by an nvidia-smi loop.  Reads
-    only; nothing is set."""
+    region by a separate process (NVML every millisecond: the timed region
+    of a short run is only ~10 ms), so the sampling never competes with the
+    timed loop for the interpreter; an nvidia-smi loop if NVML is missing.
+    Reads only; nothing is set."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NVML_BITS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
                  ("sw_power_cap", 0x4))
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, period_ms: float = 1.0):
         self.idx = device_index
+        self.period_ms = period_ms
         self.proc = None
-        self.nvml = None
+        self.kind = None
         self.rows = []
-        self.stop = threading.Event()
 
-    def _nvml_handle(self):
+    def __enter__(self):
         import torch
         uuid = str(torch.cuda.get_device_properties(self.idx).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
         try:
-            import pynvml
-        except ImportError:
-            pynvml = _CtypesNvml()  # the driver's libnvidia-ml through its C API
-        pynvml.nvmlInit()
-        try:
-            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
+            self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--clock-sampler", uuid,
+                                          str(self.idx), str(self.period_ms)],
+                                         stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            if self.proc.stdout.readline().strip() == "ready":
+                self.kind = "nvml"
+                return self
+            self.proc.kill()
+            self.proc.wait()
         except Exception:
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.idx)
-
-    def __enter__(self):
-        try:
-            nv, h = self._nvml_handle()
-            self.nvml = (nv, h)
-            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
-            self._sample_nvml()
-            self.t = threading.Thread(target=self._poll_nvml, daemon=True)
-            self.t.start()
-            return self
-        except Exception:
-            self.nvml = None
+            pass
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            self.kind = "smi"
         except Exception:
             self.proc = None
         return self
 
-    def _sample_nvml(self):
-        nv, h = self.nvml
-        sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-        bits = int(nv.nvmlDeviceGetCurrentClocksEventReasons(h))
-        self.rows.append(("nvml", sm, self.max_mhz, bits))
-
-    def _poll_nvml(self):
-        while not self.stop.wait(0.001):
-            try:
-                self._sample_nvml()
-            except Exception:
-                return
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
-
     def __exit__(self, *a):
-        if self.nvml:
-            self.stop.set()
-            self.t.join(timeout=5)
-            try:
-                self._sample_nvml()
-            except Exception:
-                pass
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
+        if not self.proc:
+            return
+        try:
+            if self.kind == "nvml":
+                self.proc.stdin.close()
+                out = self.proc.stdout.read()
+                self.proc.wait(timeout=10)
+                for line in out.splitlines():
+                    p = line.split()
+                    if len(p) == 3:
+                        self.rows.append((float(p[0]), float(p[1]), int(p[2])))
+            else:
+                self.proc.terminate()
+                out = self.proc.stdout.read()
+                self.proc.wait(timeout=10)
+                self.rows = [[x.strip() for x in line.split(",")] for line in out.splitlines()]
+        except Exception:
+            self.proc.kill()
 
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        if self.rows[0][0] == "nvml":
-            reasons = sorted({n for r in self.rows for n, b in self.NVML_BITS if r[3] & b})
-            return {"sm_mhz": statistics.median(r[1] for r in self.rows), "sm_max_mhz": self.max_mhz,
-                    "reasons": reasons, "samples": len(self.rows), "source": "nvml"}
+        if self.kind == "nvml":
+            reasons = sorted({n for r in self.rows for n, b in self.NVML_BITS if r[2] & b})
+            return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": self.rows[0][1],
+                    "reasons": reasons, "samples": len(self.rows), "source": "nvml, separate process"}
         sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -191,7 +206,7 @@ class ClockSampler:
                 if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(self.rows), "source": "nvidia-smi"}
 
 
 def build_workload(n_frames=300):
@@ -202,23 +217,43 @@ def build_workload(n_frames=300):
 
 
 # ---------------------------------------------------------------- reference arm (CPU oracle)
-def oracle_frame_sample(model, L, R, subsample=16, phase=0):
-    """One stereo frame through the float64 oracle: all anchors filtered,
-    derived and projected, blending on 1/subsample of the pixel rows; the
-    blend time is scaled by `subsample` to a full frame.  Returns seconds."""
+def cpu_info() -> dict:
+    """The host's CPU model and the cores this process may run on."""
+    name = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        nproc = len(os.sched_getaffinity(0))
+    except AttributeError:
+        nproc = os.cpu_count()
+    return {"cpu_model": name, "nproc": nproc}
+
+
+def oracle_frame(model, L, R):
+    """One stereo frame through the float64 oracle: filtering, derivation,
+    projection and tiled blending of every pixel of both eyes.  Returns
+    (seconds, [(rgb, T, margin, contributors) of each eye])."""
     import oracle
-    t_fixed = t_blend = 0.0
-    for cam in (L, R):
-        t0 = time.perf_counter()
-        vr = oracle.view_gaussians(model, cam)
-        t1 = time.perf_counter()
-        ys = np.arange(phase % subsample, cam.height, subsample)
-        px, py = np.meshgrid(np.arange(cam.width), ys)
-        oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px.ravel(), py.ravel())
-        t2 = time.perf_counter()
-        t_fixed += t1 - t0
-        t_blend += t2 - t1
-    return t_fixed + t_blend * subsample
+    t0 = time.perf_counter()
+    outs = [oracle.render_view(model, cam)[0] for cam in (L, R)]
+    return time.perf_counter() - t0, outs
+
+
+def oracle_one_thread(model, L, R) -> float:
+    """Seconds of one stereo oracle frame on a single thread."""
+    import oracle
+    n = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        return oracle_frame(model, L, R)[0]
+    finally:
+        oracle.set_threads(n)
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -240,26 +275,31 @@ def job_rate(world: int, steps: int, total_ms: float) -> float:
 
 
 def run_reference(args, rank, world):
+    """The CPU float64 oracle as it stands on the host's cores: each step is
+    one whole stereo frame of the path (every 10th frame: step s renders
+    frame 10 s mod 300), warm-up steps the frames halfway between."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     model, frames, _ = build_workload()
+    n = len(frames)
     for w in range(args.warmup):
-        oracle_frame_sample(model, *frames[w % len(frames)], phase=w)
-    ts = []
-    for s in range(args.steps):
-        f = (args.warmup + s * 37) % len(frames)
-        ts.append(oracle_frame_sample(model, *frames[f], phase=s))
+        oracle_frame(model, *frames[(10 * w + 5) % n])
+    ts = [oracle_frame(model, *frames[(10 * s) % n])[0] for s in range(args.steps)]
+    t1 = oracle_one_thread(model, *frames[150])
     mean = float(np.mean(ts))
     cores = oracle.num_threads()
-    sample = ("per step: one stereo frame of the path, full filtering/derivation/projection in float64, "
-              "blending on every 16th pixel row, blend time x16")
+    info = cpu_info()
+    sample = (f"per step one whole stereo frame (both eyes, every pixel) of the path, frames 0, 10, 20, ... in "
+              f"float64 on {cores} threads; one frame (150) also on 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": 1.0 / mean, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "CPU float64 oracle", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": 1.0 / mean, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "form": "CPU float64 oracle (plain method)", "l2": "n/a (CPU)",
+                       "p99_ms": float(np.percentile(ts, 99)) * 1e3, **info},
+            "cpu_baseline": {"value": 1.0 / mean, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "value_1thread": 1.0 / t1, **info},
             "e2e": {"value": 1.0 / mean, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -284,10 +324,27 @@ FP32_LANE_OPS = 148 * 128 * 2.032e9  # SMs x FP32 lanes x max SM clock: FP32 lan
 # operations (offset, quadratic form, opacity product and clamp, the two
 # thresholds, T update, colour accumulation) and one exponential
 OPS_PER_EVAL = 20
-# DRAM bytes (read + write) of one launch from an ncu capture of the same
-# kernel build and tiling (profiles/k_blend_city2M.md: frame 151 of the path);
-# reported as the roofline's traffic only when the timed run uses that tiling.
-NCU_TRAFFIC = {"k_blend": {(16, 64, 0): {"bytes": 12.773e6 + 1.707e6, "frame": 151}}}
+# DRAM bytes (read + write) of one launch of a kernel from one ncu capture,
+# with the tiling and the frame it was taken on and the SHA-256 prefix of the
+# kernel's source file at the time: reported as the roofline's traffic only
+# while the source is unchanged and the timed run uses that tiling, else null.
+NCU_TRAFFIC = {"k_blend": {"file": "paper_2502_14938_b300/csrc/raster.cu", "sha16": None, "tiling": (16, 64, 0),
+                           "bytes": None, "frame": None}}
+
+
+def _src_sha16(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, tiling_key):
+    c = NCU_TRAFFIC.get(kernel)
+    if not c or c["bytes"] is None or tuple(c["tiling"]) != tuple(tiling_key) or _src_sha16(c["file"]) != c["sha16"]:
+        return None, "no capture of the current kernel source at this tiling"
+    return c["bytes"], f"ncu dram bytes of one launch, frame {c['frame']}, tiles {tuple(c['tiling'])}"
+
+
 # The blend's algorithmic work is counted on the paper's rasteriser tiling
 # (16x16 tiles, one block per tile), so it does not depend on the tuned shape
 WORK_TILING = (16, 16, 0)
@@ -566,6 +623,9 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
     return r, mid, outs, ms, wall
 
 
+STAGE_NAMES = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
+
+
 def stage_profile(model, frames, form, n, flush, tiling=None, count=True):
     """Per-stage CUDA-event times on the library's stream (eager launches), with the timed run's tiling."""
     import paper_2502_14938_b300 as pkg
@@ -578,11 +638,13 @@ def stage_profile(model, frames, form, n, flush, tiling=None, count=True):
     outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     stage = np.zeros(8)
     acc = {"visible_anchors": 0, "derived_anchors": 0, "records": 0, "valid_records": 0, "pairs": 0}
+    stage_rows = []
     for s in range(n):
         set_pair(rt, mid, *frames[s % len(frames)])
         flush.fill_(s & 0xFF)
         st = rt.render_frame(outs)
         stage += np.array(st["ms_stage"])
+        stage_rows.append([float(x) for x in st["ms_stage"][:7]])
         for k in acc:
             acc[k] += st[k]
     rt.close()
@@ -605,8 +667,10 @@ def stage_profile(model, frames, form, n, flush, tiling=None, count=True):
             else:
                 acc["blend_walk16"] += w
         rw.close()
-    names = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
-    return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, {k: v / n for k, v in acc.items()}
+    names = STAGE_NAMES
+    res = {k: v / n for k, v in acc.items()}
+    res["stage_rows"] = [dict(zip(names, row)) for row in stage_rows]
+    return {nm: float(stage[i] / n) for i, nm in enumerate(names)}, res
 
 
 def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
@@ -631,13 +695,12 @@ def roofline(stage_ms, st, form, W, H, n_anchors, tiling):
         peak = FP32_LANE_OPS / 1e12
         rates = pkg.native.pipe_rates()
         key = (tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])
-        cap = NCU_TRAFFIC["k_blend"].get(key)
+        traffic, traffic_src = ncu_traffic("k_blend", key)
         return {"kernel": "k_blend", "bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32-op/s",
                 "frac": ach / peak,
                 "peak_src": "nominal: 148 SMs x 128 FP32 lanes x 2.032 GHz; work = 20 FP32 ops per evaluation "
                             "of the walk over 16x16 tile lists",
-                "traffic": cap["bytes"] if cap else None,
-                "traffic_src": f"ncu dram bytes, frame {cap['frame']}, tiles {key}" if cap else None,
+                "traffic": traffic, "traffic_src": traffic_src,
                 "evals_per_launch": walk16, "walk_evals_timed_tiling": walk, "issued_evals_per_launch": ev,
                 "evals_per_s": walk16 / dur, "exp2_frac_of_measured": walk16 / dur / rates["exp2_per_s"],
                 "measured_rates": rates, "ms_per_launch": stage_ms[dom],
@@ -776,6 +839,20 @@ def run_batched(args, flush):
             "reuse_frac_mean": float(np.mean(reuse)), "tune_s": t_tune, "gen_s": t_gen}
 
 
+def _vr3(vr):
+    return vr.rec, vr.depth32, vr.gid
+
+
+def judged_psnr(samples, refs):
+    """Per frame of refs: PSNR of both eyes' sampled values against refs[f]."""
+    out = []
+    for f, (r0, r1) in refs.items():
+        got = samples[f].astype(np.float64)
+        mse = (np.mean((got[0] - r0) ** 2) + np.mean((got[1] - r1) ** 2)) / 2
+        out.append(10 * np.log10(1.0 / max(mse, 1e-10)))
+    return out
+
+
 def run_learned(model, flush, steps):
     """Cache + learned-reuse form on the look-around path (seed 12, 80-95%
     frame-to-frame overlap): 100k labels collected on paths 20-29, GPU
@@ -792,6 +869,18 @@ def run_learned(model, flush, steps):
     theta, losses = reuse.train(Z, Y, gen.reuse_mlp_init(7), epochs=40, batch=4096, lr=2e-3)
     t_train = time.perf_counter() - t0
     path = gen.stereo_frames(gen.reuse_path(12))
+    import oracle
+    rs = np.random.default_rng(12)
+    W, H = path[0][0].width, path[0][0].height
+    sample = {f: (rs.integers(0, W, 20000), rs.integers(0, H, 20000)) for f in range(5, len(path), 10)}
+    qb = oracle.OrcQuant()
+    qb.mode = 1
+    refs, plain = {}, {}
+    for f, (px, py) in sample.items():
+        U = oracle.unified_camera(*path[f])
+        refs[f] = [oracle.render(*_vr3(oracle.view_gaussians(model, c, derive_cam=U, quant=qb)), W, H, True, px, py)[0]
+                   for c in path[f]]
+        plain[f] = [oracle.render(*_vr3(oracle.view_gaussians(model, c)), W, H, True, px, py)[0] for c in path[f]]
     out = {"path": "look-around path seed 12 (120 frames)", "collect_s": t_collect, "train_s": t_train,
            "samples": st["samples"], "positive_frac": st["positive_frac"], "final_loss": float(losses[-1])}
     for name, th in (("depth", None), ("learned", theta)):
@@ -819,10 +908,18 @@ def run_learned(model, flush, steps):
         torch.cuda.synchronize()
         r.close()
         ms = np.array([a.elapsed_time(b) for a, b in evs])
-        ev = reuse.evaluate(model, path, th)
+        ev = reuse.evaluate(model, path, th, sample=sample)
+        p_form = judged_psnr(ev["samples"], refs)
+        p_plain = judged_psnr(ev["samples"], plain)
         out[name] = {"fps": 1000.0 / float(ms.mean()), "ms_mean": float(ms.mean()),
                      "p99_ms": float(np.percentile(ms, 99)), **{k: ev[k] for k in
-                     ("reuse_frac", "wrong_reuse_frac", "psnr_db_min", "psnr_db_mean")}}
+                     ("reuse_frac", "wrong_reuse_frac", "psnr_db_min", "psnr_db_mean")},
+                     "oracle_psnr_db_min": min(p_form), "oracle_psnr_db_mean": float(np.mean(p_form)),
+                     "plain_oracle_psnr_db_min": min(p_plain)}
+    out["psnr"] = ("psnr_db_*: whole images against the GPU's same form without the cache; oracle_psnr_db_*: "
+                   "20k sampled pixels per eye on every 10th frame against the float64 oracle of the same form "
+                   "without the cache (unified camera, bf16-rounded derivation); plain_oracle_psnr_db_min: the "
+                   "same pixels against the float64 oracle of the plain per-eye method")
     return out
 
 
@@ -846,6 +943,64 @@ def form_quality(r, mid, outs, frames, refs):
         psnr.append(10 * np.log10(1.0 / max(mse, 1e-10)))  # identical images count as 100 dB
         maxabs.append(mx)
     return {"psnr_db": psnr, "max_abs": maxabs, "frames": sorted(refs)}, reuse
+
+
+def quality_pass(model, frames, rends, ref_frames, head):
+    """Every form of `rends` ({form: (renderer, model id, outs)}) renders the
+    path in order from frame 0 with an empty cache (so reuse is live), with
+    frame statistics.  At each frame of `ref_frames` the float64 oracle
+    renders both eyes of the plain method (whole images; timed: these are
+    the CPU baseline's frames) and every form is compared with it: PSNR
+    over all pixels, channels and both eyes; max-abs over all pixels; and,
+    for the parity tolerance, max-abs over the decided pixels (no alpha or
+    stop decision of the oracle within 1e-4 of its threshold) and the share
+    of pixels that are not decided.  Returns (quality per form, per-frame
+    rows of the `head` form, oracle seconds per reference frame)."""
+    import torch
+    for r, _, _ in rends.values():
+        r.cache_reset()
+    keys = ("psnr_db", "max_abs", "max_abs_decided", "near_threshold_frac")
+    q = {form: {"frames": [], **{k: [] for k in keys}} for form in rends}
+    rows, cpu_s = [], []
+    refs_set = set(ref_frames)
+    for f in range(max(ref_frames) + 1):
+        st_head = None
+        for form, (r, mid, outs) in rends.items():
+            set_pair(r, mid, *frames[f])
+            st = r.render_frame(outs)
+            if form == head:
+                st_head = st
+        row = {"frame": f, "visible_anchors": int(st_head["visible_anchors"]),
+               "derived_anchors": int(st_head["derived_anchors"]), "records": int(st_head["records"]),
+               "valid_records": int(st_head["valid_records"]), "pairs": int(st_head["pairs"]),
+               "cache_depth": int(st_head["cache_depth"]),
+               "update_rate": st_head["derived_anchors"] / max(1, st_head["visible_anchors"])}
+        if f in refs_set:
+            t, refs = oracle_frame(model, *frames[f])
+            cpu_s.append(t)
+            dev = [(torch.from_numpy(ref).cuda(), torch.from_numpy(mg).cuda() >= 1e-4) for ref, _, mg, _ in refs]
+            for form, (r, mid, outs) in rends.items():
+                mse = mx = mxd = nt = 0.0
+                for v in range(2):
+                    ref, ok = dev[v]
+                    err = (outs[v].double() - ref).abs()
+                    mse += float((err * err).mean()) / 2
+                    mx = max(mx, float(err.max()))
+                    e_ok = err.amax(dim=-1)[ok]
+                    mxd = max(mxd, float(e_ok.max()) if e_ok.numel() else 0.0)
+                    nt += (1.0 - float(ok.double().mean())) / 2
+                vals = (10 * np.log10(1.0 / max(mse, 1e-10)), mx, mxd, nt)  # identical images count as 100 dB
+                q[form]["frames"].append(f)
+                for k, x in zip(keys, vals):
+                    q[form][k].append(x)
+            row.update({k: q[head][k][-1] for k in keys})
+        rows.append(row)
+    for form in q:
+        if q[form]["psnr_db"]:
+            q[form]["psnr_db_min"] = min(q[form]["psnr_db"])
+            q[form]["max_abs_decided_max"] = max(q[form]["max_abs_decided"])
+            q[form]["near_threshold_frac_max"] = max(q[form]["near_threshold_frac"])
+    return q, rows, cpu_s
 
 
 def per_frame_tile_bits(W, H, tiling):
@@ -892,33 +1047,44 @@ def run_ours(args, rank, world):
                                        tune=args.autotune)
     total_ms = max_over_ranks(float(ms.sum()), world)
     others = {}
-    compare_renderers = {}
+    rends = {form: (r, mid, outs)}
     for f2 in args.compare:
         if f2 == form:
             continue
         r2, mid2, outs2, ms2, _ = time_form(model, frames, f2, args.steps, args.warmup, flush, 1, tune=args.autotune)
         others[f2] = {"fps": 1000.0 / float(ms2.mean()), "ms_mean": float(ms2.mean()),
                       "p99_ms": float(np.percentile(ms2, 99)), "tiling": r2.tiling}
-        r2.mid, r2.outs = mid2, outs2
-        compare_renderers[f2] = r2
+        rends[f2] = (r2, mid2, outs2)
     if rank != 0:
         return
     mean_ms = total_ms / args.steps
     fps = job_rate(world, args.steps, total_ms)
     stage_ms, per_frame = stage_profile(model, frames, form, min(args.steps, len(frames)), flush, r.tiling)
+    stage_rows = per_frame.pop("stage_rows")
     roof = roofline(stage_ms, per_frame, form, W, H, model.n, r.tiling)
     stage_gbs = stage_hbm(stage_ms, per_frame, form, W, H, model.n)
 
-    # ---- quality: PSNR and max-abs of sampled frames against the float64
-    # oracle (plain method), each form rendered in path order from an empty
-    # cache so reuse is live; the oracle images are made once
+    # ---- quality: every form against the float64 oracle of the plain method
+    # on every 10th frame of the path (whole images, both eyes), each form
+    # rendered in path order from an empty cache; the oracle's frames are
+    # timed as the CPU baseline
     import oracle
-    refs = {f: [oracle.render_view(model, cam)[0][0] for cam in frames[f]] for f in args.psnr_frames}
-    q, reuse_frac = form_quality(r, mid, outs, frames, refs)
-    for f2, r2 in compare_renderers.items():
-        others[f2]["quality"], _ = form_quality(r2, r2.mid, r2.outs, frames, refs)
-        r2.close()
+    q_all, frame_rows, cpu_s = quality_pass(model, frames, rends, args.psnr_frames, form)
+    for f2 in others:
+        others[f2]["quality"] = q_all[f2]
+        rends[f2][0].close()
+    q = q_all[form]
     psnrs = q["psnr_db"]
+    reuse_frac = [1.0 - x["update_rate"] for x in frame_rows]
+    if args.log:
+        with open(args.log, "w") as fl:
+            for row in frame_rows:
+                f = row["frame"]
+                if f < len(ms):
+                    row["ms"] = float(ms[f])
+                if f < len(stage_rows):
+                    row["stage_ms_eager"] = stage_rows[f]
+                fl.write(json.dumps(row) + "\n")
 
     # ---- end to end through the public API with host buffers: the headline
     # form with display images (RGBA8) and pipelined host frames (frame n+1
@@ -959,16 +1125,18 @@ def run_ours(args, rank, world):
     learned = run_learned(model, flush, args.steps) if args.learned else None
 
     cores = oracle.num_threads()
-    cts = [oracle_frame_sample(model, *frames[f], phase=i) for i, f in enumerate((0, 150))]
-    cpu = {"value": 1.0 / float(np.mean(cts)), "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": "2 stereo frames (0, 150): full float64 filtering/derivation/projection, "
-                     "blending on every 16th pixel row scaled x16"}
+    t1 = oracle_one_thread(model, *frames[150])
+    cpu = {"value": len(cpu_s) / float(np.sum(cpu_s)), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"the {len(cpu_s)} quality reference frames (every 10th frame of the path): whole stereo "
+                     f"frames, every pixel of both eyes, float64, {cores} threads; frame 150 also on 1 thread",
+           "value_1thread": 1.0 / t1, **cpu_info()}
 
     launches_per_frame = launches_per_frame_of(form, per_frame_tile_bits(W, H, r.tiling))
     cfg = {"workload": WORKLOAD, "form": form, **FORMS[form], "tiling": r.tiling,
            "l2": "flushed between frames (256 MB write, untimed)",
            "p99_ms": float(np.percentile(ms, 99)), "wall_fps": args.steps / wall,
            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db": psnrs, "max_abs": q["max_abs"],
+           "max_abs_decided": q["max_abs_decided"], "near_threshold_frac": q["near_threshold_frac"],
            "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
            "e2e_sync_f32": e2e_sync_f32, "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "stage_hbm": stage_gbs, "per_frame": per_frame, "gen_s": t_gen}
@@ -981,6 +1149,8 @@ def run_ours(args, rank, world):
 
 
 def main():
+    if len(sys.argv) == 5 and sys.argv[1] == "--clock-sampler":
+        return clock_sampler_main(sys.argv[2], int(sys.argv[3]), float(sys.argv[4]))
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
@@ -989,7 +1159,10 @@ def main():
     ap.add_argument("--form", default=HEADLINE, choices=sorted(FORMS))
     ap.add_argument("--compare", nargs="*", default=["plain", "bf16_unified", "fp8_unified", "cached_fp8_unified"],
                     help="other forms timed for comparison")
-    ap.add_argument("--psnr-frames", type=int, nargs="*", default=[0, 150, 299])
+    ap.add_argument("--psnr-frames", type=int, nargs="*", default=list(range(0, 300, 10)),
+                    help="path frames compared with the float64 oracle (default: every 10th frame)")
+    ap.add_argument("--log", default=None, help="JSON lines file: one line per path frame of the timed form "
+                    "(counts, cache depth, update rate, event ms, eager stage ms, PSNR / max-abs at oracle frames)")
     ap.add_argument("--profile", action="store_true", help="minimal run for ncu (no extras)")
     ap.add_argument("--frame", type=int, default=150, help="first path frame of a --profile run")
     ap.add_argument("--tile", type=int, nargs=3, default=[16, 16, 0], metavar=("W", "H", "BPS"),

@@ -305,15 +305,20 @@ GSC_API int gsc_version(void);
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * The call allocates nothing: its working memory is a fixed 32,800-byte
  * device array inside the library, present on every GPU that loads the
- * library until the process exits.  The first call on a device looks that
- * array's address up (cudaGetSymbolAddress, with the device current); make
- * that first call before any stream capture.  Calls whose work overlaps on
- * the GPU (other threads or streams) share the array and race: serialise
- * them.  The call is synchronous: it returns after the scan has finished on
- * the stream.  Returns GSC_OK; GSC_ERR_INVALID_ARG for bad pointers or n, or
- * when the sum of the inputs reaches 2^30 (the results are then not valid);
+ * library until the process exits.  Every call looks that array's address
+ * up (cudaGetSymbolAddress) for the device and context current at the call;
+ * no address is kept between calls.  The call reads an error word back and
+ * synchronises the stream, so it must not be made on a stream that is being
+ * captured into a CUDA graph: such a call returns GSC_ERR_INVALID_ARG and
+ * enqueues nothing.  Calls whose work overlaps on the GPU (other threads or
+ * streams) share the array and race: serialise them.  The call is
+ * synchronous: it returns after the scan has finished on the stream.
+ * Returns GSC_OK; GSC_ERR_INVALID_ARG for bad pointers or n, for a
+ * capturing stream, or when the sum of the inputs reaches 2^30;
  * GSC_ERR_TIMEOUT if a bounded device-side wait gave up; GSC_ERR_CUDA if a
- * CUDA call failed. */
+ * CUDA call failed.  After GSC_ERR_INVALID_ARG for the sum and after
+ * GSC_ERR_TIMEOUT the contents of d_out and *d_total are unspecified; the
+ * next call starts from a cleared error word. */
 GSC_API int gsc_scan_u32_noalloc(const uint32_t* d_in, uint32_t* d_out, uint64_t n, uint32_t* d_total,
                                  void* cuda_stream);
 

@@ -96,6 +96,7 @@ def lib():
         L.orc_round_e4m3.argtypes = [C.c_double]
         L.orc_round_e4m3.restype = C.c_double
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -106,6 +107,11 @@ def _p(a: Optional[np.ndarray]):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 # ------------------------------------------------------------------ cameras

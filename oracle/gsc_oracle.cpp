@@ -452,7 +452,14 @@ float orc_depth32(const orc_camera* c, const float* xa, const float* o) {
 // visible index i and Gaussian j (ascending global id a*k + j).  Per record
 // (stride ORC_REC = 16 doubles): valid, mean x, mean y, conic A, B, C,
 // opacity, colour r, g, b, depth (fp64), tau = 2 ln(255 o), Sigma'xx, xy, yy,
-// spare.  depth32 is the pinned ordering depth.  A record is valid iff the
+// e_mean.  depth32 is the pinned ordering depth.  e_mean (pixels) is the
+// distance a float32 evaluation of the projection can move the 2D mean:
+// the camera-relative position, the rotation sums and the perspective
+// divide each carry an error of a few float32 ulps of the quantities they
+// combine, which at the image reaches f (1 + |x'| + |y'|)(1 + max(|x'|, |y'|))
+// ulps of a unit (x' = (m_x - c_x) / f_x, y' = (m_y - c_y) / f_y: the
+// tangent offsets), independent of depth; the term takes 4 such ulps
+// (2^-22) of that plus of max(|m_x|, |m_y|), per axis its larger value.  A record is valid iff the
 // Gaussian is kept (alpha > 0), its pinned depth is > znear and det > 0.
 int orc_project_records(const orc_model* m, const orc_camera* c, const uint32_t* ids, int64_t n,
                         const double* attrs, const uint8_t* kept, double* rec, float* depth32) {
@@ -484,6 +491,11 @@ int orc_project_records(const orc_model* m, const orc_camera* c, const uint32_t*
       out[10] = pr[8];
       out[11] = 2.0 * std::log(255.0 * at[0]);
       out[12] = pr[2]; out[13] = pr[3]; out[14] = pr[4];
+      const double ux = std::fabs(pr[0] - (double)c->cx) / (double)c->fx;
+      const double uy = std::fabs(pr[1] - (double)c->cy) / (double)c->fy;
+      const double sp = (1.0 + ux + uy) * (1.0 + std::max(ux, uy));
+      const double mm = std::max(std::fabs(pr[0]), std::fabs(pr[1]));
+      out[15] = std::ldexp(std::max((double)c->fx, (double)c->fy) * sp + mm, -22);
     }
   }
   return 0;
@@ -677,12 +689,11 @@ int orc_render(const double* rec, const float* depth32, const int64_t* gid, int6
       const double araw = g[6] * std::exp(-0.5 * q);
       const double al = std::min(0.99, araw);
       // distance of the 1/255 decision from its threshold in log-opacity,
-      // less what float32 pixel coordinates of the mean can move it: an
-      // error e in the mean shifts q/2 by up to |grad_mean(q/2)|_1 e, and a
-      // float32 projection places the mean within a few ulps of its value
+      // less what a float32 projection's error in the mean can move it: an
+      // error e in the mean shifts q/2 by up to |grad_mean(q/2)|_1 e, with e
+      // the record's e_mean
       const double grad = std::fabs(g[3] * dx + g[4] * dy) + std::fabs(g[4] * dx + g[5] * dy);
-      const double epos = std::ldexp(std::max(std::max(std::fabs(g[1]), std::fabs(g[2])), 16.0), -21);
-      const double ma = std::fabs(std::log(araw * 255.0)) - grad * epos;
+      const double ma = std::fabs(std::log(araw * 255.0)) - grad * g[15];
       if (ma < mg) mg = ma;
       if (al < 1.0 / 255.0) continue;
       const double tt = T * (1.0 - al);
@@ -736,6 +747,16 @@ int64_t orc_blend_trace(const double* araw, const double* col, int64_t n, double
 // Format conversions used by the precision forms (exposed for their pins).
 float orc_round_bf16(float x) { return round_bf16(x); }
 double orc_round_e4m3(double x) { return round_e4m3(x); }
+
+// Threads of the parallel loops (timing the oracle at 1 thread and at all
+// cores); the arithmetic and its order per pixel / anchor do not depend on it.
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 
 int orc_num_threads(void) {
 #ifdef _OPENMP

@@ -12,17 +12,17 @@
 //
 // The array costs 4100 x 8 = 32,800 bytes on every GPU that loads the
 // library, held until the process exits.  Host code cannot use the array's
-// name as a device address, so the address is looked up once per device
-// with cudaGetSymbolAddress (under a mutex, on the first call made while
-// that device is current) and passed to the kernels.  Every call shares the
+// name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress for the device (and context) current at the call and
+// passes it to the kernels; nothing is cached across calls, so a reset
+// device or another context on the same device gets its own array's
+// address.  Every call shares the
 // array: the call resets the tile counter and error word and advances an
 // epoch, so look-back words left by earlier calls are never mistaken for
 // this call's; two calls whose kernels overlap on the GPU (other host
 // threads, other streams) race on the array and must be serialised by the
 // caller.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "gsc.h"
 #include "gsc_internal.cuh"
@@ -38,7 +38,6 @@ constexpr uint32_t NA_WORDS = NA_MAX_TILES + 4;  // look-back words + control wo
 constexpr uint32_t NA_CTRL = NA_MAX_TILES;       // [ctrl] tile counter, [ctrl+1] epoch, [ctrl+2] error bits
 constexpr uint32_t NA_ERR_SUM = 16u;             // the running sum reached 2^30
 constexpr uint32_t NA_SPIN = 1u << 20;
-constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scan_scratch[NA_WORDS];
 
@@ -114,10 +113,6 @@ __global__ void __launch_bounds__(NA_NT) k_noalloc_scan(const uint32_t* in, uint
   }
 }
 
-std::mutex g_mu;
-unsigned long long* g_addr[NA_MAX_DEVICES] = {};
-int g_nsm[NA_MAX_DEVICES] = {};
-
 }  // namespace
 }  // namespace gsc
 
@@ -126,25 +121,21 @@ extern "C" int gsc_scan_u32_noalloc(const uint32_t* d_in, uint32_t* d_out, uint6
   using namespace gsc;
   if (n > GSC_NOALLOC_SCAN_MAX_N) return GSC_ERR_INVALID_ARG;
   if (n > 0 && (!d_in || !d_out)) return GSC_ERR_INVALID_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return GSC_ERR_CUDA;
-  unsigned long long* scratch = nullptr;
-  int nsm = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scan_scratch) != cudaSuccess || !p) return GSC_ERR_CUDA;
-      int sms = 0;
-      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-        return GSC_ERR_CUDA;
-      g_nsm[dev] = sms;
-      g_addr[dev] = static_cast<unsigned long long*>(p);
-    }
-    scratch = g_addr[dev];
-    nsm = g_nsm[dev];
-  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the call ends by reading the error word back and synchronising the
+  // stream, neither of which a stream under capture allows
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return GSC_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return GSC_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GSC_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    return GSC_ERR_CUDA;
+  // the device address of this context's copy of the array (the array's
+  // name in host code is only a stand-in for it)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scan_scratch) != cudaSuccess || !p) return GSC_ERR_CUDA;
+  unsigned long long* scratch = static_cast<unsigned long long*>(p);
   if (n == 0) {
     if (d_total && cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s) != cudaSuccess) return GSC_ERR_CUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? GSC_OK : GSC_ERR_CUDA;

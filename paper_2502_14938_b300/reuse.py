@@ -8,7 +8,9 @@ train()     gsc_reuse_train from an initial parameter vector
 evaluate()  renders a path with the depth rule or with the predictor (label
             collection on, so every reuse decision can be scored) and
             reports reuse and wrong-reuse rates and PSNR against the same
-            form without the cache (so only the reuse error is measured)
+            form without the cache (so only the reuse error is measured);
+            it also returns the rendered values at given pixels of given
+            frames, for a caller that judges them against reference images
 save() / load()  the flat float32 parameter vector, with a small header
 """
 from __future__ import annotations
@@ -80,12 +82,14 @@ def train(z: np.ndarray, y: np.ndarray, theta0: np.ndarray, epochs: int = 40, ba
 
 
 def evaluate(model, path: Sequence[Tuple], theta: Optional[np.ndarray] = None, precision: str = "bf16",
-             psnr_every: int = 1) -> Dict:
+             psnr_every: int = 1, sample: Optional[Dict[int, Tuple[np.ndarray, np.ndarray]]] = None) -> Dict:
     """Render a stereo path from an empty cache with the depth rule (theta
     None) or the predictor; score every reuse by its label (a reuse of a
     line whose label is 0 is wrong) and the images by PSNR against the same
     form (precision, unified stereo) without the cache, every `psnr_every`
-    frames."""
+    frames.  sample: {frame: (px, py)}; the result's "samples" then holds,
+    per listed frame, the two eyes' rendered values at those pixels
+    ([2, n, 3] float32)."""
     import torch
     mode = "depth" if theta is None else "learned"
     r = Renderer(max_views=2, precision=precision, reuse=mode, stereo_unify=True, flags=FLAG_REUSE_COLLECT)
@@ -97,9 +101,14 @@ def evaluate(model, path: Sequence[Tuple], theta: Optional[np.ndarray] = None, p
     outs, routs = _outs(path[0][0]), _outs(path[0][0])
     vis = hits = wrong = cand = good = 0
     psnrs = []
+    samples = {}
     for f, (L, R) in enumerate(path):
         _pair(r, mid, L, R)
         st = r.render_frame(outs)
+        if sample and f in sample:
+            px, py = sample[f]
+            ix, iy = torch.as_tensor(px, device="cuda").long(), torch.as_tensor(py, device="cuda").long()
+            samples[f] = np.stack([o[iy, ix].cpu().numpy() for o in outs])
         z, y, vi = r.reuse_collect(0)
         vstat, _ = r.debug_cache(0)
         hit = (vstat & 0x80000000) != 0
@@ -121,7 +130,8 @@ def evaluate(model, path: Sequence[Tuple], theta: Optional[np.ndarray] = None, p
     return {"mode": mode, "frames": len(path), "reuse_frac": hits / max(vis, 1),
             "wrong_reuse_frac": wrong / max(hits, 1), "wrong_per_visible": wrong / max(vis, 1),
             "reusable_frac": good / max(vis, 1), "candidates_frac": cand / max(vis, 1),
-            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db_mean": float(np.mean(psnrs)) if psnrs else None}
+            "psnr_db_min": min(psnrs) if psnrs else None, "psnr_db_mean": float(np.mean(psnrs)) if psnrs else None,
+            "samples": samples}
 
 
 def save(path: str, theta: np.ndarray) -> None:

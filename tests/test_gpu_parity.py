@@ -20,6 +20,10 @@ pytestmark = pytest.mark.gpu
 
 PIX_TOL = 1e-3
 MARGIN = 1e-4
+# Share of pixels allowed to be undecided (some threshold decision of the
+# oracle within MARGIN, after the float32 mean-position term): 0.4-1.3%
+# measured on city frames of the ascending path.
+NEAR_FRAC = 0.02
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,28 +59,30 @@ def check_image(got, ref, margin, tag="", tol=PIX_TOL):
         k = np.unravel_index(np.argmax(np.where(ok[..., None] if err.ndim > ok.ndim else ok, err, 0)), err.shape)
         raise AssertionError(f"{tag}: max-abs {e_ok:.3e} on decided pixels at {k}: got {got[k[:-1]]} "
                              f"ref {ref[k[:-1]]} margin {margin[k[:-1]]}")
-    assert frac < 0.01, f"{tag}: {frac:.4f} of pixels near a threshold"
+    assert frac < NEAR_FRAC, f"{tag}: {frac:.4f} of pixels near a threshold"
     # near-threshold pixels still differ by at most one threshold-sized term
     if (~ok).any():
         assert err[~ok].max() < 0.05, f"{tag}: near-threshold pixel off by {err[~ok].max():.3e}"
     return e_ok, frac
 
 
-def check_keygen_and_sort(r, cams, tile=16):
+def check_keygen_and_sort(r, cams, tile=16, tile_h=None):
     """Stage-isolated: the GPU's float32 records through the oracle's float32
-    coverage give the same per-record tile counts, and sorting the oracle's
-    pairs by (tile key, depth key, record) gives the GPU's sorted pairs."""
+    coverage (tiles tile x tile_h pixels, tile_h defaulting to tile) give the
+    same per-record tile counts, and sorting the oracle's pairs by (tile key,
+    depth key, record) gives the GPU's sorted pairs and tile ranges."""
+    tw, th = tile, tile if tile_h is None else tile_h
     rec, dkey, cnt = r.debug_records()
     view = (rec[:, 11].view(np.uint32) & 0xFFFF).astype(np.int32)
     valid = (rec[:, 11].view(np.uint32) >> 31).astype(np.uint8)
-    ntiles = [((c.width + tile - 1) // tile) * ((c.height + tile - 1) // tile) for c in cams]
+    ntiles = [((c.width + tw - 1) // tw) * ((c.height + th - 1) // th) for c in cams]
     base = np.concatenate([[0], np.cumsum(ntiles)])
     keys_all, vals_all = [], []
     counts = np.zeros(len(rec), np.uint32)
     for v, c in enumerate(cams):
         sel = np.nonzero(view == v)[0]
         cn, k, vv = oracle.keygen_f32(rec[sel, 0], rec[sel, 1], rec[sel, 2], rec[sel, 3], rec[sel, 4],
-                                      rec[sel, 6], np.zeros(len(sel)), valid[sel], c.width, c.height, tile, tile)
+                                      rec[sel, 6], np.zeros(len(sel)), valid[sel], c.width, c.height, tw, th)
         counts[sel] = cn
         keys_all.append(k.astype(np.int64) + base[v])
         vals_all.append(sel[vv])

@@ -60,10 +60,17 @@ def test_gradient_matches_oracle_backprop():
     g, loss = r.debug_reuse_grad(Z, y)
     loss64, g64 = P.grad64(theta, Z, y)
     assert abs(loss - loss64) <= 1e-5 * loss64
-    # float32 sums of <= 4099 terms: normwise relative error per tensor
+    # every weight-gradient entry within 1e-2 of the float64 backprop,
+    # relative to the entry, with an absolute floor of 1e-4 of the tensor's
+    # largest entry for entries that cancel toward zero in the float32 sums
+    # of <= 4099 per-sample terms
     cuts = [0, P.NZ * P.NH, P.NZ * P.NH + P.NH, P.NZ * P.NH + 2 * P.NH, P.NPARAM]
     for a, b in zip(cuts[:-1], cuts[1:]):
-        err = np.linalg.norm(g[a:b] - g64[a:b]) / np.linalg.norm(g64[a:b])
+        ga, ra = g[a:b].astype(np.float64), g64[a:b]
+        tol = 1e-2 * np.abs(ra) + 1e-4 * np.abs(ra).max()
+        bad = np.abs(ga - ra) > tol
+        assert not bad.any(), (a, b, int(bad.sum()), int(np.argmax(np.abs(ga - ra) / tol)))
+        err = np.linalg.norm(ga - ra) / np.linalg.norm(ra)
         assert err < 1e-4, (a, b, err)
     r.close()
 
@@ -160,13 +167,29 @@ def test_collected_samples_match_oracle(precision):
     r.close()
 
 
+def oracle_judged_psnr(model, path, ev, refs):
+    """Per judged frame: PSNR of the sampled pixels of both eyes against the
+    float64 oracle's values there."""
+    out = []
+    for f, (ref0, ref1) in refs.items():
+        got = ev["samples"][f].astype(np.float64)
+        mse = (np.mean((got[0] - ref0) ** 2) + np.mean((got[1] - ref1) ** 2)) / 2
+        out.append(10 * np.log10(1.0 / max(mse, 1e-10)))
+    return np.array(out)
+
+
 def test_learned_beats_depth_rule_on_held_out_path():
     """Gain test: 100k labels from the look-around paths with seeds 20-29 on
-    the 2M-anchor city, GPU training, then the held-out path (seed 30):
-    against the depth rule of Eq. 4 the predictor must at least halve the
-    share of wrong reuses and raise the worst frame's PSNR (against the same
-    form without the cache) by >= 3 dB while still reusing more than half
-    the anchors."""
+    the 2M-anchor city, GPU training, then the held-out path (seed 30).
+    Against the depth rule of Eq. 4 the predictor must at least halve the
+    share of wrong reuses while still reusing more than half the anchors.
+    The oracle judges the error that reuse adds: on every 10th frame,
+    sampled pixels of both eyes against the float64 oracle's image of the
+    same form without the cache (unified stereo camera, BF16-rounded
+    derivation); the predictor's worst frame must be >= 3 dB above the depth
+    rule's and >= 40 dB.  PSNR against the plain float64 oracle (per-eye
+    derivation) is reported beside it: near the camera the unified view
+    direction of Eq. 5-6 alone can cost more than the reuse does."""
     from paper_2502_14938_b300 import reuse
     model, _ = gen.city_workload(n_frames=2)
     train_paths = [gen.stereo_frames(gen.reuse_path(s)) for s in range(20, 30)]
@@ -175,8 +198,32 @@ def test_learned_beats_depth_rule_on_held_out_path():
     theta, losses = reuse.train(Z, Y, gen.reuse_mlp_init(7), epochs=40, batch=4096, lr=2e-3)
     assert losses[-1] < 0.5 * losses[0]
     held = gen.stereo_frames(gen.reuse_path(30))
-    dep = reuse.evaluate(model, held, None)
-    lrn = reuse.evaluate(model, held, theta)
+    rs = np.random.default_rng(30)
+    W, H = held[0][0].width, held[0][0].height
+    judged = list(range(5, len(held), 10))
+    sample = {f: (rs.integers(0, W, 20000), rs.integers(0, H, 20000)) for f in judged}
+    q = oracle.OrcQuant()
+    q.mode = 1
+    refs, plain = {}, {}
+    for f in judged:
+        px, py = sample[f]
+        U = oracle.unified_camera(*held[f])
+        refs[f], plain[f] = [], []
+        for cam in held[f]:
+            vr = oracle.view_gaussians(model, cam, derive_cam=U, quant=q)
+            refs[f].append(oracle.render(vr.rec, vr.depth32, vr.gid, W, H, True, px, py)[0])
+            vp = oracle.view_gaussians(model, cam)
+            plain[f].append(oracle.render(vp.rec, vp.depth32, vp.gid, W, H, True, px, py)[0])
+    dep = reuse.evaluate(model, held, None, sample=sample)
+    lrn = reuse.evaluate(model, held, theta, sample=sample)
+    p_dep, p_lrn = oracle_judged_psnr(model, held, dep, refs), oracle_judged_psnr(model, held, lrn, refs)
+    q_dep, q_lrn = oracle_judged_psnr(model, held, dep, plain), oracle_judged_psnr(model, held, lrn, plain)
+    print(f"oracle-judged worst frame (form without the cache): depth rule {p_dep.min():.2f} dB, "
+          f"predictor {p_lrn.min():.2f} dB; against the plain oracle {q_dep.min():.2f} / {q_lrn.min():.2f} dB; "
+          f"against the GPU's uncached form {dep['psnr_db_min']:.2f} / {lrn['psnr_db_min']:.2f} dB; "
+          f"wrong reuses {dep['wrong_reuse_frac']:.3f} / {lrn['wrong_reuse_frac']:.3f}")
     assert lrn["wrong_reuse_frac"] <= 0.5 * dep["wrong_reuse_frac"], (dep, lrn)
-    assert lrn["psnr_db_min"] >= dep["psnr_db_min"] + 3.0, (dep, lrn)
     assert lrn["reuse_frac"] > 0.5, lrn
+    assert p_lrn.min() >= p_dep.min() + 3.0, (p_dep, p_lrn)
+    assert p_lrn.min() >= 40.0, p_lrn
+    assert q_lrn.min() >= q_dep.min(), (q_dep, q_lrn)
