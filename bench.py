@@ -623,6 +623,7 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
     return r, mid, outs, ms, wall
 
 
+# eager stage events of the library (GSC_FLAG_TIMING)
 STAGE_NAMES = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
 
 
@@ -775,9 +776,9 @@ def run_batched(args, flush):
     cam_lists = [cams(f, lambda sc: mids[sc]) for f in frames]
 
     def timed(setup, render):
-        for f in range(n):  # grow buffers, warm the graph
+        for f in range(n):  # grow buffers (synchronous frames), warm the graph
             setup(f)
-            render()
+            render(True)
         torch.cuda.synchronize()
         for rr in rends:
             rr.cache_reset()
@@ -787,7 +788,7 @@ def run_batched(args, flush):
             setup(f)
             flush.fill_(f & 0xFF)
             evs[f][0].record(stream)
-            render()
+            render(False)
             evs[f][1].record(stream)
         torch.cuda.synchronize()
         ms = np.array([a.elapsed_time(b) for a, b in evs])
@@ -797,12 +798,12 @@ def run_batched(args, flush):
 
     rends = [r]
     r.set_tiling(16, 16, 0)
-    untuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda: r.render_frame(outs, stats=False))
+    untuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda st: r.render_frame(outs, stats=st))
     r.set_cameras(cam_lists[0])
     t1 = time.perf_counter()
     best = autotune.tune(r, outs, args.tiling_cache, reps=3)
     t_tune = time.perf_counter() - t1
-    tuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda: r.render_frame(outs, stats=False))
+    tuned = timed(lambda f: r.set_cameras(cam_lists[f]), lambda st: r.render_frame(outs, stats=st))
     reuse = []
     for f in range(n):
         r.set_cameras(cam_lists[f])
@@ -823,9 +824,9 @@ def run_batched(args, flush):
         for rv, sel, cl in sep:
             rv.set_cameras(cl[f])
 
-    def sep_render():
+    def sep_render(st):
         for rv, sel, _ in sep:
-            rv.render_frame([outs[i] for i in sel], stats=False)
+            rv.render_frame([outs[i] for i in sel], stats=st)
 
     separate = timed(sep_setup, sep_render)
     for rv, _, _ in sep:

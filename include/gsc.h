@@ -197,9 +197,12 @@ GSC_API int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n);
 /* Render one frame: out_rgb[i] is a caller-owned DEVICE pointer to a float32
  * [height][width][3] image for camera i.  With stats != NULL the call waits
  * for the frame, grows the pair buffer and re-renders if it overflowed, and
- * fills *stats.  With stats == NULL the call only enqueues work; a pair
- * overflow or a wait timeout of such a frame is reported by the next
- * synchronising call (GSC_ERR_CAPACITY / GSC_ERR_TIMEOUT). */
+ * fills *stats.  With stats == NULL the call only enqueues work; a buffer
+ * overflow or a wait timeout of any such frame since the last synchronising
+ * call is reported by the next synchronising call (a render with stats,
+ * gsc_synchronize): GSC_ERR_TIMEOUT, or GSC_ERR_CAPACITY after the buffers
+ * have been grown to what those frames asked for.  The images of such a
+ * frame are then invalid; render it again. */
 GSC_API int gsc_render_frame(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats);
 
 /* Same as gsc_render_frame, but out_rgb[i] are HOST pointers (pinned or

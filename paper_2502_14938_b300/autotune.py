@@ -39,8 +39,8 @@ def time_frames(renderer, outs, reps: int = 5, warmup: int = 2, setups: Optional
     for setup in (setups or [None]):
         if setup is not None:
             setup()
-        for _ in range(warmup):
-            renderer.render_frame(outs, stats=False)
+        for _ in range(warmup):  # synchronous frames: buffers grow to this tiling's needs
+            renderer.render_frame(outs, stats=True)
         torch.cuda.synchronize()
         ts = []
         for _ in range(reps):

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -126,7 +127,8 @@ struct gsc_ctx {
   cudaEvent_t ev_rendered[2] = {}, ev_copied[2] = {};
   int hslot = 0;
   bool hpending[2] = {false, false};
-  bool keep_err = false;  // the frame being enqueued is a pipelined host frame
+  bool keep_err = false;  // the frame being enqueued is one nobody waits for (pipelined host / no stats)
+  bool async_since_sync = false;  // frames without statistics were enqueued since the last synchronising call
 };
 
 namespace {
@@ -659,19 +661,60 @@ void fill_stats(gsc_ctx* ctx, gsc_frame_stats* st) {
   }
 }
 
+// Errors of frames nobody waited for (pipelined host frames, frames without
+// statistics): a timeout, or an overflow, after which the buffers are grown
+// to what those frames asked for; their images are invalid.
+int take_sticky_error(gsc_ctx* ctx) {
+  uint32_t e[3] = {0, 0, 0};  // err_sticky, need_sticky[0..1]
+  static_assert(offsetof(FrameDev, need_sticky) == offsetof(FrameDev, err_sticky) + 4, "sticky words");
+  CK(cudaMemcpy(e, &ctx->d_fd->err_sticky, sizeof e, cudaMemcpyDeviceToHost));
+  if (!e[0]) return GSC_OK;
+  CK(cudaMemset(&ctx->d_fd->err_sticky, 0, sizeof e));
+  if (e[0] & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up in an unwaited frame");
+  if (e[0] & ERR_REC_OVERFLOW) {
+    unsigned long long worst = 0;
+    for (const auto& cam : ctx->cams) worst += (unsigned long long)K * ctx->models[cam.model_id].n;
+    unsigned long long need = (unsigned long long)e[1] + e[1] / 2 + 1024;
+    need = std::min<unsigned long long>(std::min(need, worst), 0x3FFFFFFFull);
+    if (need > ctx->rec_cap) {
+      int r = alloc_records(ctx, (uint32_t)need);
+      if (r) return r;
+    }
+  }
+  if (e[0] & ERR_PAIR_OVERFLOW) {
+    unsigned long long need = (unsigned long long)e[2] + e[2] / 4 + 1024;
+    need = std::min<unsigned long long>(need, 0x3FFFFFFFull);
+    if (need > ctx->pair_cap) {
+      int r = alloc_pairs(ctx, (uint32_t)need);
+      if (r) return r;
+    }
+  }
+  return fail(ctx, GSC_ERR_CAPACITY, "an unwaited frame overflowed a buffer (its images are invalid); buffers grown "
+                                     "to %u records, %u pairs", ctx->rec_cap, ctx->pair_cap);
+}
+
 int render_impl(gsc_ctx* ctx, void* const* out_dev, float* const* out_T, gsc_frame_stats* stats, bool sync) {
   if (!ctx->cams_set) return fail(ctx, GSC_ERR_STATE, "gsc_set_cameras must come first");
   if (ctx->cfg.reuse == GSC_REUSE_LEARNED && !ctx->reuse_set)
     return fail(ctx, GSC_ERR_STATE, "the learned reuse form needs predictor weights (gsc_reuse_set_weights)");
-  if (ctx->pending && sync) {
-    // report an earlier asynchronous frame's problem before starting this one
-    int r = finish_frame(ctx);
+  if (sync && (ctx->pending || ctx->async_since_sync)) {
+    // report the problems of earlier frames rendered without statistics
+    // (each kept its error bits on the device) before starting this one
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pending = false;
+    ctx->async_since_sync = false;
+    int r = take_sticky_error(ctx);
     if (r) return r;
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
+    ctx->keep_err = !sync;
     int r = enqueue_frame(ctx, out_dev, out_T);
+    ctx->keep_err = false;
     if (r) return r;
-    if (!sync) return GSC_OK;
+    if (!sync) {
+      ctx->async_since_sync = true;
+      return GSC_OK;
+    }
     r = finish_frame(ctx);
     if (r == GSC_ERR_CAPACITY) {  // grown: render the frame again
       ctx->replay_next = ctx->n_caches > 0;
@@ -1053,15 +1096,6 @@ int ensure_host_images(gsc_ctx* ctx, int set, void** outs) {
   return GSC_OK;
 }
 
-// Error bits of all frames since the last read (asynchronous frames).
-int take_sticky_error(gsc_ctx* ctx) {
-  uint32_t e = 0;
-  CK(cudaMemcpy(&e, &ctx->d_fd->err_sticky, 4, cudaMemcpyDeviceToHost));
-  if (!e) return GSC_OK;
-  CK(cudaMemset(&ctx->d_fd->err_sticky, 0, 4));
-  if (e & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up in a pipelined frame");
-  return fail(ctx, GSC_ERR_CAPACITY, "a pipelined frame overflowed a buffer; render a synchronous frame to grow it");
-}
 }  // namespace
 
 int gsc_render_frame_host(gsc_ctx* ctx, void* const* out_rgb, gsc_frame_stats* stats) {
@@ -1358,8 +1392,10 @@ int gsc_debug_cache(gsc_ctx* ctx, uint32_t d, uint32_t* vstat, uint64_t cap, uin
 int gsc_synchronize(gsc_ctx* ctx) {
   if (!ctx) return GSC_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
-  if (ctx->pending) return finish_frame(ctx);
-  return GSC_OK;
+  if (!ctx->pending && !ctx->async_since_sync) return GSC_OK;
+  ctx->pending = false;
+  ctx->async_since_sync = false;
+  return take_sticky_error(ctx);
 }
 
 // ------------------------------------------------------------------ debug exports

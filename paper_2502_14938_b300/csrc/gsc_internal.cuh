@@ -67,7 +67,7 @@ struct FrameIn {  // host -> device per frame
   uint32_t spin_limit;
   uint32_t total_tiles, tile_bits;
   uint32_t out_format;               // gsc_out_format
-  uint32_t keep_err;                 // 1: OR the frame's error bits into err_sticky (pipelined host frames)
+  uint32_t keep_err;                 // 1: OR the frame's error bits into err_sticky (frames nobody waits for)
   uint32_t pad[3];
   float bg[4];
   unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
@@ -109,6 +109,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
   alignas(16) uint32_t hist_depth[4 * 256];
   alignas(16) uint32_t hist_tile[4 * 256];
   uint32_t err_sticky;          // error bits of all frames since the host last read them
+  uint32_t need_sticky[2];      // largest records / pairs those frames asked for
   // blend work of the frame, counted only by the counting blend variant:
   // [0] (pixel, Gaussian) evaluations of the front-to-back walk (every
   //     Gaussian of the tile's list up to and including the one a pixel

@@ -348,6 +348,15 @@ __device__ __forceinline__ unsigned blend_record(PixState& ps, const BlendSmem& 
   return stopped;
 }
 
+// A frame whose statistics nobody waits for keeps its error bits and its
+// buffer needs until the host's next synchronising call reads them.
+__device__ __forceinline__ void keep_frame_error(FrameDev* fd, const FrameIn* fin) {
+  if (!fin->keep_err || !fd->err) return;
+  atomicOr(&fd->err_sticky, fd->err);
+  atomicMax(&fd->need_sticky[0], fd->n_records_need);
+  atomicMax(&fd->need_sticky[1], fd->n_pairs);
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, FrameDev* __restrict__ fd,
                                            const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -492,7 +501,7 @@ __global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend(FrameDev* __restrict_
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && fin->keep_err && fd->err) atomicOr(&fd->err_sticky, fd->err);
+  if (blockIdx.x == 0 && threadIdx.x == 0) keep_frame_error(fd, fin);
   blend_tile<COUNT>(blockIdx.x, sm, fd, ranges, vals, rec, fin);
 }
 
@@ -506,7 +515,7 @@ __global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend_persistent(FrameDev* 
                                                                    const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
   __shared__ uint32_t s_tile;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && fin->keep_err && fd->err) atomicOr(&fd->err_sticky, fd->err);
+  if (blockIdx.x == 0 && threadIdx.x == 0) keep_frame_error(fd, fin);
   const uint32_t total = fd->total_tiles;
   for (;;) {
     __syncthreads();

@@ -306,6 +306,30 @@ def test_graph_eager_host_and_growth_agree():
     assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
 
 
+def test_unwaited_frame_overflow_is_reported_and_buffers_grow():
+    """Frames rendered without statistics are not waited for: an overflow in
+    any of them is reported by the next synchronising call (after the pair
+    buffer has been grown to what they asked for), and the next frame fits."""
+    import paper_2502_14938_b300 as pkg
+    m, cam = gen.tiny_scene(), gen.tiny_camera()
+    ref_r = make_renderer(m, [cam])
+    (ref,), st_ref = render(ref_r, [cam])
+    ref_r.close()
+    r = make_renderer(m, [cam], pair_capacity=1000)
+    assert st_ref["pairs"] > 1000
+    outs = [torch.zeros((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")]
+    r.render_frame(outs, stats=False)  # overflows; nobody waits
+    r.render_frame(outs, stats=False)
+    with pytest.raises(pkg.GscError) as e:
+        r.synchronize()
+    assert e.value.code == -4
+    r.synchronize()  # reported once
+    (img,), st = render(r, [cam])
+    assert st["pairs"] == st_ref["pairs"] and st["error_flags"] == 0
+    assert np.array_equal(img, ref)
+    r.close()
+
+
 def test_invalid_arguments_are_rejected():
     import paper_2502_14938_b300 as pkg
     m, cam = gen.tiny_scene(n=50), gen.tiny_camera()
