@@ -217,6 +217,19 @@ def cull(model, cam) -> np.ndarray:
     return ids[:n]
 
 
+def cull_pair(model, left, right):
+    """The exact stereo form's filtering (a reading of Eq. 5-6, see below):
+    the ascending union of the two eyes' own visible sets (each eye's
+    frustum and LOD predicates, as `cull`), and per id a 2-bit mask of the
+    eyes that keep it (bit 0 left, bit 1 right).  Derivation then runs once
+    per id from the unified camera's centre, and each eye draws only its own
+    ids, so every eye sees exactly the anchors the per-eye method selects."""
+    a, b = cull(model, left), cull(model, right)
+    ids = np.union1d(a, b).astype(np.uint32)
+    eyes = np.isin(ids, a).astype(np.uint8) | (np.isin(ids, b).astype(np.uint8) << 1)
+    return ids, eyes
+
+
 def quant_none():
     return None
 
@@ -411,17 +424,28 @@ class ViewResult:
     gid: np.ndarray            # [V*k] global Gaussian id a*k + j
 
 
-def view_gaussians(model, cam, derive_cam=None, quant=None, attrs_override=None) -> ViewResult:
+def view_gaussians(model, cam, derive_cam=None, quant=None, attrs_override=None, pair=None) -> ViewResult:
     """Visible anchors, derived attributes and projected records of one view.
     `derive_cam` (default: `cam`) selects the anchors and the view direction
-    (the unified camera of Eq. 5-6 in the de-redundant stereo form)."""
+    (the unified camera of Eq. 5-6 in the de-redundant stereo form).  With
+    pair = (left, right) (cam one of them) the anchors are instead the
+    exact stereo form's (`cull_pair`): the union of the eyes' own sets,
+    derived from derive_cam's centre, of which `cam` draws only its own
+    (records of the other eye's anchors are not kept); a level fade is then
+    measured from `cam`, whose distances selected its anchors."""
     dc = cam if derive_cam is None else derive_cam
-    ids = cull(model, dc)
+    if pair is not None:
+        ids, eyes = cull_pair(model, *pair)
+        mine = (eyes >> (0 if cam is pair[0] else 1)) & 1
+    else:
+        ids = cull(model, dc)
     if attrs_override is not None:
         attrs, kept = attrs_override(ids)
     else:
         attrs, kept = derive(model, camera_center(dc), ids, quant)
-    rec, d32 = project_records(model, cam, ids, attrs, kept, derive_cam=dc)
+    if pair is not None:
+        kept = np.asarray(kept, np.uint8) & mine[:, None]
+    rec, d32 = project_records(model, cam, ids, attrs, kept, derive_cam=cam if pair is not None else dc)
     gid = (ids.astype(np.int64)[:, None] * model.k + np.arange(model.k)[None, :]).reshape(-1)
     return ViewResult(ids=ids, attrs=attrs, kept=kept, rec=rec, depth32=d32, gid=gid)
 

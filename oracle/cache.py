@@ -135,15 +135,16 @@ class CacheSim:
         return self.slot_attr[line[hit]].astype(np.float64)
 
 
-def cached_derive(model, dcam, sim: CacheSim, quant=None, theta=None):
+def cached_derive(model, dcam, sim: CacheSim, quant=None, theta=None, ids=None):
     """The derivation step of one frame in the cached form, for the derivation
-    camera dcam: filtering, the policy (the depth rule, or the predictor with
-    parameters theta), fresh derivation of the decoded anchors, float16 lines
-    for the hits.  Returns (ids, attrs [V,k,11], kept [V,k], hit mask, line
-    per anchor, depth used)."""
+    camera dcam: filtering (dcam's own, or the given ascending ids: the
+    exact stereo form's union of both eyes' sets), the policy (the depth
+    rule, or the predictor with parameters theta), fresh derivation of the
+    decoded anchors, float16 lines for the hits.  Returns (ids, attrs
+    [V,k,11], kept [V,k], hit mask, line per anchor, depth used)."""
     import oracle
     from oracle import predictor as P
-    ids = oracle.cull(model, dcam)
+    ids = oracle.cull(model, dcam) if ids is None else np.asarray(ids, np.uint32)
     d_now, dist = P.pinned_dir(model.pos[ids], oracle.camera_center(dcam))
     reuse = None
     if theta is not None:
@@ -167,7 +168,7 @@ def cached_derive(model, dcam, sim: CacheSim, quant=None, theta=None):
     return ids, attrs, kept, hit, line, used
 
 
-def collect_samples(model, dcam, sim: CacheSim, quant=None):
+def collect_samples(model, dcam, sim: CacheSim, quant=None, ids=None):
     """Predictor training samples of the coming frame (call before
     cached_derive for the same frame): for every visible anchor holding a
     valid line, its inputs z and its label (oracle.predictor.label of the
@@ -176,7 +177,7 @@ def collect_samples(model, dcam, sim: CacheSim, quant=None):
     how far the closest of the label's comparisons lies from its threshold."""
     import oracle
     from oracle import predictor as P
-    ids = oracle.cull(model, dcam)
+    ids = oracle.cull(model, dcam) if ids is None else np.asarray(ids, np.uint32)
     valid, line, _ = sim.peek(ids)
     v = np.nonzero(valid)[0]
     pc = oracle.camera_center(dcam)
@@ -189,10 +190,16 @@ def collect_samples(model, dcam, sim: CacheSim, quant=None):
     return v, z, P.label(cached, fresh), P.label_margin(cached, fresh)
 
 
-def project_view(model, cam, ids, attrs, kept, derive_cam=None):
+def project_view(model, cam, ids, attrs, kept, derive_cam=None, mine=None):
     """Records of one camera from attributes of the visible anchors (of the
-    derivation camera `derive_cam`, which a level fade measures from)."""
+    derivation camera `derive_cam`, which a level fade measures from).  In
+    the exact stereo form `mine` marks the ids this camera keeps itself
+    (bit of oracle.cull_pair's mask); the others' records are not kept and a
+    level fade is measured from the camera."""
     import oracle
+    if mine is not None:
+        kept = np.asarray(kept, np.uint8) & np.asarray(mine, np.uint8)[:, None]
+        derive_cam = cam
     rec, d32 = oracle.project_records(model, cam, ids, attrs, kept, derive_cam=derive_cam)
     gid = (np.asarray(ids, np.int64)[:, None] * model.k + np.arange(model.k)[None, :]).reshape(-1)
     return oracle.ViewResult(ids=ids, attrs=attrs, kept=kept, rec=rec, depth32=d32, gid=gid)

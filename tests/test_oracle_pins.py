@@ -298,6 +298,50 @@ def test_unified_camera_contains_both_eyes():
         assert len(u) < 1.2 * len(a)
 
 
+def test_exact_stereo_sets_are_the_eyes_own():
+    """The exact stereo form's filtering: the union of the eyes' sets, each
+    eye recovering exactly its own set from the mask (city scene with LOD)."""
+    m = gen.city_scene(n=300_000, seed=5)
+    poses = gen.city_path(n_frames=40, seed=6, start=(-100.0, 50.0), h0=3.0, h1=120.0)
+    for pose in poses[::13]:
+        L, R = gen.stereo_pair(gen.look_rotation(pose.yaw, pose.pitch), pose.pos, 1920, 1080, 60.0)
+        ids, eyes = oracle.cull_pair(m, L, R)
+        a, b = oracle.cull(m, L), oracle.cull(m, R)
+        assert np.all(np.diff(ids.astype(np.int64)) > 0)
+        assert np.array_equal(ids[(eyes & 1) != 0], a) and np.array_equal(ids[(eyes & 2) != 0], b)
+        assert np.all(eyes != 0) and len(ids) == len(np.union1d(a, b))
+
+
+def test_exact_stereo_form_equals_per_eye_for_a_view_independent_model():
+    """If the MLPs ignore the view direction (its W1 rows zero), deriving once
+    from the unified camera changes nothing, so the exact stereo form must
+    give the plain per-eye image bit for bit.  On the same frames the paper's
+    enclosing unified frustum does not (it admits anchors an eye's own filter
+    drops), nor does drawing the whole union in each eye."""
+    m = gen.city_scene(n=300_000, seed=5)
+    for h in range(3):
+        m.W1[h][32:35, :] = 0.0
+    poses = gen.city_path(n_frames=40, seed=6, start=(-100.0, 50.0), h0=3.0, h1=120.0)
+    union_differs = enclosing_differs = 0
+    for pose in (poses[15], poses[18]):
+        L, R = gen.stereo_pair(gen.look_rotation(pose.yaw, pose.pitch), pose.pos, 480, 270, 60.0)
+        U = oracle.unified_camera(L, R)
+        ids, _ = oracle.cull_pair(m, L, R)
+        attrs, kept = oracle.derive(m, oracle.camera_center(U), ids)
+        gid = (ids.astype(np.int64)[:, None] * m.k + np.arange(m.k)[None, :]).reshape(-1)
+        for cam in (L, R):
+            (plain, T0, _, _), _ = oracle.render_view(m, cam)
+            vr = oracle.view_gaussians(m, cam, derive_cam=U, pair=(L, R))
+            exact, T1, _, _ = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height)
+            assert np.array_equal(exact, plain) and np.array_equal(T0, T1)
+            rec, d32 = oracle.project_records(m, cam, ids, attrs, kept)  # the whole union in this eye
+            union_differs += not np.array_equal(oracle.render(rec, d32, gid, cam.width, cam.height)[0], plain)
+            ve = oracle.view_gaussians(m, cam, derive_cam=U)  # Eq. 6's enclosing frustum
+            enclosing_differs += not np.array_equal(oracle.render(ve.rec, ve.depth32, ve.gid, cam.width,
+                                                                  cam.height)[0], plain)
+    assert union_differs >= 2 and enclosing_differs >= 3
+
+
 # ---------------------------------------------------------------- exact tile coverage
 def test_tile_coverage_exact_vs_dense_sampling():
     """A tile is listed iff the hull of its pixel centres meets the ellipse
