@@ -317,8 +317,15 @@ FORMS = {
     "fp8": dict(precision="fp8", stereo_unify=False, reuse="off"),
     "fp8_unified": dict(precision="fp8", stereo_unify=True, reuse="off"),
     "cached_fp8_unified": dict(precision="fp8", stereo_unify=True, reuse="depth"),
+    # exact stereo form: each eye filters its own anchors, the union is derived once
+    "exact": dict(precision="fp32", stereo_unify="exact", reuse="off"),
+    "bf16_exact": dict(precision="bf16", stereo_unify="exact", reuse="off"),
+    "cached_exact": dict(precision="fp32", stereo_unify="exact", reuse="depth"),
+    "cached_bf16_exact": dict(precision="bf16", stereo_unify="exact", reuse="depth"),
+    "fp8_exact": dict(precision="fp8", stereo_unify="exact", reuse="off"),
+    "cached_fp8_exact": dict(precision="fp8", stereo_unify="exact", reuse="depth"),
 }
-HEADLINE = "cached_bf16_unified"
+HEADLINE = "cached_bf16_exact"
 FP32_LANE_OPS = 148 * 128 * 2.032e9  # SMs x FP32 lanes x max SM clock: FP32 lane operations / s
 # Algorithmic work of one (pixel, Gaussian) evaluation of the blend: ~20 FP32
 # operations (offset, quadratic form, opacity product and clamp, the two
@@ -366,10 +373,10 @@ def set_pair(r, mid, L, R):
 # form with one optimisation removed at a time (the paper's "w/o kernels",
 # its PyTorch op-by-op pipeline, has no counterpart here: every stage is a
 # kernel of this library).
-ABLATION = (("full: cached + BF16 + unified stereo", "cached_bf16_unified"),
+ABLATION = (("full: cached + BF16 + shared stereo derivation", "cached_bf16_exact"),
             ("w/o de-redundancy (per-eye derivation)", "cached_bf16"),
-            ("w/o reuse", "bf16_unified"),
-            ("w/o BF16 (FP32 MLPs)", "cached_unified"),
+            ("w/o reuse", "bf16_exact"),
+            ("w/o BF16 (FP32 MLPs)", "cached_exact"),
             ("none: plain FP32, per eye, no cache", "plain"))
 
 
@@ -742,7 +749,7 @@ def stage_hbm(stage_ms, st, form, W, H, n_anchors):
     return out
 
 
-BATCHED_FORM = dict(stereo_unify=True, precision="bf16", reuse="depth")
+BATCHED_FORM = dict(stereo_unify="exact", precision="bf16", reuse="depth")
 
 
 def run_batched(args, flush):
@@ -833,7 +840,8 @@ def run_batched(args, flush):
         rv.close()
     r.close()
     return {"workload": "3 city scenes 0.5M/2M/4M anchors, 8 viewers, 13 images (5 stereo pairs + 3 mono, "
-                        "1280x720..1920x1080), BF16 + cache + unified stereo, one frame = all 13 images",
+                        "1280x720..1920x1080), BF16 + cache + shared (exact) stereo derivation, one frame = all "
+                        "13 images",
             "frames": n, "images": n_img, "pixels_per_frame": pixels, "tuned": tuned,
             "tiling": {k: best[k] for k in ("tile_w", "tile_h", "blocks_per_sm", "ms")},
             "untuned_16x16_per_tile": untuned, "separate_contexts": separate,
@@ -1158,7 +1166,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default=HEADLINE, choices=sorted(FORMS))
-    ap.add_argument("--compare", nargs="*", default=["plain", "bf16_unified", "fp8_unified", "cached_fp8_unified"],
+    ap.add_argument("--compare", nargs="*", default=["plain", "bf16_exact", "cached_bf16_unified", "fp8_exact",
+                                                     "cached_fp8_exact"],
                     help="other forms timed for comparison")
     ap.add_argument("--psnr-frames", type=int, nargs="*", default=list(range(0, 300, 10)),
                     help="path frames compared with the float64 oracle (default: every 10th frame)")

@@ -94,11 +94,18 @@ typedef enum {
 #define GSC_FLAG_REUSE_COLLECT 0x8u /* reuse forms: record predictor inputs + labels (gsc_reuse_collect) */
 #define GSC_FLAG_BLEND_WORK 0x10u  /* blend counts its work per frame (gsc_debug_blend_work); slower */
 
+enum { GSC_STEREO_OFF = 0, GSC_STEREO_UNIFIED = 1, GSC_STEREO_EXACT = 2 };
+
 typedef struct {
   uint32_t max_views;        /* cameras per frame, 1..GSC_MAX_VIEWS */
   uint32_t precision;        /* gsc_precision of the derivation MLPs */
   uint32_t reuse;            /* gsc_reuse_mode */
-  uint32_t stereo_unify;     /* 1: cameras with a stereo partner share one Eq. 5-6 derivation */
+  uint32_t stereo_unify;     /* cameras with a stereo partner share one derivation from the Eq. 5-6
+                                unified camera (its centre gives the view direction, one cache):
+                                1 the unified camera's frustum and LOD filter the anchors for both eyes
+                                (Eq. 6); 2 (GSC_STEREO_EXACT) the union of the two eyes' own filters,
+                                each eye drawing only its own anchors, so that every eye's anchor
+                                set is the per-eye method's; 0 off (per-eye derivation) */
   uint32_t cache_gaussians;  /* cache capacity in Gaussians per derivation view (0 = 4M) */
   uint32_t max_depth;        /* D_max of Alg. 1 (0 = 10) */
   uint32_t tile_w, tile_h;   /* blend tile in pixels (0 = 16 x 16): tile_w in {8, 16, 32}, tile_h a power of

@@ -23,6 +23,12 @@ extern "C" {
  * lower-indexed camera.  Unit: uint32 ids. */
 GSC_API int gsc_debug_visible(gsc_ctx* ctx, uint32_t d, uint32_t* ids, uint64_t cap, uint64_t* n);
 
+/* Exact stereo form (stereo_unify = GSC_STEREO_EXACT): for derivation view
+ * d's visible anchors (as gsc_debug_visible), a mask of the cameras whose
+ * own filter keeps each (bit 0: the pair's lower-indexed camera, bit 1: the
+ * other).  Only meaningful for exact stereo views.  Unit: uint8 masks. */
+GSC_API int gsc_debug_visible_eyes(gsc_ctx* ctx, uint32_t d, uint8_t* eyes, uint64_t cap, uint64_t* n);
+
 /* Number of derivation views of the last frame and the camera each feeds. */
 GSC_API int gsc_debug_dviews(gsc_ctx* ctx, uint32_t* n_dviews, int32_t* first_cam /* [GSC_MAX_VIEWS] */);
 

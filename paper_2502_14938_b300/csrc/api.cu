@@ -71,6 +71,8 @@ struct gsc_ctx {
   uint32_t vis_cap = 0, n_vis_slots = 0;
   uint32_t* d_vis_buf = nullptr;
   uint32_t** d_vis_tab = nullptr;
+  uint8_t* d_eye_buf = nullptr;   // exact stereo views: eye mask per visible anchor (same slots)
+  uint8_t** d_eye_tab = nullptr;
   float* d_dbg_buf = nullptr;
   float** d_dbg_tab = nullptr;
   uint32_t rec_cap = 0;
@@ -362,7 +364,8 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
   for (int m : ctx->models_used)
-    launch_cull(ctx->d_models, m, ctx->models[m].dev.lod_r != nullptr, fd, ctx->d_vis_tab, ctx->st_cull, ctx->n_sm,
+    launch_cull(ctx->d_models, m, ctx->models[m].dev.lod_r != nullptr, fd, ctx->d_vis_tab, ctx->d_eye_tab, ctx->st_cull,
+                ctx->n_sm,
                 s);
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
@@ -380,7 +383,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
                        ctx->cfg.reuse == GSC_REUSE_LEARNED, collect ? ctx->attrs_fresh : nullptr, ctx->st_scan,
                        ctx->n_sm, s);
-  launch_tables(fd, caches, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
+  launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   for (int m : ctx->models_used)
     if (tc)
@@ -560,6 +563,7 @@ void prepare_frame_cameras(const gsc_ctx* ctx, FrameIn& F) {
     }
     F.dview_cam[nd][0] = (int)c;
     F.dview_cam[nd][1] = pair ? p : -1;
+    F.dview_exact[nd] = pair && ctx->cfg.stereo_unify == GSC_STEREO_EXACT ? 1 : 0;
     F.dview_of_cam[c] = (int)nd;
     ++nd;
   }
@@ -806,6 +810,8 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cudaMemset(ctx->d_fd, 0, sizeof(FrameDev)) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (cudaMalloc((void**)&ctx->d_models, sizeof(ModelDev) * MAX_MODELS) != cudaSuccess) return bail(GSC_ERR_OOM);
   if (cudaMalloc((void**)&ctx->d_vis_tab, sizeof(uint32_t*) * MAXV) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMalloc((void**)&ctx->d_eye_tab, sizeof(uint8_t*) * MAXV) != cudaSuccess) return bail(GSC_ERR_OOM);
+  if (cudaMemset(ctx->d_eye_tab, 0, sizeof(uint8_t*) * MAXV) != cudaSuccess) return bail(GSC_ERR_CUDA);
   if (cudaMalloc((void**)&ctx->sb.hist, sizeof(uint32_t) * 4 * 256) != cudaSuccess) return bail(GSC_ERR_OOM);
   if (alloc_pairs(ctx, (uint32_t)cfg.pair_capacity) != GSC_OK) return bail(GSC_ERR_OOM);
   *out = ctx;
@@ -821,7 +827,7 @@ void gsc_destroy(gsc_ctx* ctx) {
     dfree(m.feat.p); dfree(m.offs.p); dfree(m.scale.p); dfree(m.w32.p);
     dfree(m.feat_bf16.p); dfree(m.w_tc.p); dfree(m.feat_fp8.p); dfree(m.w_tc8.p);
   }
-  void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
+  void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_eye_buf, ctx->d_eye_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
@@ -1018,6 +1024,10 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
     std::vector<uint32_t*> tab(MAXV, nullptr);
     for (uint32_t i = 0; i < slots; ++i) tab[i] = ctx->d_vis_buf + (size_t)vcap * i;
     CK(cudaMemcpy(ctx->d_vis_tab, tab.data(), sizeof(uint32_t*) * MAXV, cudaMemcpyHostToDevice));
+    if ((r = dalloc(ctx, &ctx->d_eye_buf, (size_t)vcap * slots))) return r;
+    std::vector<uint8_t*> etab(MAXV, nullptr);
+    for (uint32_t i = 0; i < slots; ++i) etab[i] = ctx->d_eye_buf + (size_t)vcap * i;
+    CK(cudaMemcpy(ctx->d_eye_tab, etab.data(), sizeof(uint8_t*) * MAXV, cudaMemcpyHostToDevice));
     ctx->vis_cap = vcap;
     ctx->n_vis_slots = slots;
     if (ctx->cfg.flags & GSC_FLAG_DEBUG_ATTRS) {
@@ -1419,6 +1429,16 @@ int gsc_debug_visible(gsc_ctx* ctx, uint32_t d, uint32_t* ids, uint64_t cap, uin
   *n = cnt;
   if (!ctx->d_vis_buf || d >= ctx->n_vis_slots) return cnt ? GSC_ERR_STATE : GSC_OK;
   return dbg_copy(ctx, ids, ctx->d_vis_buf + (size_t)ctx->vis_cap * d, cnt, cap, 4);
+}
+
+int gsc_debug_visible_eyes(gsc_ctx* ctx, uint32_t d, uint8_t* eyes, uint64_t cap, uint64_t* n) {
+  int r = dbg_sync(ctx);
+  if (r) return r;
+  if (d >= MAXV || !n) return fail(ctx, GSC_ERR_INVALID_ARG, "bad view");
+  uint32_t cnt = ctx->h_cnt->vis_count[d];
+  *n = cnt;
+  if (!ctx->d_eye_buf || d >= ctx->n_vis_slots) return cnt ? GSC_ERR_STATE : GSC_OK;
+  return dbg_copy(ctx, eyes, ctx->d_eye_buf + (size_t)ctx->vis_cap * d, cnt, cap, 1);
 }
 
 int gsc_debug_dviews(gsc_ctx* ctx, uint32_t* n_dviews, int32_t* first_cam) {

@@ -41,6 +41,7 @@ struct ProjTab {              // every derivation view, for the projection
   int model[MAXV];
   const uint32_t* vstat[MAXV];
   const uint2* lattr[MAXV];
+  const uint8_t* eyes[MAXV];  // exact stereo views: eye mask per visible anchor (else null)
   ProjCam cam[MAXV][2];
 };
 

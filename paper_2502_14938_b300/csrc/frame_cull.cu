@@ -23,6 +23,7 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
     fd->dcam[lane] = F.dcam[lane];
     fd->dview_cam[lane][0] = F.dview_cam[lane][0];
     fd->dview_cam[lane][1] = F.dview_cam[lane][1];
+    fd->dview_exact[lane] = F.dview_exact[lane];
     fd->vis_count[lane] = 0;
   }
   if (lane == 0) {
@@ -93,8 +94,9 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) 
 
 // ------------------------------------------------------------------ culling (K1)
 // Anchor filtering (Sec. 3.2; Alg. 1 "anchors indexing and filtering"): for
-// every derivation view of this model, frustum test with a 1.3 guard band and
-// the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max 2^-l)^2,
+// every derivation view of this model (for an exact stereo view: for each of
+// its two cameras, the view keeping the union), frustum test with a 1.3 guard
+// band and the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max 2^-l)^2,
 // level 0 always; with Octree-GS level offsets the threshold is the anchor's
 // own radius r_a = d_max 2^(Delta_a - l), rounded to float32 at load: the
 // RADIUS instantiation).  Float32 with an explicit operation order.  Each thread
@@ -109,10 +111,12 @@ constexpr int CULL_GROUP = 8;    // views tested together (one warp walks back p
 
 template <bool RADIUS>
 __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
-                                                  uint32_t* const* __restrict__ vis, unsigned long long* status) {
+                                                  uint32_t* const* __restrict__ vis, uint8_t* const* __restrict__ eyes,
+                                                  unsigned long long* status) {
   __shared__ int s_d[CULL_MAXD];
   __shared__ int s_nd;
-  __shared__ float s_cam[CULL_MAXD][20];
+  __shared__ float s_cam[CULL_MAXD][2][20];
+  __shared__ int s_ncam[CULL_MAXD];
   __shared__ float s_thr2[32];  // plain rule: (d_max 2^-l)^2 per level, +inf at level 0
   __shared__ uint32_t s_warp[CULL_NT / 32 + 1];
   __shared__ uint32_t s_total[CULL_MAXD];
@@ -130,9 +134,13 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
   }
   __syncthreads();
   const int nd = s_nd;
-  for (int i = threadIdx.x; i < nd * 20; i += CULL_NT) {
-    const int ld = i / 20, f = i % 20;
-    const CamDev& c = fd->dcam[s_d[ld]];
+  if (threadIdx.x < (unsigned)nd) s_ncam[threadIdx.x] = fd->dview_exact[s_d[threadIdx.x]] ? 2 : 1;
+  for (int i = threadIdx.x; i < nd * 40; i += CULL_NT) {
+    const int ld = i / 40, k = (i / 20) & 1, f = i % 20;
+    const int d = s_d[ld];
+    const bool exact = fd->dview_exact[d] != 0;
+    if (k == 1 && !exact) continue;
+    const CamDev& c = exact ? fd->cam[fd->dview_cam[d][k]] : fd->dcam[d];
     float v;
     if (f < 9) v = c.R[f];
     else if (f < 12) v = c.t[f - 9];
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
     else if (f == 16) v = c.gx;
     else if (f == 17) v = c.gy;
     else v = 0.f;
-    s_cam[ld][f] = v;
+    s_cam[ld][k][f] = v;
   }
   if (!RADIUS && threadIdx.x < 32) {
     const float thr = ldexpf(md.lod_dmax, -(int)threadIdx.x);
@@ -204,6 +212,8 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
       }
     }
     for (int g0 = 0; g0 < nd; g0 += CULL_GROUP) {  // views g0 .. g0 + 7 of this model
+      // mask[u]: bits 0-7 the view keeps anchor i, bits 8-15 / 16-23 its first /
+      // second camera does (exact stereo views)
       uint32_t excl[CULL_GROUP], mask[CULL_GROUP];
 #pragma unroll
       for (int u = 0; u < CULL_GROUP; ++u) {
@@ -211,25 +221,29 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
         excl[u] = 0;
         mask[u] = 0;
         if (ld >= nd) continue;
-        const float* c = s_cam[ld];
         uint32_t m = 0;
+        for (int k = 0; k < s_ncam[ld]; ++k) {
+          const float* c = s_cam[ld][k];
+          uint32_t mk = 0;
 #pragma unroll
-        for (int i = 0; i < CULL_IPT; ++i) {
-          if (!RADIUS && lv[i] < 0) continue;
-          const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
-          const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
-          const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
-          bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-          if (v) {
-            const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
-            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : s_thr2[lv[i]]);
+          for (int i = 0; i < CULL_IPT; ++i) {
+            if (!RADIUS && lv[i] < 0) continue;
+            const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
+            const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
+            const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
+            bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
+            if (v) {
+              const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
+              const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+              v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : s_thr2[lv[i]]);
+            }
+            if (v) mk |= 1u << i;
           }
-          if (v) m |= 1u << i;
+          m |= mk | (mk << (8 + 8 * k));
         }
         mask[u] = m;
         uint32_t tot;
-        excl[u] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m), s_warp, &tot);
+        excl[u] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m & 0xFFu), s_warp, &tot);
         if (threadIdx.x == 0) s_total[ld] = tot;
       }
       __syncthreads();
@@ -257,11 +271,14 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
         const int lw = g0 + u;
         if (lw >= nd) continue;
         uint32_t* out = vis[s_d[lw]];
+        uint8_t* eo = s_ncam[lw] == 2 ? eyes[s_d[lw]] : nullptr;
         uint32_t o = s_base[lw] + excl[u];
-        uint32_t m = mask[u];
+        const uint32_t mm = mask[u];
+        uint32_t m = mm & 0xFFu;
         while (m) {
           const int i = __ffs(m) - 1;
           m &= m - 1;
+          if (eo) eo[o] = (uint8_t)(((mm >> (8 + i)) & 1u) | (((mm >> (16 + i)) & 1u) << 1));
           out[o++] = a0 + (uint32_t)i;
         }
       }
@@ -271,11 +288,11 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
 }
 
 void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
-                 unsigned long long* status, int n_sm, cudaStream_t s) {
+                 uint8_t* const* eyes_dev, unsigned long long* status, int n_sm, cudaStream_t s) {
   if (radius)
-    k_cull<true><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
+    k_cull<true><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, status);
   else
-    k_cull<false><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, status);
+    k_cull<false><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, status);
 }
 
 // ------------------------------------------------------------------ plan

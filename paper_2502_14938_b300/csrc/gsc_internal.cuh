@@ -76,6 +76,7 @@ struct FrameIn {  // host -> device per frame
   CamDev dcam[MAXV];                 // derivation views (unified camera of a stereo pair, Eq. 5-6)
   int32_t dview_of_cam[MAXV];
   int32_t dview_cam[MAXV][2];
+  int32_t dview_exact[MAXV];         // 1: a stereo pair filtered by the union of its eyes' own filters
 };
 
 struct FrameDev {  // device-resident per-frame plan and counters
@@ -88,6 +89,8 @@ struct FrameDev {  // device-resident per-frame plan and counters
   CamDev dcam[MAXV];
   int32_t dview_of_cam[MAXV];
   int32_t dview_cam[MAXV][2];   // cameras fed by a derivation view (-1 unused)
+  int32_t dview_exact[MAXV];    // 1: the view's anchors are the union of its two cameras' own sets,
+                                // with a per-anchor mask of the cameras that keep it (exact stereo form)
   // after culling
   uint32_t vis_count[MAXV];
   uint32_t item_base[MAXV + 1];  // prefix over derivation views of vis_count
@@ -403,8 +406,10 @@ constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
+// eyes_dev: per derivation view, the eye mask of each visible anchor (bit e:
+// camera dview_cam[d][e] keeps it), written for exact stereo views only.
 void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
-                 unsigned long long* status, int n_sm, cudaStream_t s);
+                 uint8_t* const* eyes_dev, unsigned long long* status, int n_sm, cudaStream_t s);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();
 cudaError_t prepare_derive_tc();
@@ -416,8 +421,8 @@ struct DViewSet;
 struct ProjTab;
 size_t dview_set_bytes();
 size_t proj_tab_bytes();
-void launch_tables(const FrameDev* fd, const CacheDev* caches, DViewSet* tabs, ProjTab* ptab, int n_models,
-                   cudaStream_t s);
+void launch_tables(const FrameDev* fd, const CacheDev* caches, uint8_t* const* eyes_dev, DViewSet* tabs,
+                   ProjTab* ptab, int n_models, cudaStream_t s);
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                       float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, const CUtensorMap* tmap,
                       uint4* compact, bool fp8, int n_sm, cudaStream_t s);

@@ -15,6 +15,21 @@ namespace gsc {
 
 constexpr int PJ_NT = 256;
 
+// Octree-GS level fade of anchor a (level >= 1) seen from centre pc: w =
+// clamp(u / beta, 0, 1), u = log2(r_a / d) the levels it lies inside its
+// switching distance.  d^2 is the cull's float32 squared distance (same
+// operations, same centre), so u >= 0 exactly for every anchor that filter
+// kept; u = log1p((r^2 - d^2) / d^2) / (2 ln 2), with r^2 - d^2 rounded once,
+// stays accurate relative to itself as the anchor nears its switch.
+__device__ __forceinline__ float lod_fade(const ModelDev& md, uint32_t a, float xa, float ya, float za,
+                                          const float* pc) {
+  const float ra = __ldg(md.lod_r + a);
+  const float dx = __fsub_rn(xa, pc[0]), dy = __fsub_rn(ya, pc[1]), dz = __fsub_rn(za, pc[2]);
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  const float u = 0.72134752f * log1pf(__fdiv_rn(fmaf(ra, ra, -d2), d2));
+  return fminf(1.f, fmaxf(0.f, __fdiv_rn(u, md.lod_beta)));
+}
+
 __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict__ models, FrameDev* __restrict__ fd,
                                                    uint32_t* const* __restrict__ vis, const float4* __restrict__ attrs,
                                                    const CacheDev* __restrict__ caches, Records rec,
@@ -34,6 +49,7 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
       const bool cached = caches && d < MAX_CACHES && caches[d].active;
       P.vstat[d] = cached ? caches[d].vstat : nullptr;
       P.lattr[d] = cached ? caches[d].slot_attr : nullptr;
+      P.eyes[d] = nullptr;  // (frames always pass the table; exact stereo views need it)
       for (int e = 0; e < 2; ++e) fill_projcam(P.cam[d][e], fd, fd->dview_cam[d][e]);
     }
     P.ibase[nd] = fd->n_items;
@@ -43,6 +59,7 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
   const int* s_model = P.model;
   const uint32_t* const* s_vstat = P.vstat;
   const uint2* const* s_lattr = P.lattr;
+  const uint8_t* const* s_eyes = P.eyes;
   ProjCam (*s_cam)[2] = P.cam;
   const uint32_t n = fd->n_items * (uint32_t)K;
   const uint32_t rec_cap = fd->n_records;
@@ -76,20 +93,13 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
       a2 = attrs[3 * (size_t)g + 2];
     }
     const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
+    // Octree-GS level fade, from this frame's distance (so after the cache),
+    // measured from the camera whose filter selected the anchor: the
+    // derivation camera, or in an exact stereo view each eye itself
+    const bool fade = md.lod_beta > 0.f && __ldg(md.lod_r + a) < INFINITY;
+    const uint8_t eb = s_eyes[d] ? s_eyes[d][vi] : (uint8_t)3;
     float alpha = a0.x;
-    if (md.lod_beta > 0.f) {  // Octree-GS level fade, from this frame's distance (so after the cache)
-      const float ra = __ldg(md.lod_r + a);
-      if (ra < INFINITY) {  // level >= 1: u = log2(r_a / d) levels inside the switching distance
-        // d^2 is the cull's float32 squared distance (same operations), so u >= 0 exactly for
-        // every anchor the cull kept; u = log1p((r^2 - d^2) / d^2) / (2 ln 2), with r^2 - d^2
-        // rounded once, keeps u accurate relative to itself as the anchor nears its switch
-        const float* pc = fd->dcam[d].pc;  // the derivation camera, as in the cull
-        const float dx = __fsub_rn(xa, pc[0]), dy = __fsub_rn(ya, pc[1]), dz = __fsub_rn(za, pc[2]);
-        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        const float u = 0.72134752f * log1pf(__fdiv_rn(fmaf(ra, ra, -d2), d2));
-        alpha = alpha * fminf(1.f, fmaxf(0.f, __fdiv_rn(u, md.lod_beta)));
-      }
-    }
+    if (fade && !s_eyes[d]) alpha *= lod_fade(md, a, xa, ya, za, fd->dcam[d].pc);
     const bool kept = alpha > 0.f;
     const float col[3] = {a0.y, a0.z, a0.w};
     const float s[3] = {a1.x, a1.y, a1.z};
@@ -105,7 +115,13 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
       if (r >= rec_cap) continue;
       const float rel[3] = {((xa - pc.pc[0]) - pc.pc_lo[0]) + o3[0], ((ya - pc.pc[1]) - pc.pc_lo[1]) + o3[1],
                             ((za - pc.pc[2]) - pc.pc_lo[2]) + o3[2]};
-      const uint32_t key = project_write(pc, rec, r, mu, rel, alpha, kept, col, s, q, TW, TH);
+      float alpha_e = alpha;
+      bool kept_e = kept;
+      if (s_eyes[d]) {  // exact stereo view: this eye draws only the anchors its own filter kept
+        if (fade) alpha_e = a0.x * lod_fade(md, a, xa, ya, za, pc.pc);
+        kept_e = ((eb >> e) & 1u) && alpha_e > 0.f;
+      }
+      const uint32_t key = project_write(pc, rec, r, mu, rel, alpha_e, kept_e, col, s, q, TW, TH);
       if (key != INVALID_KEY) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xFFu], 1u);
@@ -133,7 +149,8 @@ void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, 
 // of the projection table and of its model's decoder view set (at its rank
 // among the model's views); lane m closes model m's set.
 __global__ void k_tables(const FrameDev* __restrict__ fd, const CacheDev* __restrict__ caches,
-                         DViewSet* __restrict__ tabs, ProjTab* __restrict__ ptab, int n_models) {
+                         uint8_t* const* __restrict__ eyes, DViewSet* __restrict__ tabs, ProjTab* __restrict__ ptab,
+                         int n_models) {
   const int lane = (int)(threadIdx.x & 31u);
   const int nd = (int)fd->n_dviews;
   auto work = [&](int d) -> uint32_t {
@@ -147,6 +164,7 @@ __global__ void k_tables(const FrameDev* __restrict__ fd, const CacheDev* __rest
     ptab->model[d] = m;
     ptab->vstat[d] = cached ? caches[d].vstat : nullptr;
     ptab->lattr[d] = cached ? caches[d].slot_attr : nullptr;
+    ptab->eyes[d] = fd->dview_exact[d] ? eyes[d] : nullptr;
     int r = 0;
     uint32_t acc = 0;
     for (int e = 0; e < d; ++e)
@@ -187,9 +205,9 @@ __global__ void k_tables(const FrameDev* __restrict__ fd, const CacheDev* __rest
 size_t dview_set_bytes() { return sizeof(DViewSet); }
 size_t proj_tab_bytes() { return sizeof(ProjTab); }
 
-void launch_tables(const FrameDev* fd, const CacheDev* caches, DViewSet* tabs, ProjTab* ptab, int n_models,
-                   cudaStream_t s) {
-  k_tables<<<1, 32, 0, s>>>(fd, caches, tabs, ptab, n_models);
+void launch_tables(const FrameDev* fd, const CacheDev* caches, uint8_t* const* eyes, DViewSet* tabs, ProjTab* ptab,
+                   int n_models, cudaStream_t s) {
+  k_tables<<<1, 32, 0, s>>>(fd, caches, eyes, tabs, ptab, n_models);
 }
 
 }  // namespace gsc

@@ -26,6 +26,10 @@ PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 OUT_FORMAT = {"f32": 0, "rgba8": 1}
 DEPTH_GUIDE = {"linear": 0, "exp": 1, "staged": 2}
 REUSE = {"off": 0, "depth": 1, "learned": 2}
+# stereo_unify: False / "off"; True / "unified" (Eq. 5-6's camera filters for
+# both eyes); "exact" (the union of the eyes' own filters, each eye drawing
+# its own anchors); the derivation is shared in both
+STEREO = {False: 0, "off": 0, True: 1, "unified": 1, "exact": 2}
 FLAG_DEBUG_ATTRS = 0x1
 FLAG_DEBUG_T = 0x2
 FLAG_TIMING = 0x4
@@ -100,6 +104,7 @@ def lib():
             "gsc_cache_reset": (I, [P]),
             "gsc_synchronize": (I, [P]),
             "gsc_debug_visible": (I, [P, U32, P, U64, P]),
+            "gsc_debug_visible_eyes": (I, [P, U32, P, U64, P]),
             "gsc_debug_dviews": (I, [P, P, P]),
             "gsc_debug_attrs": (I, [P, U32, P, U64, P]),
             "gsc_debug_records": (I, [P, P, P, P, U64, P]),
@@ -198,7 +203,7 @@ class Renderer:
     """One gsc_ctx: load_model / set_cameras / render_frame / cache_reset."""
 
     def __init__(self, max_views: int = 2, precision: str = "fp32", reuse: str = "off",
-                 stereo_unify: bool = False, tile: tuple = (16, 16), pair_capacity: int = 0,
+                 stereo_unify=False, tile: tuple = (16, 16), pair_capacity: int = 0,
                  bg=(0.0, 0.0, 0.0), use_graph: bool = True, flags: int = 0, stream=None,
                  cache_gaussians: int = 0, max_depth: int = 0, blocks_per_sm: int = 0, out_format: str = "f32",
                  depth_guide: str = "linear"):
@@ -206,7 +211,7 @@ class Renderer:
         cfg.max_views = max_views
         cfg.precision = PREC[precision]
         cfg.reuse = REUSE[reuse]
-        cfg.stereo_unify = 1 if stereo_unify else 0
+        cfg.stereo_unify = STEREO[stereo_unify]
         cfg.tile_w, cfg.tile_h = tile
         cfg.pair_capacity = pair_capacity
         for i in range(3):
@@ -373,6 +378,14 @@ class Renderer:
         self._check(lib().gsc_debug_visible(self.ctx, d, None, 0, C.byref(n)))
         out = np.zeros(max(n.value, 1), np.uint32)
         self._check(lib().gsc_debug_visible(self.ctx, d, _p(out), n.value, C.byref(n)))
+        return out[: n.value]
+
+    def debug_visible_eyes(self, d: int) -> np.ndarray:
+        """Exact stereo views: per visible anchor of view d, bit e = camera e of the pair keeps it."""
+        n = C.c_uint64()
+        self._check(lib().gsc_debug_visible_eyes(self.ctx, d, None, 0, C.byref(n)))
+        out = np.zeros(max(n.value, 1), np.uint8)
+        self._check(lib().gsc_debug_visible_eyes(self.ctx, d, _p(out), n.value, C.byref(n)))
         return out[: n.value]
 
     def debug_dviews(self):

@@ -1,7 +1,10 @@
 """Parity of the exact configuration the frame-rate headline is measured on:
-the city model, stereo 1920x1080, cached derivation with the unified stereo
-camera (Sec. 4, Eq. 4-6) and BF16 tensor-core MLPs, blended on 16x64 tiles
-(the tiling the autotuner picks for it).
+the city model, stereo 1920x1080, cached derivation shared by the two eyes
+through the unified stereo camera (Sec. 4, Eq. 4-6) and BF16 tensor-core
+MLPs, blended on 16x64 tiles (the tiling the autotuner picks for it).  Both
+stereo readings are covered: "exact" (each eye filters its own anchors, the
+union is derived once; the headline) and "unified" (Eq. 6's camera filters
+for both eyes).
 
 - Cache decisions (hit / line per visible anchor, next reuse depth) are
   bit-exact against the oracle's simulation of Alg. 1 over every rendered
@@ -65,12 +68,14 @@ def sample_pixels(rs, cam, n=20000):
     return np.r_[px, (cam.width - 16) + tx.ravel()], np.r_[py, ty.ravel()]
 
 
-@pytest.mark.parametrize("precision,start,n", [("bf16", 0, 40), ("bf16", 150, 8), ("bf16", 292, 8),
-                                               ("fp32", 0, 12), ("fp32", 292, 8)])
-def test_headline_form_at_16x64(city, precision, start, n):
+@pytest.mark.parametrize("stereo,precision,start,n", [("exact", "bf16", 0, 40), ("exact", "bf16", 150, 8),
+                                                      ("exact", "bf16", 172, 10), ("exact", "bf16", 292, 8),
+                                                      ("exact", "fp32", 0, 12), ("exact", "fp32", 292, 8),
+                                                      ("unified", "bf16", 0, 12), ("unified", "fp32", 292, 8)])
+def test_headline_form_at_16x64(city, stereo, precision, start, n):
     model, frames = city
     L0, R0 = frames[start]
-    r = make_renderer(model, [L0, R0], partners=[1, 0], reuse="depth", stereo_unify=True, precision=precision)
+    r = make_renderer(model, [L0, R0], partners=[1, 0], reuse="depth", stereo_unify=stereo, precision=precision)
     r.set_tiling(*TILING)
     sim = CacheSim(model.n, LINES, max_depth=10)
     quant = bf16_quant() if precision == "bf16" else None
@@ -81,7 +86,13 @@ def test_headline_form_at_16x64(city, precision, start, n):
         set_cams(r, [L, R], [1, 0])
         imgs, st = render(r, [L, R])
         U = oracle.unified_camera(L, R)
-        ids, attrs, kept, hit, line, used = cached_derive(model, U, sim, quant)
+        eyes = None
+        if stereo == "exact":
+            union, eyes = oracle.cull_pair(model, L, R)
+            ids, attrs, kept, hit, line, used = cached_derive(model, U, sim, quant, ids=union)
+            assert np.array_equal(r.debug_visible_eyes(0), eyes), f
+        else:
+            ids, attrs, kept, hit, line, used = cached_derive(model, U, sim, quant)
         assert np.array_equal(r.debug_visible(0), ids), f
         ghit, gline = gpu_lines(r.debug_cache(0)[0])
         assert np.array_equal(ghit, hit) and np.array_equal(gline, line), f
@@ -93,10 +104,10 @@ def test_headline_form_at_16x64(city, precision, start, n):
         assert n_pairs == st["pairs"] > 0
         for v, cam in enumerate((L, R)):
             px, py = sample_pixels(rs, cam)
-            vr = project_view(model, cam, ids, attrs, kept)
+            vr = project_view(model, cam, ids, attrs, kept, mine=None if eyes is None else (eyes >> v) & 1)
             ref, _, mg, _ = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
             got = imgs[v][py, px]
-            tag = f"{precision} cached unified 16x64 frame {f} eye {v}"
+            tag = f"{precision} cached {stereo} 16x64 frame {f} eye {v}"
             if precision == "fp32":
                 check_image(got, ref, mg, tag, CACHED_PIX_TOL)
             else:

@@ -104,6 +104,35 @@ def test_cached_unified_octree_path(city_octree):
     r.close()
 
 
+def test_cached_exact_stereo_octree_path(city_octree):
+    """The exact stereo form with level offsets and the fade: each eye's own
+    radius rule selects its anchors (masks bit-exact) and the fade of an eye
+    is measured from that eye; decisions exact, images within the cache
+    tolerance of the oracle's simulation."""
+    model, frames = city_octree
+    L0, R0 = frames[0]
+    r = make_renderer(model, [L0, R0], partners=[1, 0], reuse="depth", stereo_unify="exact")
+    sim = CacheSim(model.n, (4 << 20) // 10, max_depth=10)
+    rs = np.random.default_rng(8)
+    for f in range(0, 14):
+        L, R = frames[f]
+        set_cams(r, [L, R], [1, 0])
+        imgs, st = render(r, [L, R])
+        U = oracle.unified_camera(L, R)
+        union, eyes = oracle.cull_pair(model, L, R)
+        ids, attrs, kept, hit, line, used = cached_derive(model, U, sim, ids=union)
+        assert np.array_equal(r.debug_visible(0), ids) and np.array_equal(r.debug_visible_eyes(0), eyes), f
+        ghit, gline = gpu_lines(r.debug_cache(0)[0])
+        assert np.array_equal(ghit, hit) and np.array_equal(gline, line), f
+        if f % 13 in (0, 12):
+            for v, cam in enumerate((L, R)):
+                px, py = sample_pixels(rs, cam)
+                vr = project_view(model, cam, ids, attrs, kept, mine=(eyes >> v) & 1)
+                ref, _, mg, _ = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+                check_image(imgs[v][py, px], ref, mg, f"cached exact octree frame {f} eye {v}", CACHED_PIX_TOL)
+    r.close()
+
+
 def test_invalid_level_offsets_are_rejected():
     import paper_2502_14938_b300 as pkg
     m = gen.tiny_scene(n=64)

@@ -260,6 +260,36 @@ def test_city_unified_stereo(city):
     r.close()
 
 
+@pytest.mark.parametrize("frame", [100, 180])
+def test_city_exact_stereo(city, frame):
+    """The exact stereo form: the view's anchors are the union of the eyes'
+    own sets with a mask of the eyes keeping each, derived once from the
+    unified camera's centre; each eye draws its own anchors (plain float32
+    form: pixels within 1e-3 of the oracle's exact-form images)."""
+    import paper_2502_14938_b300 as pkg
+    model, frames = city
+    L, R = frames[frame]
+    r = make_renderer(model, [L, R], partners=[1, 0], flags=pkg.FLAG_DEBUG_ATTRS, stereo_unify="exact")
+    imgs, st = render(r, [L, R])
+    nd, first = r.debug_dviews()
+    assert nd == 1 and first == [0]
+    U = oracle.unified_camera(L, R)
+    ids, eyes = oracle.cull_pair(model, L, R)
+    assert np.array_equal(r.debug_visible(0), ids)
+    assert np.array_equal(r.debug_visible_eyes(0), eyes)
+    attrs, kept = oracle.derive(model, oracle.camera_center(U), ids)
+    check_attrs(r.debug_attrs(0), attrs, model.scale[ids], "exact attrs")
+    check_keygen_and_sort(r, [L, R])
+    rs = np.random.default_rng(frame)
+    for v, cam in enumerate((L, R)):
+        px = rs.integers(0, cam.width, 20000)
+        py = rs.integers(0, cam.height, 20000)
+        vr = oracle.view_gaussians(model, cam, derive_cam=U, pair=(L, R))
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        check_image(imgs[v][py, px], ref, mg, f"exact f{frame} eye {v}")
+    r.close()
+
+
 # ------------------------------------------------------------------ sort and scan kernels
 @pytest.mark.parametrize("n,bits", [(1, 8), (1000, 7), (4097, 14), (1_000_003, 32), (5_000_000, 17)])
 def test_radix_sort_matches_stable_argsort(n, bits):
