@@ -95,6 +95,8 @@ def lib():
         L.orc_round_bf16.restype = C.c_float
         L.orc_round_e4m3.argtypes = [C.c_double]
         L.orc_round_e4m3.restype = C.c_double
+        L.orc_e4m3_two_term.argtypes = [C.c_double, C.c_double, P]
+        L.orc_e4m3_two_term.restype = C.c_double
         L.orc_num_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -372,6 +374,13 @@ def round_bf16(x: float) -> float:
 
 def round_e4m3(x: float) -> float:
     return float(lib().orc_round_e4m3(float(x)))
+
+
+def e4m3_two_term(v: float, s: float):
+    """(hi + lo, hi): the FP8 form's two-term E4M3 expansion of v at scale s."""
+    hi = C.c_double()
+    tot = lib().orc_e4m3_two_term(float(v), float(s), C.byref(hi))
+    return float(tot), float(hi.value)
 
 
 E4M3_MAX = 448.0

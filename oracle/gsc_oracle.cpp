@@ -117,6 +117,20 @@ double round_e4m3(double x) {
   return std::copysign(out, x);
 }
 
+// Two-term E4M3 expansion of v at scale s (a power of two): hi = e4m3(v / s),
+// lo = e4m3(v / s - hi), both in units of s (round to nearest even,
+// saturating); returns (hi + lo) s and, with hi_out, hi s.  v / s and the
+// residual are exact in double.  The FP8 form keeps its weights and hidden
+// activations this way: two E4M3 tensors at one per-tensor scale whose sum
+// carries about twice the mantissa bits.
+double e4m3_two_term(double v, double s, double* hi_out) {
+  const double x = v / s;
+  const double hi = round_e4m3(x);
+  const double lo = round_e4m3(x - hi);
+  if (hi_out) *hi_out = hi * s;
+  return (hi + lo) * s;
+}
+
 // ---------------------------------------------------------------- cameras
 void center64(const orc_camera* c, double p[3]) {
   // p = -R^T t, summed in a fixed order
@@ -279,29 +293,38 @@ int orc_lod_weight(const orc_model* m, const orc_camera* c, const uint32_t* ids,
 //     q_j     = z_cov[7j+3..7j+6] / |.|    (w, x, y, z); identity if |.| < 1e-12
 // attrs: [n][k][11] = alpha, c(3), s(3), q(4); kept: [n][k].
 // With q->mode != 0 the inputs, weights and hidden activations are rounded as
-// the precision form does (the sums stay float64).
+// the precision form does (the sums stay float64): mode 1 all to bf16; mode 2
+// (FP8-E4M3, per-tensor power-of-two scales) the inputs to one E4M3 term and
+// the weights and hidden activations to two-term E4M3 expansions, the second
+// layer summing h_hi W_hi + h_lo W_hi + h_hi W_lo (no h_lo W_lo term).
 int orc_derive(const orc_model* m, const double* view_pos, const uint32_t* ids, int64_t n,
                const orc_quant* qz, double* attrs, uint8_t* kept, double* raw_out) {
   if (!m || !ids || !attrs) return -1;
   const int k = m->k;
   const int outd[3] = {k, 3 * k, 7 * k};
   const int mode = qz ? qz->mode : 0;
-  // pre-round the weights once
-  std::vector<double> W1q[3], W2q[3];
+  // pre-round the weights once (FP8: W2q holds the leading term of each
+  // W2 weight, W2r the second; W1q the two-term sum)
+  std::vector<double> W1q[3], W2q[3], W2r[3];
   for (int h = 0; h < 3; ++h) {
     W1q[h].resize(IN * HID);
     W2q[h].resize((size_t)HID * outd[h]);
+    W2r[h].assign((size_t)HID * outd[h], 0.0);
     for (int i = 0; i < IN * HID; ++i) {
       float w = m->W1[h][i];
       if (mode == 1) W1q[h][i] = round_bf16(w);
-      else if (mode == 2) W1q[h][i] = round_e4m3((double)w / qz->s_w1[h]) * qz->s_w1[h];
+      else if (mode == 2) W1q[h][i] = e4m3_two_term(w, qz->s_w1[h], nullptr);
       else W1q[h][i] = w;
     }
     for (int i = 0; i < HID * outd[h]; ++i) {
       float w = m->W2[h][i];
       if (mode == 1) W2q[h][i] = round_bf16(w);
-      else if (mode == 2) W2q[h][i] = round_e4m3((double)w / qz->s_w2[h]) * qz->s_w2[h];
-      else W2q[h][i] = w;
+      else if (mode == 2) {
+        double hi;
+        const double all = e4m3_two_term(w, qz->s_w2[h], &hi);
+        W2q[h][i] = hi;
+        W2r[h][i] = all - hi;
+      } else W2q[h][i] = w;
     }
   }
 #pragma omp parallel for schedule(static)
@@ -320,19 +343,30 @@ int orc_derive(const orc_model* m, const double* view_pos, const uint32_t* ids, 
     }
     double z[3][7 * 16];
     for (int h = 0; h < 3; ++h) {
-      double hid[HID];
+      double hid[HID], hlo[HID];
       for (int o = 0; o < HID; ++o) {
         double s = 0.0;
         for (int c = 0; c < IN; ++c) s += x[c] * W1q[h][c * HID + o];
         s += (double)m->b1[h][o];
         s = s > 0.0 ? s : 0.0;
+        hlo[o] = 0.0;
         if (mode == 1) s = round_bf16((float)s);
-        else if (mode == 2) s = round_e4m3(s / qz->s_h[h]) * qz->s_h[h];
+        else if (mode == 2) {
+          double hi;
+          const double all = e4m3_two_term(s, qz->s_h[h], &hi);
+          hlo[o] = all - hi;
+          s = hi;
+        }
         hid[o] = s;
       }
+      // FP8: (h_hi + h_lo)(W_hi + W_lo) without the h_lo W_lo term
       for (int o = 0; o < outd[h]; ++o) {
         double s = 0.0;
-        for (int c = 0; c < HID; ++c) s += hid[c] * W2q[h][(size_t)c * outd[h] + o];
+        for (int c = 0; c < HID; ++c) {
+          const size_t wi = (size_t)c * outd[h] + o;
+          s += hid[c] * W2q[h][wi];
+          if (mode == 2) s += hlo[c] * W2q[h][wi] + hid[c] * W2r[h][wi];
+        }
         z[h][o] = s + (double)m->b2[h][o];
       }
     }
@@ -747,6 +781,8 @@ int64_t orc_blend_trace(const double* araw, const double* col, int64_t n, double
 // Format conversions used by the precision forms (exposed for their pins).
 float orc_round_bf16(float x) { return round_bf16(x); }
 double orc_round_e4m3(double x) { return round_e4m3(x); }
+
+double orc_e4m3_two_term(double v, double s, double* hi) { return e4m3_two_term(v, s, hi); }
 
 // Threads of the parallel loops (timing the oracle at 1 thread and at all
 // cores); the arithmetic and its order per pixel / anchor do not depend on it.

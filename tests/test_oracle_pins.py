@@ -446,6 +446,67 @@ def test_fp8_scales_are_tight_powers_of_two_and_bound_the_hidden_layer():
     assert oracle.pow2_ceil(3e-5) == 2.0 ** -15
 
 
+def test_e4m3_two_term_expansion():
+    """The FP8 form's two-term expansion: both terms are E4M3 numbers at the
+    scale (torch's float8 cast returns them unchanged), the leading term is
+    the one-term rounding, and the sum is within 2^-7 relative of the value
+    over the normal range (the second term rounds the first's error, itself
+    within 2^-4 relative, to 3 mantissa bits)."""
+    import torch
+    rs = np.random.default_rng(5)
+    s = 2.0 ** -6
+    for v in np.concatenate([rs.uniform(-1, 1, 2000) * 10.0 ** rs.uniform(-2, 0.8, 2000), [0.0, 7.0, -0.3]]):
+        tot, hi = oracle.e4m3_two_term(v, s)
+        lo = tot - hi
+        for term in (hi / s, lo / s):
+            t = torch.tensor([term], dtype=torch.float64).to(torch.float8_e4m3fn).to(torch.float64).item()
+            assert t == term
+        assert hi == oracle.round_e4m3(v / s) * s
+        if abs(v) / s >= 2.0 ** -6 * 2 ** 4:  # leading term normal, residual not deep subnormal
+            assert abs(tot - v) <= 2.0 ** -7 * abs(v)
+
+
+def test_fp8_form_error_is_the_inputs_rounding(tiny):
+    """Two-term weights and hidden activations remove the rounding error
+    that one-term E4M3 adds on top of the inputs' own rounding.  Against a
+    numpy forward pass with torch's float8 casts: the oracle's mode-2 error
+    (RMS over opacity and colour, against float64) is close to the error of
+    rounding the inputs alone and well below rounding everything once."""
+    import torch
+    m, cam = tiny
+    ids = oracle.cull(m, cam)[:600]
+    pc = oracle.camera_center(cam)
+    q = oracle.fp8_scales(m)
+    a64, _ = oracle.derive(m, pc, ids)
+    a8, _ = oracle.derive(m, pc, ids, q)
+
+    def e4(v, sc):
+        t = torch.from_numpy(np.asarray(v / sc, np.float64)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+        return t * sc
+
+    d = m.pos[ids].astype(np.float64) - pc
+    x = np.concatenate([m.feat[ids].astype(np.float64), d / np.linalg.norm(d, axis=1, keepdims=True)], axis=1)
+
+    def attrs(round_x, round_rest):
+        z = []
+        for h in range(3):
+            W1, W2 = m.W1[h].astype(np.float64), m.W2[h].astype(np.float64)
+            xx = e4(x, q.s_x) if round_x else x
+            w1 = e4(W1, q.s_w1[h]) if round_rest else W1
+            w2 = e4(W2, q.s_w2[h]) if round_rest else W2
+            hid = np.maximum(xx @ w1 + m.b1[h], 0.0)
+            hid = e4(hid, q.s_h[h]) if round_rest else hid
+            z.append(hid @ w2 + m.b2[h])
+        z = np.concatenate(z, axis=1)
+        k = m.k
+        return np.concatenate([np.tanh(z[:, :k])[..., None], (1 / (1 + np.exp(-z[:, k:4 * k]))).reshape(-1, k, 3)], -1)
+
+    rms = lambda a: float(np.sqrt(np.mean((a - a64[..., :4]) ** 2)))
+    e_inputs, e_once, e_form = rms(attrs(True, False)), rms(attrs(True, True)), rms(a8[..., :4])
+    assert rms(attrs(False, False)) < 1e-12
+    assert e_form <= 1.3 * e_inputs and e_form <= 0.75 * e_once, (e_inputs, e_once, e_form)
+
+
 def test_e4m3_rounding_closed_forms():
     """E4M3: 3 mantissa bits, bias 7, subnormal spacing 2^-9, largest finite 448, saturating."""
     cases = {1.0: 1.0, 1.0625: 1.0, 1.1875: 1.25, 1.125: 1.125, 448.0: 448.0, 460.0: 448.0, 1e6: 448.0,
