@@ -4,8 +4,12 @@
 // FP8 uses per-tensor power-of-two scales (inputs, each head's W1 / W2 and
 // hidden layer): the accumulators are multiplied back by s_x s_w1 (layer 1)
 // and s_h s_w2 (layer 2), the hidden layer is divided by s_h before it is
-// rounded to E4M3.  Operand tiles are the same 16-byte core matrices either
-// way: 8 bf16 or 16 e4m3 per K-chunk, K = 16 or 32 per MMA.
+// rounded to E4M3.  The weights and the hidden activations are two-term E4M3
+// expansions at their scale (hi, and lo = e4m3(value - hi)): layer 1 adds the
+// MMAs with W1_lo, layer 2 those of H_lo x W2 and H x W2_lo, into the same
+// FP32 accumulators; the inputs stay one E4M3 term.  Operand tiles are the
+// same 16-byte core matrices either way: 8 bf16 or 16 e4m3 per K-chunk, K =
+// 16 or 32 per MMA.
 //
 // One CTA (8 warps) takes tiles of 128 visible anchors:
 //   TMA      features of the 128 anchors (a compact BF16 copy made by
@@ -39,9 +43,10 @@ namespace gsc {
 constexpr int TC_NT = 256;
 constexpr int TC_M = 128;
 // Shared-memory image of one CTA (bytes).  X: XCH K-chunks x 128 rows x 16 B;
-// W1cat: XCH x 96 rows; W2bd: HCH x 160 rows; H: HCH x 128 rows; then fp32
-// b1 [96] (FP8: + s1 [96] dequant, r1 [96] 1/s_h), b2 [160] (FP8: + s2
-// [160] dequant), per-row metadata, 2 mbarriers and the TMEM address.
+// W1cat: XCH x 96 rows; W2bd: HCH x 160 rows; H: HCH x 128 rows (FP8: each
+// of W1, W2 and H followed by its second term, same size); then fp32 b1 [96]
+// (FP8: + s1 [96] dequant, r1 [96] 1/s_h), b2 [160] (FP8: + s2 [160]
+// dequant), per-row metadata, 2 mbarriers and the TMEM address.
 template <bool FP8>
 struct TcL {
   static constexpr int XCH = FP8 ? 4 : 6, HCH = FP8 ? 6 : 12;
@@ -51,9 +56,12 @@ struct TcL {
   static constexpr int ZERO_CH = FP8 ? 3 : 5;                 // always-zero chunk
   static constexpr uint32_t A = 0;
   static constexpr uint32_t W1 = A + XCH * 2048;
-  static constexpr uint32_t W2 = W1 + XCH * 1536;
-  static constexpr uint32_t H = W2 + HCH * 2560;
-  static constexpr uint32_t B1 = H + HCH * 2048;
+  static constexpr uint32_t W1LO = W1 + XCH * 1536;
+  static constexpr uint32_t W2 = W1LO + (FP8 ? XCH * 1536 : 0);
+  static constexpr uint32_t W2LO = W2 + HCH * 2560;
+  static constexpr uint32_t H = W2LO + (FP8 ? HCH * 2560 : 0);
+  static constexpr uint32_t HLO = H + HCH * 2048;
+  static constexpr uint32_t B1 = HLO + (FP8 ? HCH * 2048 : 0);
   static constexpr uint32_t S1 = B1 + 96 * 4;
   static constexpr uint32_t R1 = S1 + 96 * 4;
   static constexpr uint32_t B2 = FP8 ? R1 + 96 * 4 : S1;
@@ -69,7 +77,7 @@ constexpr uint32_t TC_SMEM = 84 * 1024;
 // mbarrier for the weight image (+24)
 static_assert(TcL<false>::BAR + 32 <= TC_SMEM && TcL<true>::BAR + 32 <= TC_SMEM,
               "shared-memory image exceeds the allocation");
-static_assert(TcL<false>::IMG == 65536 && TcL<true>::IMG == 36224, "weight image sizes");
+static_assert(TcL<false>::IMG == 65536 && TcL<true>::IMG == 70016, "weight image sizes");
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_SPIN = 1u << 22;
 
@@ -165,6 +173,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&p);
 }
+// Four e4m3 bytes (element 0 lowest) -> four floats.
+__device__ __forceinline__ void unpack_e4m3x4(uint32_t v, float out[4]) {
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(v & 0xFFFFu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(v >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
 // Four floats -> four e4m3 bytes (round to nearest even, saturating), element 0 lowest.
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
   const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
@@ -326,6 +343,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       for (int ks = 0; ks < L::K1; ++ks)
         mma_tc<FP8>(tmem, make_sdesc(sbase + L::A + ks * 4096, 2048, 128),
                     make_sdesc(sbase + L::W1 + ks * 3072, 1536, 128), IDESC1, ks > 0 ? 1u : 0u);
+      if constexpr (FP8) {  // + X W1_lo
+#pragma unroll
+        for (int ks = 0; ks < L::K1; ++ks)
+          mma_tc<FP8>(tmem, make_sdesc(sbase + L::A + ks * 4096, 2048, 128),
+                      make_sdesc(sbase + L::W1LO + ks * 3072, 1536, 128), IDESC1, 1u);
+      }
       mma_commit(mma_bar);
     }
     mma_pending = true;
@@ -351,9 +374,17 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
           float h[16];
 #pragma unroll
           for (int u = 0; u < 16; ++u) h[u] = fmaxf(fmaf(v[u], s_s1[c0 + u], s_b1[c0 + u]), 0.f) * s_r1[c0 + u];
-          *reinterpret_cast<uint4*>(smem + L::H + (c0 / 16) * 2048 + row * 16) =
-              make_uint4(pack_e4m3x4(h[0], h[1], h[2], h[3]), pack_e4m3x4(h[4], h[5], h[6], h[7]),
-                         pack_e4m3x4(h[8], h[9], h[10], h[11]), pack_e4m3x4(h[12], h[13], h[14], h[15]));
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {  // h = hi + lo: lo rounds the (exact) residual h - hi
+            hi[u] = pack_e4m3x4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+            float r[4];
+            unpack_e4m3x4(hi[u], r);
+            lo[u] = pack_e4m3x4(h[4 * u] - r[0], h[4 * u + 1] - r[1], h[4 * u + 2] - r[2], h[4 * u + 3] - r[3]);
+          }
+          *reinterpret_cast<uint4*>(smem + L::H + (c0 / 16) * 2048 + row * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(smem + L::HLO + (c0 / 16) * 2048 + row * 16) =
+              make_uint4(lo[0], lo[1], lo[2], lo[3]);
         } else {
           uint32_t pk[8];
 #pragma unroll
@@ -376,6 +407,15 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       for (int ks = 0; ks < L::K2; ++ks)
         mma_tc<FP8>(tmem + 96, make_sdesc(sbase + L::H + ks * 4096, 2048, 128),
                     make_sdesc(sbase + L::W2 + ks * 5120, 2560, 128), IDESC2, ks > 0 ? 1u : 0u);
+      if constexpr (FP8) {  // + H_lo W2 + H W2_lo
+#pragma unroll
+        for (int ks = 0; ks < L::K2; ++ks) {
+          mma_tc<FP8>(tmem + 96, make_sdesc(sbase + L::HLO + ks * 4096, 2048, 128),
+                      make_sdesc(sbase + L::W2 + ks * 5120, 2560, 128), IDESC2, 1u);
+          mma_tc<FP8>(tmem + 96, make_sdesc(sbase + L::H + ks * 4096, 2048, 128),
+                      make_sdesc(sbase + L::W2LO + ks * 5120, 2560, 128), IDESC2, 1u);
+        }
+      }
       mma_commit(mma_bar);
     }
     mma_pending = true;
@@ -451,6 +491,25 @@ __global__ void k_to_e4m3(const float* __restrict__ src, float inv_scale, uint8_
 
 void launch_to_e4m3(const float* src, float inv_scale, void* dst, size_t n, cudaStream_t s) {
   if (n) k_to_e4m3<<<1024, 256, 0, s>>>(src, inv_scale, static_cast<uint8_t*>(dst), n);
+}
+
+// Two-term e4m3 expansion: hi = e4m3(x), lo = e4m3(x - hi) (the residual is
+// exact in float32), round to nearest even, saturating.
+__global__ void k_to_e4m3_two_term(const float* __restrict__ src, uint8_t* __restrict__ hi, uint8_t* __restrict__ lo,
+                                   size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = src[i];
+    const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+    const __half_raw hr = __nv_cvt_fp8_to_halfraw(h, __NV_E4M3);
+    const float hf = __half2float(*reinterpret_cast<const __half*>(&hr));
+    hi[i] = (uint8_t)h;
+    lo[i] = (uint8_t)__nv_cvt_float_to_fp8(x - hf, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+void launch_to_e4m3_two_term(const float* src, void* hi, void* lo, size_t n, cudaStream_t s) {
+  if (n)
+    k_to_e4m3_two_term<<<256, 256, 0, s>>>(src, static_cast<uint8_t*>(hi), static_cast<uint8_t*>(lo), n);
 }
 
 // Tensor map of the compact feature buffer: rows of 32 bf16 (64 bytes) with
@@ -561,10 +620,11 @@ Fp8Scales fp8_scales(const float* feat, size_t n, const float* const W1[3], cons
   return S;
 }
 
-// The 36,224-byte FP8 image (layout TcL<true>): e4m3 W1cat [96 x 64 K] and
-// block-diagonal W2bd [160 x 96 K] (each weight divided by its head's scale,
-// converted on the device), the zeroed H area, then fp32 b1, s1 = s_x s_w1,
-// r1 = 1 / s_h per hidden unit and b2, s2 = s_h s_w2 per output row.
+// The 70,016-byte FP8 image (layout TcL<true>): e4m3 W1cat [96 x 64 K] and
+// its second term, block-diagonal W2bd [160 x 96 K] and its second term
+// (each weight divided by its head's scale, split on the device), the
+// zeroed H and H_lo areas, then fp32 b1, s1 = s_x s_w1, r1 = 1 / s_h per
+// hidden unit and b2, s2 = s_h s_w2 per output row.
 cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                            const float* const b2[3], const Fp8Scales& S, void* d_img, cudaStream_t s) {
   using L = TcL<true>;
@@ -602,12 +662,13 @@ cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], c
   if (e != cudaSuccess) return e;
   uint8_t* img = static_cast<uint8_t*>(d_img);
   if ((e = cudaMemcpy(d_pre, pre.data(), pre.size() * 4, cudaMemcpyHostToDevice)) == cudaSuccess) {
-    launch_to_e4m3(d_pre, 1.0f, img, pre.size(), s);
+    launch_to_e4m3_two_term(d_pre, img + (L::W1 - L::W1), img + (L::W1LO - L::W1), n_w1, s);
+    launch_to_e4m3_two_term(d_pre + n_w1, img + (L::W2 - L::W1), img + (L::W2LO - L::W1), n_w2, s);
     e = cudaStreamSynchronize(s);
   }
   cudaFree(d_pre);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemset(img + (L::H - L::W1), 0, L::HCH * 2048)) != cudaSuccess) return e;
+  if ((e = cudaMemset(img + (L::H - L::W1), 0, 2 * L::HCH * 2048)) != cudaSuccess) return e;
   return cudaMemcpy(img + (L::B1 - L::W1), tail.data(), tail.size() * 4, cudaMemcpyHostToDevice);
 }
 

@@ -138,7 +138,7 @@ struct ModelDev {
   const void* feat_bf16;  // [N][32] bf16 (tensor-core forms)
   const void* w_tc;       // tensor-core weight image, bf16 (65,536 bytes)
   const void* feat_fp8;   // [N][32] e4m3 of feature / s_x (FP8 form)
-  const void* w_tc8;      // tensor-core weight image, e4m3 + scales (36,224 bytes)
+  const void* w_tc8;      // tensor-core weight image, two-term e4m3 + scales (70,016 bytes)
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
@@ -433,10 +433,11 @@ struct Fp8Scales {
 };
 Fp8Scales fp8_scales(const float* feat, size_t n, const float* const W1[3], const float* const b1[3],
                      const float* const W2[3]);
-constexpr size_t TC8_IMAGE_BYTES = 36224;
+constexpr size_t TC8_IMAGE_BYTES = 70016;
 cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                            const float* const b2[3], const Fp8Scales& S, void* d_img, cudaStream_t s);
 void launch_to_e4m3(const float* src, float inv_scale, void* dst, size_t n, cudaStream_t s);
+void launch_to_e4m3_two_term(const float* src, void* hi, void* lo, size_t n, cudaStream_t s);
 void pack_tc_weights(const float* const W1[3], const float* const b1[3], const float* const W2[3],
                      const float* const b2[3], std::vector<uint8_t>& img);
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,

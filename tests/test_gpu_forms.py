@@ -100,14 +100,16 @@ def test_bf16_and_fp32_agree_on_integer_stages(city):
 
 
 # ------------------------------------------------------------------ FP8-E4M3
-# One E4M3 step is 2^-3 relative: an input or hidden value that lies near an
-# E4M3 rounding midpoint rounds one way from the GPU's float32 and the other
-# from the oracle's float64, and moves the outputs it feeds by up to a few
-# 1e-2.  Most attributes agree to float32 accuracy; the test bounds the share
-# that does not and the size of the rest.
+# One E4M3 step is 2^-3 relative: an input value that lies near an E4M3
+# rounding midpoint rounds one way from the GPU's float32 and the other from
+# the oracle's float64 (the inputs are one term), and moves the outputs it
+# feeds by up to a few 1e-2; a hidden value's two-term expansion absorbs such
+# a flip in its second term.  Most attributes agree to float32 accuracy; the
+# test bounds the share that does not and the size of the rest.
 FP8_CLOSE = 1e-4      # scale-relative agreement of an attribute
-FP8_CLOSE_FRAC = 0.9  # share of attributes that must agree that closely
-FP8_MAX = 0.3         # bound on any attribute's scale-relative difference
+FP8_CLOSE_FRAC = 0.999  # share of attributes that must agree that closely
+FP8_MAX = 1e-2        # bound on any attribute's scale-relative difference
+FP8_PSNR = 40.0       # the form against the plain float64 oracle
 
 
 def check_attrs_fp8(got, ref, s_a, tag):
@@ -115,6 +117,7 @@ def check_attrs_fp8(got, ref, s_a, tag):
     scale[..., 4:7] = np.asarray(s_a, np.float64)[:, None, None]
     rel = np.abs(got.astype(np.float64) - ref) / scale
     close = np.mean(rel <= FP8_CLOSE)
+    print(f"{tag}: {close:.4f} of attributes within {FP8_CLOSE}, worst {rel.max():.3e}")
     assert close >= FP8_CLOSE_FRAC and rel.max() <= FP8_MAX, f"{tag}: close {close:.3f}, worst {rel.max():.3e}"
     return close, rel.max()
 
@@ -130,7 +133,7 @@ def test_fp8_tiny_scene():
     check_attrs_fp8(r.debug_attrs(0), attrs_q, m.scale[ids], "fp8 tiny")
     check_keygen_and_sort(r, [cam])
     (ref, T, mg, nc), _ = oracle.render_view(m, cam)
-    assert oracle.psnr(img, ref) >= 30.0
+    assert oracle.psnr(img, ref) >= FP8_PSNR
     r.close()
 
 
@@ -156,5 +159,5 @@ def test_fp8_city_stereo(city, frame):
         ref, _, _, _ = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
         p = oracle.psnr(imgs[v][py, px], ref)
         print(f"fp8 city frame {frame} eye {v}: {p:.2f} dB")
-        assert p >= 30.0, f"fp8 city frame {frame} eye {v}: {p:.2f} dB"
+        assert p >= FP8_PSNR, f"fp8 city frame {frame} eye {v}: {p:.2f} dB"
     r.close()
