@@ -370,14 +370,16 @@ def set_pair(r, mid, L, R):
 
 
 # Synthetic ablation in the manner of the paper's Tables 5-6: the headline
-# form with one optimisation removed at a time (the paper's "w/o kernels",
-# its PyTorch op-by-op pipeline, has no counterpart here: every stage is a
-# kernel of this library).
-ABLATION = (("full: cached + BF16 + shared stereo derivation", "cached_bf16_exact"),
-            ("w/o de-redundancy (per-eye derivation)", "cached_bf16"),
-            ("w/o reuse", "bf16_exact"),
-            ("w/o BF16 (FP32 MLPs)", "cached_exact"),
-            ("none: plain FP32, per eye, no cache", "plain"))
+# form with one optimisation removed at a time; "w/o fused kernels" runs the
+# FP32 decoder as separate operators through device memory (GSC_FLAG_UNFUSED,
+# the counterpart of the paper's operator-by-operator pipeline) and compares
+# with the fused FP32 row above it.
+ABLATION = (("full: cached + BF16 + shared stereo derivation", "cached_bf16_exact", 0),
+            ("w/o de-redundancy (per-eye derivation)", "cached_bf16", 0),
+            ("w/o reuse", "bf16_exact", 0),
+            ("w/o BF16 (FP32 MLPs)", "cached_exact", 0),
+            ("w/o fused kernels (FP32 decoder as separate operators)", "cached_exact", 0x20),
+            ("none: plain FP32, per eye, no cache", "plain", 0))
 
 
 def run_ablation(args):
@@ -388,18 +390,20 @@ def run_ablation(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     tiling = tuple(args.tile)
     rows = []
-    for name, form in ABLATION:
+    for name, form, flags in ABLATION:
         torch.cuda.synchronize()
         free0, res0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
-        r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, 1, tiling=tiling)
+        r, mid, outs, ms, wall = time_form(model, frames, form, args.steps, args.warmup, flush, 1, tiling=tiling,
+                                           flags=flags)
         torch.cuda.synchronize()
         lib_bytes = (free0 - torch.cuda.mem_get_info()[0]) - (torch.cuda.memory_reserved() - res0)
         r.close()
         stage, _ = stage_profile(model, frames, form, min(args.steps, len(frames)), flush,
-                                 {"tile_w": tiling[0], "tile_h": tiling[1], "blocks_per_sm": tiling[2]}, count=False)
+                                 {"tile_w": tiling[0], "tile_h": tiling[1], "blocks_per_sm": tiling[2]}, count=False,
+                                 flags=flags)
         dec = stage["cull+plan"] + stage["derive+project"]
         mean, p99 = float(np.mean(ms)), float(np.percentile(ms, 99))
-        rows.append({"method": name, "form": form, "avg_fps": 1e3 / mean, "fps_1pct_low": 1e3 / p99,
+        rows.append({"method": name, "form": form, "unfused": bool(flags & 0x20), "avg_fps": 1e3 / mean, "fps_1pct_low": 1e3 / p99,
                      "ms_mean": mean, "decoding_ms": dec, "rasterization_ms": sum(stage.values()) - dec,
                      "device_gib": lib_bytes / 2 ** 30})
     for row in rows:
@@ -573,13 +577,13 @@ def run_profile(args):
           flush=True)
 
 
-def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=False, tiling=None):
+def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=False, tiling=None, flags=0):
     """Per-frame CUDA-event times (ms) of `steps` frames of the path; L2 flushed between frames.
     tune: pick the blend tiling (tile shape, blocks/SM) with the project's autotuner on the
     middle frame of the path first; tiling: a fixed (W, H, blocks/SM) instead."""
     import torch
     W, H = frames[0][0].width, frames[0][0].height
-    r, mid = make_renderer(model, form)
+    r, mid = make_renderer(model, form, flags=flags)
     outs = [torch.empty((H, W, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     for f in range(len(frames)):  # one pass over the path with stats grows buffers to its needs
         set_pair(r, mid, *frames[f])
@@ -634,12 +638,12 @@ def time_form(model, frames, form, steps, warmup, flush, world, clk=None, tune=F
 STAGE_NAMES = ["cull+plan", "derive+project", "sort_depth", "scan+keygen", "sort_tile", "ranges", "blend"]
 
 
-def stage_profile(model, frames, form, n, flush, tiling=None, count=True):
+def stage_profile(model, frames, form, n, flush, tiling=None, count=True, flags=0):
     """Per-stage CUDA-event times on the library's stream (eager launches), with the timed run's tiling."""
     import paper_2502_14938_b300 as pkg
     import torch
     W, H = frames[0][0].width, frames[0][0].height
-    rt, mid = make_renderer(model, form, flags=pkg.FLAG_TIMING, use_graph=False)
+    rt, mid = make_renderer(model, form, flags=pkg.FLAG_TIMING | flags, use_graph=False)
     set_pair(rt, mid, *frames[0])
     if tiling:
         rt.set_tiling(tiling["tile_w"], tiling["tile_h"], tiling["blocks_per_sm"])

@@ -93,6 +93,9 @@ typedef enum {
 #define GSC_FLAG_TIMING 0x4u       /* per-stage CUDA-event timing into gsc_frame_stats */
 #define GSC_FLAG_REUSE_COLLECT 0x8u /* reuse forms: record predictor inputs + labels (gsc_reuse_collect) */
 #define GSC_FLAG_BLEND_WORK 0x10u  /* blend counts its work per frame (gsc_debug_blend_work); slower */
+#define GSC_FLAG_UNFUSED 0x20u     /* FP32 only: the derivation as separate operators through device memory
+                                      (gather, GEMM, ReLU, GEMM, split, activation): the ablation's decoder
+                                      without fused kernels; the same arithmetic as the fused one */
 
 enum { GSC_STEREO_OFF = 0, GSC_STEREO_UNIFIED = 1, GSC_STEREO_EXACT = 2 };
 

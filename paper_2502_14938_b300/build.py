@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgsc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "frame_cull.cu", "derive_f32.cu", "derive_tc.cu", "project.cu", "cache.cu", "sort.cu", "raster.cu", "reuse.cu", "noalloc_scan.cu", "probe.cu"]
+SOURCES = ["api.cu", "frame_cull.cu", "derive_f32.cu", "derive_unfused.cu", "derive_tc.cu", "project.cu", "cache.cu", "sort.cu", "raster.cu", "reuse.cu", "noalloc_scan.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]

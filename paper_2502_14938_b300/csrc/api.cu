@@ -79,6 +79,8 @@ struct gsc_ctx {
   Records rec{};
   uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr, *big = nullptr;
   float4* attrs = nullptr;  // derived attributes, 3 float4 per Gaussian in frame item order
+  float* unfused = nullptr;  // GSC_FLAG_UNFUSED: the operators' intermediate tensors
+  size_t unfused_items = 0;
   uint32_t pair_cap = 0;
   uint32_t *pk0 = nullptr, *pv0 = nullptr, *pk1 = nullptr, *pv1 = nullptr;
   uint32_t ranges_cap = 0;
@@ -389,6 +391,9 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     if (tc)
       launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
                        &ctx->tmap_feat, ctx->compact, fp8, ctx->n_sm, s);
+    else if (ctx->cfg.flags & GSC_FLAG_UNFUSED)
+      launch_derive_unfused(ctx->d_models, &ctx->models[m].dev, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab,
+                            ctx->d_tabs, ctx->unfused, ctx->unfused_items, ctx->n_sm, s);
     else
       launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
                         ctx->n_sm, s);
@@ -768,6 +773,8 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
   if (cfg.out_format > GSC_OUT_RGBA8) return GSC_ERR_INVALID_ARG;
   if (cfg.depth_guide > GSC_GUIDE_STAGED) return GSC_ERR_INVALID_ARG;
   if (cfg.precision > GSC_PREC_FP8 || cfg.reuse > GSC_REUSE_LEARNED) return GSC_ERR_INVALID_ARG;
+  if ((cfg.flags & GSC_FLAG_UNFUSED) && cfg.precision != GSC_PREC_FP32) return GSC_ERR_INVALID_ARG;
+  if (cfg.stereo_unify > GSC_STEREO_EXACT) return GSC_ERR_INVALID_ARG;
   if ((cfg.flags & GSC_FLAG_REUSE_COLLECT) && cfg.reuse == GSC_REUSE_OFF) return GSC_ERR_INVALID_ARG;
   if (cfg.pair_capacity > 0x3FFFFFFFull) cfg.pair_capacity = 0x3FFFFFFFull;
 
@@ -831,7 +838,7 @@ void gsc_destroy(gsc_ctx* ctx) {
                   ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
-                  ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab};
+                  ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab, ctx->unfused};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
   dfree(ctx->d_caches);
@@ -1036,6 +1043,15 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
       for (uint32_t i = 0; i < slots; ++i) dt[i] = ctx->d_dbg_buf + (size_t)vcap * K * 11 * i;
       if (!ctx->d_dbg_tab) CK(cudaMalloc((void**)&ctx->d_dbg_tab, sizeof(float*) * MAXV));
       CK(cudaMemcpy(ctx->d_dbg_tab, dt.data(), sizeof(float*) * MAXV, cudaMemcpyHostToDevice));
+    }
+  }
+  // unfused decoder: intermediate tensors for every visible anchor of every view
+  if (ctx->cfg.flags & GSC_FLAG_UNFUSED) {
+    const size_t items = (size_t)ctx->vis_cap * ctx->n_vis_slots;
+    if (items > ctx->unfused_items) {
+      if ((r = dalloc(ctx, &ctx->unfused, unfused_scratch_floats(items)))) return r;
+      ctx->unfused_items = items;
+      invalidate_graph(ctx);
     }
   }
   // tensor-core forms: compact bf16 feature rows for every visible anchor of a model

@@ -443,6 +443,15 @@ void pack_tc_weights(const float* const W1[3], const float* const b1[3], const f
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                        float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, int n_sm,
                        cudaStream_t s);
+// The derivation as separate operators through device memory (the
+// ablation's unfused decoder; float32): scratch holds
+// unfused_scratch_floats(items_cap) floats, items_cap >= the decoded anchors
+// of the model's views; h_model is the model's device description as the
+// host holds it.
+size_t unfused_scratch_floats(size_t items);
+void launch_derive_unfused(const ModelDev* models, const ModelDev* h_model, int model, FrameDev* fd,
+                           uint32_t* const* vis, float4* attrs, float* const* dbg_attrs, const DViewSet* tabs,
+                           float* scratch, size_t items_cap, int n_sm, cudaStream_t s);
 // derived attributes (3 float4 per Gaussian, frame-wide item order; cache
 // hits from their lines) -> records
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,

@@ -35,6 +35,7 @@ FLAG_DEBUG_T = 0x2
 FLAG_TIMING = 0x4
 FLAG_REUSE_COLLECT = 0x8
 FLAG_BLEND_WORK = 0x10
+FLAG_UNFUSED = 0x20
 REUSE_NPARAM = 2433
 
 

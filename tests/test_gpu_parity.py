@@ -290,6 +290,38 @@ def test_city_exact_stereo(city, frame):
     r.close()
 
 
+@pytest.mark.parametrize("stereo", [False, "exact"])
+def test_unfused_decoder(city, stereo):
+    """The derivation as separate operators through device memory (the
+    ablation's decoder without fused kernels): attributes within 1e-5 of
+    the oracle and pixels within 1e-3, like the fused float32 kernel."""
+    import paper_2502_14938_b300 as pkg
+    model, frames = city
+    L, R = frames[150]
+    r = make_renderer(model, [L, R], partners=[1, 0], flags=pkg.FLAG_DEBUG_ATTRS | pkg.FLAG_UNFUSED,
+                      stereo_unify=stereo)
+    imgs, st = render(r, [L, R])
+    U = oracle.unified_camera(L, R)
+    if stereo:
+        ids, _ = oracle.cull_pair(model, L, R)
+        attrs, _ = oracle.derive(model, oracle.camera_center(U), ids)
+        check_attrs(r.debug_attrs(0), attrs, model.scale[ids], "unfused exact attrs")
+    else:
+        for v, cam in enumerate((L, R)):
+            ids = oracle.cull(model, cam)
+            attrs, _ = oracle.derive(model, oracle.camera_center(cam), ids)
+            check_attrs(r.debug_attrs(v), attrs, model.scale[ids], f"unfused eye {v}")
+    rs = np.random.default_rng(11)
+    for v, cam in enumerate((L, R)):
+        px, py = rs.integers(0, cam.width, 20000), rs.integers(0, cam.height, 20000)
+        vr = oracle.view_gaussians(model, cam, derive_cam=U if stereo else None, pair=(L, R) if stereo else None)
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        check_image(imgs[v][py, px], ref, mg, f"unfused eye {v}")
+    r.close()
+    with pytest.raises(pkg.GscError):
+        pkg.Renderer(max_views=1, precision="bf16", flags=pkg.FLAG_UNFUSED)
+
+
 # ------------------------------------------------------------------ sort and scan kernels
 @pytest.mark.parametrize("n,bits", [(1, 8), (1000, 7), (4097, 14), (1_000_003, 32), (5_000_000, 17)])
 def test_radix_sort_matches_stable_argsort(n, bits):
