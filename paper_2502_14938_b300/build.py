@@ -11,6 +11,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgsc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+# The bounds-checked variant (GSC_DEBUG_BOUNDS): data-indexed stores test
+# their index against the buffer's capacity, flag ERR_BOUNDS and skip; a
+# substitute for a device memory checker, selected by a process through the
+# GSC_LIBRARY environment variable.
+LIB_CHECKED = os.path.join(HERE, "libgsc_checked.so")
 
 SOURCES = ["api.cu", "frame_cull.cu", "derive_f32.cu", "derive_unfused.cu", "derive_tc.cu", "project.cu", "cache.cu", "sort.cu", "raster.cu", "reuse.cu", "noalloc_scan.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,17 +39,21 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, checked: bool = False) -> str:
+    """libgsc.so, or with checked=True the bounds-checked libgsc_checked.so."""
+    bdir = os.path.join(BUILD_DIR, "checked") if checked else BUILD_DIR
+    out = LIB_CHECKED if checked else LIB
+    defs = ["-DGSC_DEBUG_BOUNDS"] if checked else []
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
-    changed = force or not os.path.exists(LIB)
+    changed = force or not os.path.exists(out)
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD_DIR, s + ".o")
+        obj = os.path.join(bdir, s + ".o")
         objs.append(obj)
         if force or _stale(obj, src):
-            cmd = [nvcc, *ARCH, *FLAGS, "-dc" if False else "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj]
             if ptxas_v:
                 cmd.insert(1, "-Xptxas=-v")
             if verbose:
@@ -52,13 +61,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             subprocess.check_call(cmd)
             changed = True
     if changed:
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB + ".tmp", *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", out + ".tmp", *objs]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(out + ".tmp", out)
+    return out
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv)
+    build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv, checked="--checked" in sys.argv)

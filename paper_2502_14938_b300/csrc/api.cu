@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gsc.h"
 #include "gsc_debug.h"
 #include "gsc_internal.cuh"
@@ -22,6 +24,16 @@ using namespace gsc;
 namespace {
 
 constexpr int NSLOT = 4;  // pinned FrameIn ring
+
+// NVTX range over a scope (a no-op unless a profiler attaches a tool); the
+// frame's stages are named "gsc.<stage>" so a profiler can select their
+// kernels (eager launches) or the launches that record them (graph capture).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DevBuf {
   void* p = nullptr;
@@ -362,7 +374,9 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   cudaStream_t s = ctx->stream;
   FrameDev* fd = ctx->d_fd;
   const bool tm = ctx->timing;
+  NvtxRange frame_range("gsc.frame");
   if (tm) cudaEventRecord(ctx->ev_stage[0], s);
+  nvtxRangePushA("gsc.cull_cache");
   launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
   for (int m : ctx->models_used)
@@ -387,6 +401,8 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
                        ctx->n_sm, s);
   launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
+  nvtxRangePop();
+  nvtxRangePushA("gsc.derive_project");
   for (int m : ctx->models_used)
     if (tc)
       launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
@@ -400,6 +416,8 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->d_ptab, ctx->n_sm, s);
   if (caches && replay) launch_cache_replay_counts(ctx->d_caches, ctx->n_caches, fd, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
+  nvtxRangePop();
+  nvtxRangePushA("gsc.sort_keygen");
   uint32_t *ok = nullptr, *ov = nullptr;
   launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
                    32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov, 8, fd->hist_depth);
@@ -418,9 +436,12 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (tm) cudaEventRecord(ctx->ev_stage[5], s);
   launch_ranges(fd, pk, ctx->ranges, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[6], s);
+  nvtxRangePop();
+  nvtxRangePushA("gsc.blend");
   launch_blend(fd, ctx->ranges, pv, ctx->rec, ctx->d_fin, ctx->total_tiles, ctx->cfg.tile_w * ctx->cfg.tile_h,
                ctx->cfg.blocks_per_sm, (ctx->cfg.flags & GSC_FLAG_BLEND_WORK) != 0, ctx->n_sm, s);
   if (tm) cudaEventRecord(ctx->ev_stage[7], s);
+  nvtxRangePop();
 }
 
 int build_graph(gsc_ctx* ctx) {
@@ -588,6 +609,9 @@ int enqueue_frame(gsc_ctx* ctx, void* const* out_rgb, float* const* out_T) {
   F->tile_h = ctx->cfg.tile_h;
   F->out_format = ctx->cfg.out_format;
   F->keep_err = ctx->keep_err ? 1u : 0u;
+  F->cap_vis = ctx->vis_cap;
+  F->cap_rec = ctx->rec_cap;
+  F->cap_pairs = ctx->pair_cap;
   F->spin_limit = ctx->spin_limit;
   for (int i = 0; i < 3; ++i) F->bg[i] = ctx->cfg.bg[i];
   for (size_t i = 0; i < ctx->cams.size(); ++i) {
@@ -626,6 +650,7 @@ int finish_frame(gsc_ctx* ctx) {
   ctx->pending = false;
   const Counters& c = *ctx->h_cnt;
   if (c.err & ERR_TIMEOUT) return fail(ctx, GSC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (c.err & ERR_BOUNDS) return fail(ctx, GSC_ERR_INTERNAL, "a bounds-checked store was out of range");
   if (c.err & ERR_REC_OVERFLOW) {
     // grow to the frame's requirement plus headroom, at most the worst case
     unsigned long long worst = 0;

@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
     }
     cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
     cd.flags[cd.S + vi] = valid ? 0u : 1u;
-    if (!hit) cd.miss[atomicAdd(&cd.state[CS_MISSES], 1u)] = vi;
+    if (!hit) {
+      const uint32_t mi = atomicAdd(&cd.state[CS_MISSES], 1u);
+      if (GSC_IN_BOUNDS(mi, V, const_cast<uint32_t*>(&fd->err))) cd.miss[mi] = vi;
+    }
   }
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cd.S; s += stride)
     cd.flags[s] = (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
@@ -129,7 +132,7 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* _
       line = rank < n_free ? cd.free_list[rank] : LINE_NONE;
       cd.vstat[vi] = line;
     }
-    if (line == LINE_NONE) continue;
+    if (line == LINE_NONE || !GSC_IN_BOUNDS(line, cd.S, &fd->err)) continue;
     cd.slot_anchor[line] = a;
     cd.slot_frame[line] = t;
     cd.slot_of[a] = line;

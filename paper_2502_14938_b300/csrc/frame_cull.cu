@@ -35,6 +35,9 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
     fd->spin_limit = F.spin_limit;
     fd->total_tiles = F.total_tiles;
     fd->tile_bits = F.tile_bits;
+    fd->cap_vis = F.cap_vis;
+    fd->cap_rec = F.cap_rec;
+    fd->cap_pairs = F.cap_pairs;
     fd->n_valid = 0;
     fd->n_pairs = 0;
     fd->n_pairs_used = 0;
@@ -278,8 +281,11 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
         while (m) {
           const int i = __ffs(m) - 1;
           m &= m - 1;
-          if (eo) eo[o] = (uint8_t)(((mm >> (8 + i)) & 1u) | (((mm >> (16 + i)) & 1u) << 1));
-          out[o++] = a0 + (uint32_t)i;
+          if (GSC_IN_BOUNDS(o, fd->cap_vis, &fd->err)) {
+            if (eo) eo[o] = (uint8_t)(((mm >> (8 + i)) & 1u) | (((mm >> (16 + i)) & 1u) << 1));
+            out[o] = a0 + (uint32_t)i;
+          }
+          ++o;
         }
       }
       __syncthreads();

@@ -40,7 +40,21 @@ constexpr int WOFF_W2T = WOFF_B1 + NH;
 constexpr int WOFF_B2 = WOFF_W2T + NOUT * HID;
 constexpr int W_FLOATS = WOFF_B2 + NOUT;
 
-enum : uint32_t { ERR_PAIR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_CACHE_FULL = 4u, ERR_REC_OVERFLOW = 8u };
+enum : uint32_t { ERR_PAIR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_CACHE_FULL = 4u, ERR_REC_OVERFLOW = 8u,
+                  ERR_BOUNDS = 16u };
+
+// Stores whose index comes from data (compaction offsets, sort ranks, cache
+// lines, list cursors) are written as `if (GSC_IN_BOUNDS(i, cap, err)) p[i] =
+// v;`.  The bounds-checked build of the library (GSC_DEBUG_BOUNDS, the
+// substitute for a memory checker) tests i < cap there, and on a miss sets
+// ERR_BOUNDS in *err and skips the store; the normal build stores
+// unconditionally.
+#ifdef GSC_DEBUG_BOUNDS
+#define GSC_IN_BOUNDS(i, cap, err) \
+  ((uint64_t)(i) < (uint64_t)(cap) ? true : (atomicOr((err), (uint32_t)ERR_BOUNDS), false))
+#else
+#define GSC_IN_BOUNDS(i, cap, err) true
+#endif
 
 constexpr uint32_t INVALID_KEY = 0xFFFFFFFFu;
 constexpr uint32_t REC_VALID_BIT = 0x80000000u;
@@ -68,6 +82,9 @@ struct FrameIn {  // host -> device per frame
   uint32_t total_tiles, tile_bits;
   uint32_t out_format;               // gsc_out_format
   uint32_t keep_err;                 // 1: OR the frame's error bits into err_sticky (frames nobody waits for)
+  uint32_t cap_vis;                  // capacities of the frame's buffers (the bounds-checked build's
+  uint32_t cap_rec;                  // limits): visible ids per view, records, pairs
+  uint32_t cap_pairs;
   uint32_t pad[3];
   float bg[4];
   unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
@@ -85,6 +102,7 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t tile_w, tile_h;
   uint32_t total_tiles, tile_bits;
   uint32_t spin_limit;
+  uint32_t cap_vis, cap_rec, cap_pairs;  // buffer capacities (bounds-checked build)
   CamDev cam[MAXV];
   CamDev dcam[MAXV];
   int32_t dview_of_cam[MAXV];

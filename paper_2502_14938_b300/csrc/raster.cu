@@ -73,8 +73,11 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
       const uint32_t i = i0 + u;
       if (i < n) {
         out[i] = run;
-        if (scatter && i < scatter_n && v[u]) scatter[run] = i;
-        if (big && v[u] > big_above) big[atomicAdd(n_big, 1u)] = i;
+        if (scatter && i < scatter_n && v[u] && GSC_IN_BOUNDS(run, scatter_n, &fd->err)) scatter[run] = i;
+        if (big && v[u] > big_above) {
+          const uint32_t b = atomicAdd(n_big, 1u);
+          if (GSC_IN_BOUNDS(b, fd->cap_rec, &fd->err)) big[b] = i;
+        }
       }
       run += v[u];
     }
@@ -220,6 +223,7 @@ __global__ void k_ranges(const FrameDev* __restrict__ fd, const uint32_t* __rest
   const uint32_t n = fd->n_pairs_used;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
+    if (!GSC_IN_BOUNDS(k, fd->total_tiles, const_cast<uint32_t*>(&fd->err))) continue;
     if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
     if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
   }

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
       const uint32_t k = s_keys[p];
       const uint32_t d = (k >> shift) & 0xFFu;
       const uint32_t o = s_gofs[d] + (p - s_dstart[d]);
+      if (!GSC_IN_BOUNDS(o, n, &fd->err)) continue;
       kout[o] = k;
       vout[o] = s_vals[p];
     }

@@ -13,7 +13,9 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgsc.so")
+# GSC_LIBRARY selects another build of the library for this process (the
+# bounds-checked libgsc_checked.so), read when the library is first loaded.
+LIB_PATH = os.environ.get("GSC_LIBRARY") or os.path.join(HERE, "libgsc.so")
 
 MAX_VIEWS = 32
 K = 10

@@ -32,6 +32,16 @@ def test_every_declared_symbol_is_exported():
         assert getattr(L, n) is not None
 
 
+def test_bounds_checked_build_exports_the_same_symbols():
+    """The bounds-checked variant (GSC_DEBUG_BOUNDS) is the same ABI."""
+    from paper_2502_14938_b300 import build
+    path = build.build(checked=True)
+    names = pkg.exported_symbols()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert not [n for n in names if n not in syms]
+
+
 def test_default_config_is_filled_without_gpu():
     c = pkg.default_config()
     assert (c.tile_w, c.tile_h) == (16, 16)
