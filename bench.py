@@ -1044,11 +1044,11 @@ def per_frame_tile_bits(W, H, tiling):
 
 def launches_per_frame_of(form, tile_bits):
     """Library kernels per stereo frame of one model: frame setup, cull, plan,
-    [cache probe, scan, assign], tables, derivation (+ feature gather on the
-    tensor-core forms), projection, depth sort (4 passes), scan, key
-    generation, tile sort (one pass per 8 tile-key bits), ranges, blend."""
+    [cache probe, scan, assign], tables, derivation, projection, depth sort
+    (4 passes), scan, key generation, tile sort (one pass per 8 tile-key
+    bits), ranges, blend."""
     f = FORMS[form]
-    n = 1 + 1 + 1 + 1 + (2 if f["precision"] != "fp32" else 1) + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
+    n = 1 + 1 + 1 + 1 + 1 + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
     if f["reuse"] != "off":
         n += 3
     return n

@@ -119,10 +119,6 @@ struct gsc_ctx {
   std::vector<int> models_used;
   uint32_t spin_limit = 1u << 20;
   bool timing = false;
-  // tensor-core forms: compact feature rows of the frame + their tensor map
-  uint4* compact = nullptr;
-  uint64_t compact_rows = 0;
-  CUtensorMap tmap_feat{};
   // caches of derived Gaussians, one per derivation view (Sec. 4)
   int n_caches = 0;
   CacheDev h_caches[MAX_CACHES] = {};
@@ -391,7 +387,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     for (int m : ctx->models_used)
       if (tc)
         launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
-                         &ctx->tmap_feat, ctx->compact, fp8, ctx->n_sm, s);
+                         fp8, ctx->n_sm, s);
       else
         launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
                           ctx->n_sm, s);
@@ -406,7 +402,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   for (int m : ctx->models_used)
     if (tc)
       launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
-                       &ctx->tmap_feat, ctx->compact, fp8, ctx->n_sm, s);
+                       fp8, ctx->n_sm, s);
     else if (ctx->cfg.flags & GSC_FLAG_UNFUSED)
       launch_derive_unfused(ctx->d_models, &ctx->models[m].dev, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab,
                             ctx->d_tabs, ctx->unfused, ctx->unfused_items, ctx->n_sm, s);
@@ -862,7 +858,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_eye_buf, ctx->d_eye_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
-                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->compact, ctx->attrs,
+                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->attrs,
                   ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab, ctx->unfused};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);
@@ -1076,17 +1072,6 @@ int gsc_set_cameras(gsc_ctx* ctx, const gsc_camera* cams, uint32_t n) {
     if (items > ctx->unfused_items) {
       if ((r = dalloc(ctx, &ctx->unfused, unfused_scratch_floats(items)))) return r;
       ctx->unfused_items = items;
-      invalidate_graph(ctx);
-    }
-  }
-  // tensor-core forms: compact bf16 feature rows for every visible anchor of a model
-  if (ctx->cfg.precision != GSC_PREC_FP32) {
-    const uint64_t rows = (uint64_t)ctx->vis_cap * ctx->n_vis_slots;
-    if (rows > ctx->compact_rows) {
-      if ((r = dalloc(ctx, &ctx->compact, (size_t)rows * 4))) return r;  // 64 bytes = 4 x uint4 per row
-      if (encode_feat_tmap(&ctx->tmap_feat, ctx->compact, rows, ctx->cfg.precision == GSC_PREC_FP8) != 0)
-        return fail(ctx, GSC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-      ctx->compact_rows = rows;
       invalidate_graph(ctx);
     }
   }

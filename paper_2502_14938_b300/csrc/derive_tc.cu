@@ -12,10 +12,11 @@
 // 16 or 32 per MMA.
 //
 // One CTA (8 warps) takes tiles of 128 visible anchors:
-//   TMA      features of the 128 anchors (a compact BF16 copy made by
-//            k_gather_bf16) arrive as four 8-column boxes, each exactly one
-//            K-column of 8x16-byte core matrices of the no-swizzle K-major
-//            operand layout; the view direction column is written by threads
+//   load     the features of the 128 anchors come straight from the model's
+//            BF16 (E4M3) feature table, 16-byte vector loads by the threads
+//            (a thread per row and K-chunk half), stored as K-columns of
+//            8x16-byte core matrices of the no-swizzle K-major operand
+//            layout; the view direction column likewise
 //   MMA1     D1[128 x 96] = X[128 x 48] W1cat^T       (3 x K=16, TMEM cols 0-95)
 //   epi 1    H = bf16(ReLU(D1 + b1)) into shared memory, same operand layout
 //   MMA2     D2[128 x 160] = H[128 x 96] W2bd^T       (6 x K=16, TMEM cols 96-255)
@@ -51,7 +52,7 @@ template <bool FP8>
 struct TcL {
   static constexpr int XCH = FP8 ? 4 : 6, HCH = FP8 ? 6 : 12;
   static constexpr int K1 = FP8 ? 2 : 3, K2 = FP8 ? 3 : 6;  // MMA K-steps
-  static constexpr int FEAT_CH = FP8 ? 2 : 4;                 // chunks the TMA fills
+  static constexpr int FEAT_CH = FP8 ? 2 : 4;                 // feature chunks (16 B of a row each)
   static constexpr int DIR_CH = FP8 ? 2 : 4;                  // direction chunk
   static constexpr int ZERO_CH = FP8 ? 3 : 5;                 // always-zero chunk
   static constexpr uint32_t A = 0;
@@ -102,12 +103,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
 }
 // Untiled bulk copy global -> shared (both 16-byte aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -189,38 +184,13 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
   return (lo & 0xFFFFu) | (hi << 16);
 }
 
-// ------------------------------------------------------------------ gather
-// Compact BF16 (64-byte rows) or E4M3 (32-byte rows) features of this
-// model's visible anchors, in the model-local item order of the derivation
-// kernel: the TMA source.
-template <bool FP8>
-__global__ void k_gather_feat(const ModelDev* __restrict__ models, int model, const FrameDev* __restrict__ fd,
-                              uint32_t* const* __restrict__ vis, uint4* __restrict__ out,
-                              const CacheDev* __restrict__ caches, const DViewSet* __restrict__ tabs) {
-  constexpr uint32_t PARTS = FP8 ? 2u : 4u;  // uint4 per row
-  __shared__ DViewSet S;
-  load_dview_set(S, tabs, fd, model, caches);
-  const uint4* src = reinterpret_cast<const uint4*>(FP8 ? models[model].feat_fp8 : models[model].feat_bf16);
-  const uint32_t total = S.base[S.nd];
-  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total * PARTS; u += gridDim.x * blockDim.x) {
-    const uint32_t item = u / PARTS, part = u % PARTS;
-    int ld = 0;
-    while (item >= S.base[ld + 1]) ++ld;
-    const uint32_t w = item - S.base[ld];
-    const uint32_t vi = S.miss[ld] ? S.miss[ld][w] : w;
-    const uint32_t a = vis[S.d[ld]][vi];
-    out[u] = src[(size_t)a * PARTS + part];
-  }
-}
-
 // ------------------------------------------------------------------ derivation
 template <bool FP8>
 __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restrict__ models, int model,
                                                         FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
                                                         float4* __restrict__ attrs, float* const* __restrict__ dbg_attrs,
                                                         const CacheDev* __restrict__ caches,
-                                                        const DViewSet* __restrict__ tabs,
-                                                        const __grid_constant__ CUtensorMap tmap_feat) {
+                                                        const DViewSet* __restrict__ tabs) {
   using L = TcL<FP8>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ DViewSet S;
@@ -236,7 +206,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   const float* s_s2 = reinterpret_cast<const float*>(smem + L::S2);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR + 16);
-  const uint32_t tma_bar = smem_u32(bars), mma_bar = smem_u32(bars + 1);
+  const uint32_t mma_bar = smem_u32(bars + 1);
   const uint32_t sbase = smem_u32(smem);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -249,7 +219,6 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     if (t < TC_M) zc[t] = make_uint4(0, 0, 0, 0);
   }
   if (t == 0) {
-    mbar_init(tma_bar, 1);
     mbar_init(mma_bar, 1);
     mbar_init(w_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -274,14 +243,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   const uint32_t rec_cap = fd->n_records;
   constexpr uint32_t IDESC1 = FP8 ? make_idesc_e4m3(128, 96) : make_idesc_bf16(128, 96);
   constexpr uint32_t IDESC2 = FP8 ? make_idesc_e4m3(128, 160) : make_idesc_bf16(128, 160);
-  uint32_t tma_phase = 0, mma_phase = 0;
+  uint32_t mma_phase = 0;
   bool failed = false;
-  bool tma_pending = false, mma_pending = false;
+  bool mma_pending = false;
   bool w_pending = true;  // the weight image is waited for just before the first MMA, so that its
-                          // copy overlaps the first tile's metadata loads and feature copy
+                          // copy overlaps the first tile's metadata and feature loads
 
   for (uint32_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    // ---- metadata, view direction chunk, TMA of the feature chunks
+    // ---- metadata, view direction chunk, feature chunks
     if (t < TC_M) {
       const uint32_t item = tile * TC_M + t;
       int ld = -1;
@@ -303,6 +272,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         const float vn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         dx *= vn; dy *= vn; dz *= vn;
       }
+      if (ld < 0) m_anchor[t] = 0;  // a valid row to load; its results are not stored
       m_ld[t] = ld;
       uint4 dirc;
       if constexpr (FP8) {
@@ -314,21 +284,17 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       reinterpret_cast<uint4*>(smem + L::A + L::DIR_CH * 2048)[t] = dirc;
       fence_proxy_async();
     }
-    if (t == 0) {
-      mbar_expect_tx(tma_bar, L::FEAT_CH * 2048);
+    __syncthreads();  // the tile's anchor ids
+    {  // feature rows: thread t loads K-chunks of row t % 128 (16 bytes each)
+      const uint4* ft = reinterpret_cast<const uint4*>(FP8 ? md.feat_fp8 : md.feat_bf16);
+      const int row = t & (TC_M - 1), h = t >> 7;
+      const size_t a = m_anchor[row];
 #pragma unroll
-      for (int c = 0; c < L::FEAT_CH; ++c)  // x in elements: 8 bf16 or 16 e4m3 = 16 bytes per chunk
-        tma_load_2d(sbase + L::A + c * 2048, &tmap_feat, (FP8 ? 16 : 8) * c, (int)(tile * TC_M), tma_bar);
+      for (int c = h * (L::FEAT_CH / 2); c < (h + 1) * (L::FEAT_CH / 2); ++c)
+        reinterpret_cast<uint4*>(smem + L::A + c * 2048)[row] = __ldg(ft + a * L::FEAT_CH + c);
+      fence_proxy_async();  // generic-proxy writes, read by the MMA's async proxy
     }
-    tma_pending = true;
     __syncthreads();
-    bool ok = mbar_wait(tma_bar, tma_phase);
-    tma_phase ^= 1;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    tma_pending = false;
     if (w_pending) {
       if (__syncthreads_or(!mbar_wait(w_bar, 0))) {
         failed = true;
@@ -352,7 +318,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
       mma_commit(mma_bar);
     }
     mma_pending = true;
-    ok = mbar_wait(mma_bar, mma_phase);
+    bool ok = mbar_wait(mma_bar, mma_phase);
     mma_phase ^= 1;
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -458,7 +424,6 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     if (t == 0) atomicOr(&fd->err, ERR_TIMEOUT);
     // drain what may still be in flight (bounded) before the memory goes away
     if (w_pending) (void)mbar_wait(w_bar, 0);
-    if (tma_pending) (void)mbar_wait(tma_bar, tma_phase ^ 1);
     if (mma_pending) (void)mbar_wait(mma_bar, mma_phase ^ 1);
   }
   tc_fence_before();
@@ -512,32 +477,6 @@ void launch_to_e4m3_two_term(const float* src, void* hi, void* lo, size_t n, cud
     k_to_e4m3_two_term<<<256, 256, 0, s>>>(src, static_cast<uint8_t*>(hi), static_cast<uint8_t*>(lo), n);
 }
 
-// Tensor map of the compact feature buffer: rows of 32 bf16 (64 bytes) with
-// boxes of 8 columns, or of 32 e4m3 (32 bytes) with boxes of 16 columns;
-// 128 rows per box, so a box is one K-chunk of core matrices.
-int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows, bool fp8) {
-  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-      return -1;
-    fn = reinterpret_cast<EncodeFn>(p);
-  }
-  const cuuint64_t dims[2] = {32, rows};
-  const cuuint64_t strides[1] = {fp8 ? 32u : 64u};
-  const cuuint32_t box[2] = {fp8 ? 16u : 8u, 128};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
-                        strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : -1;
-}
 
 // bf16 round-to-nearest-even of a float (host side, for the weight image).
 static uint16_t host_bf16(float f) {
@@ -673,16 +612,12 @@ cudaError_t make_tc8_image(const float* const W1[3], const float* const b1[3], c
 }
 
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, const CUtensorMap* tmap,
-                      uint4* compact, bool fp8, int n_sm, cudaStream_t s) {
-  if (fp8) {
-    k_gather_feat<true><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches, tabs);
-    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs, *tmap);
-  } else {
-    k_gather_feat<false><<<n_sm * 4, 256, 0, s>>>(models, model, fd, vis, compact, caches, tabs);
-    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs,
-                                                        *tmap);
-  }
+                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, bool fp8, int n_sm,
+                      cudaStream_t s) {
+  if (fp8)
+    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
+  else
+    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
 }
 
 }  // namespace gsc

@@ -442,9 +442,8 @@ size_t proj_tab_bytes();
 void launch_tables(const FrameDev* fd, const CacheDev* caches, uint8_t* const* eyes_dev, DViewSet* tabs,
                    ProjTab* ptab, int n_models, cudaStream_t s);
 void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
-                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, const CUtensorMap* tmap,
-                      uint4* compact, bool fp8, int n_sm, cudaStream_t s);
-int encode_feat_tmap(CUtensorMap* map, void* base, uint64_t rows, bool fp8);
+                      float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, bool fp8, int n_sm,
+                      cudaStream_t s);
 // FP8-E4M3 form: per-tensor power-of-two scales, the weight image, feature conversion
 struct Fp8Scales {
   float sx, sw1[3], sw2[3], sh[3];
