@@ -100,8 +100,9 @@ struct gsc_ctx {
   SortBufs sb{};
   uint32_t status_tiles = 0;  // sort look-back tiles allocated
   uint32_t scan_tiles = 0;    // scan look-back words allocated
-  unsigned long long* st_cull = nullptr;
-  uint32_t st_cull_words = 0;
+  uint32_t* cull_masks = nullptr;  // the cull's keep masks [views][mask words] and tile counts [views][tiles]
+  uint32_t* cull_cnt = nullptr;
+  uint32_t cull_mask_stride = 0, cull_cnt_stride = 0, cull_views = 0;
   unsigned long long* st_scan = nullptr;
   // results of the last frame's sequence
   uint32_t* order_out = nullptr;  // records in depth order
@@ -228,12 +229,18 @@ int ensure_status(gsc_ctx* ctx) {
     CK(cudaMemset(ctx->st_scan, 0, (size_t)need_scan * sizeof(unsigned long long)));
     ctx->scan_tiles = need_scan;
   }
-  const uint32_t cw = ((models_max_n(ctx) + 2047u) / 2048u + 1u) * (uint32_t)MAXV;  // a look-back word per view
-  if (cw > ctx->st_cull_words) {
-    int r = dalloc(ctx, &ctx->st_cull, (size_t)cw);
-    if (r) return r;
-    CK(cudaMemset(ctx->st_cull, 0, (size_t)cw * sizeof(unsigned long long)));
-    ctx->st_cull_words = cw;
+  const uint32_t mw = cull_mask_words(models_max_n(ctx)), ct = cull_tiles(models_max_n(ctx));
+  const uint32_t views = std::max<uint32_t>(ctx->n_vis_slots, 1u);
+  if (mw > ctx->cull_mask_stride || ct > ctx->cull_cnt_stride || views > ctx->cull_views) {
+    const uint32_t mws = std::max(mw, ctx->cull_mask_stride), cts = std::max(ct, ctx->cull_cnt_stride);
+    const uint32_t vs = std::max(views, ctx->cull_views);
+    int r;
+    if ((r = dalloc(ctx, &ctx->cull_masks, (size_t)mws * vs)) || (r = dalloc(ctx, &ctx->cull_cnt, (size_t)cts * vs)))
+      return r;
+    ctx->cull_mask_stride = mws;
+    ctx->cull_cnt_stride = cts;
+    ctx->cull_views = vs;
+    invalidate_graph(ctx);
   }
   return GSC_OK;
 }
@@ -376,9 +383,8 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
   cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
   for (int m : ctx->models_used)
-    launch_cull(ctx->d_models, m, ctx->models[m].dev.lod_r != nullptr, fd, ctx->d_vis_tab, ctx->d_eye_tab, ctx->st_cull,
-                ctx->n_sm,
-                s);
+    launch_cull(ctx->d_models, &ctx->models[m].dev, m, fd, ctx->d_vis_tab, ctx->d_eye_tab, ctx->cull_masks,
+                ctx->cull_cnt, ctx->cull_mask_stride, ctx->cull_cnt_stride, s);
   launch_plan(fd, ctx->rec_cap, s);
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
   const bool collect = caches && (ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && !replay;
@@ -858,7 +864,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_eye_buf, ctx->d_eye_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
                   ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
-                  ctx->sb.status, ctx->st_cull, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->attrs,
+                  ctx->sb.status, ctx->cull_masks, ctx->cull_cnt, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->attrs,
                   ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab, ctx->unfused};
   for (void* p : bufs) dfree(p);
   for (int i = 0; i < ctx->n_caches; ++i) free_cache(ctx->h_caches[i]);

@@ -99,48 +99,52 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) 
 // Anchor filtering (Sec. 3.2; Alg. 1 "anchors indexing and filtering"): for
 // every derivation view of this model (for an exact stereo view: for each of
 // its two cameras, the view keeping the union), frustum test with a 1.3 guard
-// band and the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max 2^-l)^2,
-// level 0 always; with Octree-GS level offsets the threshold is the anchor's
-// own radius r_a = d_max 2^(Delta_a - l), rounded to float32 at load: the
-// RADIUS instantiation).  Float32 with an explicit operation order.  Each thread
-// owns CULL_IPT consecutive anchors; a block scan of per-thread counts plus a
-// decoupled look-back across tiles gives an order-preserving compaction
-// (ascending anchor ids), one pass over the positions.
+// band and the distance LOD rule (level l >= 1 drawn iff |x - p|^2 <= (d_max
+// 2^-l)^2, level 0 always; with Octree-GS level offsets the threshold is the
+// anchor's own radius r_a = d_max 2^(Delta_a - l), rounded to float32 at
+// load: the RADIUS instantiation).  Float32 with an explicit operation order.
+//
+// Two passes over tiles of CULL_TILE anchors (CULL_IPT consecutive anchors
+// per thread), with no waits between blocks:
+//   count  each thread's keep masks per view (bits 0-7 the view keeps
+//          anchor i, 8-15 / 16-23 the first / second camera of an exact
+//          stereo view does) to device memory, and per tile and view the
+//          number kept
+//   write  per tile and view the exclusive prefix of the tiles before it (a
+//          block-wide sum of their counts), a block scan of the threads'
+//          counts, and the kept ids in ascending order (with their eye
+//          masks); the last tile sets the view's visible count.
+// The order-preserving compaction is the same as a scan over all anchors.
 constexpr int CULL_NT = 256;
 constexpr int CULL_IPT = 8;
 constexpr int CULL_TILE = CULL_NT * CULL_IPT;
-constexpr int CULL_MAXD = MAXV;  // derivation views of one model (look-back words per tile)
-constexpr int CULL_GROUP = 8;    // views tested together (one warp walks back per view)
+constexpr int CULL_MAXD = MAXV;  // derivation views of one model
+
+// Derivation views of this model and their cameras (shared memory), set up by every block.
+struct CullViews {
+  int d[CULL_MAXD];
+  int ncam[CULL_MAXD];
+  float cam[CULL_MAXD][2][20];
+  float thr2[32];  // plain rule: (d_max 2^-l)^2 per level, +inf at level 0
+  int nd;
+};
 
 template <bool RADIUS>
-__global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict__ models, int model, FrameDev* fd,
-                                                  uint32_t* const* __restrict__ vis, uint8_t* const* __restrict__ eyes,
-                                                  unsigned long long* status) {
-  __shared__ int s_d[CULL_MAXD];
-  __shared__ int s_nd;
-  __shared__ float s_cam[CULL_MAXD][2][20];
-  __shared__ int s_ncam[CULL_MAXD];
-  __shared__ float s_thr2[32];  // plain rule: (d_max 2^-l)^2 per level, +inf at level 0
-  __shared__ uint32_t s_warp[CULL_NT / 32 + 1];
-  __shared__ uint32_t s_total[CULL_MAXD];
-  __shared__ uint32_t s_base[CULL_MAXD];
-  __shared__ uint32_t s_tile;
-
-  const ModelDev md = models[model];
+__device__ __forceinline__ void cull_views_setup(CullViews& V, const ModelDev& md, int model, const FrameDev* fd) {
   if (threadIdx.x == 0) {
     int nd = 0;
     for (uint32_t d = 0; d < fd->n_dviews; ++d) {
       if (fd->dcam[d].model != model) continue;
-      if (nd < CULL_MAXD) s_d[nd++] = (int)d;
+      if (nd < CULL_MAXD) V.d[nd++] = (int)d;
     }
-    s_nd = nd;
+    V.nd = nd;
   }
   __syncthreads();
-  const int nd = s_nd;
-  if (threadIdx.x < (unsigned)nd) s_ncam[threadIdx.x] = fd->dview_exact[s_d[threadIdx.x]] ? 2 : 1;
+  const int nd = V.nd;
+  if (threadIdx.x < (unsigned)nd) V.ncam[threadIdx.x] = fd->dview_exact[V.d[threadIdx.x]] ? 2 : 1;
   for (int i = threadIdx.x; i < nd * 40; i += CULL_NT) {
     const int ld = i / 40, k = (i / 20) & 1, f = i % 20;
-    const int d = s_d[ld];
+    const int d = V.d[ld];
     const bool exact = fd->dview_exact[d] != 0;
     if (k == 1 && !exact) continue;
     const CamDev& c = exact ? fd->cam[fd->dview_cam[d][k]] : fd->dcam[d];
@@ -152,154 +156,176 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull(const ModelDev* __restrict_
     else if (f == 16) v = c.gx;
     else if (f == 17) v = c.gy;
     else v = 0.f;
-    s_cam[ld][k][f] = v;
+    V.cam[ld][k][f] = v;
   }
   if (!RADIUS && threadIdx.x < 32) {
     const float thr = ldexpf(md.lod_dmax, -(int)threadIdx.x);
-    s_thr2[threadIdx.x] = threadIdx.x == 0 ? INFINITY : __fmul_rn(thr, thr);
+    V.thr2[threadIdx.x] = threadIdx.x == 0 ? INFINITY : __fmul_rn(thr, thr);
   }
   __syncthreads();
+}
+
+template <bool RADIUS>
+__global__ void __launch_bounds__(CULL_NT, 4) k_cull_count(const ModelDev* __restrict__ models, int model,
+                                                        const FrameDev* __restrict__ fd, uint32_t* __restrict__ masks,
+                                                        uint32_t* __restrict__ tile_cnt, uint32_t mask_stride,
+                                                        uint32_t cnt_stride) {
+  __shared__ CullViews V;
+  __shared__ uint32_t s_cnt[CULL_MAXD];
+  const ModelDev md = models[model];
+  cull_views_setup<RADIUS>(V, md, model, fd);
+  const int nd = V.nd;
   if (nd == 0) return;
-
+  if (threadIdx.x < (unsigned)nd) s_cnt[threadIdx.x] = 0;
   const uint32_t n = md.n;
-  const uint32_t ntiles = (n + CULL_TILE - 1) / CULL_TILE;
-  const uint32_t epoch = fd->frame * 64u + (uint32_t)(SLOT_CULL + model);
-  const uint32_t spin = fd->spin_limit;
-
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&fd->ctr[SLOT_CULL + model], 1u);
-    __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= ntiles) break;
-    const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
-    float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
-    int lv[CULL_IPT];     // plain rule: level, -1 past the end
-    float rr[CULL_IPT];   // radius rule: the anchor's switching radius (+inf at level 0);
-                          // past the end the position is NaN, which fails the frustum test
-    static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
-    if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
-      const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
-      const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
-      const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
-      x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
-      y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
-      z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
-      if (RADIUS) {
-        const float4 r0 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0));
-        const float4 r1 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0) + 1);
-        rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w; rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
-      } else {
-        const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
-#pragma unroll
-        for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
-      }
+  const uint32_t t = blockIdx.x;
+  const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
+  float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
+  int lv[CULL_IPT];     // plain rule: level, -1 past the end
+  float rr[CULL_IPT];   // radius rule: the anchor's switching radius (+inf at level 0);
+                        // past the end the position is NaN, which fails the frustum test
+  static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
+  if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
+    const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
+    const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
+    const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
+    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+    y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
+    z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
+    if (RADIUS) {
+      const float4 r0 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0));
+      const float4 r1 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0) + 1);
+      rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w; rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
     } else {
+      const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
+#pragma unroll
+      for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < CULL_IPT; ++i) {
+      const uint32_t a = a0 + i;
+      if (a < n) {
+        x[i] = __ldg(md.px + a);
+        y[i] = __ldg(md.py + a);
+        z[i] = __ldg(md.pz + a);
+        if (RADIUS)
+          rr[i] = __ldg(md.lod_r + a);
+        else
+          lv[i] = md.level[a];
+      } else if (RADIUS) {
+        x[i] = y[i] = z[i] = __int_as_float(0x7fffffff);
+        rr[i] = 0.f;
+      } else {
+        x[i] = y[i] = z[i] = 0.f;
+        lv[i] = -1;
+      }
+    }
+  }
+  __syncthreads();  // s_cnt cleared
+  for (int ld = 0; ld < nd; ++ld) {
+    uint32_t m = 0;
+    for (int k = 0; k < V.ncam[ld]; ++k) {
+      const float* c = V.cam[ld][k];
+      uint32_t mk = 0;
 #pragma unroll
       for (int i = 0; i < CULL_IPT; ++i) {
-        const uint32_t a = a0 + i;
-        if (a < n) {
-          x[i] = __ldg(md.px + a);
-          y[i] = __ldg(md.py + a);
-          z[i] = __ldg(md.pz + a);
-          if (RADIUS)
-            rr[i] = __ldg(md.lod_r + a);
-          else
-            lv[i] = md.level[a];
-        } else if (RADIUS) {
-          x[i] = y[i] = z[i] = __int_as_float(0x7fffffff);
-          rr[i] = 0.f;
-        } else {
-          x[i] = y[i] = z[i] = 0.f;
-          lv[i] = -1;
+        if (!RADIUS && lv[i] < 0) continue;
+        const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
+        const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
+        const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
+        bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
+        if (v) {
+          const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
+          const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+          v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : V.thr2[lv[i]]);
         }
+        if (v) mk |= 1u << i;
+      }
+      m |= mk | (mk << (8 + 8 * k));
+    }
+    masks[(size_t)ld * mask_stride + (size_t)t * CULL_NT + threadIdx.x] = m;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(m & 0xFFu));
+    if ((threadIdx.x & 31u) == 0 && c) atomicAdd(&s_cnt[ld], c);
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)nd) tile_cnt[(size_t)threadIdx.x * cnt_stride + t] = s_cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __restrict__ models, int model,
+                                                        FrameDev* __restrict__ fd, uint32_t* const* __restrict__ vis,
+                                                        uint8_t* const* __restrict__ eyes,
+                                                        const uint32_t* __restrict__ masks,
+                                                        const uint32_t* __restrict__ tile_cnt, uint32_t mask_stride,
+                                                        uint32_t cnt_stride) {
+  __shared__ int s_d[CULL_MAXD];
+  __shared__ int s_exact[CULL_MAXD];
+  __shared__ int s_nd;
+  __shared__ uint32_t s_warp[CULL_NT / 32 + 1];
+  __shared__ uint32_t s_red[CULL_NT / 32];
+  const ModelDev& md = models[model];
+  if (threadIdx.x == 0) {
+    int nd = 0;
+    for (uint32_t d = 0; d < fd->n_dviews; ++d) {
+      if (fd->dcam[d].model != model) continue;
+      if (nd < CULL_MAXD) {
+        s_exact[nd] = fd->dview_exact[d];
+        s_d[nd++] = (int)d;
       }
     }
-    for (int g0 = 0; g0 < nd; g0 += CULL_GROUP) {  // views g0 .. g0 + 7 of this model
-      // mask[u]: bits 0-7 the view keeps anchor i, bits 8-15 / 16-23 its first /
-      // second camera does (exact stereo views)
-      uint32_t excl[CULL_GROUP], mask[CULL_GROUP];
+    s_nd = nd;
+  }
+  __syncthreads();
+  const int nd = s_nd;
+  const uint32_t t = blockIdx.x;
+  const uint32_t ntiles = (md.n + CULL_TILE - 1) / CULL_TILE;
+  const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
+  for (int ld = 0; ld < nd; ++ld) {
+    // prefix of the tiles before this one: a block-wide sum of their counts
+    const uint32_t* tc = tile_cnt + (size_t)ld * cnt_stride;
+    uint32_t p = 0;
+    for (uint32_t u = threadIdx.x; u < t; u += CULL_NT) p += tc[u];
+    p = __reduce_add_sync(0xffffffffu, p);
+    if ((threadIdx.x & 31u) == 0) s_red[threadIdx.x >> 5] = p;
+    const uint32_t m = masks[(size_t)ld * mask_stride + (size_t)t * CULL_NT + threadIdx.x];
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m & 0xFFu), s_warp, &tot);  // syncs
+    uint32_t pre = 0;
 #pragma unroll
-      for (int u = 0; u < CULL_GROUP; ++u) {
-        const int ld = g0 + u;
-        excl[u] = 0;
-        mask[u] = 0;
-        if (ld >= nd) continue;
-        uint32_t m = 0;
-        for (int k = 0; k < s_ncam[ld]; ++k) {
-          const float* c = s_cam[ld][k];
-          uint32_t mk = 0;
-#pragma unroll
-          for (int i = 0; i < CULL_IPT; ++i) {
-            if (!RADIUS && lv[i] < 0) continue;
-            const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
-            const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
-            const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
-            bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-            if (v) {
-              const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
-              const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-              v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : s_thr2[lv[i]]);
-            }
-            if (v) mk |= 1u << i;
-          }
-          m |= mk | (mk << (8 + 8 * k));
-        }
-        mask[u] = m;
-        uint32_t tot;
-        excl[u] = block_exclusive_scan<CULL_NT>((uint32_t)__popc(m & 0xFFu), s_warp, &tot);
-        if (threadIdx.x == 0) s_total[ld] = tot;
+    for (int w = 0; w < CULL_NT / 32; ++w) pre += s_red[w];
+    const int d = s_d[ld];
+    uint32_t* out = vis[d];
+    uint8_t* eo = s_exact[ld] ? eyes[d] : nullptr;
+    uint32_t o = pre + ex;
+    uint32_t mm = m & 0xFFu;
+    while (mm) {
+      const int i = __ffs(mm) - 1;
+      mm &= mm - 1;
+      if (GSC_IN_BOUNDS(o, fd->cap_vis, &fd->err)) {
+        if (eo) eo[o] = (uint8_t)(((m >> (8 + i)) & 1u) | (((m >> (16 + i)) & 1u) << 1));
+        out[o] = a0 + (uint32_t)i;
       }
-      __syncthreads();
-      const int ld = g0 + (int)(threadIdx.x >> 5);
-      if (ld < nd && (int)(threadIdx.x >> 5) < CULL_GROUP) {  // warp u publishes view g0 + u's count, walks back
-        const bool l0 = (threadIdx.x & 31u) == 0;
-        const uint32_t tot = s_total[ld];
-        unsigned long long* w = status + (size_t)t * CULL_MAXD + ld;
-        uint32_t pre = 0;
-        if (t == 0) {
-          if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, tot));
-        } else {
-          if (l0) st_relaxed_u64(w, lb_pack(epoch, 1u, tot));
-          pre = lb_exclusive_warp(status + ld, CULL_MAXD, t, epoch, spin, &fd->err);
-          if (l0) st_relaxed_u64(w, lb_pack(epoch, 2u, pre + tot));
-        }
-        if (l0) {
-          s_base[ld] = pre;
-          if (t == ntiles - 1) fd->vis_count[s_d[ld]] = pre + tot;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < CULL_GROUP; ++u) {
-        const int lw = g0 + u;
-        if (lw >= nd) continue;
-        uint32_t* out = vis[s_d[lw]];
-        uint8_t* eo = s_ncam[lw] == 2 ? eyes[s_d[lw]] : nullptr;
-        uint32_t o = s_base[lw] + excl[u];
-        const uint32_t mm = mask[u];
-        uint32_t m = mm & 0xFFu;
-        while (m) {
-          const int i = __ffs(m) - 1;
-          m &= m - 1;
-          if (GSC_IN_BOUNDS(o, fd->cap_vis, &fd->err)) {
-            if (eo) eo[o] = (uint8_t)(((mm >> (8 + i)) & 1u) | (((mm >> (16 + i)) & 1u) << 1));
-            out[o] = a0 + (uint32_t)i;
-          }
-          ++o;
-        }
-      }
-      __syncthreads();
+      ++o;
     }
+    if (t == ntiles - 1 && threadIdx.x == 0) fd->vis_count[d] = pre + tot;
+    __syncthreads();  // s_red is reused by the next view
   }
 }
 
-void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
-                 uint8_t* const* eyes_dev, unsigned long long* status, int n_sm, cudaStream_t s) {
-  if (radius)
-    k_cull<true><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, status);
+void launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
+                 uint8_t* const* eyes_dev, uint32_t* masks, uint32_t* tile_cnt, uint32_t mask_stride,
+                 uint32_t cnt_stride, cudaStream_t s) {
+  const uint32_t ntiles = (h_model->n + CULL_TILE - 1) / CULL_TILE;
+  if (ntiles == 0) return;
+  if (h_model->lod_r)
+    k_cull_count<true><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
   else
-    k_cull<false><<<n_sm * 4, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, status);
+    k_cull_count<false><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
+  k_cull_write<<<ntiles, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, masks, tile_cnt, mask_stride, cnt_stride);
 }
+
+uint32_t cull_tiles(uint32_t n_anchors) { return (n_anchors + CULL_TILE - 1) / CULL_TILE; }
+uint32_t cull_mask_words(uint32_t n_anchors) { return cull_tiles(n_anchors) * CULL_NT; }
 
 // ------------------------------------------------------------------ plan
 __global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {

@@ -424,10 +424,18 @@ constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
-// eyes_dev: per derivation view, the eye mask of each visible anchor (bit e:
-// camera dview_cam[d][e] keeps it), written for exact stereo views only.
-void launch_cull(const ModelDev* md, int model, bool radius, FrameDev* fd, uint32_t* const* vis_dev,
-                 uint8_t* const* eyes_dev, unsigned long long* status, int n_sm, cudaStream_t s);
+// Anchor filtering of one model in two passes (keep masks and per-tile
+// counts, then the ids): vis_dev / eyes_dev per derivation view the visible
+// ids and, for exact stereo views, each one's eye mask (bit e: camera
+// dview_cam[d][e] keeps it); masks [views][mask_stride] and tile_cnt
+// [views][cnt_stride] are the passes' working arrays (cull_mask_words /
+// cull_tiles of the model's anchors per view).  h_model: the model's device
+// description as the host holds it.
+void launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
+                 uint8_t* const* eyes_dev, uint32_t* masks, uint32_t* tile_cnt, uint32_t mask_stride,
+                 uint32_t cnt_stride, cudaStream_t s);
+uint32_t cull_tiles(uint32_t n_anchors);
+uint32_t cull_mask_words(uint32_t n_anchors);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
 cudaError_t prepare_derive_f32();
 cudaError_t prepare_derive_tc();
