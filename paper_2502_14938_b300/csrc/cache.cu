@@ -9,14 +9,21 @@
 //   probe    per visible anchor: hit (valid line with age <= depth), refresh
 //            (valid line, older than depth) or new (no valid line; lines past
 //            D_max are invalid); misses go to a work list for the decoder;
-//            per line: free iff unused or past D_max
-//   scan     one scan over [free flags of the S lines | new flags of the
-//            visible anchors]: ranks of free lines (and the free list, in
+//            per line below the high-water mark hw: free iff unused or past
+//            D_max
+//   scan     one scan over [free flags of lines 0 .. hw-1 | new flags of the
+//            visible anchors]: ranks of those free lines (and their list, in
 //            ascending order) and of new anchors (ascending)
 //   assign   the i-th new anchor takes the i-th free line (none left: decoded
 //            but not cached); decoded lines are stamped with t; then the
 //            policy: next depth = H(misses / visible) in [1, D_max] (Eq. 4;
 //            H linear, exponential or staged, gsc_depth_guide).
+// The free lines in ascending order are those below hw followed by hw,
+// hw + 1, ..., S - 1: a line is first used only when every free line below
+// it is taken, so no line at or above hw has ever held an anchor.  Scanning
+// below hw alone therefore gives the assignment of a scan over all S lines,
+// at the cost of the working set (~60k lines on the city path) instead of
+// the capacity (400k).
 // The decoder writes fresh attributes of misses into their lines; the
 // projection reads hits from their lines.
 //
@@ -46,7 +53,7 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
   __shared__ float s_w[LEARNED ? RPARAM : 1];
   const CacheDev cd = caches[c];
   const uint32_t V = fd->vis_count[c];
-  const uint32_t t = cd.state[CS_T], depth = cd.state[CS_DEPTH], D = cd.state[CS_DMAX];
+  const uint32_t t = cd.state[CS_T], depth = cd.state[CS_DEPTH], D = cd.state[CS_DMAX], hw = cd.state[CS_HW];
   const uint32_t* ids = vis[c];
   const uint32_t stride = gridDim.x * blockDim.x;
   if (LEARNED) {
@@ -76,15 +83,15 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
       hit = valid && age <= depth;
     }
     cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
-    cd.flags[cd.S + vi] = valid ? 0u : 1u;
+    cd.flags[hw + vi] = valid ? 0u : 1u;
     if (!hit) {
       const uint32_t mi = atomicAdd(&cd.state[CS_MISSES], 1u);
       if (GSC_IN_BOUNDS(mi, V, const_cast<uint32_t*>(&fd->err))) cd.miss[mi] = vi;
     }
   }
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cd.S; s += stride)
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < hw; s += stride)
     cd.flags[s] = (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
-  if (blockIdx.x == 0 && threadIdx.x == 0) cd.state[CS_SCAN_N] = cd.S + V;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cd.state[CS_SCAN_N] = hw + V;
 }
 
 // Eq. 4 with the guiding function of the configuration (gsc_depth_guide).
@@ -109,15 +116,18 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* _
   const CamDev& cam = fd->dcam[c];
   const ModelDev& md = models[cam.model];
   const uint32_t V = fd->vis_count[c];
-  const uint32_t t = cd.state[CS_T];
-  const uint32_t n_free = V ? cd.ranks[cd.S] : cd.state[CS_SCAN_TOT];  // free lines precede the new flags
+  const uint32_t t = cd.state[CS_T], hw = cd.state[CS_HW];
+  // free lines below hw (their flags precede the new flags); then hw .. S-1
+  const uint32_t n_free = V ? cd.ranks[hw] : cd.state[CS_SCAN_TOT];
   const uint32_t* ids = vis[c];
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // bookkeeping and the policy for the next frame
     uint32_t* st = cd.state;
     const uint32_t m = st[CS_MISSES];
+    const uint32_t n_new = st[CS_SCAN_TOT] - n_free;
     st[CS_VIS] = V;
-    st[CS_FREE] = n_free;
-    st[CS_NEW] = st[CS_SCAN_TOT] - n_free;
+    st[CS_FREE] = n_free + (cd.S - hw);
+    st[CS_NEW] = n_new;
+    st[CS_HW_NEXT] = n_new > n_free ? min(cd.S, hw + (n_new - n_free)) : hw;
     st[CS_DEPTH] = next_depth(st[CS_DEPTH], V, m, st[CS_DMAX], st[CS_GUIDE]);
     atomicSub(&fd->n_derived, V - m);
     if (c == 0) fd->cache_depth = st[CS_DEPTH];
@@ -127,9 +137,9 @@ __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* _
     if (st & LINE_HIT) continue;
     const uint32_t a = ids[vi];
     uint32_t line = st;
-    if (cd.flags[cd.S + vi]) {
-      const uint32_t rank = cd.ranks[cd.S + vi] - n_free;
-      line = rank < n_free ? cd.free_list[rank] : LINE_NONE;
+    if (cd.flags[hw + vi]) {
+      const uint32_t rank = cd.ranks[hw + vi] - n_free;
+      line = rank < n_free ? cd.free_list[rank] : (rank - n_free < cd.S - hw ? hw + (rank - n_free) : LINE_NONE);
       cd.vstat[vi] = line;
     }
     if (line == LINE_NONE || !GSC_IN_BOUNDS(line, cd.S, &fd->err)) continue;
@@ -216,7 +226,7 @@ void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, Fr
       k_cache_probe<false><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
     if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
     launch_scan_u32(h.flags, nullptr, h.state + CS_SCAN_N, h.ranks, h.state + CS_SCAN_TOT, scan_status, fd,
-                    SLOT_CACHE + 2 * c, n_sm, s, h.free_list, h.S);
+                    SLOT_CACHE + 2 * c, n_sm, s, h.free_list, h.S, nullptr, nullptr, 0, h.state + CS_HW);
     k_cache_assign<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models);
   }
 }

@@ -160,8 +160,12 @@ struct ModelDev {
 };
 
 // One derivation view's cache of derived Gaussians (Sec. 4).
+// CS_HW: lines at or above it have never held an anchor this cache's life
+// (assignment takes free lines in ascending order, so used lines stay below
+// it); the probe and the scan cover lines [0, CS_HW) only.  CS_HW_NEXT: the
+// value for the next frame, written by the assignment, taken at the tick.
 enum : int { CS_T = 0, CS_DEPTH, CS_MISSES, CS_NEW, CS_FREE, CS_VIS, CS_DMAX, CS_S, CS_SCAN_N, CS_SCAN_TOT, CS_GUIDE,
-             CS_WORDS };
+             CS_HW, CS_HW_NEXT, CS_WORDS };
 constexpr uint32_t LINE_HIT = 0x80000000u;   // vstat: the anchor reuses its line
 constexpr uint32_t LINE_NONE = 0x7FFFFFFFu;  // vstat: decoded without a line
 struct CacheDev {
@@ -170,9 +174,9 @@ struct CacheDev {
   uint32_t* slot_frame;   // [S] frame of the line's last decode
   uint2* slot_attr;       // [S][K][3]: 12 float16 per Gaussian (alpha, c, s, q, 0)
   uint32_t* vstat;        // [visible] line | LINE_HIT, or LINE_NONE
-  uint32_t* flags;        // [S + visible]: line is free, then visible anchor is new
-  uint32_t* ranks;        // [S + visible]: exclusive prefix of flags (one scan)
-  uint32_t* free_list;    // [S] free lines in ascending order
+  uint32_t* flags;        // [hw + visible]: line is free (lines below CS_HW), then visible anchor is new
+  uint32_t* ranks;        // [hw + visible]: exclusive prefix of flags (one scan)
+  uint32_t* free_list;    // [S] free lines below CS_HW in ascending order
   uint32_t* miss;         // [visible] visible indices to decode
   uint32_t* state;        // [CS_WORDS]
   float4* slot_dir;       // [S] unit direction camera -> anchor when the line was decoded
@@ -516,11 +520,12 @@ void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
 // Records covering more than KG_SMALL tiles get their pairs from a warp each.
 constexpr uint32_t KG_SMALL = 32;
 // big / n_big: indices i with cnt > big_above are appended (the large
-// records of key generation), else null.
+// records of key generation), else null.  scatter_n_dev: the scatter bound
+// read on the device (replaces scatter_n), else null.
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
                      cudaStream_t s, uint32_t* scatter = nullptr, uint32_t scatter_n = 0, uint32_t* big = nullptr,
-                     uint32_t* n_big = nullptr, uint32_t big_above = 0);
+                     uint32_t* n_big = nullptr, uint32_t big_above = 0, const uint32_t* scatter_n_dev = nullptr);
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s);
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s);

@@ -8,8 +8,8 @@ namespace gsc {
 // ------------------------------------------------------------------ scan (K6)
 // Exclusive prefix sum of cnt[order[i]] (or cnt[i] without order) for
 // i < *n_ptr, one pass with a decoupled look-back; *total_out = the sum.
-// With scatter: for i < scatter_n with cnt[i] = 1, scatter[out[i]] = i (the
-// positions of the set flags, in ascending order).  With big: every i whose
+// With scatter: for i < scatter_n (or *scatter_n_dev) with cnt[i] = 1,
+// scatter[out[i]] = i (the positions of the set flags, in ascending order).  With big: every i whose
 // count exceeds big_above is appended to big (order unspecified).
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_IPT = 4;  // 1024-element tiles: a frame's ~0.5M counts spread over every SM
@@ -20,11 +20,12 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
                                                   uint32_t* total_out, unsigned long long* status, FrameDev* fd,
                                                   int slot, uint32_t* __restrict__ scatter, uint32_t scatter_n,
                                                   uint32_t* __restrict__ big, uint32_t* __restrict__ n_big,
-                                                  uint32_t big_above) {
+                                                  uint32_t big_above, const uint32_t* __restrict__ scatter_n_dev) {
   __shared__ uint32_t s_warp[SCAN_NT / 32 + 1];
   __shared__ uint32_t s_base;
   __shared__ uint32_t s_tile;
   const uint32_t n = *n_ptr;
+  if (scatter_n_dev) scatter_n = *scatter_n_dev;
   const uint32_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   const uint32_t epoch = fd->frame * 64u + (uint32_t)slot;
   const uint32_t spin = fd->spin_limit;
@@ -88,9 +89,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
 void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t* n_ptr, uint32_t* out,
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
                      cudaStream_t s, uint32_t* scatter, uint32_t scatter_n, uint32_t* big, uint32_t* n_big,
-                     uint32_t big_above) {
+                     uint32_t big_above, const uint32_t* scatter_n_dev) {
   k_scan<<<n_sm * 4, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n, big,
-                                      n_big, big_above);
+                                      n_big, big_above, scatter_n_dev);
 }
 
 // ------------------------------------------------------------------ key generation (K7)
