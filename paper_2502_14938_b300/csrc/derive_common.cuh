@@ -30,7 +30,6 @@ struct DViewSet {
   const uint32_t* vstat[MAXV]; // cached views: line status per visible index
   uint2* lattr[MAXV];          // cached views: float16 line attributes
   float pc[MAXV][6];        // double-float centre of each derivation camera
-  ProjCam cam[MAXV][2];     // cameras fed by each view (cam = 0xFFFFFFFF unused)
 };
 
 // Per-frame tables in device memory, written once by k_tables so that the
@@ -92,7 +91,6 @@ __device__ __forceinline__ void build_dview_set(DViewSet& S, const FrameDev* fd,
       S.pc[nd][u] = fd->dcam[d].pc[u];
       S.pc[nd][3 + u] = fd->dcam[d].pc_lo[u];
     }
-    for (int e = 0; e < 2; ++e) fill_projcam(S.cam[nd][e], fd, fd->dview_cam[d][e]);
     ++nd;
   }
   S.base[nd] = acc;
@@ -116,16 +114,26 @@ __device__ __forceinline__ void load_dview_set(DViewSet& S, const DViewSet* __re
 // the oracle uses for its ordering depth).  The geometry uses camera-relative
 // coordinates rel = ((x_a - c_hi) - c_lo) + o, which avoid the cancellation of
 // R x + t at city scale.
+// The pinned ordering depth of a Gaussian at mu.
+__device__ __forceinline__ float pinned_tz(const ProjCam& c, const float mu[3]) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mu[0]), __fmul_rn(c.R[7], mu[1])), __fmul_rn(c.R[8], mu[2])),
+                   c.t[2]);
+}
+// The record's first test (kept, in front of the near plane, opacity at
+// least 1/255): records that fail it are only their invalid key.
+__device__ __forceinline__ bool record_may_draw(const ProjCam& c, const float mu[3], float alpha, bool kept) {
+  return kept && (pinned_tz(c, mu) > c.znear) && (alpha >= (1.0f / 255.0f));
+}
+
 __device__ __forceinline__ uint32_t project_write(const ProjCam& c, Records rec, uint32_t r, const float mu[3],
                                               const float rel[3], float alpha, bool kept, const float col[3],
                                               const float s[3], const float q[4], int TW, int TH) {
-  const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mu[0]), __fmul_rn(c.R[7], mu[1])),
-                                       __fmul_rn(c.R[8], mu[2])), c.t[2]);
+  const float tz = pinned_tz(c, mu);
   float4 geo = make_float4(0.f, 0.f, 0.f, 0.f), cop = make_float4(0.f, 0.f, 0.f, tz);
   uint32_t flag = c.cam;
   uint32_t cnt = 0;
   float4 colv = make_float4(col[0], col[1], col[2], 0.f);
-  const bool valid = kept && (tz > c.znear) && (alpha >= (1.0f / 255.0f));
+  const bool valid = record_may_draw(c, mu, alpha, kept);
   if (valid) {
     // camera coordinates R mu + t as R (mu - pc) + (t + R pc): the large
     // parts cancel exactly in the camera-relative position
@@ -198,24 +206,40 @@ __device__ __forceinline__ uint32_t project_write(const ProjCam& c, Records rec,
 // Stored as 3 float4 at attrs[3 idx ..]: (alpha, c), (s, q_w), (q_x, q_y, q_z, 0),
 // and as 12 float16 (round to nearest even) at line[0..2] when given.
 // dbg (optional): the 11 attributes at dbg[11 (i K + j)].
+// FAST (the tensor-core forms): sigmoid(x) = 1 / (1 + 2^(-x log2 e)) and
+// tanh(x) = 2 sigmoid(2x) - 1 (odd series near 0) from the exp2 and reciprocal approximations of
+// the special-function unit (__expf, __fdividef; relative errors ~1e-6, far
+// inside those forms' rounding of inputs, weights and hidden layer) instead
+// of the correctly rounded library sequences: the epilogue of a tile has
+// only 8 warps per CTA, so its dependent instruction chains set its time.
 __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
   const __half2 h = __floats2half2_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+__device__ __forceinline__ float sigmoid_fast(float x) {
+  return __fdividef(1.0f, 1.0f + __expf(-fminf(fmaxf(x, -80.f), 80.f)));
+}
+// tanh(x); near 0 its odd series x - x^3/3 (error below 2^-34 x for
+// |x| < 2^-6), so that the sign, which carries the Gaussian's mask, is x's
+__device__ __forceinline__ float tanh_fast(float x) {
+  return fabsf(x) < 0.015625f ? x - x * x * x * (1.0f / 3.0f) : 2.0f * sigmoid_fast(2.0f * x) - 1.0f;
+}
+
+template <bool FAST = false>
 __device__ __forceinline__ void gaussian_activate_store(const float z[11], int j, uint32_t i, float sa, float4* attrs,
                                                         size_t idx, float* dbg, uint2* line = nullptr) {
-  const float alpha = tanhf(z[0]);
+  const float alpha = FAST ? tanh_fast(z[0]) : tanhf(z[0]);
   float col[3], s[3], q[4];
 #pragma unroll
-  for (int u = 0; u < 3; ++u) col[u] = 1.0f / (1.0f + expf(-z[1 + u]));
+  for (int u = 0; u < 3; ++u) col[u] = FAST ? sigmoid_fast(z[1 + u]) : 1.0f / (1.0f + expf(-z[1 + u]));
 #pragma unroll
-  for (int u = 0; u < 3; ++u) s[u] = sa * (1.0f / (1.0f + expf(-z[4 + u])));
+  for (int u = 0; u < 3; ++u) s[u] = sa * (FAST ? sigmoid_fast(z[4 + u]) : 1.0f / (1.0f + expf(-z[4 + u])));
   const float qn2 = z[7] * z[7] + z[8] * z[8] + z[9] * z[9] + z[10] * z[10];
   if (qn2 < 1e-24f) {
     q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
   } else {
-    const float iq = 1.0f / sqrtf(qn2);
+    const float iq = FAST ? rsqrtf(qn2) : 1.0f / sqrtf(qn2);
 #pragma unroll
     for (int u = 0; u < 4; ++u) q[u] = z[7 + u] * iq;
   }

@@ -39,6 +39,7 @@ struct DFMeta {
   int ld[DF_TA];          // view slot in the DViewSet (-1: empty item)
   float pos[DF_TA][3];
   float sa[DF_TA];
+  uint32_t line[DF_TA];   // cache line the decode rewrites, or LINE_NONE
 };
 
 template <int HEAD, int O0, int O1>
@@ -104,6 +105,12 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
         const uint32_t a = vis[S.d[ld]][vi];
         M.anchor[t] = a;
         M.vi[t] = vi;
+        uint32_t line = LINE_NONE;
+        if (S.vstat[ld]) {
+          const uint32_t st = S.vstat[ld][vi];
+          if (st != LINE_NONE && !(st & LINE_HIT)) line = st;
+        }
+        M.line[t] = line;
         const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
         M.pos[t][0] = xa; M.pos[t][1] = ya; M.pos[t][2] = za;
         M.sa[t] = __ldg(md.scale + a);
@@ -199,11 +206,7 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
       for (int u = 0; u < 7; ++u) z[4 + u] = zr[4 * K + 7 * j + u];
       float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
       const size_t idx = (size_t)(S.gbase[ld] + M.vi[a]) * K + j;
-      uint2* line = nullptr;
-      if (S.vstat[ld]) {
-        const uint32_t st = S.vstat[ld][M.vi[a]];
-        if (st != LINE_NONE && !(st & LINE_HIT)) line = S.lattr[ld] + ((size_t)st * K + j) * 3;
-      }
+      uint2* line = M.line[a] != LINE_NONE ? S.lattr[ld] + ((size_t)M.line[a] * K + j) * 3 : nullptr;
       if (idx < rec_cap) gaussian_activate_store(z, j, M.vi[a], M.sa[a], attrs, idx, dbg, line);
     }
     __syncthreads();

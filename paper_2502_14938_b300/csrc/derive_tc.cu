@@ -12,11 +12,12 @@
 // 16 or 32 per MMA.
 //
 // One CTA (8 warps) takes tiles of 128 visible anchors:
-//   load     the features of the 128 anchors come straight from the model's
-//            BF16 (E4M3) feature table, 16-byte vector loads by the threads
-//            (a thread per row and K-chunk half), stored as K-columns of
-//            8x16-byte core matrices of the no-swizzle K-major operand
-//            layout; the view direction column likewise
+//   load     thread t < 128 fetches row t: the anchor's id, position, scale
+//            and line status and, in the same round trip, its feature row
+//            straight from the model's BF16 (E4M3) feature table (16-byte
+//            vector loads), stored as K-columns of 8x16-byte core matrices of
+//            the no-swizzle K-major operand layout; the view direction
+//            column likewise
 //   MMA1     D1[128 x 96] = X[128 x 48] W1cat^T       (3 x K=16, TMEM cols 0-95)
 //   epi 1    H = bf16(ReLU(D1 + b1)) into shared memory, same operand layout
 //   MMA2     D2[128 x 160] = H[128 x 96] W2bd^T       (6 x K=16, TMEM cols 96-255)
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   int* m_ld = reinterpret_cast<int*>(m_vi + TC_M);
   float* m_pos = reinterpret_cast<float*>(m_ld + TC_M);  // [3][128]
   float* m_sa = m_pos + 3 * TC_M;
+  uint32_t* m_line = reinterpret_cast<uint32_t*>(m_sa + TC_M);  // line to write, or LINE_NONE
   const float* s_b1 = reinterpret_cast<const float*>(smem + L::B1);
   const float* s_s1 = reinterpret_cast<const float*>(smem + L::S1);
   const float* s_r1 = reinterpret_cast<const float*>(smem + L::R1);
@@ -251,18 +253,29 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
 
   for (uint32_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     // ---- metadata, view direction chunk, feature chunks
-    if (t < TC_M) {
+    if (t < TC_M) {  // thread t: row t's metadata, view direction and feature chunks
       const uint32_t item = tile * TC_M + t;
       int ld = -1;
-      float dx = 0.f, dy = 0.f, dz = 0.f;
+      uint32_t a = 0, vi = 0, line = LINE_NONE;  // rows past the end load anchor 0; nothing is stored
       if (item < total) {
         ld = 0;
         while (item >= S.base[ld + 1]) ++ld;
         const uint32_t w = item - S.base[ld];
-        const uint32_t vi = S.miss[ld] ? S.miss[ld][w] : w;
-        const uint32_t a = vis[S.d[ld]][vi];
-        m_anchor[t] = a;
-        m_vi[t] = vi;
+        vi = S.miss[ld] ? S.miss[ld][w] : w;
+        a = vis[S.d[ld]][vi];
+        if (S.vstat[ld]) {  // a miss with a line (refresh or new) rewrites it
+          const uint32_t st = S.vstat[ld][vi];
+          if (st != LINE_NONE && !(st & LINE_HIT)) line = st;
+        }
+      }
+      // the feature row (16-byte K-chunks into the operand layout) is
+      // fetched beside the position and scale: one round trip for both
+      const uint4* ft = reinterpret_cast<const uint4*>(FP8 ? md.feat_fp8 : md.feat_bf16) + (size_t)a * L::FEAT_CH;
+      uint4 fc[L::FEAT_CH];
+#pragma unroll
+      for (int c = 0; c < L::FEAT_CH; ++c) fc[c] = __ldg(ft + c);
+      float dx = 0.f, dy = 0.f, dz = 0.f;
+      if (ld >= 0) {
         const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
         m_pos[t] = xa; m_pos[TC_M + t] = ya; m_pos[2 * TC_M + t] = za;
         m_sa[t] = __ldg(md.scale + a);
@@ -272,8 +285,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         const float vn = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         dx *= vn; dy *= vn; dz *= vn;
       }
-      if (ld < 0) m_anchor[t] = 0;  // a valid row to load; its results are not stored
+      m_anchor[t] = a;
+      m_vi[t] = vi;
+      m_line[t] = line;
       m_ld[t] = ld;
+#pragma unroll
+      for (int c = 0; c < L::FEAT_CH; ++c) reinterpret_cast<uint4*>(smem + L::A + c * 2048)[t] = fc[c];
       uint4 dirc;
       if constexpr (FP8) {
         const float ix = md.fp8_inv_sx;  // 1 / s_x, a power of two
@@ -282,19 +299,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         dirc = make_uint4(pack_bf16x2(dx, dy), pack_bf16x2(dz, 0.f), 0u, 0u);
       }
       reinterpret_cast<uint4*>(smem + L::A + L::DIR_CH * 2048)[t] = dirc;
-      fence_proxy_async();
-    }
-    __syncthreads();  // the tile's anchor ids
-    {  // feature rows: thread t loads K-chunks of row t % 128 (16 bytes each)
-      const uint4* ft = reinterpret_cast<const uint4*>(FP8 ? md.feat_fp8 : md.feat_bf16);
-      const int row = t & (TC_M - 1), h = t >> 7;
-      const size_t a = m_anchor[row];
-#pragma unroll
-      for (int c = h * (L::FEAT_CH / 2); c < (h + 1) * (L::FEAT_CH / 2); ++c)
-        reinterpret_cast<uint4*>(smem + L::A + c * 2048)[row] = __ldg(ft + a * L::FEAT_CH + c);
       fence_proxy_async();  // generic-proxy writes, read by the MMA's async proxy
     }
-    __syncthreads();
+    __syncthreads();  // the tile's rows
     if (w_pending) {
       if (__syncthreads_or(!mbar_wait(w_bar, 0))) {
         failed = true;
@@ -397,6 +404,11 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
     {
       const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
       const int ld = m_ld[row];
+      const uint32_t vi = m_vi[row], mline = m_line[row];
+      const float sa = m_sa[row];
+      float* dbg = ld >= 0 && dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
+      const size_t idx0 = ld >= 0 ? (size_t)(S.gbase[ld] + vi) * K : 0;
+      uint2* lbase = ld >= 0 && mline != LINE_NONE ? S.lattr[ld] + (size_t)mline * K * 3 : nullptr;
       const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + 96u;
 #pragma unroll 1
       for (int jj = 0; jj < 5; ++jj) {
@@ -407,14 +419,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
         float z[11];
 #pragma unroll
         for (int u = 0; u < 11; ++u) z[u] = FP8 ? fmaf(v[u], s_s2[16 * j + u], s_b2[16 * j + u]) : v[u] + s_b2[16 * j + u];
-        float* dbg = dbg_attrs ? dbg_attrs[S.d[ld]] : nullptr;
-        const size_t idx = (size_t)(S.gbase[ld] + m_vi[row]) * K + j;
-        uint2* line = nullptr;
-        if (S.vstat[ld]) {
-          const uint32_t st = S.vstat[ld][m_vi[row]];
-          if (st != LINE_NONE && !(st & LINE_HIT)) line = S.lattr[ld] + ((size_t)st * K + j) * 3;
-        }
-        if (idx < rec_cap) gaussian_activate_store(z, j, m_vi[row], m_sa[row], attrs, idx, dbg, line);
+        const size_t idx = idx0 + j;
+        uint2* line = lbase ? lbase + (size_t)j * 3 : nullptr;
+        if (idx < rec_cap) gaussian_activate_store<true>(z, j, vi, sa, attrs, idx, dbg, line);
       }
     }
     tc_fence_before();

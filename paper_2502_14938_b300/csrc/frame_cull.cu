@@ -6,27 +6,36 @@ namespace gsc {
 // ------------------------------------------------------------------ frame setup
 // The cameras' constants and the derivation views (with the unified camera
 // of each stereo pair, Eq. 5-6) are prepared in float64 by the library's host
-// code, which has fast float64; this warp copies them into the frame plan,
-// resets the per-frame counters and advances each cache's frame counter
-// (lane c < n_caches, Alg. 1 tick).
-__global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, CacheDev* __restrict__ caches,
-                              int n_caches) {
+// code, which has fast float64; this block copies them into the frame plan
+// (word by word across its threads), resets the per-frame counters and
+// histograms and advances each cache's frame counter (thread c < n_caches,
+// Alg. 1 tick).
+constexpr int FB_NT = 256;
+static_assert(sizeof(CamDev) % 4 == 0, "cameras are copied as words");
+
+__global__ void __launch_bounds__(FB_NT) k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin,
+                                                       CacheDev* __restrict__ caches, int n_caches) {
   if (blockIdx.x != 0) return;
   const FrameIn& F = *fin;
-  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t t = threadIdx.x;
   const uint32_t nc = F.n_cams, nd = F.n_dviews;
-  if (lane < nc) {
-    fd->cam[lane] = F.cam[lane];
-    fd->dview_of_cam[lane] = F.dview_of_cam[lane];
+  {
+    constexpr uint32_t CW = sizeof(CamDev) / 4;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(F.cam);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(fd->cam);
+    for (uint32_t i = t; i < nc * CW; i += FB_NT) dst[i] = src[i];
+    src = reinterpret_cast<const uint32_t*>(F.dcam);
+    dst = reinterpret_cast<uint32_t*>(fd->dcam);
+    for (uint32_t i = t; i < nd * CW; i += FB_NT) dst[i] = src[i];
   }
-  if (lane < nd) {
-    fd->dcam[lane] = F.dcam[lane];
-    fd->dview_cam[lane][0] = F.dview_cam[lane][0];
-    fd->dview_cam[lane][1] = F.dview_cam[lane][1];
-    fd->dview_exact[lane] = F.dview_exact[lane];
-    fd->vis_count[lane] = 0;
+  if (t < nc) fd->dview_of_cam[t] = F.dview_of_cam[t];
+  if (t < nd) {
+    fd->dview_cam[t][0] = F.dview_cam[t][0];
+    fd->dview_cam[t][1] = F.dview_cam[t][1];
+    fd->dview_exact[t] = F.dview_exact[t];
+    fd->vis_count[t] = 0;
   }
-  if (lane == 0) {
+  if (t == 0) {
     fd->frame = fd->frame + 1;
     fd->n_cams = nc;
     fd->n_dviews = nd;
@@ -47,25 +56,24 @@ __global__ void k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin, Cac
     fd->blend_work[0] = 0;
     fd->blend_work[1] = 0;
   }
-  fd->ctr[lane] = 0;
-  fd->ctr[32 + lane] = 0;
+  if (t < 64) fd->ctr[t] = 0;
   {  // the two sorts' digit histograms (filled by the key producers)
     uint4* h = reinterpret_cast<uint4*>(fd->hist_depth);
     uint4* h2 = reinterpret_cast<uint4*>(fd->hist_tile);
-    for (uint32_t i = lane; i < 256; i += 32) {
-      h[i] = make_uint4(0, 0, 0, 0);
-      h2[i] = make_uint4(0, 0, 0, 0);
-    }
+    static_assert(FB_NT == 256, "one uint4 of each histogram per thread");
+    h[t] = make_uint4(0, 0, 0, 0);
+    h2[t] = make_uint4(0, 0, 0, 0);
   }
-  if ((int)lane < n_caches && caches[lane].active) {
-    uint32_t* st = caches[lane].state;
+  if ((int)t < n_caches && caches[t].active) {
+    uint32_t* st = caches[t].state;
     st[CS_T] += 1u;
     st[CS_MISSES] = 0;
+    st[CS_HW] = st[CS_HW_NEXT];
   }
 }
 
 void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s) {
-  k_frame_begin<<<1, 32, 0, s>>>(fd, fin, caches, n_caches);
+  k_frame_begin<<<1, FB_NT, 0, s>>>(fd, fin, caches, n_caches);
 }
 
 // New epoch for standalone uses of the look-back kernels (debug sort / scan).
@@ -109,7 +117,11 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) 
 //   count  each thread's keep masks per view (bits 0-7 the view keeps
 //          anchor i, 8-15 / 16-23 the first / second camera of an exact
 //          stereo view does) to device memory, and per tile and view the
-//          number kept
+//          number kept.  A camera keeps an anchor iff both its LOD and its
+//          frustum test pass; the LOD test runs first for every anchor and
+//          rejects all but a few percent of a city-scale model, and each
+//          warp then runs the frustum tests on its LOD survivors only, 32 at
+//          a time (the same float32 operations, so the same decisions)
 //   write  per tile and view the exclusive prefix of the tiles before it (a
 //          block-wide sum of their counts), a block scan of the threads'
 //          counts, and the kept ids in ascending order (with their eye
@@ -172,6 +184,8 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_count(const ModelDev* __res
                                                         uint32_t cnt_stride) {
   __shared__ CullViews V;
   __shared__ uint32_t s_cnt[CULL_MAXD];
+  __shared__ uint16_t s_list[CULL_NT / 32][32 * CULL_IPT];  // per warp: LOD survivors
+  __shared__ uint32_t s_mask[CULL_NT];                      // per thread: keep masks being built
   const ModelDev md = models[model];
   cull_views_setup<RADIUS>(V, md, model, fd);
   const int nd = V.nd;
@@ -180,73 +194,113 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_count(const ModelDev* __res
   const uint32_t n = md.n;
   const uint32_t t = blockIdx.x;
   const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
-  float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
-  int lv[CULL_IPT];     // plain rule: level, -1 past the end
-  float rr[CULL_IPT];   // radius rule: the anchor's switching radius (+inf at level 0);
-                        // past the end the position is NaN, which fails the frustum test
-  static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
-  if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
-    const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
-    const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
-    const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
-    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
-    y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
-    z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
-    if (RADIUS) {
-      const float4 r0 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0));
-      const float4 r1 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0) + 1);
-      rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w; rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
-    } else {
-      const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
-#pragma unroll
-      for (int i = 0; i < CULL_IPT; ++i) lv[i] = (int)(((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < CULL_IPT; ++i) {
-      const uint32_t a = a0 + i;
-      if (a < n) {
-        x[i] = __ldg(md.px + a);
-        y[i] = __ldg(md.py + a);
-        z[i] = __ldg(md.pz + a);
-        if (RADIUS)
-          rr[i] = __ldg(md.lod_r + a);
-        else
-          lv[i] = md.level[a];
-      } else if (RADIUS) {
-        x[i] = y[i] = z[i] = __int_as_float(0x7fffffff);
-        rr[i] = 0.f;
+  __syncthreads();  // s_cnt cleared
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint16_t* list = s_list[warp];
+  for (int ld = 0; ld < nd; ++ld) {
+    const int ncam = V.ncam[ld];
+    // (positions are loaded per view, so that they are not live across the
+    // survivor pass; a second view finds them in L1)
+    float x[CULL_IPT], y[CULL_IPT], z[CULL_IPT];
+    float thr[CULL_IPT];  // squared LOD distance: (d_max 2^-l)^2 from the level table, or the
+                          // anchor's own radius squared; -1 past the end (never kept)
+    static_assert(CULL_IPT == 8, "a thread loads two float4 per coordinate and 8 level bytes");
+    if (a0 + CULL_IPT <= n) {  // 32-byte aligned runs (a0 is a multiple of 8; arrays are 256-byte aligned)
+      const float4 x0 = __ldg(reinterpret_cast<const float4*>(md.px + a0)), x1 = __ldg(reinterpret_cast<const float4*>(md.px + a0) + 1);
+      const float4 y0 = __ldg(reinterpret_cast<const float4*>(md.py + a0)), y1 = __ldg(reinterpret_cast<const float4*>(md.py + a0) + 1);
+      const float4 z0 = __ldg(reinterpret_cast<const float4*>(md.pz + a0)), z1 = __ldg(reinterpret_cast<const float4*>(md.pz + a0) + 1);
+      x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w; x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+      y[0] = y0.x; y[1] = y0.y; y[2] = y0.z; y[3] = y0.w; y[4] = y1.x; y[5] = y1.y; y[6] = y1.z; y[7] = y1.w;
+      z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w; z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
+      if (RADIUS) {
+        const float4 r0 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0));
+        const float4 r1 = __ldg(reinterpret_cast<const float4*>(md.lod_r + a0) + 1);
+        const float rr[CULL_IPT] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+  #pragma unroll
+        for (int i = 0; i < CULL_IPT; ++i) thr[i] = __fmul_rn(rr[i], rr[i]);
       } else {
+        const uint2 l8 = __ldg(reinterpret_cast<const uint2*>(md.level + a0));
+  #pragma unroll
+        for (int i = 0; i < CULL_IPT; ++i) thr[i] = V.thr2[((i < 4 ? l8.x : l8.y) >> (8 * (i & 3))) & 0xFFu];
+      }
+    } else {
+  #pragma unroll
+      for (int i = 0; i < CULL_IPT; ++i) {
+        const uint32_t a = a0 + i;
         x[i] = y[i] = z[i] = 0.f;
-        lv[i] = -1;
+        thr[i] = -1.f;
+        if (a < n) {
+          x[i] = __ldg(md.px + a);
+          y[i] = __ldg(md.py + a);
+          z[i] = __ldg(md.pz + a);
+          if (RADIUS) {
+            const float r = __ldg(md.lod_r + a);
+            thr[i] = __fmul_rn(r, r);
+          } else {
+            thr[i] = V.thr2[md.level[a]];
+          }
+        }
       }
     }
-  }
-  __syncthreads();  // s_cnt cleared
-  for (int ld = 0; ld < nd; ++ld) {
-    uint32_t m = 0;
-    for (int k = 0; k < V.ncam[ld]; ++k) {
+    // LOD of every anchor for each camera (the cheap test, which keeps a few
+    // percent of the city): bit i of lod0 / lod1
+    uint32_t lod0 = 0u, lod1 = 0u;
+    for (int k = 0; k < ncam; ++k) {
       const float* c = V.cam[ld][k];
-      uint32_t mk = 0;
+      const float px = c[12], py = c[13], pz = c[14];
+      uint32_t lk = 0u;
 #pragma unroll
       for (int i = 0; i < CULL_IPT; ++i) {
-        if (!RADIUS && lv[i] < 0) continue;
-        const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], x[i]), __fmul_rn(c[1], y[i])), __fmul_rn(c[2], z[i])), c[9]);
-        const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], x[i]), __fmul_rn(c[4], y[i])), __fmul_rn(c[5], z[i])), c[10]);
-        const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], x[i]), __fmul_rn(c[7], y[i])), __fmul_rn(c[8], z[i])), c[11]);
-        bool v = (Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z));
-        if (v) {
-          const float dx = __fsub_rn(x[i], c[12]), dy = __fsub_rn(y[i], c[13]), dz = __fsub_rn(z[i], c[14]);
-          const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-          v = d2 <= (RADIUS ? __fmul_rn(rr[i], rr[i]) : V.thr2[lv[i]]);
-        }
-        if (v) mk |= 1u << i;
+        const float dx = __fsub_rn(x[i], px), dy = __fsub_rn(y[i], py), dz = __fsub_rn(z[i], pz);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        if (d2 <= thr[i]) lk |= 1u << i;
       }
-      m |= mk | (mk << (8 + 8 * k));
+      if (k == 0) lod0 = lk; else lod1 = lk;
     }
+    // the warp's LOD survivors, compacted: entry = anchor slot (lane * 8 + i)
+    // | the cameras whose LOD kept it << 8
+    const uint32_t cand = lod0 | lod1;
+    const uint32_t nc = (uint32_t)__popc(cand);
+    uint32_t inc = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    uint32_t pos = inc - nc;
+    for (uint32_t cm = cand; cm; cm &= cm - 1) {
+      const int i = __ffs(cm) - 1;
+      list[pos++] = (uint16_t)((lane << 3) | i | (((lod0 >> i) & 1u) << 8) | (((lod1 >> i) & 1u) << 9));
+    }
+    s_mask[threadIdx.x] = 0u;
+    __syncwarp();
+    // frustum tests of the survivors, 32 at a time across the warp
+    for (uint32_t j = lane; j < ((total + 31u) & ~31u); j += 32u) {
+      if (j < total) {
+        const uint32_t e = list[j];
+        const uint32_t owner = (e >> 3) & 31u, i = e & 7u;
+        const uint32_t a = t * CULL_TILE + ((uint32_t)warp * 32u + owner) * CULL_IPT + i;
+        const float xa = __ldg(md.px + a), ya = __ldg(md.py + a), za = __ldg(md.pz + a);
+        uint32_t bits = 0;
+        for (int k = 0; k < ncam; ++k) {
+          if (!((e >> (8 + k)) & 1u)) continue;
+          const float* c = V.cam[ld][k];
+          const float X = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[0], xa), __fmul_rn(c[1], ya)), __fmul_rn(c[2], za)), c[9]);
+          const float Y = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[3], xa), __fmul_rn(c[4], ya)), __fmul_rn(c[5], za)), c[10]);
+          const float Z = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c[6], xa), __fmul_rn(c[7], ya)), __fmul_rn(c[8], za)), c[11]);
+          if ((Z > c[15]) && (fabsf(X) <= __fmul_rn(c[16], Z)) && (fabsf(Y) <= __fmul_rn(c[17], Z)))
+            bits |= (1u << i) | (1u << (8 + 8 * k + i));
+        }
+        if (bits) atomicOr(&s_mask[warp * 32 + (int)owner], bits);
+      }
+    }
+    __syncwarp();
+    const uint32_t m = s_mask[threadIdx.x];
     masks[(size_t)ld * mask_stride + (size_t)t * CULL_NT + threadIdx.x] = m;
     const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(m & 0xFFu));
-    if ((threadIdx.x & 31u) == 0 && c) atomicAdd(&s_cnt[ld], c);
+    if (lane == 0 && c) atomicAdd(&s_cnt[ld], c);
+    __syncwarp();  // s_mask and the list are reused by the next view
   }
   __syncthreads();
   if (threadIdx.x < (unsigned)nd) tile_cnt[(size_t)threadIdx.x * cnt_stride + t] = s_cnt[threadIdx.x];

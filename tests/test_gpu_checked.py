@@ -3,9 +3,10 @@ GSC_DEBUG_BOUNDS): every data-indexed store (compaction offsets, cache lines
 and miss lists, scan scatters, sort ranks, tile ranges) tests its index
 against the buffer's capacity and, on a miss, flags the frame and skips the
 store.  It stands in for a device memory checker.  A child process loads it
-(GSC_LIBRARY) and renders the tiny scene, the city path's headline form and
-a batched multi-model frame; no frame may flag an out-of-range store, and
-the images must equal those of the normal build."""
+(GSC_LIBRARY) and renders the tiny scene, 14 frames of the city path in the
+headline form and a batched multi-model frame (13 images, cached BF16 exact
+stereo, per-tile and persistent blend); no frame may flag an out-of-range
+store, and the images must equal those of the normal build."""
 import os
 import subprocess
 import sys
@@ -34,6 +35,15 @@ r.set_tiling(16, 64, 0)
 for f in range(0, 40, 3):
     imgs, st = render(r, list(frames[f]))
     out[f"city{{f}}"] = np.stack(imgs); out[f"city{{f}}_err"] = st["error_flags"]
+r.close()
+from test_gpu_batched import batched_renderer, render_all
+models, viewers, frame_fn = gen.multiviewer_workload(scale=0.02, size_scale=0.25)
+images = frame_fn(40)
+r, _ = batched_renderer(models, images, stereo_unify="exact", precision="bf16", reuse="depth", tile=(16, 64))
+for bps in (0, 4):  # one block per tile, then the persistent blend
+    r.set_tiling(16, 64, bps)
+    imgs, st = render_all(r, images)
+    out[f"batched{{bps}}"] = np.concatenate([i.ravel() for i in imgs]); out[f"batched{{bps}}_err"] = st["error_flags"]
 r.close()
 np.savez({path!r}, **out)
 """
