@@ -1043,14 +1043,17 @@ def per_frame_tile_bits(W, H, tiling):
 
 
 def launches_per_frame_of(form, tile_bits):
-    """Library kernels per stereo frame of one model: frame setup, cull, plan,
-    [cache probe, scan, assign], tables, derivation, projection, depth sort
-    (4 passes), scan, key generation, tile sort (one pass per 8 tile-key
-    bits), ranges, blend."""
+    """Library kernels per stereo frame of one model: frame setup, the cull's
+    two passes (the second also runs the depth-rule cache probe), plan,
+    [cache scan, assign; a learned probe as its own kernel], tables,
+    derivation, projection, depth sort (4 passes), scan, key generation,
+    tile sort (one pass per 8 tile-key bits), ranges, blend."""
     f = FORMS[form]
-    n = 1 + 1 + 1 + 1 + 1 + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
+    n = 1 + 2 + 1 + 1 + 1 + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
     if f["reuse"] != "off":
-        n += 3
+        n += 2
+    if f["reuse"] == "learned":
+        n += 1
     return n
 
 

@@ -137,6 +137,10 @@ struct gsc_ctx {
   void* d_hbuf[2][MAXV] = {};
   size_t d_hbuf_bytes[2][MAXV] = {};
   cudaStream_t copy_stream = nullptr;
+  // second branch of the frame graph: the plan and the frame tables run
+  // beside the cache's scan and assignment (ev_fork / ev_join)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_rendered[2] = {}, ev_copied[2] = {};
   int hslot = 0;
   bool hpending[2] = {false, false};
@@ -380,28 +384,50 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   NvtxRange frame_range("gsc.frame");
   if (tm) cudaEventRecord(ctx->ev_stage[0], s);
   nvtxRangePushA("gsc.cull_cache");
-  launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, s);
-  cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ctx->total_tiles, s);
+  launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, ctx->ranges,
+                     ctx->total_tiles, s);
+  CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
+  const bool learned = ctx->cfg.reuse == GSC_REUSE_LEARNED;
+  // The cull's write pass probes the caches by the depth rule as it writes
+  // the ids (with a model without anchors, whose cull launches nothing, the
+  // probe kernel runs instead)
+  bool fuse = !ctx->models_used.empty();
+  for (int m : ctx->models_used) fuse = fuse && ctx->models[m].dev.n > 0;
+  const bool probed = fuse && caches && !replay && !learned;
+  CullProbe probe{probed ? caches : nullptr};
   for (int m : ctx->models_used)
     launch_cull(ctx->d_models, &ctx->models[m].dev, m, fd, ctx->d_vis_tab, ctx->d_eye_tab, ctx->cull_masks,
-                ctx->cull_cnt, ctx->cull_mask_stride, ctx->cull_cnt_stride, s);
-  launch_plan(fd, ctx->rec_cap, s);
-  CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
+                ctx->cull_cnt, ctx->cull_mask_stride, ctx->cull_cnt_stride, probe, s);
   const bool collect = caches && (ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && !replay;
   const bool tc = ctx->cfg.precision != GSC_PREC_FP32, fp8 = ctx->cfg.precision == GSC_PREC_FP8;
-  if (collect)  // fresh attributes of every visible anchor, for the labels
-    for (int m : ctx->models_used)
-      if (tc)
-        launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
-                         fp8, ctx->n_sm, s);
-      else
-        launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
-                          ctx->n_sm, s);
-  if (caches && !replay)
+  if (probed && !collect) {
+    // the cache decisions are taken: the plan and the frame tables (one warp
+    // each) run on a second branch beside the scan and assignment of the
+    // free lines, which they do not read (the plan adds to n_derived, the
+    // assignment subtracts the hits from it)
+    cudaEventRecord(ctx->ev_fork, s);
+    cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
+    launch_plan(fd, ctx->rec_cap, ctx->aux_stream);
+    launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), ctx->aux_stream);
+    cudaEventRecord(ctx->ev_join, ctx->aux_stream);
     launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
-                       ctx->cfg.reuse == GSC_REUSE_LEARNED, collect ? ctx->attrs_fresh : nullptr, ctx->st_scan,
-                       ctx->n_sm, s);
-  launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
+                       learned, nullptr, ctx->st_scan, ctx->n_sm, s, probed);
+    cudaStreamWaitEvent(s, ctx->ev_join, 0);
+  } else {
+    launch_plan(fd, ctx->rec_cap, s);
+    if (collect)  // fresh attributes of every visible anchor, for the labels
+      for (int m : ctx->models_used)
+        if (tc)
+          launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
+                           fp8, ctx->n_sm, s);
+        else
+          launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs_fresh, nullptr, nullptr, nullptr,
+                            ctx->n_sm, s);
+    if (caches && !replay)
+      launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
+                         learned, collect ? ctx->attrs_fresh : nullptr, ctx->st_scan, ctx->n_sm, s, probed);
+    launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), s);
+  }
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   nvtxRangePop();
   nvtxRangePushA("gsc.derive_project");
@@ -822,7 +848,11 @@ int gsc_create(gsc_ctx** out, const gsc_config* cfg_in, void* cuda_stream) {
       cudaMalloc((void**)&ctx->d_ptab, proj_tab_bytes()) != cudaSuccess)
     return bail(GSC_ERR_OOM);
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(GSC_ERR_CUDA);
+  if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(GSC_ERR_CUDA);
   for (int i = 0; i < 2; ++i)
     if (cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming) != cudaSuccess ||
@@ -879,6 +909,9 @@ void gsc_destroy(gsc_ctx* ctx) {
   for (int i = 0; i < 9; ++i)
     if (ctx->ev_stage[i]) cudaEventDestroy(ctx->ev_stage[i]);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
   if (ctx->copy_stream) {

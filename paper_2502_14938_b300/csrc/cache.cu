@@ -64,23 +64,22 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
   const ModelDev& md = models[cam.model];
   for (uint32_t vi = blockIdx.x * blockDim.x + threadIdx.x; vi < V; vi += stride) {
     const uint32_t a = ids[vi];
+    if (!LEARNED) {
+      cache_probe_depth(cd, a, vi, t, depth, D, hw, V, const_cast<uint32_t*>(&fd->err));
+      continue;
+    }
     const uint32_t s = cd.slot_of[a];
     bool valid = s < cd.S && cd.slot_anchor[s] == a;
     const uint32_t age = valid ? t - cd.slot_frame[s] : 0xFFFFFFFFu;
     valid = valid && age <= D;
-    bool hit;
-    if (LEARNED) {
-      hit = false;
-      if (valid) {
-        float dn[3], z[RZ];
-        const float dist = anchor_dir(md, cam, a, dn);
-        const float4 dl4 = cd.slot_dir[s];
-        const float dl[3] = {dl4.x, dl4.y, dl4.z};
-        reuse_features(reinterpret_cast<const float*>(md.feat + (size_t)a * (FDIM / 4)), dn, dl, dist, z);
-        hit = reuse_logit(s_w, z) >= 0.f;
-      }
-    } else {
-      hit = valid && age <= depth;
+    bool hit = false;
+    if (valid) {
+      float dn[3], z[RZ];
+      const float dist = anchor_dir(md, cam, a, dn);
+      const float4 dl4 = cd.slot_dir[s];
+      const float dl[3] = {dl4.x, dl4.y, dl4.z};
+      reuse_features(reinterpret_cast<const float*>(md.feat + (size_t)a * (FDIM / 4)), dn, dl, dist, z);
+      hit = reuse_logit(s_w, z) >= 0.f;
     }
     cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
     cd.flags[hw + vi] = valid ? 0u : 1u;
@@ -89,8 +88,7 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
       if (GSC_IN_BOUNDS(mi, V, const_cast<uint32_t*>(&fd->err))) cd.miss[mi] = vi;
     }
   }
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < hw; s += stride)
-    cd.flags[s] = (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < hw; s += stride) cd.flags[s] = cache_line_free(cd, s, t, D);
   if (blockIdx.x == 0 && threadIdx.x == 0) cd.state[CS_SCAN_N] = hw + V;
 }
 
@@ -216,13 +214,13 @@ __global__ void k_cache_replay_counts(CacheDev* caches, int n, FrameDev* fd) {
 // caches: device array; host: its host-side mirror (same device pointers).
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
-                        unsigned long long* scan_status, int n_sm, cudaStream_t s) {
+                        unsigned long long* scan_status, int n_sm, cudaStream_t s, bool probed) {
   for (int c = 0; c < n_caches; ++c) {
     if (!host[c].active) continue;
     const CacheDev& h = host[c];
     if (learned)
       k_cache_probe<true><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
-    else
+    else if (!probed)
       k_cache_probe<false><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
     if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
     launch_scan_u32(h.flags, nullptr, h.state + CS_SCAN_N, h.ranks, h.state + CS_SCAN_TOT, scan_status, fd,

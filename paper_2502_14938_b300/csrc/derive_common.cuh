@@ -108,6 +108,61 @@ __device__ __forceinline__ void load_dview_set(DViewSet& S, const DViewSet* __re
   __syncthreads();
 }
 
+// The frame's tables, by one warp (lane = its lane) once the visible sets,
+// the plan and the cache decisions are final: lane d fills derivation view
+// d's entries of the projection table and of its model's decoder view set
+// (at its rank among the model's views); lane m closes model m's set.
+__device__ __forceinline__ void frame_tables_warp(const FrameDev* __restrict__ fd, const CacheDev* __restrict__ caches,
+                                                  uint8_t* const* __restrict__ eyes, DViewSet* __restrict__ tabs,
+                                                  ProjTab* __restrict__ ptab, int n_models, int lane) {
+  const int nd = (int)fd->n_dviews;
+  auto work = [&](int d) -> uint32_t {
+    const bool cached = caches && d < MAX_CACHES && caches[d].active;
+    return cached ? caches[d].state[CS_MISSES] : fd->vis_count[d];
+  };
+  if (lane < nd) {
+    const int d = lane, m = fd->dcam[d].model;
+    const bool cached = caches && d < MAX_CACHES && caches[d].active;
+    const uint32_t ib = fd->item_base[d];
+    ptab->ibase[d] = ib;
+    ptab->model[d] = m;
+    ptab->vstat[d] = cached ? caches[d].vstat : nullptr;
+    ptab->lattr[d] = cached ? caches[d].slot_attr : nullptr;
+    ptab->eyes[d] = fd->dview_exact[d] ? eyes[d] : nullptr;
+    int r = 0;
+    uint32_t acc = 0;
+    for (int e = 0; e < d; ++e)
+      if (fd->dcam[e].model == m) {
+        ++r;
+        acc += work(e);
+      }
+    DViewSet& S = tabs[m];
+    S.d[r] = d;
+    S.base[r] = acc;
+    S.gbase[r] = ib;
+    S.miss[r] = cached ? caches[d].miss : nullptr;
+    S.vstat[r] = cached ? caches[d].vstat : nullptr;
+    S.lattr[r] = cached ? caches[d].slot_attr : nullptr;
+    for (int u = 0; u < 3; ++u) {
+      S.pc[r][u] = fd->dcam[d].pc[u];
+      S.pc[r][3 + u] = fd->dcam[d].pc_lo[u];
+    }
+    for (int e = 0; e < 2; ++e) fill_projcam(ptab->cam[d][e], fd, fd->dview_cam[d][e]);
+  }
+  if (lane == 0) ptab->ibase[nd] = fd->n_items;
+  if (lane < n_models) {
+    int c = 0;
+    uint32_t tot = 0;
+    for (int d = 0; d < nd; ++d)
+      if (fd->dcam[d].model == lane) {
+        ++c;
+        tot += work(d);
+      }
+    tabs[lane].nd = c;
+    tabs[lane].base[c] = tot;
+  }
+}
+
 // EWA projection of one Gaussian + opacity-aware exact tile count.
 // Decisions use the pinned depth: mu32 = x_a + o (float32 adds) and
 // tz = ((R6 mu_x + R7 mu_y) + R8 mu_z) + t2 without contraction (the order

@@ -1,20 +1,23 @@
 // Frame setup, anchor filtering (K1) and the per-frame plan.
-#include "gsc_internal.cuh"
+#include "derive_common.cuh"
 
 namespace gsc {
 
 // ------------------------------------------------------------------ frame setup
 // The cameras' constants and the derivation views (with the unified camera
 // of each stereo pair, Eq. 5-6) are prepared in float64 by the library's host
-// code, which has fast float64; this block copies them into the frame plan
+// code, which has fast float64; block 0 copies them into the frame plan
 // (word by word across its threads), resets the per-frame counters and
 // histograms and advances each cache's frame counter (thread c < n_caches,
-// Alg. 1 tick).
+// Alg. 1 tick); every block clears its share of the tile ranges.
 constexpr int FB_NT = 256;
 static_assert(sizeof(CamDev) % 4 == 0, "cameras are copied as words");
 
 __global__ void __launch_bounds__(FB_NT) k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin,
-                                                       CacheDev* __restrict__ caches, int n_caches) {
+                                                       CacheDev* __restrict__ caches, int n_caches,
+                                                       uint2* __restrict__ ranges, uint32_t n_tiles) {
+  // every block: its share of the tile ranges, cleared (tiles without pairs keep [0, 0))
+  for (uint32_t i = blockIdx.x * FB_NT + threadIdx.x; i < n_tiles; i += gridDim.x * FB_NT) ranges[i] = make_uint2(0, 0);
   if (blockIdx.x != 0) return;
   const FrameIn& F = *fin;
   const uint32_t t = threadIdx.x;
@@ -72,8 +75,10 @@ __global__ void __launch_bounds__(FB_NT) k_frame_begin(FrameDev* fd, const Frame
   }
 }
 
-void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s) {
-  k_frame_begin<<<1, FB_NT, 0, s>>>(fd, fin, caches, n_caches);
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, uint2* ranges,
+                        uint32_t n_tiles, cudaStream_t s) {
+  const uint32_t blocks = n_tiles > 4u * FB_NT ? (n_tiles + 4u * FB_NT - 1) / (4u * FB_NT) : 1u;
+  k_frame_begin<<<blocks, FB_NT, 0, s>>>(fd, fin, caches, n_caches, ranges, n_tiles);
 }
 
 // New epoch for standalone uses of the look-back kernels (debug sort / scan).
@@ -101,6 +106,32 @@ __global__ void k_wait_probe(FrameDev* fd, unsigned long long* words) {
 
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s) {
   k_wait_probe<<<1, 32, 0, s>>>(fd, words);
+}
+
+// ------------------------------------------------------------------ plan
+// Item and record bases of the frame's views and cameras (one thread).
+__device__ __forceinline__ void plan_thread(FrameDev* fd, uint32_t rec_cap) {
+  uint32_t acc = 0;
+  for (uint32_t d = 0; d < fd->n_dviews; ++d) {
+    fd->item_base[d] = acc;
+    acc += fd->vis_count[d];
+  }
+  fd->item_base[fd->n_dviews] = acc;
+  fd->n_items = acc;
+  atomicAdd(&fd->n_derived, acc);  // (from 0) lowered by the cache policy when views reuse, in either order
+  unsigned long long r = 0;
+  for (uint32_t c = 0; c < fd->n_cams; ++c) {
+    fd->rec_base[c] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+    r += (unsigned long long)K * fd->vis_count[fd->dview_of_cam[c]];
+  }
+  fd->rec_base[fd->n_cams] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+  fd->n_records_need = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
+  if (r > rec_cap) {
+    atomicOr(&fd->err, ERR_REC_OVERFLOW);
+    fd->n_records = rec_cap;
+  } else {
+    fd->n_records = (uint32_t)r;
+  }
 }
 
 // ------------------------------------------------------------------ culling (K1)
@@ -311,7 +342,7 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __res
                                                         uint8_t* const* __restrict__ eyes,
                                                         const uint32_t* __restrict__ masks,
                                                         const uint32_t* __restrict__ tile_cnt, uint32_t mask_stride,
-                                                        uint32_t cnt_stride) {
+                                                        uint32_t cnt_stride, CullProbe probe_cfg) {
   __shared__ int s_d[CULL_MAXD];
   __shared__ int s_exact[CULL_MAXD];
   __shared__ int s_nd;
@@ -335,6 +366,18 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __res
   const uint32_t ntiles = (md.n + CULL_TILE - 1) / CULL_TILE;
   const uint32_t a0 = t * CULL_TILE + threadIdx.x * CULL_IPT;
   for (int ld = 0; ld < nd; ++ld) {
+    const int d = s_d[ld];
+    // the view's cache, probed by the depth rule as each id is written
+    const bool probe = probe_cfg.caches && d < MAX_CACHES && probe_cfg.caches[d].active;
+    CacheDev cd{};
+    uint32_t ct = 0, cdepth = 0, cD = 0, chw = 0;
+    if (probe) {
+      cd = probe_cfg.caches[d];
+      ct = cd.state[CS_T];
+      cdepth = cd.state[CS_DEPTH];
+      cD = cd.state[CS_DMAX];
+      chw = cd.state[CS_HW];
+    }
     // prefix of the tiles before this one: a block-wide sum of their counts
     const uint32_t* tc = tile_cnt + (size_t)ld * cnt_stride;
     uint32_t p = 0;
@@ -347,7 +390,6 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __res
     uint32_t pre = 0;
 #pragma unroll
     for (int w = 0; w < CULL_NT / 32; ++w) pre += s_red[w];
-    const int d = s_d[ld];
     uint32_t* out = vis[d];
     uint8_t* eo = s_exact[ld] ? eyes[d] : nullptr;
     uint32_t o = pre + ex;
@@ -356,55 +398,42 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __res
       const int i = __ffs(mm) - 1;
       mm &= mm - 1;
       if (GSC_IN_BOUNDS(o, fd->cap_vis, &fd->err)) {
+        const uint32_t a = a0 + (uint32_t)i;
         if (eo) eo[o] = (uint8_t)(((m >> (8 + i)) & 1u) | (((m >> (16 + i)) & 1u) << 1));
-        out[o] = a0 + (uint32_t)i;
+        out[o] = a;
+        if (probe) cache_probe_depth(cd, a, o, ct, cdepth, cD, chw, fd->cap_vis, &fd->err);
       }
       ++o;
     }
-    if (t == ntiles - 1 && threadIdx.x == 0) fd->vis_count[d] = pre + tot;
+    if (probe)  // free flags of the lines below the high-water mark, spread over the blocks
+      for (uint32_t l = t * CULL_NT + threadIdx.x; l < chw; l += gridDim.x * CULL_NT) cd.flags[l] = cache_line_free(cd, l, ct, cD);
+    if (t == ntiles - 1 && threadIdx.x == 0) {
+      fd->vis_count[d] = pre + tot;
+      if (probe) cd.state[CS_SCAN_N] = chw + pre + tot;
+    }
     __syncthreads();  // s_red is reused by the next view
   }
 }
 
-void launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
+bool launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
                  uint8_t* const* eyes_dev, uint32_t* masks, uint32_t* tile_cnt, uint32_t mask_stride,
-                 uint32_t cnt_stride, cudaStream_t s) {
+                 uint32_t cnt_stride, CullProbe probe, cudaStream_t s) {
   const uint32_t ntiles = (h_model->n + CULL_TILE - 1) / CULL_TILE;
-  if (ntiles == 0) return;
+  if (ntiles == 0) return false;
   if (h_model->lod_r)
     k_cull_count<true><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
   else
     k_cull_count<false><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
-  k_cull_write<<<ntiles, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, masks, tile_cnt, mask_stride, cnt_stride);
+  k_cull_write<<<ntiles, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, masks, tile_cnt, mask_stride, cnt_stride,
+                                          probe);
+  return true;
 }
 
 uint32_t cull_tiles(uint32_t n_anchors) { return (n_anchors + CULL_TILE - 1) / CULL_TILE; }
 uint32_t cull_mask_words(uint32_t n_anchors) { return cull_tiles(n_anchors) * CULL_NT; }
 
-// ------------------------------------------------------------------ plan
 __global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint32_t acc = 0;
-  for (uint32_t d = 0; d < fd->n_dviews; ++d) {
-    fd->item_base[d] = acc;
-    acc += fd->vis_count[d];
-  }
-  fd->item_base[fd->n_dviews] = acc;
-  fd->n_items = acc;
-  fd->n_derived = acc;  // lowered by the cache policy when views reuse
-  unsigned long long r = 0;
-  for (uint32_t c = 0; c < fd->n_cams; ++c) {
-    fd->rec_base[c] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
-    r += (unsigned long long)K * fd->vis_count[fd->dview_of_cam[c]];
-  }
-  fd->rec_base[fd->n_cams] = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
-  fd->n_records_need = (uint32_t)(r < 0xFFFFFFFFull ? r : 0xFFFFFFFFull);
-  if (r > rec_cap) {
-    atomicOr(&fd->err, ERR_REC_OVERFLOW);
-    fd->n_records = rec_cap;
-  } else {
-    fd->n_records = (uint32_t)r;
-  }
+  if (threadIdx.x == 0 && blockIdx.x == 0) plan_thread(fd, rec_cap);
 }
 
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s) { k_plan<<<1, 32, 0, s>>>(fd, rec_cap); }

@@ -186,6 +186,32 @@ struct CacheDev {
   uint32_t active;
 };
 
+// Depth-rule probe of visible anchor vi (anchor a) of a view's cache (Alg. 1,
+// Eq. 4's reuse depth): hit = a valid line decoded at most `depth` frames
+// ago; lines older than D are invalid.  Writes the line status and the
+// anchor's new flag (at hw + vi) and appends a miss to the decoder's list
+// (bounded by miss_cap).  Used by the cache probe kernel and by the cull's
+// write pass, which probes each id as it writes it.
+__device__ __forceinline__ void cache_probe_depth(const CacheDev& cd, uint32_t a, uint32_t vi, uint32_t t,
+                                                  uint32_t depth, uint32_t D, uint32_t hw, uint32_t miss_cap,
+                                                  uint32_t* err) {
+  const uint32_t s = cd.slot_of[a];
+  bool valid = s < cd.S && cd.slot_anchor[s] == a;
+  const uint32_t age = valid ? t - cd.slot_frame[s] : 0xFFFFFFFFu;
+  valid = valid && age <= D;
+  const bool hit = valid && age <= depth;
+  cd.vstat[vi] = hit ? (s | LINE_HIT) : (valid ? s : LINE_NONE);
+  cd.flags[hw + vi] = valid ? 0u : 1u;
+  if (!hit) {
+    const uint32_t mi = atomicAdd(&cd.state[CS_MISSES], 1u);
+    if (GSC_IN_BOUNDS(mi, miss_cap, err)) cd.miss[mi] = vi;
+  }
+}
+// Free flag of line s (unused, or past D_max) for the scan of free lines.
+__device__ __forceinline__ uint32_t cache_line_free(const CacheDev& cd, uint32_t s, uint32_t t, uint32_t D) {
+  return (cd.slot_anchor[s] == 0xFFFFFFFFu || t - cd.slot_frame[s] > D) ? 1u : 0u;
+}
+
 struct Records {
   float4* geo;    // mean x, mean y, A, B
   float4* cop;    // C, opacity, tau_cov, depth
@@ -425,7 +451,9 @@ enum : int { SLOT_CULL = 0, SLOT_SCAN = 8, SLOT_SORT1 = 12, SLOT_SORT2 = 20, SLO
              SLOT_CACHE = 32 };
 constexpr int MAX_CACHES = 16;  // two scan slots each in [SLOT_CACHE, 64)
 
-void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, cudaStream_t s);
+// Frame setup; also clears ranges[0 .. n_tiles).
+void launch_frame_begin(FrameDev* fd, const FrameIn* fin, CacheDev* caches, int n_caches, uint2* ranges,
+                        uint32_t n_tiles, cudaStream_t s);
 void launch_bump_epoch(FrameDev* fd, uint32_t spin_limit, cudaStream_t s);
 void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
 // Anchor filtering of one model in two passes (keep masks and per-tile
@@ -435,9 +463,16 @@ void launch_wait_probe(FrameDev* fd, unsigned long long* words, cudaStream_t s);
 // [views][cnt_stride] are the passes' working arrays (cull_mask_words /
 // cull_tiles of the model's anchors per view).  h_model: the model's device
 // description as the host holds it.
-void launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
+// probe.caches (the frame's caches, device array, or null): the write pass
+// runs the depth-rule probe of the model's views' caches as it writes each
+// id, and the free flags of their lines (the probe kernel is then left out).
+// Returns false (nothing launched) for a model without anchors.
+struct CullProbe {
+  CacheDev* caches;
+};
+bool launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDev* fd, uint32_t* const* vis_dev,
                  uint8_t* const* eyes_dev, uint32_t* masks, uint32_t* tile_cnt, uint32_t mask_stride,
-                 uint32_t cnt_stride, cudaStream_t s);
+                 uint32_t cnt_stride, CullProbe probe, cudaStream_t s);
 uint32_t cull_tiles(uint32_t n_anchors);
 uint32_t cull_mask_words(uint32_t n_anchors);
 void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s);
@@ -508,7 +543,7 @@ void launch_reuse_batch(const ReuseTrain& T, uint32_t n_total, uint32_t b0, uint
 void launch_reuse_epoch_end(const ReuseTrain& T, cudaStream_t s);
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
-                        unsigned long long* scan_status, int n_sm, cudaStream_t s);
+                        unsigned long long* scan_status, int n_sm, cudaStream_t s, bool probed = false);
 void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s);
 // hist: digit histograms already accumulated by the key producer (the
 // histogram kernel is skipped; with drop_invalid, *n_valid_out must hold the
