@@ -10,7 +10,10 @@
 //            (valid line, older than depth) or new (no valid line; lines past
 //            D_max are invalid); misses go to a work list for the decoder;
 //            per line below the high-water mark hw: free iff unused or past
-//            D_max
+//            D_max.  The depth rule runs inside the cull's write pass
+//            (cache_probe_depth, as each id is written); k_cache_probe runs
+//            the learned rule, and the depth rule when a model of the frame
+//            has no anchors (its cull launches nothing)
 //   scan     one scan over [free flags of lines 0 .. hw-1 | new flags of the
 //            visible anchors]: ranks of those free lines (and their list, in
 //            ascending order) and of new anchors (ascending)

@@ -541,6 +541,8 @@ int reuse_blocks(uint32_t nb);
 void launch_reuse_batch(const ReuseTrain& T, uint32_t n_total, uint32_t b0, uint32_t nb, float lr, float loss_scale,
                         cudaStream_t s);
 void launch_reuse_epoch_end(const ReuseTrain& T, cudaStream_t s);
+// The cache kernels of a frame: probe (unless probed: the cull's write pass
+// ran the depth-rule probe), collection labels, free-line scan, assignment.
 void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, FrameDev* fd, uint32_t* const* vis,
                         const ModelDev* models, const float* reuse_w, bool learned, const float4* attrs_fresh,
                         unsigned long long* scan_status, int n_sm, cudaStream_t s, bool probed = false);
