@@ -122,7 +122,7 @@ class CacheSim:
             self.slot_dir[line[dec]] = np.asarray(d_now, np.float32)[dec]
         used = self.depth
         self.last = dict(visible=len(ids), misses=int((~hit).sum()), hits=int(hit.sum()),
-                         new=len(new_idx), cached_new=n)
+                         new=len(new_idx), cached_new=n, free=len(free))
         self.depth = next_depth(self.depth, len(ids), int((~hit).sum()), self.D, self.guide)
         return hit, line, used
 

@@ -64,6 +64,9 @@ def test_cached_tiny_path_matches_oracle_simulation(pair_capacity):
         assert np.array_equal(ghit, hit), f
         assert np.array_equal(gline, line), f
         assert cst["depth"] == sim.depth, f
+        # the frame's counts: misses, new anchors, free lines (lines at or above the
+        # high-water mark count as free without being scanned)
+        assert (cst["misses"], cst["new"], cst["free"]) == (sim.last["misses"], sim.last["new"], sim.last["free"]), f
         assert st["derived_anchors"] == int((~hit).sum())
         vr = project_view(m, cam, ids, attrs, kept)
         ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height)
