@@ -90,6 +90,7 @@ struct gsc_ctx {
   uint32_t rec_cap = 0;
   Records rec{};
   uint32_t *s1k0 = nullptr, *s1v0 = nullptr, *s1k1 = nullptr, *s1v1 = nullptr, *offs = nullptr, *big = nullptr;
+  uint32_t *s1k2 = nullptr, *s1v2 = nullptr;  // the depth sort's result
   float4* attrs = nullptr;  // derived attributes, 3 float4 per Gaussian in frame item order
   float* unfused = nullptr;  // GSC_FLAG_UNFUSED: the operators' intermediate tensors
   size_t unfused_items = 0;
@@ -213,7 +214,7 @@ uint32_t models_max_n(const gsc_ctx* ctx) {
 }
 
 int ensure_status(gsc_ctx* ctx) {
-  // sort tiles hold 2048 or 4096 keys (256 digit words each); scan tiles
+  // sort tiles hold 2048 or 4096 keys (256 or 512 digit words each); scan tiles
   // 1024 elements (the pair offsets run over records, a cache's scan over
   // its lines and the visible anchors, the standalone scan over up to the
   // pair capacity)
@@ -222,9 +223,9 @@ int ensure_status(gsc_ctx* ctx) {
   const uint32_t need_scan = std::max({(ctx->rec_cap + 1023u) / 1024u, (ctx->pair_cap + 1023u) / 1024u,
                                        (ctx->vis_cap + lines + 1023u) / 1024u}) + 1u;
   if (need > ctx->status_tiles) {
-    int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 256);
+    int r = dalloc(ctx, &ctx->sb.status, (size_t)need * 512);  // up to 512 digit words per tile
     if (r) return r;
-    CK(cudaMemset(ctx->sb.status, 0, (size_t)need * 256 * sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->sb.status, 0, (size_t)need * 512 * sizeof(unsigned long long)));
     ctx->status_tiles = need;
   }
   if (need_scan > ctx->scan_tiles) {
@@ -256,7 +257,8 @@ int alloc_records(gsc_ctx* ctx, uint32_t cap) {
       (r = dalloc(ctx, &ctx->rec.key, cap)) ||
       (r = dalloc(ctx, &ctx->rec.cnt, cap)) || (r = dalloc(ctx, &ctx->s1k0, cap)) ||
       (r = dalloc(ctx, &ctx->s1v0, cap)) || (r = dalloc(ctx, &ctx->s1k1, cap)) ||
-      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)) ||
+      (r = dalloc(ctx, &ctx->s1v1, cap)) || (r = dalloc(ctx, &ctx->s1k2, cap)) || (r = dalloc(ctx, &ctx->s1v2, cap)) ||
+      (r = dalloc(ctx, &ctx->offs, cap)) || (r = dalloc(ctx, &ctx->big, cap)) ||
       (r = dalloc(ctx, &ctx->attrs, (size_t)cap * 3)))
     return r;
   if ((ctx->cfg.flags & GSC_FLAG_REUSE_COLLECT) && (r = dalloc(ctx, &ctx->attrs_fresh, (size_t)cap * 3))) return r;
@@ -446,10 +448,10 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
   nvtxRangePop();
   nvtxRangePushA("gsc.sort_keygen");
-  uint32_t *ok = nullptr, *ov = nullptr;
-  launch_sort_impl(ctx->rec.key, nullptr, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, &fd->n_records, &fd->n_valid,
-                   32, 1, SLOT_SORT1, fd, ctx->sb, ctx->n_sm, s, &ok, &ov, 8, fd->hist_depth);
-  ctx->order_out = ov;
+  launch_depth_sort(ctx->rec.key, ctx->s1k0, ctx->s1v0, ctx->s1k1, ctx->s1v1, ctx->s1k2, ctx->s1v2, &fd->n_records,
+                    &fd->n_valid, SLOT_SORT1, fd, ctx->sb, fd->hist_depth, ctx->n_sm, s);
+  const uint32_t* ov = ctx->s1v2;
+  ctx->order_out = ctx->s1v2;
   if (tm) cudaEventRecord(ctx->ev_stage[3], s);
   launch_scan_u32(ctx->rec.cnt, ov, &fd->n_valid, ctx->offs, &fd->n_pairs, ctx->st_scan, fd, SLOT_SCAN, ctx->n_sm, s,
                   nullptr, 0, ctx->big, &fd->n_big, KG_SMALL);
@@ -602,6 +604,11 @@ void prepare_frame_cameras(const gsc_ctx* ctx, FrameIn& F) {
   uint32_t bits = 1;
   while ((1u << bits) < tb && bits < 31) ++bits;
   F.tile_bits = bits;
+  // the depth sort's base: bits of the smallest near plane (positive floats
+  // order as their bits, and every valid depth exceeds its camera's plane)
+  float zmin = nc ? F.cam[0].znear : 1.f;
+  for (uint32_t c = 1; c < nc; ++c) zmin = std::min(zmin, F.cam[c].znear);
+  std::memcpy(&F.depth_base, &zmin, 4);
   uint32_t nd = 0;
   for (uint32_t c = 0; c < nc; ++c) F.dview_of_cam[c] = -1;
   for (uint32_t c = 0; c < nc; ++c) {
@@ -893,7 +900,7 @@ void gsc_destroy(gsc_ctx* ctx) {
   }
   void* bufs[] = {ctx->d_models, ctx->d_vis_buf, ctx->d_vis_tab, ctx->d_eye_buf, ctx->d_eye_tab, ctx->d_dbg_buf, ctx->d_dbg_tab, ctx->rec.geo,
                   ctx->rec.cop, ctx->rec.col, ctx->rec.aux, ctx->rec.key, ctx->rec.cnt, ctx->s1k0, ctx->s1v0, ctx->s1k1,
-                  ctx->s1v1, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
+                  ctx->s1v1, ctx->s1k2, ctx->s1v2, ctx->offs, ctx->big, ctx->pk0, ctx->pv0, ctx->pk1, ctx->pv1, ctx->ranges, ctx->sb.hist,
                   ctx->sb.status, ctx->cull_masks, ctx->cull_cnt, ctx->st_scan, ctx->d_fin, ctx->d_fd, ctx->attrs,
                   ctx->attrs_fresh, ctx->rw_theta, ctx->rw_w, ctx->d_tabs, ctx->d_ptab, ctx->unfused};
   for (void* p : bufs) dfree(p);

@@ -58,13 +58,15 @@ __global__ void __launch_bounds__(FB_NT) k_frame_begin(FrameDev* fd, const Frame
     fd->err = 0;
     fd->blend_work[0] = 0;
     fd->blend_work[1] = 0;
+    fd->depth_base = F.depth_base;
+    fd->depth_wide = 0;
   }
   if (t < 64) fd->ctr[t] = 0;
   {  // the two sorts' digit histograms (filled by the key producers)
     uint4* h = reinterpret_cast<uint4*>(fd->hist_depth);
     uint4* h2 = reinterpret_cast<uint4*>(fd->hist_tile);
-    static_assert(FB_NT == 256, "one uint4 of each histogram per thread");
-    h[t] = make_uint4(0, 0, 0, 0);
+    static_assert(FB_NT == 256 && DEPTH_HIST_WORDS % 4 == 0, "uint4 stores");
+    for (uint32_t i = t; i < DEPTH_HIST_WORDS / 4; i += FB_NT) h[i] = make_uint4(0, 0, 0, 0);
     h2[t] = make_uint4(0, 0, 0, 0);
   }
   if ((int)t < n_caches && caches[t].active) {

@@ -85,7 +85,8 @@ struct FrameIn {  // host -> device per frame
   uint32_t cap_vis;                  // capacities of the frame's buffers (the bounds-checked build's
   uint32_t cap_rec;                  // limits): visible ids per view, records, pairs
   uint32_t cap_pairs;
-  uint32_t pad[3];
+  uint32_t depth_base;               // bits of the smallest near plane of the frame's cameras
+  uint32_t pad[2];
   float bg[4];
   unsigned long long out_rgb[MAXV];  // float* [H][W][3] per camera (device)
   unsigned long long out_T[MAXV];    // float* [H][W] per camera or 0
@@ -95,6 +96,8 @@ struct FrameIn {  // host -> device per frame
   int32_t dview_cam[MAXV][2];
   int32_t dview_exact[MAXV];         // 1: a stereo pair filtered by the union of its eyes' own filters
 };
+
+constexpr int DEPTH_HIST_WORDS = 3 * 512 + 256;
 
 struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t frame;               // frame counter, starts at 1 (epochs of look-back words)
@@ -124,11 +127,14 @@ struct FrameDev {  // device-resident per-frame plan and counters
   uint32_t n_derived;           // anchors decoded this frame (visible minus cache hits)
   uint32_t cache_depth;         // reuse depth of derivation view 0 for the next frame
   uint32_t ctr[64];             // dynamic tile counters of look-back kernels
-  // digit histograms (4 passes x 256) of the two sorts, accumulated by the
-  // kernels that produce their keys (projection: depth keys of valid
-  // records; key generation: tile keys of the written pairs)
-  alignas(16) uint32_t hist_depth[4 * 256];
+  // digit histograms of the two sorts, accumulated by the kernels that
+  // produce their keys: projection, the valid depth keys minus depth_base
+  // (3 x 512 for the 9-bit digits, then 256 for bits 24-31); key
+  // generation, the tile keys of the written pairs (4 x 256)
+  alignas(16) uint32_t hist_depth[DEPTH_HIST_WORDS];
   alignas(16) uint32_t hist_tile[4 * 256];
+  uint32_t depth_base;          // bits of the nearest near plane: every valid depth key is above it
+  uint32_t depth_wide;          // 1: some valid depth key - depth_base needs more than 27 bits
   uint32_t err_sticky;          // error bits of all frames since the host last read them
   uint32_t need_sticky[2];      // largest records / pairs those frames asked for
   // blend work of the frame, counted only by the counting blend variant:
@@ -550,6 +556,11 @@ void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cu
 // hist: digit histograms already accumulated by the key producer (the
 // histogram kernel is skipped; with drop_invalid, *n_valid_out must hold the
 // kept count too), or null.
+// The frame's record sort by depth (sort.cu): three 9-bit passes, and a
+// fourth on bits 24-31 when fd->depth_wide; the result in (k2, v2).
+void launch_depth_sort(const uint32_t* kin, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* k2,
+                       uint32_t* v2, const uint32_t* n_in, const uint32_t* n_valid, int slot_base, FrameDev* fd,
+                       SortBufs sb, const uint32_t* hist, int n_sm, cudaStream_t s);
 void launch_sort_impl(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                       uint32_t* v1, const uint32_t* n_in, uint32_t* n_valid_out, int bits, int drop_invalid,
                       int slot_base, FrameDev* fd, SortBufs sb, int n_sm, cudaStream_t s, uint32_t** kout,

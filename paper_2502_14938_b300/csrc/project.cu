@@ -38,12 +38,15 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
                                                    const CacheDev* __restrict__ caches, Records rec,
                                                    const ProjTab* __restrict__ ptab) {
   __shared__ ProjTab P;
-  __shared__ uint32_t s_h[4][256];  // digit histograms of this block's valid depth keys
-  __shared__ uint32_t s_nv;
+  __shared__ uint32_t s_h[DEPTH_HIST_WORDS];  // digit histograms of this block's valid depth keys
+  __shared__ uint32_t s_nv, s_wide, s_dbase;
   __shared__ uint8_t s_own[PJ_NT / 32][64];  // per warp: owning lane of each surviving record
   __shared__ float s_stage[PJ_NT / 32][PS_WORDS][32];  // per warp: the owners' record inputs
-  for (int i = threadIdx.x; i < 4 * 256; i += PJ_NT) (&s_h[0][0])[i] = 0;
-  if (threadIdx.x == 0) s_nv = 0;
+  for (int i = threadIdx.x; i < DEPTH_HIST_WORDS; i += PJ_NT) s_h[i] = 0;
+  if (threadIdx.x == 0) {
+    s_nv = s_wide = 0;
+    s_dbase = fd->depth_base;
+  }
   if (ptab) {
     stage_table(P, ptab);
   } else if (threadIdx.x == 0) {
@@ -185,20 +188,25 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
       const float ws[3] = {stage[PS_S][src], stage[PS_S + 1][src], stage[PS_S + 2][src]};
       const float wq[4] = {stage[PS_Q][src], stage[PS_Q + 1][src], stage[PS_Q + 2][src], stage[PS_Q + 3][src]};
       const uint32_t key = project_write(pc, rec, r, mu, rel, stage[PS_A + e][src], true, wcol, ws, wq, TW, TH);
-      if (key != INVALID_KEY) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 0xFFu], 1u);
+      if (key != INVALID_KEY) {  // the depth sort's digits of key - base: 3 x 9 bits, and bits 24-31
+        const uint32_t kb = key - s_dbase;
+        atomicAdd(&s_h[kb & 511u], 1u);
+        atomicAdd(&s_h[512 + ((kb >> 9) & 511u)], 1u);
+        atomicAdd(&s_h[1024 + ((kb >> 18) & 511u)], 1u);
+        atomicAdd(&s_h[1536 + (kb >> 24)], 1u);
+        if (kb >> 27) s_wide = 1u;
         atomicAdd(&s_nv, 1u);
       }
     }
     __syncwarp();  // owners and the staging rows are rewritten by the next round
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 4 * 256; i += PJ_NT) {
-    const uint32_t c = (&s_h[0][0])[i];
+  for (int i = threadIdx.x; i < DEPTH_HIST_WORDS; i += PJ_NT) {
+    const uint32_t c = s_h[i];
     if (c) atomicAdd(&fd->hist_depth[i], c);
   }
   if (threadIdx.x == 0 && s_nv) atomicAdd(&fd->n_valid, s_nv);
+  if (threadIdx.x == 0 && s_wide) atomicOr(&fd->depth_wide, 1u);
 }
 
 void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, const float4* attrs,

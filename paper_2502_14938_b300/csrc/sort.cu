@@ -1,5 +1,6 @@
-// LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits,
-// "onesweep" style: one kernel computes the digit histograms of every pass;
+// LSD radix sort of (uint32 key, uint32 value) pairs, 8- or 9-bit digits,
+// "onesweep" style: one kernel computes the digit histograms of every pass
+// (or the key producer accumulates them);
 // each pass is then one kernel in which a block ranks a tile of keys
 // (warp match + per-warp digit counters, stable), obtains its per-digit
 // global offsets by a decoupled look-back over the preceding tiles, and
@@ -48,28 +49,42 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ 
 
 // NT threads per block (NT / 32 warps each ranking 32 x IPT keys), tiles of
 // NT x IPT keys; the keys and values of a tile are staged in dynamic shared
-// memory.  Threads 0..255 own one digit each for the histograms, scans and
-// the look-back.
-template <int NT, int IPT>
-__global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+// memory.  Digits of DB bits (8: 256 digits, 9: 512); threads 0..2^DB - 1
+// own one digit each for the histograms, scans and the look-back (digit
+// status words at a stride of 2^DB per tile).  Optional, all read on the
+// device: key_sub (subtracted from every kept key as it is read), run_if
+// (the pass runs only if *run_if != 0) and use_alt (if *use_alt != 0 the
+// output goes to kout_alt / vout_alt).
+template <int NT, int IPT, int DB = 8>
+__global__ void __launch_bounds__(NT, 2) k_sort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                   const uint32_t* __restrict__ n_ptr, int shift,
                                                   const uint32_t* __restrict__ hist_p, int drop_invalid,
-                                                  unsigned long long* status, FrameDev* fd, int slot) {
-  constexpr int TILE = NT * IPT, WARPS = NT / 32;
-  static_assert(NT >= 256, "one thread per digit");
-  __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_whist[WARPS][256];
-  __shared__ uint32_t s_dstart[256];
-  __shared__ uint32_t s_gofs[256];
+                                                  unsigned long long* status, FrameDev* fd, int slot,
+                                                  const uint32_t* __restrict__ key_sub, const uint32_t* __restrict__ run_if,
+                                                  uint32_t* __restrict__ kout_alt, uint32_t* __restrict__ vout_alt,
+                                                  const uint32_t* __restrict__ use_alt) {
+  constexpr int TILE = NT * IPT, WARPS = NT / 32, NDIG = 1 << DB;
+  constexpr uint32_t DMASK = NDIG - 1;
+  static_assert(NT >= NDIG, "one thread per digit");
+  __shared__ uint32_t s_gbase[NDIG];
+  __shared__ uint32_t s_whist[WARPS][NDIG];
+  __shared__ uint32_t s_dstart[NDIG];
+  __shared__ uint32_t s_gofs[NDIG];
   __shared__ uint32_t s_warp[NT / 32 + 1];
   __shared__ uint32_t s_tile;
   extern __shared__ uint32_t s_kv[];  // keys [TILE], values [TILE]
   uint32_t* s_keys = s_kv;
   uint32_t* s_vals = s_kv + TILE;
 
+  if (run_if && *run_if == 0u) return;
+  if (use_alt && *use_alt != 0u) {
+    kout = kout_alt;
+    vout = vout_alt;
+  }
+  const uint32_t ksub = key_sub ? *key_sub : 0u;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const bool dig = tid < 256u;
+  const bool dig = tid < (uint32_t)NDIG;
   {
     uint32_t tot;
     const uint32_t g = block_exclusive_scan<NT>(dig ? hist_p[tid] : 0u, s_warp, &tot);
@@ -83,7 +98,7 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&fd->ctr[slot], 1u);
-    for (int i = tid; i < WARPS * 256; i += NT) (&s_whist[0][0])[i] = 0;
+    for (int i = tid; i < WARPS * NDIG; i += NT) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= ntiles) break;
@@ -95,9 +110,10 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
       bool valid = idx < n;
       uint32_t k = valid ? kin[idx] : INVALID_KEY;
       if (drop_invalid && k == INVALID_KEY) valid = false;
+      if (valid) k -= ksub;
       key[i] = valid ? k : INVALID_KEY;
       val[i] = valid ? (vin ? vin[idx] : idx) : 0u;
-      const uint32_t d = (k >> shift) & 0xFFu;
+      const uint32_t d = (k >> shift) & DMASK;
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x1000u);
       uint32_t pre = 0;
       if (valid) pre = s_whist[warp][d];
@@ -119,7 +135,7 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
       }
     }
     if (dig)  // publish this tile's counts before the block scan
-      st_relaxed_u64(status + (size_t)t * 256 + tid, lb_pack(epoch, t == 0 ? 2u : 1u, tot_d));
+      st_relaxed_u64(status + (size_t)t * NDIG + tid, lb_pack(epoch, t == 0 ? 2u : 1u, tot_d));
     uint32_t tile_total;
     {
       const uint32_t ds = block_exclusive_scan<NT>(tot_d, s_warp, &tile_total);
@@ -129,8 +145,8 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
       const uint32_t d = tid;
       uint32_t pre = 0;
       if (t > 0) {
-        pre = lb_exclusive(status + d, 256, t, epoch, spin, &fd->err);
-        st_relaxed_u64(status + (size_t)t * 256 + d, lb_pack(epoch, 2u, pre + tot_d));
+        pre = lb_exclusive(status + d, NDIG, t, epoch, spin, &fd->err);
+        st_relaxed_u64(status + (size_t)t * NDIG + d, lb_pack(epoch, 2u, pre + tot_d));
       }
       s_gofs[d] = s_gbase[d] + pre;
     }
@@ -138,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       if (rank[i] == 0xFFFFFFFFu) continue;
-      const uint32_t d = (key[i] >> shift) & 0xFFu;
+      const uint32_t d = (key[i] >> shift) & DMASK;
       const uint32_t p = s_dstart[d] + s_whist[warp][d] + rank[i];
       s_keys[p] = key[i];
       s_vals[p] = val[i];
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
     __syncthreads();
     for (uint32_t p = tid; p < tile_total; p += NT) {
       const uint32_t k = s_keys[p];
-      const uint32_t d = (k >> shift) & 0xFFu;
+      const uint32_t d = (k >> shift) & DMASK;
       const uint32_t o = s_gofs[d] + (p - s_dstart[d]);
       if (!GSC_IN_BOUNDS(o, n, &fd->err)) continue;
       kout[o] = k;
@@ -156,17 +172,48 @@ __global__ void __launch_bounds__(NT) k_sort_pass(const uint32_t* __restrict__ k
   }
 }
 
-template <int NT, int IPT>
+template <int NT, int IPT, int DB = 8>
 void sort_pass(int blocks, cudaStream_t s, const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                const uint32_t* n_ptr, int shift, const uint32_t* hist_p, int drop_invalid, unsigned long long* status,
-               FrameDev* fd, int slot) {
-  k_sort_pass<NT, IPT><<<blocks, NT, 2 * NT * IPT * sizeof(uint32_t), s>>>(kin, vin, kout, vout, n_ptr, shift, hist_p,
-                                                                           drop_invalid, status, fd, slot);
+               FrameDev* fd, int slot, const uint32_t* key_sub = nullptr, const uint32_t* run_if = nullptr,
+               uint32_t* kout_alt = nullptr, uint32_t* vout_alt = nullptr, const uint32_t* use_alt = nullptr) {
+  k_sort_pass<NT, IPT, DB><<<blocks, NT, 2 * NT * IPT * sizeof(uint32_t), s>>>(
+      kin, vin, kout, vout, n_ptr, shift, hist_p, drop_invalid, status, fd, slot, key_sub, run_if, kout_alt, vout_alt,
+      use_alt);
 }
 
 cudaError_t prepare_sort() {
-  return cudaFuncSetAttribute(k_sort_pass<512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * 512 * 8 * sizeof(uint32_t)));
+  const int kv8 = (int)(2 * 512 * 8 * sizeof(uint32_t)), kv4 = (int)(2 * 512 * 4 * sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(k_sort_pass<512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kv8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sort_pass<512, 8, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, kv8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sort_pass<512, 4, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, kv4);
+  return e;
+}
+
+// The record sort by depth (the frame's depth keys: float bits of the
+// ordering depth, INVALID_KEY for records that cover no tile).  Every valid
+// depth exceeds the nearest near plane, so key - bits(near) keeps the order
+// and, for depths below 2^16 x near (13 km at 0.2 m), fits in 27 bits:
+// three passes of 9-bit digits, the first over every record (dropping the
+// invalid ones), the next two over the valid ones.  A frame with a larger
+// key (fd->depth_wide, set by the projection) takes a fourth pass on bits
+// 24-31 (it overlaps the third digit, which LSD order allows: the pass is
+// stable).  Buffers: (k0, v0), (k1, v1) ping-pong, (k2, v2) the result in
+// either case (the third pass writes (k2, v2), or (k0, v0) when the fourth
+// follows).  hist: the projection's histograms, 3 x 512 (9-bit digits)
+// then 256 (bits 24-31), of the valid keys minus the base.
+void launch_depth_sort(const uint32_t* kin, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* k2,
+                       uint32_t* v2, const uint32_t* n_in, const uint32_t* n_valid, int slot_base, FrameDev* fd,
+                       SortBufs sb, const uint32_t* hist, int n_sm, cudaStream_t s) {
+  sort_pass<512, 8, 9>(n_sm * 2, s, kin, nullptr, k0, v0, n_in, 0, hist, 1, sb.status, fd, slot_base,
+                       &fd->depth_base);
+  sort_pass<512, 4, 9>(n_sm * 2, s, k0, v0, k1, v1, n_valid, 9, hist + 512, 0, sb.status, fd, slot_base + 1);
+  sort_pass<512, 4, 9>(n_sm * 2, s, k1, v1, k2, v2, n_valid, 18, hist + 1024, 0, sb.status, fd, slot_base + 2,
+                       nullptr, nullptr, k0, v0, &fd->depth_wide);
+  sort_pass<512, 4, 8>(n_sm * 2, s, k0, v0, k2, v2, n_valid, 24, hist + 1536, 0, sb.status, fd, slot_base + 3,
+                       nullptr, &fd->depth_wide);
 }
 
 // Sort n_in (from device memory) pairs on bits [0, bits).  drop_invalid:

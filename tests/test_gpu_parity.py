@@ -8,6 +8,8 @@ derived attributes <= 1e-5 relative to each attribute's scale, pixels
 float32 and float64; they are excluded from the max-abs check, counted, and
 must stay rare.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -206,6 +208,33 @@ def test_empty_view_is_background():
 @pytest.fixture(scope="module")
 def city():
     return gen.city_workload()
+
+
+@pytest.mark.parametrize("znear", [0.001, 0.2])
+def test_depth_sort_base_and_wide_keys(city, znear):
+    """The record sort orders by depth key minus the bits of the nearest near
+    plane, in three 9-bit passes while that fits 27 bits.  Measured from a
+    1 mm near plane (2^16 mm = 65 m, nearer than most of the city) it does
+    not, and the sort takes its fourth pass.  Either way: the stable order
+    of the GPU's depth keys, the oracle's pairs and ranges, and sampled
+    pixels against the oracle."""
+    model, frames = city
+    L, R = [dataclasses.replace(c, znear=float(np.float32(znear))) for c in frames[150]]
+    r = make_renderer(model, [L, R], partners=[1, 0])
+    imgs, st = render(r, [L, R])
+    _, dkey, _ = r.debug_records()
+    kept = dkey[dkey != 0xFFFFFFFF].astype(np.int64)
+    span = int(kept.max()) - int(np.array([znear], np.float32).view(np.uint32)[0])
+    assert (span >= 1 << 27) == (znear < 0.01), span  # the case each frame is meant to exercise
+    check_keygen_and_sort(r, [L, R])
+    rs = np.random.default_rng(17)
+    for v, cam in enumerate((L, R)):
+        px = rs.integers(0, cam.width, 20000)
+        py = rs.integers(0, cam.height, 20000)
+        vr = oracle.view_gaussians(model, cam)
+        ref, T, mg, nc = oracle.render(vr.rec, vr.depth32, vr.gid, cam.width, cam.height, True, px, py)
+        check_image(imgs[v][py, px], ref, mg, f"znear {znear} eye {v}")
+    r.close()
 
 
 @pytest.mark.parametrize("frame", [0, 150, 299])
