@@ -1046,8 +1046,10 @@ def launches_per_frame_of(form, tile_bits):
     """Library kernels per stereo frame of one model: frame setup, the cull's
     two passes (the second also runs the depth-rule cache probe), plan,
     [cache scan, assign; a learned probe as its own kernel], tables,
-    derivation, projection, depth sort (4 passes), scan, key generation,
-    tile sort (one pass per 8 tile-key bits), ranges, blend."""
+    derivation, projection, depth sort (4 launches: three 9-bit passes and
+    a fourth that returns at once unless the frame's keys need it), scan,
+    key generation, tile sort (one pass per 8 tile-key bits), ranges,
+    blend."""
     f = FORMS[form]
     n = 1 + 2 + 1 + 1 + 1 + 1 + 4 + 1 + 1 + (tile_bits + 7) // 8 + 1 + 1
     if f["reuse"] != "off":
