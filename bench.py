@@ -338,8 +338,8 @@ OPS_PER_EVAL = 20
 # with the tiling and the frame it was taken on and the SHA-256 prefix of the
 # kernel's source file at the time: reported as the roofline's traffic only
 # while the source is unchanged and the timed run uses that tiling, else null.
-NCU_TRAFFIC = {"k_blend": {"file": "paper_2502_14938_b300/csrc/raster.cu", "sha16": "9ec46db7ebc80b92",
-                           "tiling": (16, 64, 0), "bytes": 16423168 + 1048576, "frame": 21}}
+NCU_TRAFFIC = {"k_blend": {"file": "paper_2502_14938_b300/csrc/raster.cu", "sha16": "0ae989676b4b7c24",
+                           "tiling": (16, 64, 0), "bytes": 16420864 + 2247936, "frame": 21}}
 
 
 def _src_sha16(rel: str) -> str:
@@ -1091,15 +1091,6 @@ def run_ours(args, rank, world):
         others[f2] = {"fps": 1000.0 / float(ms2.mean()), "ms_mean": float(ms2.mean()),
                       "p99_ms": float(np.percentile(ms2, 99)), "tiling": r2.tiling}
         rends[f2] = (r2, mid2, outs2)
-    # the headline form's graph without programmatic dependent launches (every
-    # kernel scheduled only after its predecessor has ended), same tiling
-    import paper_2502_14938_b300 as pkg
-    r3, _, _, ms3, _ = time_form(model, frames, form, args.steps, args.warmup, flush, 1,
-                                 tiling=(r.tiling["tile_w"], r.tiling["tile_h"], r.tiling["blocks_per_sm"]),
-                                 flags=pkg.FLAG_NO_DEP_LAUNCH)
-    r3.close()
-    no_dep = {"fps": 1000.0 / float(ms3.mean()), "ms_mean": float(ms3.mean()),
-              "p99_ms": float(np.percentile(ms3, 99))}
     if rank != 0:
         return
     mean_ms = total_ms / args.steps
@@ -1136,6 +1127,7 @@ def run_ours(args, rank, world):
     # renders while frame n's images are copied to pinned host memory); every
     # step uploads its cameras and reads both images back.  The synchronous
     # float32 variant of the same loop is reported beside it.
+    import paper_2502_14938_b300 as pkg
     up = pkg.lib().gsc_debug_frame_upload_bytes()
     n_e2e = min(args.steps, 100)
     host32 = [torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
@@ -1185,7 +1177,7 @@ def run_ours(args, rank, world):
            "max_abs_decided": q["max_abs_decided"], "near_threshold_frac": q["near_threshold_frac"],
            "psnr_frames": args.psnr_frames,
            "reuse_frac_mean": float(np.mean(reuse_frac)) if reuse_frac else None,
-           "e2e_sync_f32": e2e_sync_f32, "compare": others, "no_dep_launch": no_dep, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "stage_hbm": stage_gbs, "per_frame": per_frame, "gen_s": t_gen}
+           "e2e_sync_f32": e2e_sync_f32, "compare": others, "batched": batched, "learned_reuse": learned, "stage_ms": stage_ms, "stage_hbm": stage_gbs, "per_frame": per_frame, "gen_s": t_gen}
     line = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[FORMS[form]["precision"]],

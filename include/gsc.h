@@ -96,9 +96,6 @@ typedef enum {
 #define GSC_FLAG_UNFUSED 0x20u     /* FP32 only: the derivation as separate operators through device memory
                                       (gather, GEMM, ReLU, GEMM, split, activation): the ablation's decoder
                                       without fused kernels; the same arithmetic as the fused one */
-#define GSC_FLAG_NO_DEP_LAUNCH 0x40u /* graph replay: every kernel waits for its predecessor's end before
-                                        it is scheduled (by default a kernel following a kernel in its
-                                        stream is a programmatic dependent launch; same results) */
 
 enum { GSC_STEREO_OFF = 0, GSC_STEREO_UNIFIED = 1, GSC_STEREO_EXACT = 2 };
 

@@ -5,8 +5,8 @@ include/gsc.h); `native` is the ctypes binding with the same call names.
 """
 from .native import (GscError, Renderer, default_config, exported_symbols, lib, to_camera,
                      FLAG_DEBUG_ATTRS, FLAG_DEBUG_T, FLAG_TIMING, FLAG_REUSE_COLLECT, FLAG_BLEND_WORK,
-                     FLAG_UNFUSED, FLAG_NO_DEP_LAUNCH, REUSE_NPARAM)
+                     FLAG_UNFUSED, REUSE_NPARAM)
 
 __all__ = ["GscError", "Renderer", "default_config", "exported_symbols", "lib", "to_camera",
            "FLAG_DEBUG_ATTRS", "FLAG_DEBUG_T", "FLAG_TIMING", "FLAG_REUSE_COLLECT", "FLAG_BLEND_WORK",
-           "FLAG_UNFUSED", "FLAG_NO_DEP_LAUNCH", "REUSE_NPARAM"]
+           "FLAG_UNFUSED", "REUSE_NPARAM"]

@@ -21,10 +21,6 @@
 
 using namespace gsc;
 
-namespace gsc {
-thread_local bool g_launch_dep = false;
-}
-
 namespace {
 
 constexpr int NSLOT = 4;  // pinned FrameIn ring
@@ -387,17 +383,11 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   cudaStream_t s = ctx->stream;
   FrameDev* fd = ctx->d_fd;
   const bool tm = ctx->timing;
-  // programmatic edges (set while the graph is captured) join kernel to
-  // kernel within a stream: the frame's first kernel, the first one on the
-  // second branch and the first one after the branches join take plain ones
-  const bool dep = g_launch_dep;
   NvtxRange frame_range("gsc.frame");
   if (tm) cudaEventRecord(ctx->ev_stage[0], s);
   nvtxRangePushA("gsc.cull_cache");
-  g_launch_dep = false;
   launch_frame_begin(fd, ctx->d_fin, replay ? nullptr : ctx->d_caches, replay ? 0 : ctx->n_caches, ctx->ranges,
                      ctx->total_tiles, s);
-  g_launch_dep = dep;
   CacheDev* caches = ctx->n_caches ? ctx->d_caches : nullptr;
   const bool learned = ctx->cfg.reuse == GSC_REUSE_LEARNED;
   // The cull's write pass probes the caches by the depth rule as it writes
@@ -419,15 +409,12 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     // assignment subtracts the hits from it)
     cudaEventRecord(ctx->ev_fork, s);
     cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
-    g_launch_dep = false;
     launch_plan(fd, ctx->rec_cap, ctx->aux_stream);
-    g_launch_dep = dep;
     launch_tables(fd, caches, ctx->d_eye_tab, ctx->d_tabs, ctx->d_ptab, (int)ctx->models.size(), ctx->aux_stream);
     cudaEventRecord(ctx->ev_join, ctx->aux_stream);
     launch_cache_frame(ctx->d_caches, ctx->h_caches, ctx->n_caches, fd, ctx->d_vis_tab, ctx->d_models, ctx->rw_w,
                        learned, nullptr, ctx->st_scan, ctx->n_sm, s, probed);
     cudaStreamWaitEvent(s, ctx->ev_join, 0);
-    g_launch_dep = false;  // until the first kernel after the join
   } else {
     launch_plan(fd, ctx->rec_cap, s);
     if (collect)  // fresh attributes of every visible anchor, for the labels
@@ -446,7 +433,7 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
   if (tm) cudaEventRecord(ctx->ev_stage[1], s);
   nvtxRangePop();
   nvtxRangePushA("gsc.derive_project");
-  for (int m : ctx->models_used) {
+  for (int m : ctx->models_used)
     if (tc)
       launch_derive_tc(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
                        fp8, ctx->n_sm, s);
@@ -456,9 +443,6 @@ void enqueue_sequence(gsc_ctx* ctx, bool replay = false) {
     else
       launch_derive_f32(ctx->d_models, m, fd, ctx->d_vis_tab, ctx->attrs, ctx->d_dbg_tab, caches, ctx->d_tabs,
                         ctx->n_sm, s);
-    g_launch_dep = dep;
-  }
-  g_launch_dep = dep;
   launch_project(ctx->d_models, fd, ctx->d_vis_tab, ctx->attrs, caches, ctx->rec, ctx->d_ptab, ctx->n_sm, s);
   if (caches && replay) launch_cache_replay_counts(ctx->d_caches, ctx->n_caches, fd, s);
   if (tm) cudaEventRecord(ctx->ev_stage[2], s);
@@ -494,9 +478,7 @@ int build_graph(gsc_ctx* ctx) {
   invalidate_graph(ctx);
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  g_launch_dep = (ctx->cfg.flags & GSC_FLAG_NO_DEP_LAUNCH) == 0;
   enqueue_sequence(ctx);
-  g_launch_dep = false;
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
   if (e != cudaSuccess) return fail(ctx, GSC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   e = cudaGraphInstantiate(&ctx->gexec, g, 0);

@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(256) k_cache_probe(CacheDev* __restrict__ cach
                                                      const ModelDev* __restrict__ models,
                                                      const float* __restrict__ rw) {
   __shared__ float s_w[LEARNED ? RPARAM : 1];
-  grid_dep_begin();
   const CacheDev cd = caches[c];
   const uint32_t V = fd->vis_count[c];
   const uint32_t t = cd.state[CS_T], depth = cd.state[CS_DEPTH], D = cd.state[CS_DMAX], hw = cd.state[CS_HW];
@@ -114,7 +113,6 @@ __device__ __forceinline__ uint32_t next_depth(uint32_t depth, uint32_t V, uint3
 
 __global__ void k_cache_assign(CacheDev* __restrict__ caches, int c, FrameDev* __restrict__ fd,
                                uint32_t* const* __restrict__ vis, const ModelDev* __restrict__ models) {
-  grid_dep_begin();
   const CacheDev cd = caches[c];
   const CamDev& cam = fd->dcam[c];
   const ModelDev& md = models[cam.model];
@@ -205,7 +203,6 @@ __global__ void k_reuse_label(CacheDev* __restrict__ caches, int c, const FrameD
 // A frame rendered again after a buffer grew: its decisions and the depth
 // update were made by the first attempt; restate the frame's counts.
 __global__ void k_cache_replay_counts(CacheDev* caches, int n, FrameDev* fd) {
-  grid_dep_begin();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   uint32_t hits = 0;
   for (int c = 0; c < n; ++c) {
@@ -225,18 +222,18 @@ void launch_cache_frame(CacheDev* caches, const CacheDev* host, int n_caches, Fr
     if (!host[c].active) continue;
     const CacheDev& h = host[c];
     if (learned)
-      launch_dep(k_cache_probe<true>, n_sm * 4, 256, 0, s, caches, c, fd, vis, models, reuse_w);
+      k_cache_probe<true><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
     else if (!probed)
-      launch_dep(k_cache_probe<false>, n_sm * 4, 256, 0, s, caches, c, fd, vis, models, reuse_w);
+      k_cache_probe<false><<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models, reuse_w);
     if (attrs_fresh) k_reuse_label<<<n_sm * 4, 128, 0, s>>>(caches, c, fd, vis, models, attrs_fresh);
     launch_scan_u32(h.flags, nullptr, h.state + CS_SCAN_N, h.ranks, h.state + CS_SCAN_TOT, scan_status, fd,
                     SLOT_CACHE + 2 * c, n_sm, s, h.free_list, h.S, nullptr, nullptr, 0, h.state + CS_HW);
-    launch_dep(k_cache_assign, n_sm * 4, 256, 0, s, caches, c, fd, vis, models);
+    k_cache_assign<<<n_sm * 4, 256, 0, s>>>(caches, c, fd, vis, models);
   }
 }
 
 void launch_cache_replay_counts(CacheDev* caches, int n_caches, FrameDev* fd, cudaStream_t s) {
-  launch_dep(k_cache_replay_counts, 1, 32, 0, s, caches, n_caches, fd);
+  k_cache_replay_counts<<<1, 32, 0, s>>>(caches, n_caches, fd);
 }
 
 }  // namespace gsc

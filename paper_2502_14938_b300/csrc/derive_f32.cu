@@ -77,7 +77,6 @@ __global__ void __launch_bounds__(DF_NT, 2) k_derive_f32(const ModelDev* __restr
   __shared__ DViewSet S;
   __shared__ DFMeta M;
 
-  grid_dep_begin();
   const ModelDev md = models[model];
   load_dview_set(S, tabs, fd, model, caches);
   const int nd = S.nd;
@@ -221,7 +220,7 @@ cudaError_t prepare_derive_f32() {
 void launch_derive_f32(const ModelDev* models, int model, FrameDev* fd, uint32_t* const* vis, float4* attrs,
                        float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, int n_sm,
                        cudaStream_t s) {
-  launch_dep(k_derive_f32, n_sm * 2, DF_NT, DF_SMEM_BYTES, s, models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
+  k_derive_f32<<<n_sm * 2, DF_NT, DF_SMEM_BYTES, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
 }
 
 }  // namespace gsc

@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(TC_NT, 1) k_derive_tc(const ModelDev* __restri
   const uint32_t sbase = smem_u32(smem);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  grid_dep_begin();
   const ModelDev md = models[model];
   load_dview_set(S, tabs, fd, model, caches);
   if (blockIdx.x >= (S.base[S.nd] + TC_M - 1) / TC_M) return;  // no tile: skip weights, barriers and TMEM
@@ -623,10 +622,9 @@ void launch_derive_tc(const ModelDev* models, int model, FrameDev* fd, uint32_t*
                       float* const* dbg_attrs, const CacheDev* caches, const DViewSet* tabs, bool fp8, int n_sm,
                       cudaStream_t s) {
   if (fp8)
-    launch_dep(k_derive_tc<true>, n_sm * 2, TC_NT, TC_SMEM, s, models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
+    k_derive_tc<true><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
   else
-    launch_dep(k_derive_tc<false>, n_sm * 2, TC_NT, TC_SMEM, s, models, model, fd, vis, attrs, dbg_attrs, caches,
-               tabs);
+    k_derive_tc<false><<<n_sm * 2, TC_NT, TC_SMEM, s>>>(models, model, fd, vis, attrs, dbg_attrs, caches, tabs);
 }
 
 }  // namespace gsc

@@ -16,7 +16,6 @@ static_assert(sizeof(CamDev) % 4 == 0, "cameras are copied as words");
 __global__ void __launch_bounds__(FB_NT) k_frame_begin(FrameDev* fd, const FrameIn* __restrict__ fin,
                                                        CacheDev* __restrict__ caches, int n_caches,
                                                        uint2* __restrict__ ranges, uint32_t n_tiles) {
-  grid_dep_begin();
   // every block: its share of the tile ranges, cleared (tiles without pairs keep [0, 0))
   for (uint32_t i = blockIdx.x * FB_NT + threadIdx.x; i < n_tiles; i += gridDim.x * FB_NT) ranges[i] = make_uint2(0, 0);
   if (blockIdx.x != 0) return;
@@ -220,7 +219,6 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_count(const ModelDev* __res
   __shared__ uint32_t s_cnt[CULL_MAXD];
   __shared__ uint16_t s_list[CULL_NT / 32][32 * CULL_IPT];  // per warp: LOD survivors
   __shared__ uint32_t s_mask[CULL_NT];                      // per thread: keep masks being built
-  grid_dep_begin();
   const ModelDev md = models[model];
   cull_views_setup<RADIUS>(V, md, model, fd);
   const int nd = V.nd;
@@ -347,7 +345,6 @@ __global__ void __launch_bounds__(CULL_NT, 4) k_cull_write(const ModelDev* __res
                                                         const uint32_t* __restrict__ masks,
                                                         const uint32_t* __restrict__ tile_cnt, uint32_t mask_stride,
                                                         uint32_t cnt_stride, CullProbe probe_cfg) {
-  grid_dep_begin();
   __shared__ int s_d[CULL_MAXD];
   __shared__ int s_exact[CULL_MAXD];
   __shared__ int s_nd;
@@ -426,11 +423,11 @@ bool launch_cull(const ModelDev* md, const ModelDev* h_model, int model, FrameDe
   const uint32_t ntiles = (h_model->n + CULL_TILE - 1) / CULL_TILE;
   if (ntiles == 0) return false;
   if (h_model->lod_r)
-    launch_dep(k_cull_count<true>, ntiles, CULL_NT, 0, s, md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
+    k_cull_count<true><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
   else
-    launch_dep(k_cull_count<false>, ntiles, CULL_NT, 0, s, md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
-  launch_dep(k_cull_write, ntiles, CULL_NT, 0, s, md, model, fd, vis_dev, eyes_dev, masks, tile_cnt, mask_stride,
-             cnt_stride, probe);
+    k_cull_count<false><<<ntiles, CULL_NT, 0, s>>>(md, model, fd, masks, tile_cnt, mask_stride, cnt_stride);
+  k_cull_write<<<ntiles, CULL_NT, 0, s>>>(md, model, fd, vis_dev, eyes_dev, masks, tile_cnt, mask_stride, cnt_stride,
+                                          probe);
   return true;
 }
 
@@ -438,10 +435,9 @@ uint32_t cull_tiles(uint32_t n_anchors) { return (n_anchors + CULL_TILE - 1) / C
 uint32_t cull_mask_words(uint32_t n_anchors) { return cull_tiles(n_anchors) * CULL_NT; }
 
 __global__ void k_plan(FrameDev* fd, uint32_t rec_cap) {
-  grid_dep_begin();
   if (threadIdx.x == 0 && blockIdx.x == 0) plan_thread(fd, rec_cap);
 }
 
-void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s) { launch_dep(k_plan, 1, 32, 0, s, fd, rec_cap); }
+void launch_plan(FrameDev* fd, uint32_t rec_cap, cudaStream_t s) { k_plan<<<1, 32, 0, s>>>(fd, rec_cap); }
 
 }  // namespace gsc

@@ -56,43 +56,6 @@ enum : uint32_t { ERR_PAIR_OVERFLOW = 1u, ERR_TIMEOUT = 2u, ERR_CACHE_FULL = 4u,
 #define GSC_IN_BOUNDS(i, cap, err) true
 #endif
 
-// Programmatic dependent launch.  In the captured frame graph a kernel is
-// launched with programmatic stream serialisation (launch_dep) when the node
-// before it in its stream is a kernel: its blocks may be scheduled while that
-// kernel still runs, as soon as every block of it has issued
-// griddepcontrol.launch_dependents.  Every such kernel opens with
-// grid_dep_begin() before any memory access and before any early return:
-// griddepcontrol.wait blocks until the preceding grid has completed and its
-// writes are visible (so the chain stays ordered transitively), then the
-// kernel lets its own successor be scheduled.  In a kernel launched without
-// the attribute both instructions do nothing.
-__device__ __forceinline__ void grid_dep_begin() {
-  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Set (on the calling thread) while the frame's launch sequence is captured
-// into its graph with programmatic edges; launch_dep reads it.
-extern thread_local bool g_launch_dep;
-
-template <typename... KP, typename... A>
-inline void launch_dep(void (*kern)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
-  if (!g_launch_dep) {
-    kern<<<grid, block, smem, s>>>(args...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KP>(args)...);
-}
-
 constexpr uint32_t INVALID_KEY = 0xFFFFFFFFu;
 constexpr uint32_t REC_VALID_BIT = 0x80000000u;
 

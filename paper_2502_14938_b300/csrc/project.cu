@@ -43,7 +43,6 @@ __global__ void __launch_bounds__(PJ_NT, 4) k_project(const ModelDev* __restrict
   __shared__ uint8_t s_own[PJ_NT / 32][64];  // per warp: owning lane of each surviving record
   __shared__ float s_stage[PJ_NT / 32][PS_WORDS][32];  // per warp: the owners' record inputs
   for (int i = threadIdx.x; i < DEPTH_HIST_WORDS; i += PJ_NT) s_h[i] = 0;
-  grid_dep_begin();
   if (threadIdx.x == 0) {
     s_nv = s_wide = 0;
     s_dbase = fd->depth_base;
@@ -214,7 +213,7 @@ void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, 
                     const CacheDev* caches, Records rec, const ProjTab* ptab, int n_sm, cudaStream_t s) {
   // one wave of resident blocks (four per SM) striding over the Gaussians:
   // half the per-block histogram flushes of two waves
-  launch_dep(k_project, n_sm * 4, PJ_NT, 0, s, models, fd, vis, attrs, caches, rec, ptab);
+  k_project<<<n_sm * 4, PJ_NT, 0, s>>>(models, fd, vis, attrs, caches, rec, ptab);
 }
 
 // ------------------------------------------------------------------ frame tables
@@ -222,7 +221,6 @@ void launch_project(const ModelDev* models, FrameDev* fd, uint32_t* const* vis, 
 __global__ void k_tables(const FrameDev* __restrict__ fd, const CacheDev* __restrict__ caches,
                          uint8_t* const* __restrict__ eyes, DViewSet* __restrict__ tabs, ProjTab* __restrict__ ptab,
                          int n_models) {
-  grid_dep_begin();
   frame_tables_warp(fd, caches, eyes, tabs, ptab, n_models, (int)(threadIdx.x & 31u));
 }
 
@@ -231,7 +229,7 @@ size_t proj_tab_bytes() { return sizeof(ProjTab); }
 
 void launch_tables(const FrameDev* fd, const CacheDev* caches, uint8_t* const* eyes, DViewSet* tabs, ProjTab* ptab,
                    int n_models, cudaStream_t s) {
-  launch_dep(k_tables, 1, 32, 0, s, fd, caches, eyes, tabs, ptab, n_models);
+  k_tables<<<1, 32, 0, s>>>(fd, caches, eyes, tabs, ptab, n_models);
 }
 
 }  // namespace gsc

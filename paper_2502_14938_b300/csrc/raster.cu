@@ -24,7 +24,6 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan(const uint32_t* __restrict__ c
   __shared__ uint32_t s_warp[SCAN_NT / 32 + 1];
   __shared__ uint32_t s_base;
   __shared__ uint32_t s_tile;
-  grid_dep_begin();
   const uint32_t n = *n_ptr;
   if (scatter_n_dev) scatter_n = *scatter_n_dev;
   const uint32_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -91,8 +90,8 @@ void launch_scan_u32(const uint32_t* cnt, const uint32_t* order, const uint32_t*
                      uint32_t* total_out, unsigned long long* status, FrameDev* fd, int slot, int n_sm,
                      cudaStream_t s, uint32_t* scatter, uint32_t scatter_n, uint32_t* big, uint32_t* n_big,
                      uint32_t big_above, const uint32_t* scatter_n_dev) {
-  launch_dep(k_scan, n_sm * 4, SCAN_NT, 0, s, cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n,
-             big, n_big, big_above, scatter_n_dev);
+  k_scan<<<n_sm * 4, SCAN_NT, 0, s>>>(cnt, order, n_ptr, out, total_out, status, fd, slot, scatter, scatter_n, big,
+                                      n_big, big_above, scatter_n_dev);
 }
 
 // ------------------------------------------------------------------ key generation (K7)
@@ -121,7 +120,6 @@ __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Recor
                                                 const uint32_t* __restrict__ big) {
   __shared__ uint32_t s_h[4][256];
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
-  grid_dep_begin();
   const uint32_t n = fd->n_valid;
   const int npass = (int)((fd->tile_bits + 7u) / 8u);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -218,12 +216,11 @@ __global__ void __launch_bounds__(256) k_keygen(FrameDev* __restrict__ fd, Recor
 
 void launch_keygen(FrameDev* fd, Records rec, const uint32_t* order, const uint32_t* offs, uint32_t* pkeys,
                    uint32_t* pvals, uint32_t cap, uint32_t* big, int n_sm, cudaStream_t s) {
-  launch_dep(k_keygen, n_sm * 8, 256, 0, s, fd, rec, order, offs, pkeys, pvals, cap, big);
+  k_keygen<<<n_sm * 8, 256, 0, s>>>(fd, rec, order, offs, pkeys, pvals, cap, big);
 }
 
 // ------------------------------------------------------------------ tile ranges (K9)
 __global__ void k_ranges(const FrameDev* __restrict__ fd, const uint32_t* __restrict__ keys, uint2* __restrict__ ranges) {
-  grid_dep_begin();
   const uint32_t n = fd->n_pairs_used;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
@@ -234,7 +231,7 @@ __global__ void k_ranges(const FrameDev* __restrict__ fd, const uint32_t* __rest
 }
 
 void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, cudaStream_t s) {
-  launch_dep(k_ranges, n_sm * 8, 256, 0, s, fd, keys, ranges);
+  k_ranges<<<n_sm * 8, 256, 0, s>>>(fd, keys, ranges);
 }
 
 // ------------------------------------------------------------------ blend (K10)
@@ -509,7 +506,6 @@ __global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend(FrameDev* __restrict_
                                                         const uint32_t* __restrict__ vals, Records rec,
                                                         const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
-  grid_dep_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) keep_frame_error(fd, fin);
   blend_tile<COUNT>(blockIdx.x, sm, fd, ranges, vals, rec, fin);
 }
@@ -524,7 +520,6 @@ __global__ void __launch_bounds__(BLEND_MAX_NT, 4) k_blend_persistent(FrameDev* 
                                                                    const FrameIn* __restrict__ fin) {
   __shared__ BlendSmem sm;
   __shared__ uint32_t s_tile;
-  grid_dep_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) keep_frame_error(fd, fin);
   const uint32_t total = fd->total_tiles;
   for (;;) {
@@ -543,14 +538,14 @@ void launch_blend(FrameDev* fd, const uint2* ranges, const uint32_t* vals, Recor
   const uint32_t nt = tile_threads / BLEND_PPL, grid = n_sm * blocks_per_sm;
   if (blocks_per_sm == 0) {
     if (count)
-      launch_dep(k_blend<true>, total_tiles, nt, 0, s, fd, ranges, vals, rec, fin);
+      k_blend<true><<<total_tiles, nt, 0, s>>>(fd, ranges, vals, rec, fin);
     else
-      launch_dep(k_blend<false>, total_tiles, nt, 0, s, fd, ranges, vals, rec, fin);
+      k_blend<false><<<total_tiles, nt, 0, s>>>(fd, ranges, vals, rec, fin);
   } else {
     if (count)
-      launch_dep(k_blend_persistent<true>, grid, nt, 0, s, fd, ranges, vals, rec, fin);
+      k_blend_persistent<true><<<grid, nt, 0, s>>>(fd, ranges, vals, rec, fin);
     else
-      launch_dep(k_blend_persistent<false>, grid, nt, 0, s, fd, ranges, vals, rec, fin);
+      k_blend_persistent<false><<<grid, nt, 0, s>>>(fd, ranges, vals, rec, fin);
   }
 }
 

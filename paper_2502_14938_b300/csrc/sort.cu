@@ -77,7 +77,6 @@ __global__ void __launch_bounds__(NT, 2) k_sort_pass(const uint32_t* __restrict_
   uint32_t* s_keys = s_kv;
   uint32_t* s_vals = s_kv + TILE;
 
-  grid_dep_begin();  // before the conditional return too: the next pass waits on this one
   if (run_if && *run_if == 0u) return;
   if (use_alt && *use_alt != 0u) {
     kout = kout_alt;
@@ -178,8 +177,9 @@ void sort_pass(int blocks, cudaStream_t s, const uint32_t* kin, const uint32_t* 
                const uint32_t* n_ptr, int shift, const uint32_t* hist_p, int drop_invalid, unsigned long long* status,
                FrameDev* fd, int slot, const uint32_t* key_sub = nullptr, const uint32_t* run_if = nullptr,
                uint32_t* kout_alt = nullptr, uint32_t* vout_alt = nullptr, const uint32_t* use_alt = nullptr) {
-  launch_dep(k_sort_pass<NT, IPT, DB>, blocks, NT, 2 * NT * IPT * sizeof(uint32_t), s, kin, vin, kout, vout, n_ptr,
-             shift, hist_p, drop_invalid, status, fd, slot, key_sub, run_if, kout_alt, vout_alt, use_alt);
+  k_sort_pass<NT, IPT, DB><<<blocks, NT, 2 * NT * IPT * sizeof(uint32_t), s>>>(
+      kin, vin, kout, vout, n_ptr, shift, hist_p, drop_invalid, status, fd, slot, key_sub, run_if, kout_alt, vout_alt,
+      use_alt);
 }
 
 cudaError_t prepare_sort() {

@@ -38,7 +38,6 @@ FLAG_TIMING = 0x4
 FLAG_REUSE_COLLECT = 0x8
 FLAG_BLEND_WORK = 0x10
 FLAG_UNFUSED = 0x20
-FLAG_NO_DEP_LAUNCH = 0x40
 REUSE_NPARAM = 2433
 
 
