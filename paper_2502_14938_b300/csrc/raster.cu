@@ -265,6 +265,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// 1/x and sqrt(x) by the hardware approximations (relative errors ~1e-7):
+// the band test below only has to stay conservative, and its slack is four
+// orders of magnitude wider
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {  // a - b, round to nearest, per element
   float2 d;
   asm("{.reg .b64 ra, rb, rd;\n\t"
@@ -418,11 +431,14 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
         // on the row dy (from the mean) the ellipse spans dx = (-B dy +- sqrt(det) sqrt(ey^2 - dy^2)) / A;
         // its right- and leftmost points lie on dy = -+B ex / C, clamped to the band's rows
         const float ya = fmaxf(wy0 - myl, -c.w), yb = fminf(wy1 - myl, c.w);
-        const float iA = 1.f / A, sd = sqrtf(fmaxf(0.f, A * Cc - B * B)) * iA, bxc = B * c.z / Cc;
+        const float iA = rcp_approx(A), sd = sqrt_approx(fmaxf(0.f, A * Cc - B * B)) * iA;
+        const float bxc = B * c.z * rcp_approx(Cc), h2 = c.w * c.w, bA = B * iA;
         const float dr = fminf(fmaxf(-bxc, ya), yb), dl = fminf(fmaxf(bxc, ya), yb);
-        const float xr = mxl - B * dr * iA + sd * sqrtf(fmaxf(0.f, c.w * c.w - dr * dr));
-        const float xl = mxl - B * dl * iA - sd * sqrtf(fmaxf(0.f, c.w * c.w - dl * dl));
-        const float slack = 1e-3f * (c.z + 1.f);  // float32 rounding; the box's tau is already enlarged
+        const float xr = mxl - bA * dr + sd * sqrt_approx(fmaxf(0.f, h2 - dr * dr));
+        const float xl = mxl - bA * dl - sd * sqrt_approx(fmaxf(0.f, h2 - dl * dl));
+        // float32 rounding and the approximations (the box's tau is already
+        // enlarged); a record kept in excess only evaluates below 1/255
+        const float slack = 1e-3f * (c.z + 1.f);
         hit = xr + slack >= wx0 && xl - slack <= wx1;
       }
       if (hit) {
