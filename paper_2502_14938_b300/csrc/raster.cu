@@ -295,12 +295,13 @@ constexpr float LOG2E_HALF = 0.72134752044448170368f;   // log2(e) / 2
 constexpr float LOG2_MIN_ALPHA = -7.99435343685885793f;  // log2(1/255)
 constexpr float LOG2_CLAMP_OPACITY = -0.02180437f;      // log2(0.985): records at or above it take the 0.99 clamp
 
-struct BlendSmem {  // per warp, one slot per lane of the current chunk
+struct BlendSmem {  // per warp, one slot per record of the current chunk's work list (in list order)
   float4 fd[BLEND_MAX_WARPS][32];   // F, F, D, D
   float4 ea[BLEND_MAX_WARPS][32];   // E, E, A', A'
   float4 bc[BLEND_MAX_WARPS][32];   // B', B', C', C'
   float4 rg[BLEND_MAX_WARPS][32];   // r, r, g, g
   float2 bl[BLEND_MAX_WARPS][32];   // b, b
+  uint8_t pos[BLEND_MAX_WARPS][32];  // counting variant: the record's position in the chunk
 };
 
 __device__ __forceinline__ float2 dup2(float a, float b) { return make_float2(a, b); }
@@ -416,14 +417,17 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
     ps.thr[k] = in ? LOG2_MIN_ALPHA : INFINITY;
   }
   uint32_t n_walk = 0, n_issued = 0;  // counting variant only
+  const unsigned lt_lanes = (1u << lane) - 1u;
   for (uint32_t b = rg.x; b < rg.y; b += 32u) {
     if (!__any_sync(0xffffffffu, ps.live != 0)) break;  // every pixel of the warp has stopped
     const uint32_t idx = b + (uint32_t)lane;
-    bool hit = false, clamp = false;
+    bool hit = false;
+    uint32_t r = 0;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g;
     if (idx < rg.y) {
-      const uint32_t r = vals[idx];
-      const float4 g = rec.geo[r];   // mean x, mean y, A, B
-      const float4 c = rec.aux[r];   // C, log2(opacity), box half-width, box half-height
+      r = vals[idx];
+      g = rec.geo[r];  // mean x, mean y, A, B
+      c = rec.aux[r];  // C, log2(opacity), box half-width, box half-height
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
       hit = !(mxl + c.z < wx0 || mxl - c.z > wx1 || myl + c.w < wy0 || myl - c.w > wy1);  // box meets the band
@@ -441,35 +445,46 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
         const float slack = 1e-3f * (c.z + 1.f);
         hit = xr + slack >= wx0 && xl - slack <= wx1;
       }
-      if (hit) {
-        const float4 cl = rec.col[r];
-        const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
-        const float F = c.y - LOG2E_HALF * q0;
-        const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
-        const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
-        const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
-        sm.fd[warp][lane] = make_float4(F, F, D, D);
-        sm.ea[warp][lane] = make_float4(E, E, Ap, Ap);
-        sm.bc[warp][lane] = make_float4(Bp, Bp, Cp, Cp);
-        sm.rg[warp][lane] = make_float4(cl.x, cl.x, cl.y, cl.y);
-        sm.bl[warp][lane] = make_float2(cl.z, cl.z);
-        clamp = c.y >= LOG2_CLAMP_OPACITY;
-      }
     }
-    unsigned todo = __ballot_sync(0xffffffffu, hit);
-    const unsigned cmask = __ballot_sync(0xffffffffu, clamp);
+    // the chunk's work list: the hits, compacted into slots 0 .. nh-1 in list order
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    const uint32_t nh = (uint32_t)__popc(hm), slot = (uint32_t)__popc(hm & lt_lanes);
+    bool clamp = false;
+    if (hit) {
+      const float4 cl = rec.col[r];
+      const float mxl = g.x - ox, myl = g.y - oy;
+      const float A = g.z, B = g.w, Cc = c.x;
+      const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
+      const float F = c.y - LOG2E_HALF * q0;
+      const float D = 2.f * LOG2E_HALF * (A * mxl + B * myl);
+      const float E = 2.f * LOG2E_HALF * (B * mxl + Cc * myl);
+      const float Ap = -LOG2E_HALF * A, Bp = -2.f * LOG2E_HALF * B, Cp = -LOG2E_HALF * Cc;
+      sm.fd[warp][slot] = make_float4(F, F, D, D);
+      sm.ea[warp][slot] = make_float4(E, E, Ap, Ap);
+      sm.bc[warp][slot] = make_float4(Bp, Bp, Cp, Cp);
+      sm.rg[warp][slot] = make_float4(cl.x, cl.x, cl.y, cl.y);
+      sm.bl[warp][slot] = make_float2(cl.z, cl.z);
+      if (COUNT) sm.pos[warp][slot] = (uint8_t)lane;
+      clamp = c.y >= LOG2_CLAMP_OPACITY;
+    }
+    const unsigned cmask = __reduce_or_sync(0xffffffffu, clamp ? 1u << slot : 0u);  // by slot
     __syncwarp();
     const uint32_t cnt = min(32u, rg.y - b);
     if (COUNT) {
       n_walk += (uint32_t)__popc(ps.live) * cnt;
-      n_issued += (uint32_t)__popc(todo) * BLEND_PPL;
+      n_issued += nh * BLEND_PPL;
     }
-    while (todo) {
-      const int u = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const unsigned st = ((cmask >> u) & 1u) ? blend_record<true>(ps, sm, warp, u, X2, Y2)
-                                              : blend_record<false>(ps, sm, warp, u, X2, Y2);
-      if (COUNT && st) n_walk -= (uint32_t)__popc(st) * (cnt - 1u - (uint32_t)u);
+    if (cmask == 0u) {  // no record of the list reaches the 0.99 clamp
+      for (uint32_t u = 0; u < nh; ++u) {
+        const unsigned st = blend_record<false>(ps, sm, warp, (int)u, X2, Y2);
+        if (COUNT && st) n_walk -= (uint32_t)__popc(st) * (cnt - 1u - (uint32_t)sm.pos[warp][u]);
+      }
+    } else {
+      for (uint32_t u = 0; u < nh; ++u) {
+        const unsigned st = ((cmask >> u) & 1u) ? blend_record<true>(ps, sm, warp, (int)u, X2, Y2)
+                                                : blend_record<false>(ps, sm, warp, (int)u, X2, Y2);
+        if (COUNT && st) n_walk -= (uint32_t)__popc(st) * (cnt - 1u - (uint32_t)sm.pos[warp][u]);
+      }
     }
     __syncwarp();  // the slots are rewritten by the next chunk
   }
