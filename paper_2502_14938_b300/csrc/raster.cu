@@ -475,6 +475,9 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
       n_issued += nh * BLEND_PPL;
     }
     if (cmask == 0u) {  // no record of the list reaches the 0.99 clamp
+      // (unrolled: consecutive records' independent loads and quadratics
+      // interleave with the previous one's dependent chain)
+#pragma unroll 8
       for (uint32_t u = 0; u < nh; ++u) {
         const unsigned st = blend_record<false>(ps, sm, warp, (int)u, X2, Y2);
         if (COUNT && st) n_walk -= (uint32_t)__popc(st) * (cnt - 1u - (uint32_t)sm.pos[warp][u]);
