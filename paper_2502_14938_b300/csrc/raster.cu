@@ -423,11 +423,12 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
     const uint32_t idx = b + (uint32_t)lane;
     bool hit = false;
     uint32_t r = 0;
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), c = g, cl = g;
     if (idx < rg.y) {
       r = vals[idx];
       g = rec.geo[r];  // mean x, mean y, A, B
       c = rec.aux[r];  // C, log2(opacity), box half-width, box half-height
+      cl = rec.col[r];  // (with the geometry: one round trip for all three, hit or not)
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
       hit = !(mxl + c.z < wx0 || mxl - c.z > wx1 || myl + c.w < wy0 || myl - c.w > wy1);  // box meets the band
@@ -451,7 +452,6 @@ __device__ __forceinline__ void blend_tile(uint32_t tile_key, BlendSmem& sm, Fra
     const uint32_t nh = (uint32_t)__popc(hm), slot = (uint32_t)__popc(hm & lt_lanes);
     bool clamp = false;
     if (hit) {
-      const float4 cl = rec.col[r];
       const float mxl = g.x - ox, myl = g.y - oy;
       const float A = g.z, B = g.w, Cc = c.x;
       const float q0 = A * mxl * mxl + 2.f * B * mxl * myl + Cc * myl * myl;
