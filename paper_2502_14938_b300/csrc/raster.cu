@@ -241,13 +241,15 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 // Each warp walks the tile's record list on its own, 32 records at a time:
 // lane l loads record l of the chunk (with the blend view the projection
 // wrote for it: C, log2 opacity, box half extents), tests its opacity-aware
-// box and then the ellipse itself against the warp's band, and for a hit
-// stages the band-local quadratic of its power in the exp2 domain,
+// box and then the ellipse itself against the warp's band.  The hits are
+// the chunk's work list: compacted into consecutive shared-memory slots in
+// list order (slot = the hits of the lanes below), each holding the
+// band-local quadratic of the record's power in the exp2 domain,
 //   log2(o) - (log2 e / 2) q(D) = [F + X (D + A' X)] + Y [(E + B' X) + C' Y],
 // with (X, Y) the pixel centre relative to the band's centre (the bracket
-// in X is per lane, so a pixel costs 2 FMA).  The ballot of hits is the
-// chunk's work list: the warp visits only those records, in list order.
-// Each pixel walks them front to back:
+// in X is per lane, so a pixel costs 2 FMA).  The warp walks the slots in
+// order, eight records per unrolled step.  Each pixel walks them front to
+// back:
 //   alpha = min(0.99, 2^power), taken as 0 when the power is below
 //   log2(1/255) (alpha < 1/255 is skipped: it then changes nothing);
 //   stop before a Gaussian that would bring T (1 - alpha) below 1e-4;
@@ -255,9 +257,10 @@ void launch_ranges(FrameDev* fd, const uint32_t* keys, uint2* ranges, int n_sm, 
 // A lane's 4 vertical pixels run as two pairs on the packed FP32x2 pipe
 // (FFMA2/FMUL2: one issue slot for two pixels); staged coefficients are
 // stored twice ({a, a}) so they feed packed operands directly.  The clamp
-// to 0.99 is only applied for records whose opacity can reach it (a warp-
-// uniform branch; below opacity 0.985 the approximated 2^power stays under
-// 0.99).  A warp stops once all its pixels have; no block-wide barrier.
+// to 0.99 is only applied for records whose opacity can reach it (below
+// opacity 0.985 the approximated 2^power stays under 0.99): a chunk none
+// of whose hits can reach it walks one record form, the others test each
+// slot's bit.  A warp stops once all its pixels have; no block-wide barrier.
 constexpr int BLEND_PPL = 4;                 // pixels per lane (vertical): two packed pairs
 // 2^x by the hardware approximation (relative error ~2^-22; -inf -> 0).
 __device__ __forceinline__ float ex2_approx(float x) {

@@ -1,6 +1,6 @@
 """The bench's host-side bookkeeping, on CPU: the roofline's DRAM traffic is
-reported only while the kernel's source is the one the ncu capture was
-taken on and the timed run uses the captured tiling; the launch count per
+reported only while the kernel's code (comments aside) is the one the ncu
+capture was taken on and the timed run uses the captured tiling; the launch count per
 frame follows the form's kernels."""
 import os
 import sys
@@ -19,6 +19,16 @@ def test_traffic_only_for_the_captured_source_and_tiling(monkeypatch):
     assert bench.ncu_traffic("k_nothing", tuple(c["tiling"]))[0] is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, "k_blend", dict(c, sha16="0" * 16))  # the source changed
     assert bench.ncu_traffic("k_blend", tuple(c["tiling"]))[0] is None
+
+
+def test_source_key_ignores_comments_but_not_code(tmp_path):
+    f = tmp_path / "k.cu"
+    f.write_text("int a = 1;  // one\n\n__global__ void k() {}\n")
+    h = bench._src_sha16(str(f))
+    f.write_text("// a new header comment\nint a = 1;\n__global__ void k() {}  // edited\n")
+    assert bench._src_sha16(str(f)) == h
+    f.write_text("int a = 2;\n__global__ void k() {}\n")
+    assert bench._src_sha16(str(f)) != h
 
 
 def test_launches_per_frame_follow_the_form():
